@@ -1,0 +1,214 @@
+"""Seeded synthetic inputs for GMF fits on count matrices.
+
+This module is shared by the tests, the benchmark and the smoke check. It holds
+no part of the estimator: it draws the data (the generative laws of the
+workloads below), the random partitions and sweep orders that Algorithm 1
+samples (passed to both implementations as inputs), and a crude, deterministic
+starting point. Nothing here imports the CUDA package or the oracle.
+
+Workloads (rows = cells, columns = genes; Sec. 2, eq. 3 with an offset):
+
+* ``poisson_small``   1000 x 500 int32, Poisson, d = 5, p = 2, q = 1.
+* ``nb_medium``       20000 x 2000 int32, NB, ~85% zeros, d = 10, p = 3, q = 1.
+* ``nb_atlas``        200000 x 5000 uint16, NB, ~90% zeros, d = 20.
+* ``nb_sweep``        50000 x 3000 uint16, NB (true d = 10) for the rank sweep.
+* ``nb_project``      100000 fit + 100000 held-out cells x 3000 genes, NB, d = 20.
+
+Law (all workloads): eta = o + X B^T + Gamma Z^T + U V^T with
+X = [1, N(0,1), ...] (p columns), Z = 1_m (q = 1, so Gamma is a per-cell
+intercept), U, V, Gamma and the non-intercept columns of B ~ N(0, 0.5^2). The
+NB workloads add a library-size offset o_i = log LogNormal(0, 0.5) and draw a
+per-gene NB size alpha_j ~ Gamma(shape 2, scale 0.5). The gene intercept B[:,0]
+is N(c, 0.5^2) with c found by bisection so that the expected fraction of zero
+counts hits the target.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "WORKLOADS", "Problem", "make_problem", "partitions", "sweep_orders",
+    "n_sweeps", "crude_start", "fit_settings",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    n: int
+    m: int
+    p: int
+    q: int
+    d: int
+    family: str          # "poisson" | "negbin"
+    y_dtype: str         # "int32" | "uint16"
+    zero_frac: float | None
+    offset: bool
+    nb_row: int
+    nb_col: int
+    epochs: int
+
+
+WORKLOADS = {
+    "poisson_small": Workload("poisson_small", 1000, 500, 2, 1, 5, "poisson", "int32", None, False, 100, 100, 50),
+    "nb_medium": Workload("nb_medium", 20000, 2000, 3, 1, 10, "negbin", "int32", 0.85, True, 500, 500, 20),
+    "nb_atlas": Workload("nb_atlas", 200000, 5000, 3, 1, 20, "negbin", "uint16", 0.90, True, 2048, 1024, 10),
+    "nb_sweep": Workload("nb_sweep", 50000, 3000, 3, 1, 10, "negbin", "uint16", 0.90, True, 2048, 1024, 15),
+    "nb_project": Workload("nb_project", 200000, 3000, 3, 1, 20, "negbin", "uint16", 0.90, True, 2048, 1024, 10),
+}
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthetic data set with its true parameters (original row/column order)."""
+    Y: np.ndarray            # n x m counts, int32 or uint16, C order
+    X: np.ndarray            # n x p float64
+    Z: np.ndarray            # m x q float64
+    offset: np.ndarray       # n float64 (zeros when the workload has none)
+    B: np.ndarray            # m x p true coefficients
+    Gamma: np.ndarray        # n x q
+    U: np.ndarray            # n x d
+    V: np.ndarray            # m x d
+    nb_size: np.ndarray | None   # per-gene NB size (None for Poisson)
+    family: str
+    saturated: int = 0       # counts clipped at 65535 (uint16 workloads)
+
+    @property
+    def n(self):
+        return self.Y.shape[0]
+
+    @property
+    def m(self):
+        return self.Y.shape[1]
+
+
+def _eta(X, B, Gamma, Z, U, V, offset, rows=slice(None)):
+    e = X[rows] @ B.T + Gamma[rows] @ Z.T + U[rows] @ V.T
+    return e + offset[rows, None]
+
+
+def _zero_frac(eta, family, size):
+    mu = np.exp(np.clip(eta, -30, 30))
+    if family == "poisson":
+        return float(np.mean(np.exp(-mu)))
+    return float(np.mean(np.exp(size[None, :] * (np.log(size[None, :]) - np.log(size[None, :] + mu)))))
+
+
+def make_problem(n, m, p, q, d, family="poisson", *, seed=0, y_dtype="int32",
+                 zero_frac=None, offset=False, scale=0.5):
+    """Draw a synthetic count matrix from the GMF law (Sec. 2, eq. 3).
+
+    ``zero_frac`` (NB and Poisson) shifts the gene intercept so that the
+    expected fraction of zeros matches it; None leaves the intercept N(0, scale^2).
+    """
+    rng = np.random.default_rng(seed)
+    X = np.empty((n, p))
+    X[:, 0] = 1.0
+    if p > 1:
+        X[:, 1:] = rng.standard_normal((n, p - 1))
+    Z = np.ones((m, q)) if q >= 1 else np.zeros((m, 0))
+    if q > 1:
+        Z[:, 1:] = rng.standard_normal((m, q - 1))
+    B = scale * rng.standard_normal((m, p))
+    Gamma = scale * rng.standard_normal((n, q))
+    U = scale * rng.standard_normal((n, d))
+    V = scale * rng.standard_normal((m, d))
+    off = rng.normal(0.0, 0.5, size=n) if offset else np.zeros(n)
+    size = rng.gamma(2.0, 0.5, size=m) if family == "negbin" else None
+
+    if zero_frac is not None:
+        sub = np.sort(rng.choice(n, size=min(n, 2000), replace=False))
+        base = _eta(X, B, Gamma, Z, U, V, off, sub)
+        lo, hi = -15.0, 15.0
+        shift0 = B[:, 0].copy()
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            zf = _zero_frac(base + mid, family, size)
+            if zf > zero_frac:
+                lo = mid
+            else:
+                hi = mid
+        B[:, 0] = shift0 + 0.5 * (lo + hi)
+
+    # Counts, drawn row-chunk by row-chunk to bound memory.
+    saturated = 0
+    Y = np.empty((n, m), dtype=np.int32 if y_dtype == "int32" else np.uint16)
+    chunk = max(1, int(4_000_000 // max(m, 1)))
+    for r0 in range(0, n, chunk):
+        rows = slice(r0, min(n, r0 + chunk))
+        mu = np.exp(np.clip(_eta(X, B, Gamma, Z, U, V, off, rows), -30, 30))
+        if family == "poisson":
+            c = rng.poisson(mu)
+        else:
+            # Gamma-Poisson mixture: lambda ~ Gamma(size, mu/size), y ~ Poisson(lambda)
+            c = rng.poisson(rng.gamma(size[None, :], mu / size[None, :]))
+        top = 65535 if y_dtype == "uint16" else 2**31 - 1
+        saturated += int(np.count_nonzero(c > top))
+        Y[rows] = np.minimum(c, top)
+    return Problem(Y=np.ascontiguousarray(Y), X=X, Z=Z, offset=off, B=B, Gamma=Gamma,
+                   U=U, V=V, nb_size=size, family=family, saturated=saturated)
+
+
+def workload_problem(name, seed=0, n=None, m=None):
+    """Draw the named workload (optionally at a reduced n x m with the same law)."""
+    w = WORKLOADS[name]
+    return make_problem(n or w.n, m or w.m, w.p, w.q, w.d, w.family, seed=seed,
+                        y_dtype=w.y_dtype, zero_frac=w.zero_frac, offset=w.offset)
+
+
+def partitions(n, m, seed):
+    """Random row and column permutations: chunk c of rows is
+    row_perm[c*nb_row:(c+1)*nb_row] (the random partitions of Algorithm 1)."""
+    rng = np.random.default_rng([seed, 1])
+    return (rng.permutation(n).astype(np.int32), rng.permutation(m).astype(np.int32))
+
+
+def n_sweeps(n, m, nb_row, nb_col):
+    r = -(-n // nb_row)
+    s = -(-m // nb_col)
+    return max(r, s)
+
+
+def sweep_orders(n, m, nb_row, nb_col, epochs, seed):
+    """One random permutation of the sweep offsets per epoch (the per-block
+    sampling of I in Algorithm 1), as int32 arrays."""
+    rng = np.random.default_rng([seed, 2])
+    w = n_sweeps(n, m, nb_row, nb_col)
+    return [rng.permutation(w).astype(np.int32) for _ in range(epochs)]
+
+
+def crude_start(prob: Problem, d, *, seed=0, scale=0.1):
+    """A deterministic starting point shared by both implementations.
+
+    Gene intercepts from column means, per-cell intercepts from row sums, the
+    other coefficients zero, and small random latent factors.
+    """
+    rng = np.random.default_rng([seed, 3])
+    n, m = prob.Y.shape
+    p = prob.X.shape[1]
+    q = prob.Z.shape[1]
+    colsum = prob.Y.sum(axis=0, dtype=np.float64)
+    rowsum = prob.Y.sum(axis=1, dtype=np.float64)
+    B0 = np.zeros((m, p))
+    B0[:, 0] = np.log((colsum + 0.5) / n) - prob.offset.mean()
+    G0 = np.zeros((n, q))
+    if q >= 1:
+        expected = np.exp(prob.offset) * np.exp(B0[:, 0]).sum()
+        G0[:, 0] = np.log((rowsum + 0.5) / expected)
+        G0[:, 0] -= G0[:, 0].mean()
+    U0 = scale * rng.standard_normal((n, d))
+    V0 = scale * rng.standard_normal((m, d))
+    alpha0 = 1.0
+    return dict(B=B0, Gamma=G0, U=U0, V=V0, alpha=alpha0)
+
+
+def fit_settings(**over):
+    """Optimiser settings of the paper's sgdGMF runs (Sec. 5.2 / App. C) with the
+    unstated constants filled in; keyword arguments override."""
+    s = dict(lambda_=(0.0, 0.0, 1.0, 0.0), a1=0.1, a2=0.01, k0=0.01, k1=1e-3, tau=0.75,
+             damping=1e-3, eps=1e-8, eta_clamp=30.0, bias_corr=0, alpha_mode=0)
+    s.update(over)
+    return s

@@ -1,0 +1,414 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test targets a plausible mistake: a dropped term, a wrong sign, a wrong
+scale factor, a transposed operand, an off-by-one in t or in the schedule.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import synth
+from tests.bruteforce import BruteFit
+
+FAM = {"poisson": 0, "negbin": 1}
+
+
+def loglik(family, y, mu, alpha):
+    if family == "poisson":
+        return stats.poisson.logpmf(y, mu)
+    return stats.nbinom.logpmf(y, alpha, alpha / (alpha + mu))
+
+
+# ---------------------------------------------------------------- per entry (Sec. 3)
+
+@pytest.mark.parametrize("family", ["poisson", "negbin"])
+def test_entry_derivatives_match_finite_differences(oracle_lib, family):
+    """Ddot = d log f / d eta (score) and the observed second derivative equals
+    Dddot * alpha(mu), alpha(mu) = 1 + (y - mu)(nu'/nu + g''/g') (Sec. 3)."""
+    h1, h2 = 1e-5, 2e-3
+    for y in (0, 1, 4, 37):
+        for eta in (-2.0, 0.3, 2.5):
+            for alpha in (0.4, 2.0, 15.0):
+                for w in (1.0, 0.6):
+                    mu, dd, ddd = oracle_lib.entry(FAM[family], y, eta, w, alpha)
+                    assert mu == pytest.approx(math.exp(eta), rel=1e-15)
+                    f = lambda e: w * loglik(family, y, math.exp(e), alpha)
+                    fd1 = (f(eta + h1) - f(eta - h1)) / (2 * h1)
+                    fd2 = -(f(eta + h2) - 2 * f(eta) + f(eta - h2)) / h2 ** 2
+                    scale = 1.0 + abs(f(eta))          # finite-difference round-off grows with |f|
+                    assert dd == pytest.approx(fd1, rel=1e-7, abs=1e-9 * scale)
+                    if family == "poisson":
+                        a_mu = 1.0
+                    else:
+                        nu = mu * (1 + mu / alpha)
+                        a_mu = 1 + (y - mu) * ((1 + 2 * mu / alpha) / nu + (-1 / mu ** 2) / (1 / mu))
+                    assert ddd * a_mu == pytest.approx(fd2, rel=2e-6, abs=1e-8 * scale)
+
+
+@pytest.mark.parametrize("family", ["poisson", "negbin"])
+def test_fisher_weight_is_expected_observed_information(oracle_lib, family):
+    """Dddot is the Fisher weight: E_y[-d^2 log f/d eta^2] under y ~ f(mu)."""
+    h = 1e-4
+    for eta in (-1.0, 0.5, 1.8):
+        for alpha in (0.7, 3.0):
+            mu, _, ddd = oracle_lib.entry(FAM[family], 0, eta, 1.0, alpha)
+            ys = np.arange(0, 400)
+            pmf = np.exp(loglik(family, ys, mu, alpha))
+            f = lambda e: loglik(family, ys, math.exp(e), alpha)
+            obs = -(f(eta + h) - 2 * f(eta) + f(eta - h)) / h ** 2
+            assert float((pmf * obs).sum()) == pytest.approx(ddd, rel=1e-5)
+
+
+@pytest.mark.parametrize("family", ["poisson", "negbin"])
+def test_deviance_matches_likelihood_ratio(oracle_lib, family):
+    """D(y, mu) = -2 log{f(y, mu)/f(y, y)} (Sec. 2; Table S1, App. B); zero at
+    mu = y, positive elsewhere, linear in w."""
+    for y in (0, 1, 3, 20, 250):
+        for mu in (0.05, 1.0, 7.5, 300.0):
+            for alpha in (0.5, 4.0):
+                ref = -2 * (loglik(family, y, mu, alpha) - (loglik(family, y, y, alpha) if y > 0 else 0.0))
+                got = oracle_lib.entry_deviance(FAM[family], y, mu, 1.0, alpha)
+                assert got == pytest.approx(ref, rel=1e-9, abs=1e-10)
+                assert got >= 0
+                assert oracle_lib.entry_deviance(FAM[family], y, mu, 0.3, alpha) == pytest.approx(0.3 * got, rel=1e-12)
+        if y > 0:
+            assert abs(oracle_lib.entry_deviance(FAM[family], y, float(y), 1.0, 2.0)) < 1e-12
+
+
+# ---------------------------------------------------------------- matrix level (eq. 7-8, 15, App. B)
+
+def tiny_fit(oracle_lib, n, m, p, q, d, family, seed, nb_row=None, nb_col=None, **kw):
+    rng = np.random.default_rng(seed)
+    X = np.hstack([np.ones((n, 1)), rng.standard_normal((n, p - 1))])
+    Z = np.hstack([np.ones((m, 1)), rng.standard_normal((m, q - 1))]) if q else np.zeros((m, 0))
+    start = dict(B=0.3 * rng.standard_normal((m, p)), Gamma=0.3 * rng.standard_normal((n, q)),
+                 U=0.4 * rng.standard_normal((n, d)), V=0.4 * rng.standard_normal((m, d)), alpha=1.7)
+    off = 0.2 * rng.standard_normal(n)
+    Y = rng.poisson(2.0, size=(n, m)).astype(np.int32)
+    W = kw.pop("W", None)
+    settings = synth.fit_settings(**kw)
+    rp = kw.get("row_perm", rng.permutation(n).astype(np.int32))
+    cp = kw.get("col_perm", rng.permutation(m).astype(np.int32))
+    f = oracle_lib.OracleFit(Y, X, Z, off, start, family=family, nb_row=nb_row or n, nb_col=nb_col or m,
+                             row_perm=rp, col_perm=cp, settings=settings, W=W)
+    return f, dict(Y=Y, X=X, Z=Z, off=off, start=start, rp=rp, cp=cp, settings=settings, W=W)
+
+
+def nll(family, Y, X, Z, off, B, G, U, V, alpha, W=None):
+    eta = off[:, None] + X @ B.T + G @ Z.T + U @ V.T
+    ll = loglik(family, Y, np.exp(eta), alpha)
+    return -float((ll if W is None else W * ll).sum())
+
+
+@pytest.mark.parametrize("family", ["poisson", "negbin"])
+def test_block_gradient_matches_finite_differences(oracle_lib, family):
+    """Full-batch estimators equal d l / d theta of the negative log-likelihood
+    for every free block [Gamma, U] and [B, V] (App. B); H matches the second
+    derivative for the canonical Poisson link (Z*Z for Gamma, X*X for B)."""
+    n, m, p, q, d = 5, 4, 2, 2, 2
+    rng = np.random.default_rng(3)
+    W = rng.uniform(0.5, 1.5, size=(n, m))
+    f, D = tiny_fit(oracle_lib, n, m, p, q, d, family, seed=1, W=W)
+    Grow, Hrow, Gcol, Hcol, _ = f.block_grad(np.arange(n), np.arange(m))
+    P = {k: np.array(v, dtype=float) for k, v in D["start"].items() if k != "alpha"}
+    a = D["start"]["alpha"]
+    h, hh = 1e-5, 2e-3
+
+    def L(P):
+        return nll(family, D["Y"], D["X"], D["Z"], D["off"], P["B"], P["Gamma"], P["U"], P["V"], a, W)
+
+    def fd(name, i, c):
+        Pp = {k: v.copy() for k, v in P.items()}; Pm = {k: v.copy() for k, v in P.items()}
+        Pp[name][i, c] += h; Pm[name][i, c] -= h
+        g = (L(Pp) - L(Pm)) / (2 * h)
+        Pp[name][i, c] += hh - h; Pm[name][i, c] -= hh - h
+        h2 = (L(Pp) - 2 * L(P) + L(Pm)) / hh ** 2
+        return g, h2
+
+    for i in range(n):
+        for c in range(q + d):
+            name, cc = ("Gamma", c) if c < q else ("U", c - q)
+            g, h2 = fd(name, i, cc)
+            assert Grow[i, c] == pytest.approx(g, rel=1e-6, abs=1e-7)
+            if family == "poisson":
+                assert Hrow[i, c] == pytest.approx(h2, rel=1e-5, abs=1e-6)
+    for j in range(m):
+        for c in range(p + d):
+            name, cc = ("B", c) if c < p else ("V", c - p)
+            g, h2 = fd(name, j, cc)
+            assert Gcol[j, c] == pytest.approx(g, rel=1e-6, abs=1e-7)
+            if family == "poisson":
+                assert Hcol[j, c] == pytest.approx(h2, rel=1e-5, abs=1e-6)
+
+
+def test_block_estimators_are_unbiased_over_a_partition(oracle_lib):
+    """sum_J (|J|/m) G_row(I, J) = G_row(I, all) and likewise for the columns
+    (eq. 15 and the unbiasedness remark after it), with a ragged last chunk."""
+    n, m = 12, 7
+    f, D = tiny_fit(oracle_lib, n, m, 2, 1, 3, "negbin", seed=5)
+    I = np.arange(n)
+    full = f.block_grad(I, np.arange(m))
+    acc = [np.zeros_like(full[0]), np.zeros_like(full[1])]
+    for J in (np.array([0, 4, 6]), np.array([1, 2, 3]), np.array([5])):
+        g = f.block_grad(I, J)
+        acc[0] += len(J) / m * g[0]
+        acc[1] += len(J) / m * g[1]
+    np.testing.assert_allclose(acc[0], full[0], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(acc[1], full[1], rtol=1e-12, atol=1e-12)
+    Jall = np.arange(m)
+    acc = [np.zeros_like(full[2]), np.zeros_like(full[3])]
+    for Ic in (np.arange(0, 5), np.arange(5, 10), np.arange(10, 12)):
+        g = f.block_grad(Ic, Jall)
+        acc[0] += len(Ic) / n * g[2]
+        acc[1] += len(Ic) / n * g[3]
+    np.testing.assert_allclose(acc[0], full[2], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(acc[1], full[3], rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Algorithm 1 bookkeeping
+
+@pytest.mark.parametrize("shape,blocks", [((5, 4), (2, 3)), ((12, 7), (5, 3)), ((7, 12), (3, 5))])
+@pytest.mark.parametrize("family,bias_corr,alpha_mode", [("poisson", 0, 0), ("negbin", 1, 1), ("negbin", 0, 1)])
+def test_epochs_match_independent_matrix_form(oracle_lib, shape, blocks, family, bias_corr, alpha_mode):
+    """Three epochs of the C oracle equal an independent numpy restatement of
+    Algorithm 1 (brute force on tiny inputs, ragged chunks, both bias readings,
+    the NB shape update, and the r < s role swap)."""
+    n, m = shape
+    f, D = tiny_fit(oracle_lib, n, m, 2, 1, 2, family, seed=7, nb_row=blocks[0], nb_col=blocks[1],
+                    bias_corr=bias_corr, alpha_mode=alpha_mode, k0=0.3, k1=0.5, lambda_=(0.1, 0.2, 1.0, 0.3))
+    W = np.random.default_rng(9).uniform(0.5, 1.5, size=(n, m))
+    f, D = tiny_fit(oracle_lib, n, m, 2, 1, 2, family, seed=7, nb_row=blocks[0], nb_col=blocks[1],
+                    bias_corr=bias_corr, alpha_mode=alpha_mode, k0=0.3, k1=0.5, lambda_=(0.1, 0.2, 1.0, 0.3), W=W)
+    bf = BruteFit(D["Y"], D["X"], D["Z"], D["off"], D["start"], family, blocks[0], blocks[1], D["rp"], D["cp"],
+                  D["settings"], W=W)
+    nsw = synth.n_sweeps(n, m, blocks[0], blocks[1])
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        sigma = rng.permutation(nsw).astype(np.int32)
+        f.epoch(sigma)
+        bf.epoch(sigma)
+    for a, b in ((f.B, bf.B), (f.G, bf.G), (f.U, bf.U), (f.V, bf.V), (f.Gb_row, bf.GbR), (f.Hb_col, bf.HbC)):
+        np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-13)
+    assert f.alpha[0] == pytest.approx(bf.alpha, rel=1e-12)
+    assert int(f.t[0]) == 3 * math.ceil(n / blocks[0]) * math.ceil(m / blocks[1])
+    assert (f.cnt_row == 3 * math.ceil(m / blocks[1])).all()
+    assert (f.cnt_col == 3 * math.ceil(n / blocks[0])).all()
+
+
+def test_full_batch_unit_smoothing_is_diagonal_quasi_newton(oracle_lib):
+    """With one block (r = s = 1), a1 = a2 = 1 and the per-visit correction,
+    one epoch is one step of the diagonal quasi-Newton update (eq. 9-10):
+    theta <- theta - rho G/H with the full-data G and H."""
+    n, m = 6, 5
+    f, D = tiny_fit(oracle_lib, n, m, 2, 1, 2, "negbin", seed=2, a1=1.0, a2=1.0, bias_corr=1,
+                    k0=0.7, k1=0.0, damping=0.0, lambda_=(0.0, 0.0, 0.5, 0.5))
+    Grow, Hrow, Gcol, Hcol, _ = f.block_grad(np.arange(n), np.arange(m))
+    U0, V0, B0, G0 = f.U.copy(), f.V.copy(), f.B.copy(), f.G.copy()
+    f.epoch(np.zeros(1, dtype=np.int32))
+    lam = 0.5
+    np.testing.assert_allclose(f.U, U0 - 0.7 * (Grow[:, 1:] + lam * U0) / (Hrow[:, 1:] + lam), rtol=1e-13)
+    np.testing.assert_allclose(f.G, G0 - 0.7 * Grow[:, :1] / Hrow[:, :1], rtol=1e-13)
+    np.testing.assert_allclose(f.V, V0 - 0.7 * (Gcol[:, 2:] + lam * V0) / (Hcol[:, 2:] + lam), rtol=1e-13)
+    np.testing.assert_allclose(f.B, B0 - 0.7 * Gcol[:, :2] / Hcol[:, :2], rtol=1e-13)
+
+
+# ---------------------------------------------------------------- convergence to known optima
+
+def _intercepts_fit(oracle_lib, Y, X, settings, nb=None, seed=0):
+    n, m = Y.shape
+    rng = np.random.default_rng(seed)
+    start = dict(B=np.zeros((m, X.shape[1])), Gamma=np.zeros((n, 1)), U=np.zeros((n, 0)),
+                 V=np.zeros((m, 0)), alpha=1.0)
+    rp, cp = rng.permutation(n).astype(np.int32), rng.permutation(m).astype(np.int32)
+    return oracle_lib.OracleFit(Y, X, np.ones((m, 1)), None, start, family="poisson",
+                                nb_row=nb[0] if nb else n, nb_col=nb[1] if nb else m,
+                                row_perm=rp, col_perm=cp, settings=settings)
+
+
+def test_d0_poisson_reaches_independence_model(oracle_lib):
+    """d = 0 with a gene and a cell intercept is the Poisson independence
+    model, whose MLE is mu_ij = y_i. y_.j / y_.. (textbook closed form)."""
+    rng = np.random.default_rng(4)
+    n, m = 30, 12
+    Y = rng.poisson(np.outer(rng.uniform(1, 4, n), rng.uniform(0.5, 3, m))).astype(np.int32)
+    st = synth.fit_settings(a1=1.0, a2=1.0, bias_corr=1, k0=0.5, k1=0.0, damping=0.0, lambda_=(0, 0, 0, 0))
+    f = _intercepts_fit(oracle_lib, Y, np.ones((n, 1)), st)
+    for _ in range(400):
+        f.epoch(np.zeros(1, dtype=np.int32))
+    mu = np.exp(f.eta())
+    ref = np.outer(Y.sum(1), Y.sum(0)) / Y.sum()
+    np.testing.assert_allclose(mu, ref, rtol=1e-8)
+
+
+def _irls_vec(Y, X):
+    """Independent Poisson IRLS on the vectorised design of eta_ij = x_i'b_j + g_i."""
+    n, m = Y.shape
+    p = X.shape[1]
+    rows = []
+    for i in range(n):
+        for j in range(m):
+            r = np.zeros(m * p + n)
+            r[j * p:(j + 1) * p] = X[i]
+            r[m * p + i] = 1.0
+            rows.append(r)
+    A = np.array(rows)
+    y = Y.reshape(-1).astype(float)
+    beta = np.zeros(A.shape[1])
+    beta[:m * p:p] = np.log(Y.mean(0) + 0.1)
+    for _ in range(100):
+        eta = A @ beta
+        mu = np.exp(eta)
+        z = eta + (y - mu) / mu
+        sw = np.sqrt(mu)
+        beta = np.linalg.lstsq(A * sw[:, None], z * sw, rcond=None)[0]
+    return np.exp(A @ beta).reshape(n, m)
+
+
+def test_d0_poisson_with_covariate_matches_irls(oracle_lib):
+    rng = np.random.default_rng(8)
+    n, m = 25, 8
+    X = np.hstack([np.ones((n, 1)), rng.standard_normal((n, 1))])
+    mu0 = np.exp(0.5 + 0.4 * X[:, 1:2] * rng.standard_normal((1, m)) + 0.3 * rng.standard_normal((n, 1)))
+    Y = rng.poisson(mu0).astype(np.int32)
+    st = synth.fit_settings(a1=1.0, a2=1.0, bias_corr=1, k0=0.4, k1=0.0, damping=0.0, lambda_=(0, 0, 0, 0))
+    f = _intercepts_fit(oracle_lib, Y, X, st)
+    for _ in range(1500):
+        f.epoch(np.zeros(1, dtype=np.int32))
+    np.testing.assert_allclose(np.exp(f.eta()), _irls_vec(Y, X), rtol=1e-7)
+
+
+def test_d0_stochastic_blocks_reach_the_optimum_deviance(oracle_lib):
+    """The block-wise stochastic method (r, s > 1, smoothing on) gets within
+    1e-3 relative of the MLE deviance of the independence model."""
+    rng = np.random.default_rng(6)
+    n, m = 60, 24
+    Y = rng.poisson(np.outer(rng.uniform(1, 4, n), rng.uniform(0.5, 3, m))).astype(np.int32)
+    ref = np.outer(Y.sum(1), Y.sum(0)) / Y.sum()
+    d_opt = sum(oracle_lib.entry_deviance(0, y, mu) for y, mu in zip(Y.ravel(), ref.ravel()))
+    st = synth.fit_settings(k0=0.5, k1=0.02, tau=0.75, lambda_=(0, 0, 0, 0), bias_corr=1)
+    f = _intercepts_fit(oracle_lib, Y, np.ones((n, 1)), st, nb=(20, 8))
+    start_dev = f.deviance()
+    for e in range(300):
+        f.epoch(np.random.default_rng(e).permutation(3).astype(np.int32))
+    assert f.deviance() < start_dev
+    assert f.deviance() == pytest.approx(d_opt, rel=1e-3)
+
+
+def test_nb_moment_estimator_recovers_shape(oracle_lib):
+    """App. B moment estimator: sum w mu^2 / sum w((y-mu)^2 - mu) recovers a
+    known NB shape from data drawn with the true mu plugged in."""
+    rng = np.random.default_rng(12)
+    n, m, alpha = 400, 500, 2.0
+    b = rng.uniform(-0.5, 1.5, m)
+    g = rng.uniform(-0.5, 0.5, n)
+    mu = np.exp(b[None, :] + g[:, None])
+    Y = rng.negative_binomial(alpha, alpha / (alpha + mu)).astype(np.int32)
+    start = dict(B=b[:, None].copy(), Gamma=g[:, None].copy(), U=np.zeros((n, 0)), V=np.zeros((m, 0)), alpha=alpha)
+    f = oracle_lib.OracleFit(Y, np.ones((n, 1)), np.ones((m, 1)), None, start, family="negbin", nb_row=n,
+                             nb_col=m, row_perm=np.arange(n, dtype=np.int32), col_perm=np.arange(m, dtype=np.int32),
+                             settings=synth.fit_settings())
+    sums = f.block_grad(np.arange(n), np.arange(m))[4]
+    assert sums[0] == pytest.approx(float((mu ** 2).sum()), rel=1e-12)
+    ahat = sums[0] / sums[1]
+    # Var(y) = mu + mu^2/alpha; the ratio's sampling sd here is about 0.02.
+    assert abs(ahat - alpha) < 0.1
+
+
+# ---------------------------------------------------------------- Algorithm 2
+
+@pytest.mark.parametrize("mode", ["B1", "B2", "B3"])
+def test_orthogonalize_invariants(mode):
+    from oracle.orth import orthogonalize
+    rng = np.random.default_rng(13)
+    n, m, p, q, d = 40, 15, 2, 2, 3
+    X = np.hstack([np.ones((n, 1)), rng.standard_normal((n, p - 1))])
+    Z = np.hstack([np.ones((m, 1)), rng.standard_normal((m, q - 1))])
+    B, G = rng.standard_normal((m, p)), rng.standard_normal((n, q))
+    U, V = rng.standard_normal((n, d)), rng.standard_normal((m, d))
+    eta0 = X @ B.T + G @ Z.T + U @ V.T
+    B2, G2, U2, V2 = orthogonalize(X, Z, B, G, U, V, mode)
+    np.testing.assert_allclose(X @ B2.T + G2 @ Z.T + U2 @ V2.T, eta0, atol=1e-10)
+    np.testing.assert_allclose(X.T @ G2, 0, atol=1e-10)
+    np.testing.assert_allclose(X.T @ U2, 0, atol=1e-10)
+    if mode != "B3":
+        np.testing.assert_allclose(Z.T @ V2, 0, atol=1e-10)
+    if mode == "B1":
+        np.testing.assert_allclose(V2.T @ V2, np.eye(d), atol=1e-10)
+        S = U2.T @ U2
+        np.testing.assert_allclose(S - np.diag(np.diag(S)), 0, atol=1e-9)
+        assert np.all(np.diff(np.diag(S)) < 0)
+        assert np.all(V2[0] > 0)
+    if mode == "B2":
+        np.testing.assert_allclose(U2.T @ U2, np.eye(d), atol=1e-10)
+        assert np.all(U2[0] > 0)
+    if mode == "B3":
+        Uc = U2 - U2.mean(0)
+        np.testing.assert_allclose(Uc.T @ Uc / n, np.eye(d), atol=1e-10)
+        np.testing.assert_allclose(np.triu(V2[:d, :d], 1), 0, atol=1e-10)
+        assert np.all(np.diag(V2) > 0)
+
+
+def test_orthogonalize_b1_matches_qr_route():
+    """The explicit n x m SVD of Algorithm 2 equals the thin-QR route
+    U = Qu Ru, V = Qv Rv, svd(Ru Rv') on a 6 x 5 problem."""
+    from oracle.orth import orthogonalize
+    rng = np.random.default_rng(14)
+    n, m, d = 6, 5, 2
+    X, Z = np.ones((n, 1)), np.ones((m, 1))
+    B, G = rng.standard_normal((m, 1)), rng.standard_normal((n, 1))
+    U, V = rng.standard_normal((n, d)), rng.standard_normal((m, d))
+    B2, G2, U2, V2 = orthogonalize(X, Z, B, G, U, V, "B1")
+    Uc = U - X @ np.linalg.solve(X.T @ X, X.T @ U)
+    Vc = V - Z @ np.linalg.solve(Z.T @ Z, Z.T @ V)
+    Qu, Ru = np.linalg.qr(Uc)
+    Qv, Rv = np.linalg.qr(Vc)
+    P, S, Qt = np.linalg.svd(Ru @ Rv.T)
+    Uq, Vq = Qu @ P * S, Qv @ Qt.T
+    sgn = np.sign(Vq[0])
+    np.testing.assert_allclose(U2, Uq * sgn, atol=1e-10)
+    np.testing.assert_allclose(V2, Vq * sgn, atol=1e-10)
+
+
+# ---------------------------------------------------------------- per-cell Fisher scoring
+
+@pytest.mark.parametrize("family", ["poisson", "negbin"])
+def test_projection_converges_to_stationary_point(family):
+    from oracle.project import project_cells
+    rng = np.random.default_rng(15)
+    n, m, p, d = 6, 40, 2, 3
+    X = np.hstack([np.ones((n, 1)), rng.standard_normal((n, 1))])
+    Z = np.ones((m, 1))
+    B, V = 0.3 * rng.standard_normal((m, p)), 0.5 * rng.standard_normal((m, d))
+    mu = np.exp(X @ B.T + 0.5 * rng.standard_normal((n, d)) @ V.T)
+    Y = rng.poisson(mu)
+    U, G, dev = project_cells(Y, X, None, B, Z, V, family=family, alpha=3.0, n_steps=30, lam_u=1.0)
+    h = 1e-6
+    for i in range(n):
+        th = np.concatenate([G[i], U[i]])
+
+        def f(th):
+            e = X[i] @ B.T + th[:1] @ Z.T + th[1:] @ V.T
+            return -loglik(family, Y[i], np.exp(e), 3.0).sum() + 0.5 * (th[1:] ** 2).sum()
+
+        for c in range(len(th)):
+            e = np.zeros_like(th); e[c] = h
+            assert abs((f(th + e) - f(th - e)) / (2 * h)) < 1e-6
+
+
+def test_projection_gamma_closed_form_is_fixed_point():
+    """Poisson, u fixed (d = 0): the closed-form gamma is the exact row optimum,
+    and Fisher scoring from gamma = 0 converges to it."""
+    from oracle.project import project_cells
+    rng = np.random.default_rng(16)
+    n, m = 5, 30
+    X = np.ones((n, 1)); Z = np.ones((m, 1))
+    B = rng.standard_normal((m, 1)); V = np.zeros((m, 0))
+    Y = rng.poisson(np.exp(B[:, 0])[None, :] * rng.uniform(0.5, 2, (n, 1)))
+    _, G_cf, _ = project_cells(Y, X, None, B, Z, V, family="poisson", alpha=1.0, n_steps=0, lam_gamma=0.0)
+    _, G_1, _ = project_cells(Y, X, None, B, Z, V, family="poisson", alpha=1.0, n_steps=1, lam_gamma=0.0)
+    _, G_cold, _ = project_cells(Y, X, None, B, Z, V, family="poisson", alpha=1.0, n_steps=25, lam_gamma=0.0,
+                                 gamma_closed_form=False)
+    np.testing.assert_allclose(G_1, G_cf, atol=1e-12)
+    np.testing.assert_allclose(G_cold, G_cf, atol=1e-10)
