@@ -1,0 +1,230 @@
+/*
+ * gmf.h -- C ABI of the GB300 (sm_103a) library for block-wise adaptive SGD on
+ * generalized matrix factorization (GMF) models of count matrices
+ * (Castiglione, Segers, Clement, Risso; arXiv 2412.20509).
+ *
+ * Model (Sec. 2, eq. 1-3; offset as in Sec. 4.1 and App. B):
+ *   y_ij ~ EF(mu_ij),  log mu_ij = eta_ij = o_i + x_i'beta_j + gamma_i'z_j + u_i'v_j
+ * with rows i = 1..n (cells) and columns j = 1..m (genes); X (n x p) and
+ * Z (m x q) are fixed covariates, B (m x p), Gamma (n x q), U (n x d),
+ * V (m x d) are fitted. Families: Poisson and negative binomial with shape
+ * alpha (Table S1, App. B), log link, dispersion phi = 1.
+ *
+ * Conventions for every entry point:
+ *   - Return value: GMF_OK (0) or a negative GMF_ERR_* code; nothing throws.
+ *     gmf_last_error() returns a thread-local message for the last failure.
+ *   - Matrices are dense, row-major, C-contiguous.
+ *   - "host" pointers are ordinary CPU memory (pageable or pinned); "device"
+ *     pointers are CUDA global memory of the current device.
+ *   - stream is a cudaStream_t (NULL = legacy default stream). Work is
+ *     enqueued on it; functions documented as synchronous wait for it.
+ *   - The handle owns all of its device memory. Caller buffers are only read
+ *     during the call (or, for outputs, written before a synchronous return).
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef GMF_H
+#define GMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GMF_OK = 0,
+    GMF_ERR_ARG = -1,       /* invalid argument (shape, pointer, value) */
+    GMF_ERR_CUDA = -2,      /* a CUDA runtime/driver call failed */
+    GMF_ERR_OOM = -3,       /* device or host allocation failed */
+    GMF_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up */
+    GMF_ERR_NONFINITE = -5, /* a non-finite value was produced */
+    GMF_ERR_STATE = -6      /* handle not in a state that allows the call */
+};
+
+enum { GMF_POISSON = 0, GMF_NEGBIN = 1 };          /* log link for both */
+enum { GMF_Y_INT32 = 0, GMF_Y_UINT16 = 1 };        /* count storage type */
+enum {
+    GMF_PREC_FP32 = 0,   /* FP32 on the CUDA cores throughout (reference path) */
+    GMF_PREC_MIXED = 1   /* tcgen05 tensor cores: eta as split-BF16 (3 products),
+                            gradient/curvature contractions in BF16, FP32 accumulate */
+};
+enum { GMF_ORTH_B1 = 1, GMF_ORTH_B2 = 2, GMF_ORTH_B3 = 3 };  /* Sec. 2.1 */
+
+typedef struct gmf_model gmf_model;  /* opaque, library-owned */
+
+/*
+ * Fit configuration. Defaults in brackets are the paper's sgdGMF settings
+ * (App. C) where it states them, otherwise the library's reading.
+ */
+typedef struct {
+    int64_t n, m;        /* rows (cells) and columns (genes) of Y */
+    int32_t p, q, d;     /* columns of X, columns of Z, latent rank (d >= 0) */
+    int32_t family;      /* GMF_POISSON or GMF_NEGBIN */
+    int32_t nb_row;      /* row minibatch size n* (rows per partition chunk) */
+    int32_t nb_col;      /* column minibatch size m* */
+    int32_t bias_corr;   /* 0: c_t = (1-a2^t)/(1-a1^t), global block count t (eq. 11);
+                            1: c = (1-(1-a2)^k)/(1-(1-a1)^k), k = visits of the row/column */
+    int32_t alpha_mode;  /* NB only. 0: shape fixed; 1: stochastic moment estimator (App. B),
+                            pooled per sweep */
+    int32_t precision;   /* GMF_PREC_FP32 or GMF_PREC_MIXED */
+    int32_t reserved0;   /* must be 0 */
+    double lambda[4];    /* ridge penalties on (B, Gamma, U, V), eq. 6 [0, 0, 1, 0] */
+    double a1, a2;       /* EMA weights of eq. 12 [0.1, 0.01] */
+    double k0, k1, tau;  /* rho_t = k0 / (1 + k0 k1 t)^tau (Sec. 3.2) [0.01, 1e-3, 0.75] */
+    double damping;      /* added to every curvature estimate [1e-3] */
+    double eps;          /* floor of the NB shape update (App. B) [1e-8] */
+    double eta_clamp;    /* eta is clamped to [-eta_clamp, eta_clamp] before exp [30] */
+} gmf_config;
+
+/* Fill *cfg with the defaults above for the given sizes. */
+void gmf_config_default(gmf_config* cfg, int64_t n, int64_t m, int32_t p, int32_t q, int32_t d,
+                        int32_t family, int32_t nb_row, int32_t nb_col);
+
+/*
+ * gmf_init -- create a fit (model of Sec. 2, state of Algorithm 1).
+ *
+ * The random partitions {I_1..I_r} and {J_1..J_s} of Algorithm 1 are fixed
+ * here, once, as in the algorithm: row chunk c is rows
+ * row_perm[c*nb_row .. min(n,(c+1)*nb_row)-1], column chunk c likewise with
+ * col_perm and nb_col (the last chunk may be smaller). The library stores Y
+ * (and W) and the parameters permuted so that every block is contiguous.
+ *
+ *   Y           n x m counts, y_dtype GMF_Y_INT32 or GMF_Y_UINT16; host or
+ *               device memory as y_on_device says. Copied; counts must be >= 0.
+ *   W           NULL (all weights 1) or n x m float32 weights w_ij > 0
+ *               (a_ij(phi) = phi/w_ij, Sec. 2), same memory space as Y. Copied.
+ *   X, Z        host double, n x p and m x q.  offset: host double n, or NULL.
+ *   row_perm    host int32 permutation of 0..n-1; col_perm of 0..m-1.
+ *   B0..V0      host double starting values (m x p, n x q, n x d, m x d).
+ *   alpha0      starting NB shape (> 0; ignored for Poisson).
+ * The smoothed derivatives start at zero and t at 0. Synchronous.
+ * Errors: GMF_ERR_ARG for bad sizes/pointers/permutations, GMF_ERR_OOM, GMF_ERR_CUDA.
+ */
+int gmf_init(gmf_model** out, const gmf_config* cfg,
+             const void* Y, int32_t y_dtype, int32_t y_on_device, const float* W,
+             const double* X, const double* Z, const double* offset,
+             const int32_t* row_perm, const int32_t* col_perm,
+             const double* B0, const double* G0, const double* U0, const double* V0,
+             double alpha0, void* stream);
+
+/*
+ * gmf_update_y -- replace the counts (same n, m and dtype as at init) from
+ * host or device memory, e.g. a new batch of a streamed matrix. Asynchronous
+ * on the stream for device sources; for host sources the call returns once
+ * the host buffer may be reused.
+ */
+int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, void* stream);
+
+/* Number of sweeps per epoch: max(r, s) with r = ceil(n/nb_row), s = ceil(m/nb_col). */
+int32_t gmf_num_sweeps(const gmf_model* h);
+
+/*
+ * gmf_sgd_epoch -- one epoch of Algorithm 1: every block (I_a, J_b) once.
+ *
+ * sigma: host int32 permutation of 0..S-1, S = gmf_num_sweeps(h) (the
+ * sampling of I in Algorithm 1). With r >= s, sweep w visits the s blocks
+ * (I_{(sigma[w]+k) mod r}, J_k), k = 0..s-1; with r < s the roles swap. The
+ * blocks of one sweep are disjoint in rows and columns and run concurrently.
+ * Per block (eq. 15 with App. B, eq. 12, eq. 14): eta, mu = exp(eta), the
+ * derivatives Ddot, Dddot (Sec. 3), the minibatch gradient and diagonal
+ * curvature of [Gamma, U]_I and [B, V]_J, EMA smoothing and the local step
+ * theta <- theta - rho_t c_t Gbar/Hbar, with both sides using the block's
+ * pre-step parameters. NB with alpha_mode 1: the shape is updated once per
+ * sweep from moment sums pooled over the sweep. t advances by one per block.
+ * Asynchronous on the stream (sigma is copied before return).
+ */
+int gmf_sgd_epoch(gmf_model* h, const int32_t* sigma, void* stream);
+
+/*
+ * gmf_sgd_sweeps -- run only sweeps [w_begin, w_end) of the epoch defined by
+ * sigma (same semantics as gmf_sgd_epoch; t advances by the blocks run).
+ */
+int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begin, int32_t w_end, void* stream);
+
+/*
+ * gmf_deviance -- total deviance sum_ij D(y_ij, mu_ij) at the current
+ * parameters (Table S1; App. B for NB, with the current shape), each entry in
+ * FP32, summed per tile with compensation and combined in FP64.
+ * Synchronous; *out_total is host memory.
+ */
+int gmf_deviance(gmf_model* h, double* out_total, void* stream);
+
+/* As gmf_deviance, but writes the FP64 total to device memory d_out and does not synchronize. */
+int gmf_deviance_async(gmf_model* h, double* d_out, void* stream);
+
+/*
+ * gmf_get_params / gmf_set_params -- copy the parameters out / in, host
+ * double, original (unpermuted) order: B m x p, G (Gamma) n x q, U n x d,
+ * V m x d, and the NB shape. Any pointer may be NULL to skip it. Synchronous.
+ */
+int gmf_get_params(gmf_model* h, double* B, double* G, double* U, double* V, double* alpha, void* stream);
+int gmf_set_params(gmf_model* h, const double* B, const double* G, const double* U, const double* V,
+                   const double* alpha, void* stream);
+
+/*
+ * gmf_get_ema / gmf_set_ema -- the optimiser state of eq. 12: smoothed
+ * gradient and curvature of [Gamma, U] (n x (q+d)) and [B, V] (m x (p+d)),
+ * visit counters (n and m), and the block count t. Host, original order,
+ * synchronous; NULL pointers are skipped (t is skipped when t_io is NULL).
+ * With gmf_get_params these make a complete checkpoint.
+ */
+int gmf_get_ema(gmf_model* h, double* Gb_row, double* Hb_row, double* Gb_col, double* Hb_col,
+                int64_t* cnt_row, int64_t* cnt_col, int64_t* t_io, void* stream);
+int gmf_set_ema(gmf_model* h, const double* Gb_row, const double* Hb_row, const double* Gb_col,
+                const double* Hb_col, const int64_t* cnt_row, const int64_t* cnt_col, const int64_t* t_in,
+                void* stream);
+
+/*
+ * gmf_orthogonalize -- Algorithm 2 (Sec. 2.1 and its appendix): project Gamma
+ * and U off span(X) and V off span(Z) while moving the removed parts into B
+ * and Gamma (eta unchanged), then impose (B1), (B2) or (B3). Computed in
+ * FP64 on the device (Gram reductions over n and m) with a d x d SVD /
+ * eigen-decomposition on the host. Resets the smoothed derivatives and visit
+ * counters (they refer to the old basis). Synchronous.
+ */
+int gmf_orthogonalize(gmf_model* h, int32_t mode, void* stream);
+
+/*
+ * gmf_project_cells -- scores of new cells with the column side fixed
+ * (B, V, Z and the NB shape of the fit). Each new row i solves the row
+ * problem of Sec. 3 (rows separate given V) by n_steps exact Fisher-scoring
+ * steps on theta_i = [gamma_i, u_i] (the row step of AIRWLS, Sec. 3.1):
+ *   theta <- theta + (R' diag(Dddot_i) R + Lambda)^-1 (R' Ddot_i - Lambda theta),  R = [Z, V].
+ * Start: u_i = U_start row (NULL: zeros), gamma_i (q = 1 only) in closed form
+ * log(sum_j y_ij / sum_j exp(eta_ij without gamma)); for q != 1, gamma = 0.
+ *   Ynew      device, n_new x m counts (y_dtype)
+ *   Xnew      device float32, n_new x p;  offset_new: device float32 n_new or NULL
+ *   U_start   device float32 n_new x d or NULL
+ *   U_out     device float32 n_new x d;  G_out: device float32 n_new x q
+ *   dev_out   device float32 n_new (per-cell deviance at the result) or NULL
+ * Asynchronous on the stream. Allocates its workspace from the handle.
+ */
+int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n_new,
+                      const float* Xnew, const float* offset_new, const float* U_start,
+                      int32_t n_steps, float* U_out, float* G_out, float* dev_out, void* stream);
+
+/*
+ * gmf_trace -- enable (1) or disable (0) timing of the block-step kernels:
+ * while enabled, every block-step launch is bracketed by CUDA events recorded
+ * on the launching stream. gmf_trace_read synchronizes the stream, returns the
+ * summed kernel time in milliseconds and the number of timed launches since
+ * the last read, and resets both. Costs one event pair per launch.
+ */
+int gmf_trace(gmf_model* h, int32_t enable);
+int gmf_trace_read(gmf_model* h, double* total_ms, int64_t* launches, void* stream);
+
+/* Release the handle and all of its device memory (NULL is allowed). */
+void gmf_free(gmf_model* h);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* gmf_last_error(void);
+
+/* Library version string. */
+const char* gmf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMF_H */

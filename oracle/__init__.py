@@ -74,6 +74,8 @@ def lib():
         _lib.gmfo_block_grad.restype = C.c_int
         _lib.gmfo_sgd_epoch.argtypes = [C.c_void_p] * 4
         _lib.gmfo_sgd_epoch.restype = C.c_int
+        _lib.gmfo_sgd_sweeps.argtypes = [C.c_void_p] * 4 + [C.c_int64, C.c_int64]
+        _lib.gmfo_sgd_sweeps.restype = C.c_int
         _lib.gmfo_deviance.argtypes = [C.c_void_p] * 3
         _lib.gmfo_deviance.restype = C.c_double
         _lib.gmfo_eta_entries.argtypes = [C.c_void_p] * 5 + [C.c_int64, C.c_void_p]
@@ -151,6 +153,13 @@ class OracleFit:
         rc = lib().gmfo_sgd_epoch(C.byref(self.cfg), C.byref(self._data), C.byref(self._state), sigma.ctypes.data)
         if rc:
             raise RuntimeError(f"oracle epoch failed ({rc})")
+
+    def sweeps(self, sigma, w0, w1):
+        sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+        rc = lib().gmfo_sgd_sweeps(C.byref(self.cfg), C.byref(self._data), C.byref(self._state),
+                                   sigma.ctypes.data, int(w0), int(w1))
+        if rc:
+            raise RuntimeError(f"oracle sweeps failed ({rc})")
 
     def deviance(self):
         return lib().gmfo_deviance(C.byref(self.cfg), C.byref(self._data), C.byref(self._state))

@@ -262,14 +262,14 @@ static void chunk(const int32_t* perm, int64_t total, int64_t size, int64_t c,
     *len = hi - lo;
 }
 
-/* One epoch of Algorithm 1 on the sweep schedule described in the header. */
-int gmfo_sgd_epoch(const gmfo_config* c, const gmfo_data* D, gmfo_state* S, const int32_t* sigma) {
+/* Sweeps [w0, w1) of the epoch defined by sigma (schedule in the header). */
+int gmfo_sgd_sweeps(const gmfo_config* c, const gmfo_data* D, gmfo_state* S, const int32_t* sigma,
+                    int64_t w0, int64_t w1) {
     const int64_t r = (c->n + c->nb_row - 1) / c->nb_row;
     const int64_t s = (c->m + c->nb_col - 1) / c->nb_col;
     const int swap = r < s;
-    const int64_t nsw = swap ? s : r;     /* sweeps per epoch */
     const int64_t per = swap ? r : s;     /* blocks per sweep */
-    for (int64_t w = 0; w < nsw; w++) {
+    for (int64_t w = w0; w < w1; w++) {
         double sums[2] = {0.0, 0.0};
         const int64_t t_first = *S->t + 1;
         for (int64_t k = 0; k < per; k++) {
@@ -290,6 +290,13 @@ int gmfo_sgd_epoch(const gmfo_config* c, const gmfo_data* D, gmfo_state* S, cons
         }
     }
     return 0;
+}
+
+/* One epoch of Algorithm 1: all max(r, s) sweeps. */
+int gmfo_sgd_epoch(const gmfo_config* c, const gmfo_data* D, gmfo_state* S, const int32_t* sigma) {
+    const int64_t r = (c->n + c->nb_row - 1) / c->nb_row;
+    const int64_t s = (c->m + c->nb_col - 1) / c->nb_col;
+    return gmfo_sgd_sweeps(c, D, S, sigma, 0, r < s ? s : r);
 }
 
 /* Total deviance sum_ij D(y_ij, mu_ij) (Table S1, App. B) at the current parameters. */

@@ -1,0 +1,287 @@
+"""Python binding of ``libgmf.so``, the GB300 (sm_103a) library for block-wise
+adaptive SGD on generalized matrix factorization models (arXiv 2412.20509).
+
+Argument marshalling only: every step of the fit runs in the library's CUDA
+kernels behind the C ABI declared in ``include/gmf.h``. PyTorch provides
+device memory and streams. There is no CPU fallback: importing this package
+without a built ``libgmf.so`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgmf.so")
+
+GMF_OK, GMF_ERR_ARG, GMF_ERR_CUDA, GMF_ERR_OOM, GMF_ERR_TIMEOUT, GMF_ERR_NONFINITE, GMF_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+GMF_POISSON, GMF_NEGBIN = 0, 1
+GMF_Y_INT32, GMF_Y_UINT16 = 0, 1
+GMF_PREC_FP32, GMF_PREC_MIXED = 0, 1
+GMF_ORTH_B1, GMF_ORTH_B2, GMF_ORTH_B3 = 1, 2, 3
+
+FAMILIES = {"poisson": GMF_POISSON, "negbin": GMF_NEGBIN}
+PRECISIONS = {"fp32": GMF_PREC_FP32, "mixed": GMF_PREC_MIXED}
+ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
+
+# Every function declared in include/gmf.h.
+EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_num_sweeps", "gmf_sgd_epoch", "gmf_sgd_sweeps",
+           "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
+           "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_free", "gmf_last_error",
+           "gmf_version")
+
+
+class GmfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class gmf_config(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("p", C.c_int32), ("q", C.c_int32), ("d", C.c_int32),
+                ("family", C.c_int32), ("nb_row", C.c_int32), ("nb_col", C.c_int32), ("bias_corr", C.c_int32),
+                ("alpha_mode", C.c_int32), ("precision", C.c_int32), ("reserved0", C.c_int32),
+                ("lambda_", C.c_double * 4), ("a1", C.c_double), ("a2", C.c_double), ("k0", C.c_double),
+                ("k1", C.c_double), ("tau", C.c_double), ("damping", C.c_double), ("eps", C.c_double),
+                ("eta_clamp", C.c_double)]
+
+
+_lib = None
+VP = C.c_void_p
+
+
+def lib():
+    """Load libgmf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgmf.so not found at {LIB_PATH}; build it with __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "gmf_config_default": (None, [C.POINTER(gmf_config), C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                      C.c_int32, C.c_int32, C.c_int32]),
+        "gmf_init": (C.c_int, [C.POINTER(VP), C.POINTER(gmf_config), VP, C.c_int32, C.c_int32, VP, VP, VP, VP, VP, VP,
+                               VP, VP, VP, VP, C.c_double, VP]),
+        "gmf_update_y": (C.c_int, [VP, VP, C.c_int32, VP]),
+        "gmf_num_sweeps": (C.c_int32, [VP]),
+        "gmf_sgd_epoch": (C.c_int, [VP, VP, VP]),
+        "gmf_sgd_sweeps": (C.c_int, [VP, VP, C.c_int32, C.c_int32, VP]),
+        "gmf_deviance": (C.c_int, [VP, C.POINTER(C.c_double), VP]),
+        "gmf_deviance_async": (C.c_int, [VP, VP, VP]),
+        "gmf_get_params": (C.c_int, [VP, VP, VP, VP, VP, VP, VP]),
+        "gmf_set_params": (C.c_int, [VP, VP, VP, VP, VP, VP, VP]),
+        "gmf_get_ema": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
+        "gmf_set_ema": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
+        "gmf_orthogonalize": (C.c_int, [VP, C.c_int32, VP]),
+        "gmf_project_cells": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, VP, VP, C.c_int32, VP, VP, VP, VP]),
+        "gmf_trace": (C.c_int, [VP, C.c_int32]),
+        "gmf_trace_read": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), VP]),
+        "gmf_free": (None, [VP]),
+        "gmf_last_error": (C.c_char_p, []),
+        "gmf_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(rc):
+    if rc != GMF_OK:
+        raise GmfError(rc, lib().gmf_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision="fp32"):
+    cfg = gmf_config()
+    lib().gmf_config_default(C.byref(cfg), n, m, p, q, d, FAMILIES[family], nb_row, nb_col)
+    s = settings
+    cfg.lambda_ = (C.c_double * 4)(*s["lambda_"])
+    for k in ("a1", "a2", "k0", "k1", "tau", "damping", "eps", "eta_clamp"):
+        setattr(cfg, k, float(s[k]))
+    cfg.bias_corr = int(s["bias_corr"])
+    cfg.alpha_mode = int(s["alpha_mode"])
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return cfg
+
+
+def _f64(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+class Model:
+    """One GMF fit held on the GPU (a ``gmf_model`` handle)."""
+
+    def __init__(self, Y, X, Z, offset, start, *, family, nb_row, nb_col, row_perm, col_perm, settings,
+                 precision="fp32", W=None, stream=None):
+        import torch
+        self._h = VP()
+        on_dev = isinstance(Y, torch.Tensor) and Y.is_cuda
+        if isinstance(Y, torch.Tensor):
+            n, m = Y.shape
+            ydt = {torch.int32: GMF_Y_INT32, torch.uint16: GMF_Y_UINT16}.get(Y.dtype) if hasattr(torch, "uint16") \
+                else {torch.int32: GMF_Y_INT32}.get(Y.dtype)
+            if ydt is None:
+                raise TypeError("Y must be int32 or uint16")
+            Y = Y.contiguous()
+        else:
+            Y = np.ascontiguousarray(Y)
+            n, m = Y.shape
+            ydt = {np.dtype(np.int32): GMF_Y_INT32, np.dtype(np.uint16): GMF_Y_UINT16}.get(Y.dtype)
+            if ydt is None:
+                raise TypeError("Y must be int32 or uint16")
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        p, q = X.shape[1], Z.shape[1]
+        d = np.asarray(start["U"]).shape[1]
+        self.dims = (n, m, p, q, d)
+        self.cfg = make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision)
+        off = None if offset is None else np.ascontiguousarray(offset, dtype=np.float64)
+        B0 = _f64(start["B"], (m, p)); G0 = _f64(start["Gamma"], (n, q))
+        U0 = _f64(start["U"], (n, d)); V0 = _f64(start["V"], (m, d))
+        rp = np.ascontiguousarray(row_perm, dtype=np.int32)
+        cp = np.ascontiguousarray(col_perm, dtype=np.int32)
+        if W is not None:
+            if on_dev:
+                W = W.to(torch.float32).contiguous()
+            else:
+                W = np.ascontiguousarray(W, dtype=np.float32)
+        self._keep = (Y, W)
+        check(lib().gmf_init(C.byref(self._h), C.byref(self.cfg), _ptr(Y), ydt, int(on_dev), _ptr(W), _ptr(X), _ptr(Z),
+                             _ptr(off), _ptr(rp), _ptr(cp), _ptr(B0), _ptr(G0), _ptr(U0), _ptr(V0),
+                             float(start.get("alpha", 1.0)), _stream(stream)))
+        self._keep = None
+        self.y_dtype = ydt
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.gmf_free(h)
+            self._h = VP()
+
+    close = __del__
+
+    @property
+    def num_sweeps(self):
+        return lib().gmf_num_sweeps(self._h)
+
+    def epoch(self, sigma, stream=None):
+        sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+        check(lib().gmf_sgd_epoch(self._h, sigma.ctypes.data, _stream(stream)))
+
+    def sweeps(self, sigma, w_begin, w_end, stream=None):
+        sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+        check(lib().gmf_sgd_sweeps(self._h, sigma.ctypes.data, int(w_begin), int(w_end), _stream(stream)))
+
+    def update_y(self, Y, stream=None):
+        import torch
+        on_dev = isinstance(Y, torch.Tensor) and Y.is_cuda
+        if not on_dev:
+            Y = np.ascontiguousarray(Y) if not isinstance(Y, torch.Tensor) else Y.contiguous()
+        check(lib().gmf_update_y(self._h, _ptr(Y), int(on_dev), _stream(stream)))
+
+    def deviance(self, stream=None):
+        out = C.c_double()
+        check(lib().gmf_deviance(self._h, C.byref(out), _stream(stream)))
+        return out.value
+
+    def deviance_async(self, out, stream=None):
+        """Write the FP64 deviance into a 1-element CUDA float64 tensor."""
+        check(lib().gmf_deviance_async(self._h, out.data_ptr(), _stream(stream)))
+
+    def get_params(self, stream=None):
+        n, m, p, q, d = self.dims
+        B, G, U, V = np.empty((m, p)), np.empty((n, q)), np.empty((n, d)), np.empty((m, d))
+        a = C.c_double()
+        check(lib().gmf_get_params(self._h, _ptr(B), _ptr(G), _ptr(U), _ptr(V), C.addressof(a), _stream(stream)))
+        return dict(B=B, Gamma=G, U=U, V=V, alpha=a.value)
+
+    def set_params(self, params, stream=None):
+        n, m, p, q, d = self.dims
+        arr = [None if params.get(k) is None else _f64(params[k], s)
+               for k, s in (("B", (m, p)), ("Gamma", (n, q)), ("U", (n, d)), ("V", (m, d)))]
+        a = None if params.get("alpha") is None else C.c_double(float(params["alpha"]))
+        check(lib().gmf_set_params(self._h, *[_ptr(x) for x in arr], None if a is None else C.addressof(a),
+                                   _stream(stream)))
+
+    def get_ema(self, stream=None):
+        n, m, p, q, d = self.dims
+        out = dict(Gb_row=np.empty((n, q + d)), Hb_row=np.empty((n, q + d)), Gb_col=np.empty((m, p + d)),
+                   Hb_col=np.empty((m, p + d)), cnt_row=np.empty(n, dtype=np.int64), cnt_col=np.empty(m, dtype=np.int64))
+        t = C.c_int64()
+        check(lib().gmf_get_ema(self._h, *[_ptr(out[k]) for k in ("Gb_row", "Hb_row", "Gb_col", "Hb_col", "cnt_row",
+                                                                  "cnt_col")], C.addressof(t), _stream(stream)))
+        out["t"] = t.value
+        return out
+
+    def set_ema(self, ema, stream=None):
+        n, m, p, q, d = self.dims
+        shapes = dict(Gb_row=(n, q + d), Hb_row=(n, q + d), Gb_col=(m, p + d), Hb_col=(m, p + d))
+        arrs = [None if ema.get(k) is None else _f64(ema[k], s) for k, s in shapes.items()]
+        cnts = [None if ema.get(k) is None else np.ascontiguousarray(ema[k], dtype=np.int64)
+                for k in ("cnt_row", "cnt_col")]
+        t = None if ema.get("t") is None else C.c_int64(int(ema["t"]))
+        check(lib().gmf_set_ema(self._h, *[_ptr(x) for x in arrs], *[_ptr(x) for x in cnts],
+                                None if t is None else C.addressof(t), _stream(stream)))
+
+    def state_dict(self):
+        """Complete checkpoint (parameters + optimiser state) as numpy arrays."""
+        s = self.get_params()
+        s.update(self.get_ema())
+        return s
+
+    def load_state_dict(self, s):
+        self.set_params(s)
+        self.set_ema(s)
+
+    def trace(self, enable=True):
+        """Time every block-step launch with CUDA events on its stream."""
+        check(lib().gmf_trace(self._h, int(bool(enable))))
+
+    def trace_read(self, stream=None):
+        """(summed kernel milliseconds, launches) since the last read."""
+        ms, n = C.c_double(), C.c_int64()
+        check(lib().gmf_trace_read(self._h, C.byref(ms), C.byref(n), _stream(stream)))
+        return ms.value, n.value
+
+    def orthogonalize(self, mode="B1", stream=None):
+        check(lib().gmf_orthogonalize(self._h, ORTH[mode] if isinstance(mode, str) else int(mode), _stream(stream)))
+
+    def project_cells(self, Ynew, Xnew, offset_new=None, U_start=None, n_steps=3, with_dev=True, stream=None):
+        """Per-cell Fisher scoring of new rows; inputs are CUDA tensors."""
+        import torch
+        n_new = Ynew.shape[0]
+        _, m, p, q, d = self.dims
+        ydt = GMF_Y_INT32 if Ynew.dtype == torch.int32 else GMF_Y_UINT16
+        dev = Ynew.device
+        U = torch.empty((n_new, d), dtype=torch.float32, device=dev)
+        G = torch.empty((n_new, q), dtype=torch.float32, device=dev)
+        D = torch.empty((n_new,), dtype=torch.float32, device=dev) if with_dev else None
+        Xf = Xnew.to(torch.float32).contiguous()
+        of = None if offset_new is None else offset_new.to(torch.float32).contiguous()
+        us = None if U_start is None else U_start.to(torch.float32).contiguous()
+        check(lib().gmf_project_cells(self._h, _ptr(Ynew.contiguous()), ydt, n_new, _ptr(Xf), _ptr(of), _ptr(us),
+                                      int(n_steps), _ptr(U), _ptr(G), _ptr(D), _stream(stream)))
+        return U, G, D

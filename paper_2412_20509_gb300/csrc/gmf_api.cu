@@ -1,0 +1,560 @@
+// C ABI of the GB300 GMF library: handles, validation, permuted storage and
+// the launch sequence of each entry point. The kernels live in
+// gmf_step_simt.cu (FP32 path), gmf_step_tc.cu (tensor-core path),
+// gmf_orth.cu (Algorithm 2) and gmf_project.cu (per-cell Fisher scoring).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "gmf_internal.cuh"
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                             \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? GMF_ERR_OOM : GMF_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+extern "C" const char* gmf_last_error(void) { return g_err.c_str(); }
+extern "C" const char* gmf_version(void) { return "gmf-gb300 0.1 (sm_103a)"; }
+
+// tensor-core path hooks (gmf_step_tc.cu)
+int gmf_tc_prepare(gmf_model* h, cudaStream_t st);
+int gmf_tc_sweep(gmf_model* h, int w, long long t0, cudaStream_t st);
+void gmf_tc_free(gmf_model* h);
+// Algorithm 2 (gmf_orth.cu), per-cell projection (gmf_project.cu)
+int gmf_orth_run(gmf_model* h, int mode, cudaStream_t st, std::string* err);
+int gmf_project_run(gmf_model* h, const void* Ynew, int y16, int64_t n_new, const float* Xnew,
+                    const float* off, const float* Ustart, int n_steps, float* Uout, float* Gout, float* dev,
+                    cudaStream_t st, std::string* err);
+
+extern "C" void gmf_config_default(gmf_config* c, int64_t n, int64_t m, int32_t p, int32_t q, int32_t d,
+                                   int32_t family, int32_t nb_row, int32_t nb_col) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->n = n;
+    c->m = m;
+    c->p = p;
+    c->q = q;
+    c->d = d;
+    c->family = family;
+    c->nb_row = nb_row;
+    c->nb_col = nb_col;
+    c->lambda[0] = 0.0;
+    c->lambda[1] = 0.0;
+    c->lambda[2] = 1.0;
+    c->lambda[3] = 0.0;
+    c->a1 = 0.1;
+    c->a2 = 0.01;
+    c->k0 = 0.01;
+    c->k1 = 1e-3;
+    c->tau = 0.75;
+    c->damping = 1e-3;
+    c->eps = 1e-8;
+    c->eta_clamp = 30.0;
+    c->precision = GMF_PREC_FP32;
+}
+
+static bool is_perm(const int32_t* p, int64_t n) {
+    std::vector<char> seen((size_t)n, 0);
+    for (int64_t i = 0; i < n; i++) {
+        if (p[i] < 0 || p[i] >= n || seen[(size_t)p[i]]) return false;
+        seen[(size_t)p[i]] = 1;
+    }
+    return true;
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+static void trace_destroy(gmf_model* h) {
+    if (!h->trace_ev) return;
+    for (int i = 0; i < 2 * GMF_TRACE_POOL; i++) cudaEventDestroy(h->trace_ev[i]);
+    delete[] h->trace_ev;
+    h->trace_ev = nullptr;
+}
+
+static void release(gmf_model* h) {
+    if (!h) return;
+    trace_destroy(h);
+    if (h->tc) gmf_tc_free(h);
+    void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
+                    h->rperm, h->cperm, h->ystage, h->partR, h->partC, h->ctrR, h->ctrC, h->ctrSweep,
+                    h->nbpart, h->sigma, h->err, h->devpart, h->devtot};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete[] h->h_rperm;
+    delete[] h->h_cperm;
+    delete h;
+}
+
+extern "C" void gmf_free(gmf_model* h) { release(h); }
+
+// Host: build the permuted augmented factors L = [o|X|Gamma|U], R = [1|B|Z|V] as float32.
+static void build_factors(const gmf_model* h, const double* X, const double* Z, const double* off,
+                          const double* B, const double* G, const double* U, const double* V,
+                          std::vector<float>& L, std::vector<float>& R) {
+    const int K = h->K, p = h->p, q = h->q, d = h->d;
+    L.assign((size_t)h->n * K, 0.f);
+    R.assign((size_t)h->m * K, 0.f);
+    for (int64_t ip = 0; ip < h->n; ip++) {
+        const int64_t i = h->h_rperm[ip];
+        float* l = &L[(size_t)ip * K];
+        l[0] = off ? (float)off[i] : 0.f;
+        for (int a = 0; a < p; a++) l[1 + a] = (float)X[i * p + a];
+        for (int b = 0; b < q; b++) l[1 + p + b] = (float)G[i * q + b];
+        for (int c = 0; c < d; c++) l[1 + p + q + c] = (float)U[i * d + c];
+    }
+    for (int64_t jp = 0; jp < h->m; jp++) {
+        const int64_t j = h->h_cperm[jp];
+        float* r = &R[(size_t)jp * K];
+        r[0] = 1.f;
+        for (int a = 0; a < p; a++) r[1 + a] = (float)B[j * p + a];
+        for (int b = 0; b < q; b++) r[1 + p + b] = (float)Z[j * q + b];
+        for (int c = 0; c < d; c++) r[1 + p + q + c] = (float)V[j * d + c];
+    }
+}
+
+static int upload_y(gmf_model* h, const void* Y, int on_device, cudaStream_t st) {
+    const size_t bytes = (size_t)h->n * h->m * (h->y16 ? 2 : 4);
+    const void* src = Y;
+    if (!on_device) {
+        if (!h->ystage) CUDA_TRY(cudaMalloc(&h->ystage, bytes));
+        CUDA_TRY(cudaMemcpyAsync(h->ystage, Y, bytes, cudaMemcpyHostToDevice, st));
+        src = h->ystage;
+    }
+    CUDA_TRY(gmf_launch_permute_y(src, h->Yp, h->y16, h->n, h->m, h->rperm, h->cperm, st));
+    return GMF_OK;
+}
+
+extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, int32_t y_dtype, int32_t y_on_device,
+                        const float* W, const double* X, const double* Z, const double* offset,
+                        const int32_t* row_perm, const int32_t* col_perm, const double* B0, const double* G0,
+                        const double* U0, const double* V0, double alpha0, void* stream) {
+    if (!out) return fail(GMF_ERR_ARG, "gmf_init: out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(GMF_ERR_ARG, "gmf_init: cfg is NULL");
+    const gmf_config& c = *cfg;
+    if (c.n <= 0 || c.m <= 0) return fail(GMF_ERR_ARG, "gmf_init: n and m must be positive");
+    if (c.n > (int64_t)INT32_MAX || c.m > (int64_t)INT32_MAX)
+        return fail(GMF_ERR_ARG, "gmf_init: n and m must fit in int32");
+    if (c.p < 0 || c.q < 0 || c.d < 0) return fail(GMF_ERR_ARG, "gmf_init: p, q, d must be >= 0");
+    const int K = 1 + c.p + c.q + c.d;
+    if (K > GMF_KMAX || c.q + c.d > GMF_FREE_MAX || c.p + c.d > GMF_FREE_MAX)
+        return fail(GMF_ERR_ARG, "gmf_init: 1+p+q+d must be <= %d", GMF_KMAX);
+    if (c.family != GMF_POISSON && c.family != GMF_NEGBIN) return fail(GMF_ERR_ARG, "gmf_init: unknown family");
+    if (c.nb_row <= 0 || c.nb_col <= 0) return fail(GMF_ERR_ARG, "gmf_init: minibatch sizes must be positive");
+    if (c.bias_corr != 0 && c.bias_corr != 1) return fail(GMF_ERR_ARG, "gmf_init: bias_corr must be 0 or 1");
+    if (c.alpha_mode != 0 && c.alpha_mode != 1) return fail(GMF_ERR_ARG, "gmf_init: alpha_mode must be 0 or 1");
+    if (c.precision != GMF_PREC_FP32 && c.precision != GMF_PREC_MIXED)
+        return fail(GMF_ERR_ARG, "gmf_init: unknown precision");
+    if (c.reserved0 != 0) return fail(GMF_ERR_ARG, "gmf_init: reserved0 must be 0");
+    if (!(c.a1 > 0 && c.a1 <= 1 && c.a2 > 0 && c.a2 <= 1)) return fail(GMF_ERR_ARG, "gmf_init: a1, a2 in (0, 1]");
+    if (!(c.k0 > 0) || c.k1 < 0 || !(c.tau > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad learning-rate schedule");
+    if (c.damping < 0 || !(c.eta_clamp > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad damping or eta_clamp");
+    if (y_dtype != GMF_Y_INT32 && y_dtype != GMF_Y_UINT16) return fail(GMF_ERR_ARG, "gmf_init: bad y_dtype");
+    if (!Y || !X || !Z || !row_perm || !col_perm || !B0 || !G0 || !U0 || !V0)
+        return fail(GMF_ERR_ARG, "gmf_init: a required pointer is NULL");
+    if ((c.p > 0 && !X) || !(alpha0 > 0) ) return fail(GMF_ERR_ARG, "gmf_init: alpha0 must be > 0");
+    if (!is_perm(row_perm, c.n)) return fail(GMF_ERR_ARG, "gmf_init: row_perm is not a permutation of 0..n-1");
+    if (!is_perm(col_perm, c.m)) return fail(GMF_ERR_ARG, "gmf_init: col_perm is not a permutation of 0..m-1");
+
+    gmf_model* h = new gmf_model();
+    memset(h, 0, sizeof *h);
+    h->cfg = c;
+    cudaGetDevice(&h->device);
+    h->n = c.n;
+    h->m = c.m;
+    h->p = c.p;
+    h->q = c.q;
+    h->d = c.d;
+    h->K = K;
+    h->fr = c.q + c.d;
+    h->fc = c.p + c.d;
+    h->r = (int)((c.n + c.nb_row - 1) / c.nb_row);
+    h->s = (int)((c.m + c.nb_col - 1) / c.nb_col);
+    h->swap = h->r < h->s;
+    h->nsw = h->swap ? h->s : h->r;
+    h->per = h->swap ? h->r : h->s;
+    h->TI = (int)((std::min<int64_t>(c.nb_row, c.n) + GMF_TILE - 1) / GMF_TILE);
+    h->TJ = (int)((std::min<int64_t>(c.nb_col, c.m) + GMF_TILE - 1) / GMF_TILE);
+    h->y16 = y_dtype == GMF_Y_UINT16;
+    h->h_rperm = new int32_t[c.n];
+    h->h_cperm = new int32_t[c.m];
+    memcpy(h->h_rperm, row_perm, sizeof(int32_t) * c.n);
+    memcpy(h->h_cperm, col_perm, sizeof(int32_t) * c.m);
+    cudaStream_t st = (cudaStream_t)stream;
+
+#define INIT_TRY(expr)                   \
+    do {                                 \
+        int rc_ = (expr);                \
+        if (rc_ != GMF_OK) {             \
+            std::string keep = g_err;    \
+            release(h);                  \
+            g_err = keep;                \
+            return rc_;                  \
+        }                                \
+    } while (0)
+#define INIT_CUDA(expr) INIT_TRY(([&]() -> int { CUDA_TRY(expr); return GMF_OK; })())
+
+    const size_t nm = (size_t)c.n * c.m;
+    INIT_CUDA(cudaMalloc(&h->Yp, nm * (h->y16 ? 2 : 4)));
+    if (W) INIT_CUDA(dalloc(&h->Wp, nm));
+    INIT_CUDA(dalloc(&h->L, (size_t)c.n * K));
+    INIT_CUDA(dalloc(&h->R, (size_t)c.m * K));
+    INIT_CUDA(dalloc(&h->GbR, (size_t)c.n * h->fr));
+    INIT_CUDA(dalloc(&h->HbR, (size_t)c.n * h->fr));
+    INIT_CUDA(dalloc(&h->GbC, (size_t)c.m * h->fc));
+    INIT_CUDA(dalloc(&h->HbC, (size_t)c.m * h->fc));
+    INIT_CUDA(dalloc(&h->cntR, (size_t)c.n));
+    INIT_CUDA(dalloc(&h->cntC, (size_t)c.m));
+    INIT_CUDA(dalloc(&h->alpha, 1));
+    INIT_CUDA(dalloc(&h->rperm, (size_t)c.n));
+    INIT_CUDA(dalloc(&h->cperm, (size_t)c.m));
+    INIT_CUDA(dalloc(&h->partR, (size_t)h->per * h->TJ * GMF_TILE * 2 * std::max(h->fr, 1)));
+    INIT_CUDA(dalloc(&h->partC, (size_t)h->per * h->TI * GMF_TILE * 2 * std::max(h->fc, 1)));
+    INIT_CUDA(dalloc(&h->ctrR, (size_t)h->per * h->TI));
+    INIT_CUDA(dalloc(&h->ctrC, (size_t)h->per * h->TJ));
+    INIT_CUDA(dalloc(&h->ctrSweep, 1));
+    INIT_CUDA(dalloc(&h->nbpart, (size_t)2 * h->per * h->TI * h->TJ));
+    INIT_CUDA(dalloc(&h->sigma, (size_t)h->nsw));
+    INIT_CUDA(dalloc(&h->err, 1));
+    h->devparts = (int)(((c.n + GMF_TILE - 1) / GMF_TILE) * ((c.m + GMF_TILE - 1) / GMF_TILE));
+    INIT_CUDA(dalloc(&h->devpart, (size_t)h->devparts));
+    INIT_CUDA(dalloc(&h->devtot, 1));
+
+    INIT_CUDA(cudaMemcpyAsync(h->rperm, row_perm, sizeof(int32_t) * c.n, cudaMemcpyHostToDevice, st));
+    INIT_CUDA(cudaMemcpyAsync(h->cperm, col_perm, sizeof(int32_t) * c.m, cudaMemcpyHostToDevice, st));
+    INIT_CUDA(cudaMemsetAsync(h->GbR, 0, sizeof(float) * c.n * h->fr, st));
+    INIT_CUDA(cudaMemsetAsync(h->HbR, 0, sizeof(float) * c.n * h->fr, st));
+    INIT_CUDA(cudaMemsetAsync(h->GbC, 0, sizeof(float) * c.m * h->fc, st));
+    INIT_CUDA(cudaMemsetAsync(h->HbC, 0, sizeof(float) * c.m * h->fc, st));
+    INIT_CUDA(cudaMemsetAsync(h->cntR, 0, sizeof(int) * c.n, st));
+    INIT_CUDA(cudaMemsetAsync(h->cntC, 0, sizeof(int) * c.m, st));
+    INIT_CUDA(cudaMemsetAsync(h->ctrR, 0, sizeof(unsigned) * h->per * h->TI, st));
+    INIT_CUDA(cudaMemsetAsync(h->ctrC, 0, sizeof(unsigned) * h->per * h->TJ, st));
+    INIT_CUDA(cudaMemsetAsync(h->ctrSweep, 0, sizeof(unsigned), st));
+    INIT_CUDA(cudaMemsetAsync(h->err, 0, sizeof(unsigned), st));
+    float a0 = (float)alpha0;
+    INIT_CUDA(cudaMemcpyAsync(h->alpha, &a0, sizeof(float), cudaMemcpyHostToDevice, st));
+    {
+        std::vector<float> L, R;
+        build_factors(h, X, Z, offset, B0, G0, U0, V0, L, R);
+        INIT_CUDA(cudaMemcpyAsync(h->L, L.data(), sizeof(float) * L.size(), cudaMemcpyHostToDevice, st));
+        INIT_CUDA(cudaMemcpyAsync(h->R, R.data(), sizeof(float) * R.size(), cudaMemcpyHostToDevice, st));
+        INIT_CUDA(cudaStreamSynchronize(st));
+    }
+    INIT_TRY(upload_y(h, Y, y_on_device, st));
+    if (W) {
+        float* wsrc = (float*)W;
+        float* wtmp = nullptr;
+        if (!y_on_device) {
+            INIT_CUDA(dalloc(&wtmp, nm));
+            INIT_CUDA(cudaMemcpyAsync(wtmp, W, nm * sizeof(float), cudaMemcpyHostToDevice, st));
+            wsrc = wtmp;
+        }
+        INIT_CUDA(gmf_launch_permute_w(wsrc, h->Wp, c.n, c.m, h->rperm, h->cperm, st));
+        INIT_CUDA(cudaStreamSynchronize(st));
+        if (wtmp) cudaFree(wtmp);
+    }
+    if (c.precision == GMF_PREC_MIXED) INIT_TRY(gmf_tc_prepare(h, st));
+    INIT_CUDA(cudaStreamSynchronize(st));
+    *out = h;
+    return GMF_OK;
+}
+
+extern "C" int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, void* stream) {
+    if (!h || !Y) return fail(GMF_ERR_ARG, "gmf_update_y: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = upload_y(h, Y, y_on_device, st);
+    if (rc) return rc;
+    if (!y_on_device) CUDA_TRY(cudaStreamSynchronize(st));
+    return GMF_OK;
+}
+
+extern "C" int32_t gmf_num_sweeps(const gmf_model* h) { return h ? h->nsw : -1; }
+
+// Wait for the recorded event pairs and add their durations to the running total.
+static int trace_collect(gmf_model* h, cudaStream_t st) {
+    if (!h->trace_ev || h->trace_used == 0) return GMF_OK;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < h->trace_used; i++) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, h->trace_ev[2 * i], h->trace_ev[2 * i + 1]));
+        h->trace_ms += ms;
+    }
+    h->trace_launches += h->trace_used;
+    h->trace_used = 0;
+    return GMF_OK;
+}
+
+extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begin, int32_t w_end, void* stream) {
+    if (!h || !sigma) return fail(GMF_ERR_ARG, "gmf_sgd_sweeps: NULL argument");
+    if (w_begin < 0 || w_end > h->nsw || w_begin > w_end)
+        return fail(GMF_ERR_ARG, "gmf_sgd_sweeps: sweep range [%d, %d) outside [0, %d)", w_begin, w_end, h->nsw);
+    if (!is_perm(sigma, h->nsw)) return fail(GMF_ERR_ARG, "gmf_sgd_sweeps: sigma is not a permutation of 0..%d", h->nsw - 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(h->sigma, sigma, sizeof(int32_t) * h->nsw, cudaMemcpyHostToDevice, st));
+    const StepArgs a = gmf_make_args(h);
+    for (int w = w_begin; w < w_end; w++) {
+        const long long t0 = (long long)h->t;
+        if (h->trace_on) {
+            if (h->trace_used == GMF_TRACE_POOL) {
+                int rc = trace_collect(h, st);
+                if (rc) return rc;
+            }
+            CUDA_TRY(cudaEventRecord(h->trace_ev[2 * h->trace_used], st));
+        }
+        if (h->cfg.precision == GMF_PREC_MIXED) {
+            int rc = gmf_tc_sweep(h, w, t0 - (long long)w * h->per, st);
+            if (rc) return rc;
+        } else {
+            CUDA_TRY(gmf_launch_sweep_simt(h, a, w, t0 - (long long)w * h->per, st));
+        }
+        if (h->trace_on) {
+            CUDA_TRY(cudaEventRecord(h->trace_ev[2 * h->trace_used + 1], st));
+            h->trace_used++;
+        }
+        h->t += h->per;
+    }
+    return GMF_OK;
+}
+
+extern "C" int gmf_trace(gmf_model* h, int32_t enable) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_trace: NULL handle");
+    if (enable && !h->trace_ev) {
+        h->trace_ev = new cudaEvent_t[2 * GMF_TRACE_POOL];
+        for (int i = 0; i < 2 * GMF_TRACE_POOL; i++) CUDA_TRY(cudaEventCreate(&h->trace_ev[i]));
+    }
+    h->trace_on = enable ? 1 : 0;
+    return GMF_OK;
+}
+
+extern "C" int gmf_trace_read(gmf_model* h, double* total_ms, int64_t* launches, void* stream) {
+    if (!h || !total_ms || !launches) return fail(GMF_ERR_ARG, "gmf_trace_read: NULL argument");
+    int rc = trace_collect(h, (cudaStream_t)stream);
+    if (rc) return rc;
+    *total_ms = h->trace_ms;
+    *launches = h->trace_launches;
+    h->trace_ms = 0.0;
+    h->trace_launches = 0;
+    return GMF_OK;
+}
+
+extern "C" int gmf_sgd_epoch(gmf_model* h, const int32_t* sigma, void* stream) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_sgd_epoch: NULL handle");
+    return gmf_sgd_sweeps(h, sigma, 0, h->nsw, stream);
+}
+
+static int check_err_word(gmf_model* h, cudaStream_t st) {
+    unsigned e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, h->err, sizeof e, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (e & GMF_DEVERR_TIMEOUT) return fail(GMF_ERR_TIMEOUT, "a device-side wait timed out");
+    if (e & GMF_DEVERR_NONFINITE) return fail(GMF_ERR_NONFINITE, "a parameter update produced a non-finite value");
+    if (e & GMF_DEVERR_BOUNDS) return fail(GMF_ERR_STATE, "a device-side bounds check failed");
+    return GMF_OK;
+}
+
+extern "C" int gmf_deviance_async(gmf_model* h, double* d_out, void* stream) {
+    if (!h || !d_out) return fail(GMF_ERR_ARG, "gmf_deviance_async: NULL argument");
+    CUDA_TRY(gmf_launch_deviance(h, d_out, (cudaStream_t)stream));
+    return GMF_OK;
+}
+
+extern "C" int gmf_deviance(gmf_model* h, double* out_total, void* stream) {
+    if (!h || !out_total) return fail(GMF_ERR_ARG, "gmf_deviance: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(gmf_launch_deviance(h, h->devtot, st));
+    CUDA_TRY(cudaMemcpyAsync(out_total, h->devtot, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return check_err_word(h, st);
+}
+
+extern "C" int gmf_get_params(gmf_model* h, double* B, double* G, double* U, double* V, double* alpha,
+                              void* stream) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_get_params: NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = h->K, p = h->p, q = h->q, d = h->d;
+    std::vector<float> L((size_t)h->n * K), R((size_t)h->m * K);
+    float a = 0.f;
+    CUDA_TRY(cudaMemcpyAsync(L.data(), h->L, sizeof(float) * L.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(R.data(), h->R, sizeof(float) * R.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&a, h->alpha, sizeof(float), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t ip = 0; ip < h->n; ip++) {
+        const int64_t i = h->h_rperm[ip];
+        const float* l = &L[(size_t)ip * K];
+        if (G)
+            for (int b = 0; b < q; b++) G[i * q + b] = l[1 + p + b];
+        if (U)
+            for (int c = 0; c < d; c++) U[i * d + c] = l[1 + p + q + c];
+    }
+    for (int64_t jp = 0; jp < h->m; jp++) {
+        const int64_t j = h->h_cperm[jp];
+        const float* r = &R[(size_t)jp * K];
+        if (B)
+            for (int b = 0; b < p; b++) B[j * p + b] = r[1 + b];
+        if (V)
+            for (int c = 0; c < d; c++) V[j * d + c] = r[1 + p + q + c];
+    }
+    if (alpha) *alpha = a;
+    return check_err_word(h, st);
+}
+
+extern "C" int gmf_set_params(gmf_model* h, const double* B, const double* G, const double* U, const double* V,
+                              const double* alpha, void* stream) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_set_params: NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = h->K, p = h->p, q = h->q, d = h->d;
+    std::vector<float> L((size_t)h->n * K), R((size_t)h->m * K);
+    CUDA_TRY(cudaMemcpyAsync(L.data(), h->L, sizeof(float) * L.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(R.data(), h->R, sizeof(float) * R.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t ip = 0; ip < h->n; ip++) {
+        const int64_t i = h->h_rperm[ip];
+        float* l = &L[(size_t)ip * K];
+        if (G)
+            for (int b = 0; b < q; b++) l[1 + p + b] = (float)G[i * q + b];
+        if (U)
+            for (int c = 0; c < d; c++) l[1 + p + q + c] = (float)U[i * d + c];
+    }
+    for (int64_t jp = 0; jp < h->m; jp++) {
+        const int64_t j = h->h_cperm[jp];
+        float* r = &R[(size_t)jp * K];
+        if (B)
+            for (int b = 0; b < p; b++) r[1 + b] = (float)B[j * p + b];
+        if (V)
+            for (int c = 0; c < d; c++) r[1 + p + q + c] = (float)V[j * d + c];
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->L, L.data(), sizeof(float) * L.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->R, R.data(), sizeof(float) * R.size(), cudaMemcpyHostToDevice, st));
+    if (alpha) {
+        if (!(*alpha > 0)) return fail(GMF_ERR_ARG, "gmf_set_params: alpha must be > 0");
+        float a = (float)*alpha;
+        CUDA_TRY(cudaMemcpyAsync(h->alpha, &a, sizeof(float), cudaMemcpyHostToDevice, st));
+    }
+    CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(unsigned), st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return GMF_OK;
+}
+
+// rows of a (rows x cols) permuted float matrix <-> original-order double matrix
+static void unpermute(const std::vector<float>& src, double* dst, const int32_t* perm, int64_t rows, int cols) {
+    for (int64_t ip = 0; ip < rows; ip++)
+        for (int c = 0; c < cols; c++) dst[(int64_t)perm[ip] * cols + c] = src[(size_t)ip * cols + c];
+}
+static void permute_rows(const double* src, std::vector<float>& dst, const int32_t* perm, int64_t rows, int cols) {
+    dst.resize((size_t)rows * cols);
+    for (int64_t ip = 0; ip < rows; ip++)
+        for (int c = 0; c < cols; c++) dst[(size_t)ip * cols + c] = (float)src[(int64_t)perm[ip] * cols + c];
+}
+
+extern "C" int gmf_get_ema(gmf_model* h, double* Gb_row, double* Hb_row, double* Gb_col, double* Hb_col,
+                           int64_t* cnt_row, int64_t* cnt_col, int64_t* t_io, void* stream) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_get_ema: NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float> buf;
+    struct Item { double* dst; float* src; int64_t rows; int cols; const int32_t* perm; };
+    Item items[] = {{Gb_row, h->GbR, h->n, h->fr, h->h_rperm}, {Hb_row, h->HbR, h->n, h->fr, h->h_rperm},
+                    {Gb_col, h->GbC, h->m, h->fc, h->h_cperm}, {Hb_col, h->HbC, h->m, h->fc, h->h_cperm}};
+    for (auto& it : items) {
+        if (!it.dst) continue;
+        buf.resize((size_t)it.rows * it.cols);
+        CUDA_TRY(cudaMemcpyAsync(buf.data(), it.src, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        unpermute(buf, it.dst, it.perm, it.rows, it.cols);
+    }
+    struct CItem { int64_t* dst; int* src; int64_t rows; const int32_t* perm; };
+    CItem citems[] = {{cnt_row, h->cntR, h->n, h->h_rperm}, {cnt_col, h->cntC, h->m, h->h_cperm}};
+    for (auto& it : citems) {
+        if (!it.dst) continue;
+        std::vector<int> cb((size_t)it.rows);
+        CUDA_TRY(cudaMemcpyAsync(cb.data(), it.src, sizeof(int) * cb.size(), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t ip = 0; ip < it.rows; ip++) it.dst[it.perm[ip]] = cb[(size_t)ip];
+    }
+    if (t_io) *t_io = h->t;
+    return GMF_OK;
+}
+
+extern "C" int gmf_set_ema(gmf_model* h, const double* Gb_row, const double* Hb_row, const double* Gb_col,
+                           const double* Hb_col, const int64_t* cnt_row, const int64_t* cnt_col, const int64_t* t_in,
+                           void* stream) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_set_ema: NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float> buf;
+    struct Item { const double* src; float* dst; int64_t rows; int cols; const int32_t* perm; };
+    Item items[] = {{Gb_row, h->GbR, h->n, h->fr, h->h_rperm}, {Hb_row, h->HbR, h->n, h->fr, h->h_rperm},
+                    {Gb_col, h->GbC, h->m, h->fc, h->h_cperm}, {Hb_col, h->HbC, h->m, h->fc, h->h_cperm}};
+    for (auto& it : items) {
+        if (!it.src) continue;
+        permute_rows(it.src, buf, it.perm, it.rows, it.cols);
+        CUDA_TRY(cudaMemcpyAsync(it.dst, buf.data(), sizeof(float) * buf.size(), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    struct CItem { const int64_t* src; int* dst; int64_t rows; const int32_t* perm; };
+    CItem citems[] = {{cnt_row, h->cntR, h->n, h->h_rperm}, {cnt_col, h->cntC, h->m, h->h_cperm}};
+    for (auto& it : citems) {
+        if (!it.src) continue;
+        std::vector<int> cb((size_t)it.rows);
+        for (int64_t ip = 0; ip < it.rows; ip++) {
+            const int64_t v = it.src[it.perm[ip]];
+            if (v < 0 || v > INT32_MAX) return fail(GMF_ERR_ARG, "gmf_set_ema: visit counter out of range");
+            cb[(size_t)ip] = (int)v;
+        }
+        CUDA_TRY(cudaMemcpyAsync(it.dst, cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (t_in) {
+        if (*t_in < 0) return fail(GMF_ERR_ARG, "gmf_set_ema: t must be >= 0");
+        h->t = *t_in;
+    }
+    CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(unsigned), st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return GMF_OK;
+}
+
+extern "C" int gmf_orthogonalize(gmf_model* h, int32_t mode, void* stream) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_orthogonalize: NULL handle");
+    if (mode != GMF_ORTH_B1 && mode != GMF_ORTH_B2 && mode != GMF_ORTH_B3)
+        return fail(GMF_ERR_ARG, "gmf_orthogonalize: mode must be GMF_ORTH_B1, B2 or B3");
+    std::string err;
+    int rc = gmf_orth_run(h, mode, (cudaStream_t)stream, &err);
+    if (rc) return fail(rc, "gmf_orthogonalize: %s", err.c_str());
+    return GMF_OK;
+}
+
+extern "C" int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n_new, const float* Xnew,
+                                 const float* offset_new, const float* U_start, int32_t n_steps, float* U_out,
+                                 float* G_out, float* dev_out, void* stream) {
+    if (!h || !Ynew || !U_out || !G_out) return fail(GMF_ERR_ARG, "gmf_project_cells: NULL argument");
+    if (h->p > 0 && !Xnew) return fail(GMF_ERR_ARG, "gmf_project_cells: Xnew is NULL");
+    if (n_new <= 0 || n_new > (int64_t)INT32_MAX) return fail(GMF_ERR_ARG, "gmf_project_cells: bad n_new");
+    if (y_dtype != GMF_Y_INT32 && y_dtype != GMF_Y_UINT16) return fail(GMF_ERR_ARG, "gmf_project_cells: bad y_dtype");
+    if (n_steps < 0 || n_steps > 1000) return fail(GMF_ERR_ARG, "gmf_project_cells: n_steps in [0, 1000]");
+    std::string err;
+    int rc = gmf_project_run(h, Ynew, y_dtype == GMF_Y_UINT16, n_new, Xnew, offset_new, U_start, n_steps, U_out,
+                             G_out, dev_out, (cudaStream_t)stream, &err);
+    if (rc) return fail(rc, "gmf_project_cells: %s", err.c_str());
+    return GMF_OK;
+}

@@ -1,0 +1,117 @@
+// Internal declarations of the GB300 GMF library (not part of the C ABI).
+//
+// Storage (all device, all owned by the handle):
+//   Yp  n x m counts, rows and columns permuted by the fixed partitions, so
+//       block (I_a, J_b) is the contiguous sub-matrix rows [a*nb_row, ...),
+//       columns [b*nb_col, ...).
+//   L   n x K   augmented row factors  [o | X | Gamma | U]   (K = 1+p+q+d)
+//   R   m x K   augmented column factors [1 | B | Z | V], so eta = L R'.
+//       Row-free columns (Gamma, U) of L and their multipliers (Z, V) in R
+//       share the indices [1+p, K); column-free columns (B, V) of R and their
+//       multipliers (X, U) in L share {1..p} u [1+p+q, K).
+//   GbR/HbR n x (q+d), GbC/HbC m x (p+d): smoothed derivatives (eq. 12).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gmf.h"
+
+#define GMF_TILE 64          // SIMT tile edge (rows and columns)
+#define GMF_THREADS 256      // threads per SIMT tile CTA
+#define GMF_KMAX 64          // largest K = 1+p+q+d the SIMT path accepts
+#define GMF_FREE_MAX 64      // largest q+d or p+d
+
+// Error bits written by kernels into the handle's device status word.
+#define GMF_DEVERR_NONFINITE 1u
+#define GMF_DEVERR_TIMEOUT 2u
+#define GMF_DEVERR_BOUNDS 4u
+
+struct StepArgs {
+    int64_t n, m;
+    int p, q, d, K, fr, fc;
+    int nb_row, nb_col, r, s, per, swap;
+    int TI, TJ;                 // tiles per block along rows / columns (largest block)
+    int family, bias_corr, alpha_mode;
+    float lam[4];
+    float a1, a2, damping, eps, clamp;
+    double k0, k1, tau;
+    const void* Y;              // Yp (permuted)
+    int y16;                    // 1 if uint16 counts
+    const float* W;             // permuted weights or nullptr
+    float* L;
+    float* R;
+    float* GbR;
+    float* HbR;
+    float* GbC;
+    float* HbC;
+    int* cntR;
+    int* cntC;
+    float* alpha;               // device scalar (NB shape)
+    float* partR;               // [per][TJ][TILE][2*fr]
+    float* partC;               // [per][TI][TILE][2*fc]
+    unsigned* ctrR;             // [per][TI]
+    unsigned* ctrC;             // [per][TJ]
+    unsigned* ctrSweep;         // [1]
+    double* nbpart;             // [per*TI*TJ][2]
+    const int* sigma;           // device copy of the epoch's sweep offsets
+    unsigned* err;              // device status word
+};
+
+struct gmf_model {
+    gmf_config cfg;
+    int device;
+    int p, q, d, K, fr, fc;
+    int64_t n, m;
+    int r, s, nsw, per, swap;
+    int TI, TJ;
+    int y16;
+    // device storage
+    void* Yp;
+    float* Wp;
+    float* L;
+    float* R;
+    float* GbR;
+    float* HbR;
+    float* GbC;
+    float* HbC;
+    int* cntR;
+    int* cntC;
+    float* alpha;
+    int* rperm;
+    int* cperm;
+    void* ystage;               // staging for counts uploaded from the host
+    float* partR;
+    float* partC;
+    unsigned* ctrR;
+    unsigned* ctrC;
+    unsigned* ctrSweep;
+    double* nbpart;
+    int* sigma;
+    unsigned* err;
+    double* devpart;
+    double* devtot;
+    int devparts;
+    // host mirrors
+    int32_t* h_rperm;
+    int32_t* h_cperm;
+    int64_t t;                  // blocks processed so far
+    void* tc;                   // tensor-core path state (gmf_step_tc.cu), or nullptr
+    // kernel timing (gmf_trace)
+    int trace_on;
+    int trace_used;
+    cudaEvent_t* trace_ev;      // GMF_TRACE_POOL pairs
+    double trace_ms;
+    int64_t trace_launches;
+};
+
+#define GMF_TRACE_POOL 512
+
+// gmf_step_simt.cu
+StepArgs gmf_make_args(gmf_model* h);
+cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, long long t0, cudaStream_t st);
+cudaError_t gmf_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st);
+cudaError_t gmf_launch_permute_y(const void* src, void* dst, int y16, int64_t n, int64_t m,
+                                 const int* rperm, const int* cperm, cudaStream_t st);
+cudaError_t gmf_launch_permute_w(const float* src, float* dst, int64_t n, int64_t m,
+                                 const int* rperm, const int* cperm, cudaStream_t st);
