@@ -2,6 +2,7 @@
 // the launch sequence of each entry point. The kernels live in
 // gmf_step_simt.cu (FP32 path), gmf_step_tc.cu (tensor-core path),
 // gmf_orth.cu (Algorithm 2) and gmf_project.cu (per-cell Fisher scoring).
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -100,7 +101,7 @@ static void release(gmf_model* h) {
     if (h->tc) gmf_tc_free(h);
     void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
                     h->rperm, h->cperm, h->ystage, h->partR, h->partC, h->ctrR, h->ctrC, h->ctrSweep,
-                    h->nbpart, h->sigma, h->err, h->devpart, h->devtot};
+                    h->nbpart, h->sigma, h->rhoc, h->rho1, h->err, h->devpart, h->devtot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] h->h_rperm;
@@ -231,13 +232,15 @@ extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, i
     INIT_CUDA(dalloc(&h->alpha, 1));
     INIT_CUDA(dalloc(&h->rperm, (size_t)c.n));
     INIT_CUDA(dalloc(&h->cperm, (size_t)c.m));
-    INIT_CUDA(dalloc(&h->partR, (size_t)h->per * h->TJ * GMF_TILE * 2 * std::max(h->fr, 1)));
-    INIT_CUDA(dalloc(&h->partC, (size_t)h->per * h->TI * GMF_TILE * 2 * std::max(h->fc, 1)));
+    INIT_CUDA(dalloc(&h->partR, (size_t)h->per * h->TI * h->TJ * GMF_TILE * 2 * std::max(h->fr, 1)));
+    INIT_CUDA(dalloc(&h->partC, (size_t)h->per * h->TI * h->TJ * GMF_TILE * 2 * std::max(h->fc, 1)));
     INIT_CUDA(dalloc(&h->ctrR, (size_t)h->per * h->TI));
     INIT_CUDA(dalloc(&h->ctrC, (size_t)h->per * h->TJ));
     INIT_CUDA(dalloc(&h->ctrSweep, 1));
     INIT_CUDA(dalloc(&h->nbpart, (size_t)2 * h->per * h->TI * h->TJ));
     INIT_CUDA(dalloc(&h->sigma, (size_t)h->nsw));
+    INIT_CUDA(dalloc(&h->rhoc, (size_t)h->nsw * h->per));
+    INIT_CUDA(dalloc(&h->rho1, (size_t)h->nsw));
     INIT_CUDA(dalloc(&h->err, 1));
     h->devparts = (int)(((c.n + GMF_TILE - 1) / GMF_TILE) * ((c.m + GMF_TILE - 1) / GMF_TILE));
     INIT_CUDA(dalloc(&h->devpart, (size_t)h->devparts));
@@ -314,6 +317,23 @@ extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begi
         return fail(GMF_ERR_ARG, "gmf_sgd_sweeps: sweep range [%d, %d) outside [0, %d)", w_begin, w_end, h->nsw);
     if (!is_perm(sigma, h->nsw)) return fail(GMF_ERR_ARG, "gmf_sgd_sweeps: sigma is not a permutation of 0..%d", h->nsw - 1);
     cudaStream_t st = (cudaStream_t)stream;
+    // Step factors of every block of the range, in FP64 on the host: block k of
+    // sweep w has t = t_now + (w - w_begin) * per + k + 1.
+    {
+        const gmf_config& c = h->cfg;
+        std::vector<float> rc((size_t)h->nsw * h->per, 0.f), r1((size_t)h->nsw, 0.f);
+        for (int w = w_begin; w < w_end; w++) {
+            for (int k = 0; k < h->per; k++) {
+                const double t = (double)(h->t + (int64_t)(w - w_begin) * h->per + k + 1);
+                const double rho = c.k0 / pow(1.0 + c.k0 * c.k1 * t, c.tau);
+                const double ct = c.bias_corr == 0 ? (1.0 - pow(c.a2, t)) / (1.0 - pow(c.a1, t)) : 1.0;
+                rc[(size_t)w * h->per + k] = (float)(rho * ct);
+                if (k == 0) r1[w] = (float)rho;
+            }
+        }
+        CUDA_TRY(cudaMemcpyAsync(h->rhoc, rc.data(), sizeof(float) * rc.size(), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(h->rho1, r1.data(), sizeof(float) * r1.size(), cudaMemcpyHostToDevice, st));
+    }
     CUDA_TRY(cudaMemcpyAsync(h->sigma, sigma, sizeof(int32_t) * h->nsw, cudaMemcpyHostToDevice, st));
     const StepArgs a = gmf_make_args(h);
     for (int w = w_begin; w < w_end; w++) {
@@ -329,7 +349,7 @@ extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begi
             int rc = gmf_tc_sweep(h, w, t0 - (long long)w * h->per, st);
             if (rc) return rc;
         } else {
-            CUDA_TRY(gmf_launch_sweep_simt(h, a, w, t0 - (long long)w * h->per, st));
+            CUDA_TRY(gmf_launch_sweep_simt(h, a, w, st));
         }
         if (h->trace_on) {
             CUDA_TRY(cudaEventRecord(h->trace_ev[2 * h->trace_used + 1], st));

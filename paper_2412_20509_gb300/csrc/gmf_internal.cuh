@@ -35,7 +35,6 @@ struct StepArgs {
     int family, bias_corr, alpha_mode;
     float lam[4];
     float a1, a2, damping, eps, clamp;
-    double k0, k1, tau;
     const void* Y;              // Yp (permuted)
     int y16;                    // 1 if uint16 counts
     const float* W;             // permuted weights or nullptr
@@ -48,13 +47,15 @@ struct StepArgs {
     int* cntR;
     int* cntC;
     float* alpha;               // device scalar (NB shape)
-    float* partR;               // [per][TJ][TILE][2*fr]
-    float* partC;               // [per][TI][TILE][2*fc]
+    float* partR;               // [per][TI][TJ][TILE][2*fr]: row partials of tile (ti, tj)
+    float* partC;               // [per][TJ][TI][TILE][2*fc]: column partials of tile (ti, tj)
     unsigned* ctrR;             // [per][TI]
     unsigned* ctrC;             // [per][TJ]
     unsigned* ctrSweep;         // [1]
     double* nbpart;             // [per*TI*TJ][2]
     const int* sigma;           // device copy of the epoch's sweep offsets
+    const float* rhoc;          // [nsw][per]: rho_t * c_t per block (rho_t alone when bias_corr = 1)
+    const float* rho1;          // [nsw]: rho at the first block of each sweep (NB shape update)
     unsigned* err;              // device status word
 };
 
@@ -88,6 +89,8 @@ struct gmf_model {
     unsigned* ctrSweep;
     double* nbpart;
     int* sigma;
+    float* rhoc;
+    float* rho1;
     unsigned* err;
     double* devpart;
     double* devtot;
@@ -109,7 +112,7 @@ struct gmf_model {
 
 // gmf_step_simt.cu
 StepArgs gmf_make_args(gmf_model* h);
-cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, long long t0, cudaStream_t st);
+cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaStream_t st);
 cudaError_t gmf_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st);
 cudaError_t gmf_launch_permute_y(const void* src, void* dst, int y16, int64_t n, int64_t m,
                                  const int* rperm, const int* cperm, cudaStream_t st);

@@ -3,20 +3,23 @@
 //
 // One launch per sweep. Grid (TJ, TI, per): CTA (tj, ti, k) owns a 64 x 64
 // tile of block k of the sweep. Per tile:
-//   1. the L and R rows of the tile go to shared memory (transposed);
+//   1. the L and R rows of the tile go to shared memory, transposed for the
+//      eta product and row-major (with squares) for the two contractions;
 //   2. each thread forms a 4 x 4 micro-tile of eta = L R' in FP32, then
 //      mu = exp(eta), Ddot, Dddot (Sec. 3, log link) -> shared memory;
 //   3. row partials sum_j Ddot_ij R_jc, sum_j Dddot_ij R_jc^2 (c row-free) and
-//      column partials sum_i Ddot_ij L_ic, sum_i Dddot_ij L_ic^2 (c column-free)
-//      are written to a workspace, one slot per tile (fixed order, no atomics
-//      on values);
-//   4. an arrival counter per row strip and per column strip elects the last
-//      CTA of the strip, which sums that strip's partials in tile order and
-//      applies the scale factor, penalty, damping, EMA and step to its rows
-//      (columns). Every reader of those parameters in this sweep has arrived,
-//      so the update cannot race with a reader; no CTA waits on another.
-// The NB shape is updated once per sweep by the last CTA of the launch from
-// per-CTA moment sums (FP64) reduced in CTA order.
+//      column partials sum_i Ddot_ij L_ic, sum_i Dddot_ij L_ic^2 (c column-free):
+//      four lanes split the 64-long sum, registers hold the Ddot values, the
+//      factor operands arrive as 128-bit broadcast loads, and the four lane
+//      partials are combined by shuffles in a fixed order;
+//   4. the partials go to a workspace slot per tile (no atomics on values); an
+//      arrival counter per row strip and per column strip elects the last CTA
+//      of the strip, which sums the strip's partials in tile order and applies
+//      scale factor, penalty, damping, EMA and step to its rows (columns).
+//      Every reader of those parameters in this sweep has arrived, so the
+//      update cannot race with a reader, and no CTA waits on another.
+// rho_t * c_t of each block comes precomputed from the host (FP64 there); the
+// device does no FP64 arithmetic except the cross-CTA sums of the NB moments.
 #include <math.h>
 
 #include "gmf_internal.cuh"
@@ -24,9 +27,10 @@
 namespace {
 
 constexpr int T = GMF_TILE;
-constexpr int LD = T + 4;   // leading dimension of the transposed factor tiles
-constexpr int LDD = T + 1;  // leading dimension of the Ddot / Dddot tiles (odd)
+constexpr int LD = T + 4;   // transposed factor tiles: 16-byte aligned rows
+constexpr int LDD = T + 4;  // Ddot / Dddot tiles (row-major)
 constexpr int NW = GMF_THREADS / 32;
+constexpr int CHP = 4;      // 4-column chunks per contraction pass
 
 struct BlockGeo {
     int64_t r0, nI, c0, mJ;
@@ -54,50 +58,133 @@ __device__ __forceinline__ float load_y(const void* Y, int y16, int64_t idx) {
     return y16 ? (float)__ldg((const unsigned short*)Y + idx) : (float)__ldg((const int*)Y + idx);
 }
 
-// L (or R) rows [row0, row0+nr) -> S[c*LD + i], zero-filled to T rows.
-__device__ __forceinline__ void load_factor_tile(float* S, const float* F, int K, int64_t row0, int nr) {
+// Four consecutive counts of one row (vector load when aligned).
+__device__ __forceinline__ void load_y4(const void* Y, int y16, int64_t idx, bool vec, int valid, float y[4]) {
+    if (vec && valid == 4) {
+        if (y16) {
+            const ushort4 v = __ldg((const ushort4*)((const unsigned short*)Y + idx));
+            y[0] = v.x; y[1] = v.y; y[2] = v.z; y[3] = v.w;
+        } else {
+            const int4 v = __ldg((const int4*)((const int*)Y + idx));
+            y[0] = (float)v.x; y[1] = (float)v.y; y[2] = (float)v.z; y[3] = (float)v.w;
+        }
+        return;
+    }
+#pragma unroll
+    for (int b = 0; b < 4; b++) y[b] = b < valid ? load_y(Y, y16, idx + b) : 0.f;
+}
+
+// Rows [row0, row0+nr) of F (K columns) -> St[c*LD + i] (transposed), zero-filled.
+__device__ __forceinline__ void load_factor_T(float* St, const float* F, int K, int64_t row0, int nr) {
     for (int e = threadIdx.x; e < T * K; e += GMF_THREADS) {
         const int i = e / K, c = e - i * K;
-        S[c * LD + i] = i < nr ? F[(row0 + i) * K + c] : 0.f;
+        St[c * LD + i] = i < nr ? __ldg(F + (row0 + i) * K + c) : 0.f;
     }
 }
 
-// 4 x 4 micro-tile of eta: rows ty + 16a, columns tx + 16b.
-__device__ __forceinline__ void eta_microtile(const float* Ls, const float* Rs, int K, int tx, int ty,
-                                              float acc[4][4]) {
-#pragma unroll
-    for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int b = 0; b < 4; b++) acc[a][b] = 0.f;
-    for (int c = 0; c < K; c++) {
-        float lv[4], rv[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            lv[u] = Ls[c * LD + ty + 16 * u];
-            rv[u] = Rs[c * LD + tx + 16 * u];
+// Free-column operands of a contraction: O[i*2P + c] = F[i, col(c)], O[i*2P + P + c] = its square.
+// col(c) = c0 + c for row-free columns; c < p ? 1 + c : 1 + q + c for column-free ones.
+__device__ __forceinline__ void load_operands(float* O, const float* St, int nf, int P, int c_lo, int p, int q,
+                                              bool colfree) {
+    for (int e = threadIdx.x; e < T * P; e += GMF_THREADS) {
+        const int i = e / P, c = e - i * P;
+        float v = 0.f;
+        if (c < nf) {
+            const int col = colfree ? (c < p ? 1 + c : 1 + q + c) : c_lo + c;
+            v = St[col * LD + i];
         }
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int b = 0; b < 4; b++) acc[a][b] = fmaf(lv[a], rv[b], acc[a][b]);
+        O[i * 2 * P + c] = v;
+        O[i * 2 * P + P + c] = v * v;
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
+__device__ __forceinline__ float block_sum_f(float v, float* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) red[wid] = v;
     __syncthreads();
-    double s = 0.0;
-    for (int u = 0; u < NW; u++) s += red[u];  // fixed order, every thread the same value
+    float s = 0.f;
+#pragma unroll
+    for (int u = 0; u < NW; u++) s += red[u];  // fixed order: every thread the same value
     return s;
 }
 
-__device__ __forceinline__ double bias_factor(int mode, double a1, double a2, long long t, int visits) {
-    if (mode == 0) return (1.0 - pow(a2, (double)t)) / (1.0 - pow(a1, (double)t));
-    return (1.0 - pow(1.0 - a2, (double)visits)) / (1.0 - pow(1.0 - a1, (double)visits));
+// Contraction of one tile side. Thread (o = tid >> 2, q4 = tid & 3) owns output
+// row o (a tile row for the row side, a tile column for the column side) and
+// the summation indices kk = 4*s + q4, s < 16. D(o, kk) is read through
+// dstride_o / dstride_k. Operands O[kk][2P] (values then squares).
+// Writes sums for c < nf to dst[o*2*nf + c] (G) and dst[o*2*nf + nf + c] (H).
+__device__ __forceinline__ void contract_side(const float* __restrict__ Ds, const float* __restrict__ DDs,
+                                              int dstride_o, int dstride_k, const float* __restrict__ O, int P,
+                                              int nf, int nvalid_k, int nvalid_o, float* __restrict__ dst) {
+    const int o = threadIdx.x >> 2, q4 = threadIdx.x & 3;
+    float dv[16], ddv[16];
+#pragma unroll
+    for (int s = 0; s < 16; s++) {
+        const int kk = 4 * s + q4;
+        dv[s] = Ds[o * dstride_o + kk * dstride_k];
+        ddv[s] = DDs[o * dstride_o + kk * dstride_k];
+    }
+    const int nch = P >> 2;
+    const int kmax = (nvalid_k + 3) >> 2;  // s beyond this only sees zeros
+    for (int ch0 = 0; ch0 < nch; ch0 += CHP) {
+        float g[CHP][4], h[CHP][4];
+#pragma unroll
+        for (int u = 0; u < CHP; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) g[u][v] = h[u][v] = 0.f;
+#pragma unroll
+        for (int s = 0; s < 16; s++) {
+            if (s >= kmax) break;
+            const int kk = 4 * s + q4;
+            const float4* row = (const float4*)(O + kk * 2 * P);
+#pragma unroll
+            for (int u = 0; u < CHP; u++) {
+                if (ch0 + u < nch) {
+                    const float4 r = row[ch0 + u];
+                    const float4 r2 = row[(P >> 2) + ch0 + u];
+                    g[u][0] = fmaf(dv[s], r.x, g[u][0]);
+                    g[u][1] = fmaf(dv[s], r.y, g[u][1]);
+                    g[u][2] = fmaf(dv[s], r.z, g[u][2]);
+                    g[u][3] = fmaf(dv[s], r.w, g[u][3]);
+                    h[u][0] = fmaf(ddv[s], r2.x, h[u][0]);
+                    h[u][1] = fmaf(ddv[s], r2.y, h[u][1]);
+                    h[u][2] = fmaf(ddv[s], r2.z, h[u][2]);
+                    h[u][3] = fmaf(ddv[s], r2.w, h[u][3]);
+                }
+            }
+        }
+        // combine the four lanes of this output row: ((q0 + q1) + (q2 + q3)), identical on all four
+#pragma unroll
+        for (int u = 0; u < CHP; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                g[u][v] += __shfl_xor_sync(0xffffffffu, g[u][v], 1);
+                g[u][v] += __shfl_xor_sync(0xffffffffu, g[u][v], 2);
+                h[u][v] += __shfl_xor_sync(0xffffffffu, h[u][v], 1);
+                h[u][v] += __shfl_xor_sync(0xffffffffu, h[u][v], 2);
+            }
+        if (o < nvalid_o) {
+#pragma unroll
+            for (int u = 0; u < CHP; u++)
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    const int c = 4 * (ch0 + u) + v;
+                    if (v == q4 && c < nf) {
+                        dst[o * 2 * nf + c] = g[u][v];
+                        dst[o * 2 * nf + nf + c] = h[u][v];
+                    }
+                }
+        }
+    }
+}
+
+__device__ __forceinline__ float bias_visit(float a1, float a2, int visits) {
+    // (1 - (1-a2)^k) / (1 - (1-a1)^k), k >= 1
+    const float k = (float)visits;
+    return (1.f - expf(k * log1pf(-a2))) / (1.f - expf(k * log1pf(-a1)));
 }
 
 // Smoothed local step of eq. 12 / eq. 14 for one free parameter.
@@ -116,13 +203,26 @@ __device__ __forceinline__ void smoothed_step(float* theta, float* gbar, float* 
     if (!isfinite(nt)) atomicOr(err, GMF_DEVERR_NONFINITE);
 }
 
-__global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w, long long t0) {
-    extern __shared__ float smem[];
-    float* Ls = smem;
-    float* Rs = Ls + a.K * LD;
-    float* Ds = Rs + a.K * LD;
-    float* DDs = Ds + T * LDD;
-    __shared__ double red[NW];
+struct Smem {
+    float *Ls, *Rs, *RF, *LF, *Ds, *DDs;
+};
+
+__device__ __forceinline__ Smem carve(float* base, int K, int FRP, int FCP) {
+    Smem s;
+    s.Ls = base;
+    s.Rs = s.Ls + K * LD;
+    s.RF = s.Rs + K * LD;
+    s.LF = s.RF + T * 2 * FRP;
+    s.Ds = s.LF + T * 2 * FCP;
+    s.DDs = s.Ds + T * LDD;
+    return s;
+}
+
+__global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w) {
+    extern __shared__ __align__(16) float smem[];
+    const int FRP = (a.fr + 3) & ~3, FCP = (a.fc + 3) & ~3;
+    const Smem S = carve(smem, a.K, FRP, FCP);
+    __shared__ float red[NW];
     __shared__ int s_flag[3];
     __shared__ int s_visits[T];
     __shared__ float s_rc[T];
@@ -135,112 +235,75 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w, l
     const bool nb = a.family == GMF_NEGBIN;
     const bool moments = nb && a.alpha_mode == 1;
     const float alpha = *a.alpha;
-    const long long t = t0 + (long long)w * a.per + k + 1;
-    double s1 = 0.0, s2 = 0.0;
+    const float rhoc_blk = a.rhoc[w * a.per + k];   // rho_t * c_t (bias_corr 0) or rho_t (bias_corr 1)
+    float s1 = 0.f, s2 = 0.f;
 
     const int64_t row0 = g.r0 + (int64_t)ti * T, col0 = g.c0 + (int64_t)tj * T;
     const int nr = active ? (int)min((int64_t)T, g.nI - (int64_t)ti * T) : 0;
     const int nc = active ? (int)min((int64_t)T, g.mJ - (int64_t)tj * T) : 0;
 
     if (active) {
-        load_factor_tile(Ls, a.L, a.K, row0, nr);
-        load_factor_tile(Rs, a.R, a.K, col0, nc);
+        load_factor_T(S.Ls, a.L, a.K, row0, nr);
+        load_factor_T(S.Rs, a.R, a.K, col0, nc);
         __syncthreads();
+        load_operands(S.RF, S.Rs, a.fr, FRP, 1 + a.p, a.p, a.q, false);
+        load_operands(S.LF, S.Ls, a.fc, FCP, 0, a.p, a.q, true);
+        // eta micro-tile: rows 4ty..4ty+3, columns 4tx..4tx+3
         const int tx = tid & 15, ty = tid >> 4;
         float acc[4][4];
-        eta_microtile(Ls, Rs, a.K, tx, ty, acc);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) acc[u][v] = 0.f;
+        for (int c = 0; c < a.K; c++) {
+            const float4 lv = *(const float4*)(S.Ls + c * LD + 4 * ty);
+            const float4 rv = *(const float4*)(S.Rs + c * LD + 4 * tx);
+            const float l4[4] = {lv.x, lv.y, lv.z, lv.w}, r4[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int v = 0; v < 4; v++) acc[u][v] = fmaf(l4[u], r4[v], acc[u][v]);
+        }
+        const bool vec = ((a.m & 3) == 0) && ((col0 & 3) == 0);
 #pragma unroll
         for (int u = 0; u < 4; u++) {
+            const int il = 4 * ty + u;
+            const int jl0 = 4 * tx;
+            float y[4], wv[4] = {1.f, 1.f, 1.f, 1.f};
+            const int valid = il < nr ? max(0, min(4, nc - jl0)) : 0;
+            const int64_t idx = (row0 + il) * a.m + col0 + jl0;
+            if (valid > 0) {
+                load_y4(a.Y, a.y16, idx, vec, valid, y);
+                if (a.W)
+#pragma unroll
+                    for (int v = 0; v < 4; v++) wv[v] = v < valid ? __ldg(a.W + idx + v) : 0.f;
+            }
+            float dd[4], ddd[4];
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                const int il = ty + 16 * u, jl = tx + 16 * v;
-                float dd = 0.f, ddd = 0.f;
-                if (il < nr && jl < nc) {
-                    const int64_t idx = (row0 + il) * a.m + col0 + jl;
-                    const float y = load_y(a.Y, a.y16, idx);
-                    const float wv = a.W ? __ldg(a.W + idx) : 1.f;
+                dd[v] = ddd[v] = 0.f;
+                if (v < valid) {
                     const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
                     const float mu = expf(e);
-                    if (nb) {
-                        const float f = alpha / (alpha + mu);
-                        dd = wv * (y - mu) * f;
-                        ddd = wv * mu * f;
-                    } else {
-                        dd = wv * (y - mu);
-                        ddd = wv * mu;
-                    }
+                    const float f = nb ? alpha / (alpha + mu) : 1.f;
+                    dd[v] = wv[v] * (y[v] - mu) * f;
+                    ddd[v] = wv[v] * mu * f;
                     if (moments) {
-                        s1 += (double)(wv * mu * mu);
-                        s2 += (double)(wv * ((y - mu) * (y - mu) - mu));
+                        s1 = fmaf(wv[v] * mu, mu, s1);
+                        s2 += wv[v] * ((y[v] - mu) * (y[v] - mu) - mu);
                     }
                 }
-                Ds[il * LDD + jl] = dd;
-                DDs[il * LDD + jl] = ddd;
             }
+            *(float4*)(S.Ds + il * LDD + jl0) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+            *(float4*)(S.DDs + il * LDD + jl0) = make_float4(ddd[0], ddd[1], ddd[2], ddd[3]);
         }
         __syncthreads();
-        // Row partials: thread (il, cg) handles row-free columns c = cg, cg+4, ...
-        {
-            const int il = tid & (T - 1), cg = tid >> 6;
-            const int cR = 1 + a.p;
-            float gacc[GMF_FREE_MAX / 4], hacc[GMF_FREE_MAX / 4];
-#pragma unroll
-            for (int u = 0; u < GMF_FREE_MAX / 4; u++) gacc[u] = hacc[u] = 0.f;
-            for (int j = 0; j < nc; j++) {
-                const float dv = Ds[il * LDD + j], ddv = DDs[il * LDD + j];
-#pragma unroll
-                for (int u = 0; u < GMF_FREE_MAX / 4; u++) {
-                    const int c = cg + 4 * u;
-                    if (c < a.fr) {
-                        const float rv = Rs[(cR + c) * LD + j];
-                        gacc[u] = fmaf(dv, rv, gacc[u]);
-                        hacc[u] = fmaf(ddv, rv * rv, hacc[u]);
-                    }
-                }
-            }
-            if (il < nr) {
-                float* dst = a.partR + ((size_t)(k * a.TJ + tj) * T + il) * 2 * a.fr;
-#pragma unroll
-                for (int u = 0; u < GMF_FREE_MAX / 4; u++) {
-                    const int c = cg + 4 * u;
-                    if (c < a.fr) {
-                        dst[c] = gacc[u];
-                        dst[a.fr + c] = hacc[u];
-                    }
-                }
-            }
-        }
-        // Column partials: thread (jl, cg) handles column-free columns c = cg, cg+4, ...
-        {
-            const int jl = tid & (T - 1), cg = tid >> 6;
-            float gacc[GMF_FREE_MAX / 4], hacc[GMF_FREE_MAX / 4];
-#pragma unroll
-            for (int u = 0; u < GMF_FREE_MAX / 4; u++) gacc[u] = hacc[u] = 0.f;
-            for (int i = 0; i < nr; i++) {
-                const float dv = Ds[i * LDD + jl], ddv = DDs[i * LDD + jl];
-#pragma unroll
-                for (int u = 0; u < GMF_FREE_MAX / 4; u++) {
-                    const int c = cg + 4 * u;
-                    if (c < a.fc) {
-                        const int lc = c < a.p ? 1 + c : 1 + a.q + c;
-                        const float lv = Ls[lc * LD + i];
-                        gacc[u] = fmaf(dv, lv, gacc[u]);
-                        hacc[u] = fmaf(ddv, lv * lv, hacc[u]);
-                    }
-                }
-            }
-            if (jl < nc) {
-                float* dst = a.partC + ((size_t)(k * a.TI + ti) * T + jl) * 2 * a.fc;
-#pragma unroll
-                for (int u = 0; u < GMF_FREE_MAX / 4; u++) {
-                    const int c = cg + 4 * u;
-                    if (c < a.fc) {
-                        dst[c] = gacc[u];
-                        dst[a.fc + c] = hacc[u];
-                    }
-                }
-            }
-        }
+        float* prow = a.partR + ((size_t)((k * a.TI + ti) * a.TJ + tj) * T) * 2 * a.fr;
+        float* pcol = a.partC + ((size_t)((k * a.TJ + tj) * a.TI + ti) * T) * 2 * a.fc;
+        // row side: output row o = tile row, summation over tile columns
+        contract_side(S.Ds, S.DDs, LDD, 1, S.RF, FRP, a.fr, nc, nr, prow);
+        // column side: output o = tile column, summation over tile rows
+        contract_side(S.Ds, S.DDs, 1, LDD, S.LF, FCP, a.fc, nr, nc, pcol);
     }
 
     // ---- arrivals: elect the last CTA of each row strip and column strip
@@ -256,22 +319,21 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w, l
         }
     }
     __syncthreads();
-    const double rho = a.k0 / pow(1.0 + a.k0 * a.k1 * (double)t, a.tau);
 
     if (s_flag[0]) {  // this CTA updates rows [row0, row0 + nr) of block k
         __threadfence();
         if (tid < nr) {
             const int v = a.cntR[row0 + tid] + 1;
             s_visits[tid] = v;
-            s_rc[tid] = (float)(rho * bias_factor(a.bias_corr, a.a1, a.a2, t, v));
+            s_rc[tid] = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, v) : rhoc_blk;
         }
         __syncthreads();
-        const float scale = (float)((double)a.m / (double)g.mJ);
+        const float scale = (float)a.m / (float)g.mJ;
         for (int e = tid; e < nr * a.fr; e += GMF_THREADS) {
             const int il = e / a.fr, c = e - il * a.fr;
             float sg = 0.f, sh = 0.f;
             for (int u = 0; u < nTJ; u++) {
-                const float* src = a.partR + ((size_t)(k * a.TJ + u) * T + il) * 2 * a.fr;
+                const float* src = a.partR + ((size_t)((k * a.TI + ti) * a.TJ + u) * T + il) * 2 * a.fr;
                 sg += __ldcg(src + c);
                 sh += __ldcg(src + a.fr + c);
             }
@@ -290,15 +352,15 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w, l
         if (tid < nc) {
             const int v = a.cntC[col0 + tid] + 1;
             s_visits[tid] = v;
-            s_rc[tid] = (float)(rho * bias_factor(a.bias_corr, a.a1, a.a2, t, v));
+            s_rc[tid] = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, v) : rhoc_blk;
         }
         __syncthreads();
-        const float scale = (float)((double)a.n / (double)g.nI);
+        const float scale = (float)a.n / (float)g.nI;
         for (int e = tid; e < nc * a.fc; e += GMF_THREADS) {
             const int jl = e / a.fc, c = e - jl * a.fc;
             float sg = 0.f, sh = 0.f;
             for (int u = 0; u < nTI; u++) {
-                const float* src = a.partC + ((size_t)(k * a.TI + u) * T + jl) * 2 * a.fc;
+                const float* src = a.partC + ((size_t)((k * a.TJ + tj) * a.TI + u) * T + jl) * 2 * a.fc;
                 sg += __ldcg(src + c);
                 sh += __ldcg(src + a.fc + c);
             }
@@ -315,12 +377,12 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w, l
 
     // ---- NB shape: moment sums pooled over the sweep, one update per sweep (App. B)
     if (moments) {
-        const double S1 = block_sum(s1, red);
-        const double S2 = block_sum(s2, red);
+        const float S1 = block_sum_f(s1, red);
+        const float S2 = block_sum_f(s2, red);
         const int cta = (k * a.TI + ti) * a.TJ + tj;
         if (tid == 0) {
-            a.nbpart[2 * cta] = S1;
-            a.nbpart[2 * cta + 1] = S2;
+            a.nbpart[2 * cta] = (double)S1;
+            a.nbpart[2 * cta + 1] = (double)S2;
         }
         __threadfence();
         __syncthreads();
@@ -338,56 +400,76 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w, l
                 T2 += __ldcg(a.nbpart + 2 * c + 1);
             }
             if (T2 > 0.0) {
-                double ahat = T1 / T2;
-                if (ahat < (double)a.eps) ahat = (double)a.eps;
-                const long long tf = t0 + (long long)w * a.per + 1;
-                const double rf = a.k0 / pow(1.0 + a.k0 * a.k1 * (double)tf, a.tau);
-                *a.alpha = (float)((1.0 - rf) * (double)alpha + rf * ahat);
+                float ahat = (float)(T1 / T2);
+                if (ahat < a.eps) ahat = a.eps;
+                const float rf = a.rho1[w];
+                *a.alpha = (1.f - rf) * alpha + rf * ahat;
             }
             *a.ctrSweep = 0u;
         }
     }
 }
 
+// Unit deviance 2w[...] of Table S1 / App. B in FP32, written so that no
+// difference of two large logarithms appears when mu >> y or mu << y.
+__device__ __forceinline__ float unit_deviance(bool nb, float y, float e, float mu, float alpha) {
+    if (y > 0.f) {
+        const float r1 = (y - mu) / mu;
+        const float l1 = fabsf(r1) < 0.5f ? log1pf(r1) : logf(y) - e;  // log(y / mu)
+        if (!nb) return y * l1 - (y - mu);
+        const float r2 = (y - mu) / (mu + alpha);
+        const float lma = mu > alpha ? e + log1pf(alpha / mu) : logf(alpha) + log1pf(mu / alpha);
+        const float l2 = fabsf(r2) < 0.5f ? log1pf(r2) : logf(y + alpha) - lma;  // log((y+a)/(mu+a))
+        return y * l1 - (y + alpha) * l2;
+    }
+    return nb ? alpha * log1pf(mu / alpha) : mu;
+}
+
 // Deviance of one 64 x 64 tile of the whole (permuted) matrix.
 __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, double* part) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     float* Ls = smem;
     float* Rs = Ls + a.K * LD;
-    __shared__ double red[NW];
+    __shared__ float red[NW];
     const int tid = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.y * T, col0 = (int64_t)blockIdx.x * T;
     const int nr = (int)min((int64_t)T, a.n - row0), nc = (int)min((int64_t)T, a.m - col0);
-    load_factor_tile(Ls, a.L, a.K, row0, nr);
-    load_factor_tile(Rs, a.R, a.K, col0, nc);
+    load_factor_T(Ls, a.L, a.K, row0, nr);
+    load_factor_T(Rs, a.R, a.K, col0, nc);
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;
     float acc[4][4];
-    eta_microtile(Ls, Rs, a.K, tx, ty, acc);
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[u][v] = 0.f;
+    for (int c = 0; c < a.K; c++) {
+        const float4 lv = *(const float4*)(Ls + c * LD + 4 * ty);
+        const float4 rv = *(const float4*)(Rs + c * LD + 4 * tx);
+        const float l4[4] = {lv.x, lv.y, lv.z, lv.w}, r4[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) acc[u][v] = fmaf(l4[u], r4[v], acc[u][v]);
+    }
     const float alpha = *a.alpha;
     const bool nb = a.family == GMF_NEGBIN;
+    const bool vec = ((a.m & 3) == 0) && ((col0 & 3) == 0);
     float sum = 0.f, comp = 0.f;  // compensated (Kahan) per-thread sum
 #pragma unroll
     for (int u = 0; u < 4; u++) {
+        const int il = 4 * ty + u, jl0 = 4 * tx;
+        const int valid = il < nr ? max(0, min(4, nc - jl0)) : 0;
+        if (valid == 0) continue;
+        const int64_t idx = (row0 + il) * a.m + col0 + jl0;
+        float y[4];
+        load_y4(a.Y, a.y16, idx, vec, valid, y);
 #pragma unroll
         for (int v = 0; v < 4; v++) {
-            const int il = ty + 16 * u, jl = tx + 16 * v;
-            if (il < nr && jl < nc) {
-                const int64_t idx = (row0 + il) * a.m + col0 + jl;
-                const float y = load_y(a.Y, a.y16, idx);
-                const float wv = a.W ? __ldg(a.W + idx) : 1.f;
+            if (v < valid) {
+                const float wv = a.W ? __ldg(a.W + idx + v) : 1.f;
                 const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
-                const float mu = expf(e);
-                float dv;
-                if (nb) {
-                    if (y > 0.f)
-                        dv = y * log1pf((y - mu) / mu) - (y + alpha) * log1pf((y - mu) / (mu + alpha));
-                    else
-                        dv = alpha * log1pf(mu / alpha);
-                } else {
-                    dv = (y > 0.f ? y * log1pf((y - mu) / mu) : 0.f) - (y - mu);
-                }
-                dv *= 2.f * wv;
+                const float dv = 2.f * wv * unit_deviance(nb, y[v], e, expf(e), alpha);
                 const float yk = dv - comp;
                 const float tk = sum + yk;
                 comp = (tk - sum) - yk;
@@ -395,16 +477,23 @@ __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, doubl
             }
         }
     }
-    const double s = block_sum((double)sum, red);
-    if (tid == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    const float s = block_sum_f(sum, red);
+    if (tid == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = (double)s;
 }
 
 __global__ void sum_parts_kernel(const double* part, int count, double* out) {
     __shared__ double red[NW];
     double s = 0.0;
     for (int c = threadIdx.x; c < count; c += GMF_THREADS) s += part[c];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) *out = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int u = 0; u < NW; u++) t += red[u];
+        *out = t;
+    }
 }
 
 template <typename Ty>
@@ -415,6 +504,11 @@ __global__ void permute_kernel(const Ty* __restrict__ src, Ty* __restrict__ dst,
         Ty* d = dst + i * m;
         for (int64_t j = threadIdx.x; j < m; j += blockDim.x) d[j] = s[cperm[j]];
     }
+}
+
+size_t sweep_smem(int K, int fr, int fc) {
+    const int FRP = (fr + 3) & ~3, FCP = (fc + 3) & ~3;
+    return sizeof(float) * (2 * (size_t)K * LD + (size_t)T * 2 * FRP + (size_t)T * 2 * FCP + 2 * (size_t)T * LDD);
 }
 
 }  // namespace
@@ -447,9 +541,6 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.damping = (float)c.damping;
     a.eps = (float)c.eps;
     a.clamp = (float)c.eta_clamp;
-    a.k0 = c.k0;
-    a.k1 = c.k1;
-    a.tau = c.tau;
     a.Y = h->Yp;
     a.y16 = h->y16;
     a.W = h->Wp;
@@ -469,23 +560,20 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.ctrSweep = h->ctrSweep;
     a.nbpart = h->nbpart;
     a.sigma = h->sigma;
+    a.rhoc = h->rhoc;
+    a.rho1 = h->rho1;
     a.err = h->err;
     return a;
 }
 
-static size_t sweep_smem(int K) { return sizeof(float) * (2 * (size_t)K * LD + 2 * (size_t)T * LDD); }
-
-cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, long long t0, cudaStream_t st) {
-    const size_t smem = sweep_smem(h->K);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sweep_smem(GMF_KMAX));
+cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaStream_t st) {
+    const size_t smem = sweep_smem(h->K, h->fr, h->fc);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     dim3 grid(h->TJ, h->TI, h->per);
-    sweep_kernel<<<grid, GMF_THREADS, smem, st>>>(a, w, t0);
+    sweep_kernel<<<grid, GMF_THREADS, smem, st>>>(a, w);
     return cudaGetLastError();
 }
 
