@@ -36,9 +36,15 @@ extern "C" const char* gmf_last_error(void) { return g_err.c_str(); }
 extern "C" const char* gmf_version(void) { return "gmf-gb300 0.1 (sm_103a)"; }
 
 // tensor-core path hooks (gmf_step_tc.cu)
-int gmf_tc_prepare(gmf_model* h, cudaStream_t st);
-int gmf_tc_sweep(gmf_model* h, int w, long long t0, cudaStream_t st);
+int gmf_tc_prepare_checked(gmf_model* h, std::string* err);
+cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st);
 void gmf_tc_free(gmf_model* h);
+
+// One sweep launch of the configured path.
+static cudaError_t launch_sweep(gmf_model* h, const StepArgs& a, int w, cudaStream_t st) {
+    if (h->cfg.precision == GMF_PREC_MIXED) return gmf_tc_launch(h, w, st);
+    return gmf_launch_sweep_simt(h, a, w, st);
+}
 // Algorithm 2 (gmf_orth.cu), per-cell projection (gmf_project.cu)
 int gmf_orth_run(gmf_model* h, int mode, cudaStream_t st, std::string* err);
 int gmf_project_run(gmf_model* h, const void* Ynew, int y16, int64_t n_new, const float* Xnew,
@@ -98,6 +104,8 @@ static void trace_destroy(gmf_model* h) {
 static void release(gmf_model* h) {
     if (!h) return;
     trace_destroy(h);
+    if (h->epoch_graph) cudaGraphExecDestroy(h->epoch_graph);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->tc) gmf_tc_free(h);
     void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
                     h->rperm, h->cperm, h->ystage, h->partR, h->partC, h->ctrR, h->ctrC, h->ctrSweep,
@@ -115,7 +123,7 @@ extern "C" void gmf_free(gmf_model* h) { release(h); }
 static void build_factors(const gmf_model* h, const double* X, const double* Z, const double* off,
                           const double* B, const double* G, const double* U, const double* V,
                           std::vector<float>& L, std::vector<float>& R) {
-    const int K = h->K, p = h->p, q = h->q, d = h->d;
+    const int K = h->KP, p = h->p, q = h->q, d = h->d;
     L.assign((size_t)h->n * K, 0.f);
     R.assign((size_t)h->m * K, 0.f);
     for (int64_t ip = 0; ip < h->n; ip++) {
@@ -190,6 +198,7 @@ extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, i
     h->q = c.q;
     h->d = c.d;
     h->K = K;
+    h->KP = (K + 3) & ~3;
     h->fr = c.q + c.d;
     h->fc = c.p + c.d;
     h->r = (int)((c.n + c.nb_row - 1) / c.nb_row);
@@ -221,8 +230,8 @@ extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, i
     const size_t nm = (size_t)c.n * c.m;
     INIT_CUDA(cudaMalloc(&h->Yp, nm * (h->y16 ? 2 : 4)));
     if (W) INIT_CUDA(dalloc(&h->Wp, nm));
-    INIT_CUDA(dalloc(&h->L, (size_t)c.n * K));
-    INIT_CUDA(dalloc(&h->R, (size_t)c.m * K));
+    INIT_CUDA(dalloc(&h->L, (size_t)c.n * h->KP));
+    INIT_CUDA(dalloc(&h->R, (size_t)c.m * h->KP));
     INIT_CUDA(dalloc(&h->GbR, (size_t)c.n * h->fr));
     INIT_CUDA(dalloc(&h->HbR, (size_t)c.n * h->fr));
     INIT_CUDA(dalloc(&h->GbC, (size_t)c.m * h->fc));
@@ -280,7 +289,15 @@ extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, i
         INIT_CUDA(cudaStreamSynchronize(st));
         if (wtmp) cudaFree(wtmp);
     }
-    if (c.precision == GMF_PREC_MIXED) INIT_TRY(gmf_tc_prepare(h, st));
+    INIT_CUDA(gmf_sweep_simt_attr(h));
+    if (c.precision == GMF_PREC_MIXED) {
+        std::string err;
+        const int rc = gmf_tc_prepare_checked(h, &err);
+        if (rc != GMF_OK) {
+            release(h);
+            return fail(rc, "gmf_init: %s", err.c_str());
+        }
+    }
     INIT_CUDA(cudaStreamSynchronize(st));
     *out = h;
     return GMF_OK;
@@ -336,8 +353,34 @@ extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begi
     }
     CUDA_TRY(cudaMemcpyAsync(h->sigma, sigma, sizeof(int32_t) * h->nsw, cudaMemcpyHostToDevice, st));
     const StepArgs a = gmf_make_args(h);
+    // A whole epoch replays one captured graph of its sweep launches (the
+    // launches read sigma and the step factors from the buffers filled above).
+    if (!h->trace_on && w_begin == 0 && w_end == h->nsw) {
+        if (!h->epoch_graph) {
+            if (!h->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+            for (int w = 0; w < h->nsw; w++) {
+                cudaError_t e = launch_sweep(h, a, w, h->capture_stream);
+                if (e != cudaSuccess) {
+                    cudaStreamEndCapture(h->capture_stream, &g);
+                    if (g) cudaGraphDestroy(g);
+                    return fail(GMF_ERR_CUDA, "sweep launch during capture: %s", cudaGetErrorString(e));
+                }
+            }
+            CUDA_TRY(cudaStreamEndCapture(h->capture_stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&h->epoch_graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                h->epoch_graph = nullptr;
+                return fail(GMF_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            }
+        }
+        CUDA_TRY(cudaGraphLaunch(h->epoch_graph, st));
+        h->t += (int64_t)h->nsw * h->per;
+        return GMF_OK;
+    }
     for (int w = w_begin; w < w_end; w++) {
-        const long long t0 = (long long)h->t;
         if (h->trace_on) {
             if (h->trace_used == GMF_TRACE_POOL) {
                 int rc = trace_collect(h, st);
@@ -345,12 +388,7 @@ extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begi
             }
             CUDA_TRY(cudaEventRecord(h->trace_ev[2 * h->trace_used], st));
         }
-        if (h->cfg.precision == GMF_PREC_MIXED) {
-            int rc = gmf_tc_sweep(h, w, t0 - (long long)w * h->per, st);
-            if (rc) return rc;
-        } else {
-            CUDA_TRY(gmf_launch_sweep_simt(h, a, w, st));
-        }
+        CUDA_TRY(launch_sweep(h, a, w, st));
         if (h->trace_on) {
             CUDA_TRY(cudaEventRecord(h->trace_ev[2 * h->trace_used + 1], st));
             h->trace_used++;
@@ -414,7 +452,7 @@ extern "C" int gmf_get_params(gmf_model* h, double* B, double* G, double* U, dou
                               void* stream) {
     if (!h) return fail(GMF_ERR_ARG, "gmf_get_params: NULL handle");
     cudaStream_t st = (cudaStream_t)stream;
-    const int K = h->K, p = h->p, q = h->q, d = h->d;
+    const int K = h->KP, p = h->p, q = h->q, d = h->d;
     std::vector<float> L((size_t)h->n * K), R((size_t)h->m * K);
     float a = 0.f;
     CUDA_TRY(cudaMemcpyAsync(L.data(), h->L, sizeof(float) * L.size(), cudaMemcpyDeviceToHost, st));
@@ -445,7 +483,7 @@ extern "C" int gmf_set_params(gmf_model* h, const double* B, const double* G, co
                               const double* alpha, void* stream) {
     if (!h) return fail(GMF_ERR_ARG, "gmf_set_params: NULL handle");
     cudaStream_t st = (cudaStream_t)stream;
-    const int K = h->K, p = h->p, q = h->q, d = h->d;
+    const int K = h->KP, p = h->p, q = h->q, d = h->d;
     std::vector<float> L((size_t)h->n * K), R((size_t)h->m * K);
     CUDA_TRY(cudaMemcpyAsync(L.data(), h->L, sizeof(float) * L.size(), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(R.data(), h->R, sizeof(float) * R.size(), cudaMemcpyDeviceToHost, st));

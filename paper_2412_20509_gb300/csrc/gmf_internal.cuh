@@ -4,8 +4,9 @@
 //   Yp  n x m counts, rows and columns permuted by the fixed partitions, so
 //       block (I_a, J_b) is the contiguous sub-matrix rows [a*nb_row, ...),
 //       columns [b*nb_col, ...).
-//   L   n x K   augmented row factors  [o | X | Gamma | U]   (K = 1+p+q+d)
-//   R   m x K   augmented column factors [1 | B | Z | V], so eta = L R'.
+//   L   n x KP  augmented row factors  [o | X | Gamma | U]   (K = 1+p+q+d, KP = K
+//               rounded up to a multiple of 4, the padding columns zero)
+//   R   m x KP  augmented column factors [1 | B | Z | V], so eta = L R'.
 //       Row-free columns (Gamma, U) of L and their multipliers (Z, V) in R
 //       share the indices [1+p, K); column-free columns (B, V) of R and their
 //       multipliers (X, U) in L share {1..p} u [1+p+q, K).
@@ -30,6 +31,7 @@
 struct StepArgs {
     int64_t n, m;
     int p, q, d, K, fr, fc;
+    int KP;                     // row stride of L and R (K rounded up to a multiple of 4)
     int nb_row, nb_col, r, s, per, swap;
     int TI, TJ;                 // tiles per block along rows / columns (largest block)
     int family, bias_corr, alpha_mode;
@@ -63,6 +65,7 @@ struct gmf_model {
     gmf_config cfg;
     int device;
     int p, q, d, K, fr, fc;
+    int KP;                     // row stride of L and R: 16-byte aligned rows
     int64_t n, m;
     int r, s, nsw, per, swap;
     int TI, TJ;
@@ -106,6 +109,9 @@ struct gmf_model {
     cudaEvent_t* trace_ev;      // GMF_TRACE_POOL pairs
     double trace_ms;
     int64_t trace_launches;
+    // CUDA graph of one full epoch of FP32 sweeps (captured on first use)
+    cudaGraphExec_t epoch_graph;
+    cudaStream_t capture_stream;
 };
 
 #define GMF_TRACE_POOL 512
@@ -113,6 +119,7 @@ struct gmf_model {
 // gmf_step_simt.cu
 StepArgs gmf_make_args(gmf_model* h);
 cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaStream_t st);
+cudaError_t gmf_sweep_simt_attr(gmf_model* h);
 cudaError_t gmf_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st);
 cudaError_t gmf_launch_permute_y(const void* src, void* dst, int y16, int64_t n, int64_t m,
                                  const int* rperm, const int* cperm, cudaStream_t st);

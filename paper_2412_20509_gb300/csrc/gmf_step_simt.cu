@@ -23,36 +23,17 @@
 #include <math.h>
 
 #include "gmf_internal.cuh"
+#include "gmf_update.cuh"
 
 namespace {
+
+using namespace gmfdev;
 
 constexpr int T = GMF_TILE;
 constexpr int LD = T + 4;   // transposed factor tiles: 16-byte aligned rows
 constexpr int LDD = T + 4;  // Ddot / Dddot tiles (row-major)
 constexpr int NW = GMF_THREADS / 32;
-constexpr int CHP = 4;      // 4-column chunks per contraction pass
-
-struct BlockGeo {
-    int64_t r0, nI, c0, mJ;
-};
-
-__device__ __forceinline__ BlockGeo block_geo(const StepArgs& a, int w, int k) {
-    const int sg = a.sigma[w];
-    int rc, cc;
-    if (!a.swap) {
-        rc = (sg + k) % a.r;
-        cc = k;
-    } else {
-        rc = k;
-        cc = (sg + k) % a.s;
-    }
-    BlockGeo g;
-    g.r0 = (int64_t)rc * a.nb_row;
-    g.nI = min((int64_t)a.nb_row, a.n - g.r0);
-    g.c0 = (int64_t)cc * a.nb_col;
-    g.mJ = min((int64_t)a.nb_col, a.m - g.c0);
-    return g;
-}
+constexpr int CHP = 2;      // 4-column chunks per contraction pass
 
 __device__ __forceinline__ float load_y(const void* Y, int y16, int64_t idx) {
     return y16 ? (float)__ldg((const unsigned short*)Y + idx) : (float)__ldg((const int*)Y + idx);
@@ -74,11 +55,30 @@ __device__ __forceinline__ void load_y4(const void* Y, int y16, int64_t idx, boo
     for (int b = 0; b < 4; b++) y[b] = b < valid ? load_y(Y, y16, idx + b) : 0.f;
 }
 
-// Rows [row0, row0+nr) of F (K columns) -> St[c*LD + i] (transposed), zero-filled.
-__device__ __forceinline__ void load_factor_T(float* St, const float* F, int K, int64_t row0, int nr) {
-    for (int e = threadIdx.x; e < T * K; e += GMF_THREADS) {
-        const int i = e / K, c = e - i * K;
-        St[c * LD + i] = i < nr ? __ldg(F + (row0 + i) * K + c) : 0.f;
+// Rows [row0, row0+nr) of F (row stride KP, a multiple of 4) -> St[c*LD + i]
+// (transposed), zero-filled beyond nr. All loads of a thread are issued before
+// any store (one L2 round trip).
+__device__ __forceinline__ void load_factor_T(float* St, const float* F, int KP, int64_t row0, int nr) {
+    const int q4 = KP >> 2;                 // float4 per row
+    const int total = T * q4;               // <= 1024 for KP <= 64
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int e = threadIdx.x + u * GMF_THREADS;
+        const int i = e / q4;
+        v[u] = (e < total && i < nr) ? __ldg((const float4*)(F + (row0 + i) * KP) + (e - i * q4))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int e = threadIdx.x + u * GMF_THREADS;
+        if (e < total) {
+            const int i = e / q4, c = 4 * (e - i * q4);
+            St[(c + 0) * LD + i] = v[u].x;
+            St[(c + 1) * LD + i] = v[u].y;
+            St[(c + 2) * LD + i] = v[u].z;
+            St[(c + 3) * LD + i] = v[u].w;
+        }
     }
 }
 
@@ -96,19 +96,6 @@ __device__ __forceinline__ void load_operands(float* O, const float* St, int nf,
         O[i * 2 * P + c] = v;
         O[i * 2 * P + P + c] = v * v;
     }
-}
-
-__device__ __forceinline__ float block_sum_f(float v, float* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    float s = 0.f;
-#pragma unroll
-    for (int u = 0; u < NW; u++) s += red[u];  // fixed order: every thread the same value
-    return s;
 }
 
 // Contraction of one tile side. Thread (o = tid >> 2, q4 = tid & 3) owns output
@@ -181,28 +168,6 @@ __device__ __forceinline__ void contract_side(const float* __restrict__ Ds, cons
     }
 }
 
-__device__ __forceinline__ float bias_visit(float a1, float a2, int visits) {
-    // (1 - (1-a2)^k) / (1 - (1-a1)^k), k >= 1
-    const float k = (float)visits;
-    return (1.f - expf(k * log1pf(-a2))) / (1.f - expf(k * log1pf(-a1)));
-}
-
-// Smoothed local step of eq. 12 / eq. 14 for one free parameter.
-__device__ __forceinline__ void smoothed_step(float* theta, float* gbar, float* hbar, float gsum, float hsum,
-                                              float scale, float lam, const StepArgs& a, float rho_c,
-                                              unsigned* err) {
-    const float th = *theta;
-    const float gh = -scale * gsum + lam * th;
-    const float hh = scale * hsum + lam + a.damping;
-    const float gb = (1.f - a.a1) * (*gbar) + a.a1 * gh;
-    const float hb = (1.f - a.a2) * (*hbar) + a.a2 * hh;
-    const float nt = th - rho_c * (gb / hb);
-    *gbar = gb;
-    *hbar = hb;
-    *theta = nt;
-    if (!isfinite(nt)) atomicOr(err, GMF_DEVERR_NONFINITE);
-}
-
 struct Smem {
     float *Ls, *Rs, *RF, *LF, *Ds, *DDs;
 };
@@ -210,7 +175,7 @@ struct Smem {
 __device__ __forceinline__ Smem carve(float* base, int K, int FRP, int FCP) {
     Smem s;
     s.Ls = base;
-    s.Rs = s.Ls + K * LD;
+    s.Rs = s.Ls + K * LD;   // K here is the padded KP
     s.RF = s.Rs + K * LD;
     s.LF = s.RF + T * 2 * FRP;
     s.Ds = s.LF + T * 2 * FCP;
@@ -221,12 +186,7 @@ __device__ __forceinline__ Smem carve(float* base, int K, int FRP, int FCP) {
 __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w) {
     extern __shared__ __align__(16) float smem[];
     const int FRP = (a.fr + 3) & ~3, FCP = (a.fc + 3) & ~3;
-    const Smem S = carve(smem, a.K, FRP, FCP);
-    __shared__ float red[NW];
-    __shared__ int s_flag[3];
-    __shared__ int s_visits[T];
-    __shared__ float s_rc[T];
-
+    const Smem S = carve(smem, a.KP, FRP, FCP);
     const int tid = threadIdx.x;
     const int tj = blockIdx.x, ti = blockIdx.y, k = blockIdx.z;
     const BlockGeo g = block_geo(a, w, k);
@@ -235,7 +195,6 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w) {
     const bool nb = a.family == GMF_NEGBIN;
     const bool moments = nb && a.alpha_mode == 1;
     const float alpha = *a.alpha;
-    const float rhoc_blk = a.rhoc[w * a.per + k];   // rho_t * c_t (bias_corr 0) or rho_t (bias_corr 1)
     float s1 = 0.f, s2 = 0.f;
 
     const int64_t row0 = g.r0 + (int64_t)ti * T, col0 = g.c0 + (int64_t)tj * T;
@@ -243,13 +202,29 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w) {
     const int nc = active ? (int)min((int64_t)T, g.mJ - (int64_t)tj * T) : 0;
 
     if (active) {
-        load_factor_T(S.Ls, a.L, a.K, row0, nr);
-        load_factor_T(S.Rs, a.R, a.K, col0, nc);
+        // eta micro-tile of this thread: rows 4ty..4ty+3, columns 4tx..4tx+3.
+        // Its counts (and weights) are requested first so that the HBM latency
+        // overlaps the factor loads and the eta product.
+        const int tx = tid & 15, ty = tid >> 4;
+        const bool vec = ((a.m & 3) == 0) && ((col0 & 3) == 0);
+        float yv[4][4], wv[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int il = 4 * ty + u, jl0 = 4 * tx;
+            const int valid = il < nr ? max(0, min(4, nc - jl0)) : 0;
+            const int64_t idx = (row0 + il) * a.m + col0 + jl0;
+            if (valid > 0) load_y4(a.Y, a.y16, idx, vec, valid, yv[u]);
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                if (valid == 0) yv[u][v] = 0.f;
+                wv[u][v] = (a.W && v < valid) ? __ldg(a.W + idx + v) : 1.f;
+            }
+        }
+        load_factor_T(S.Ls, a.L, a.KP, row0, nr);
+        load_factor_T(S.Rs, a.R, a.KP, col0, nc);
         __syncthreads();
         load_operands(S.RF, S.Rs, a.fr, FRP, 1 + a.p, a.p, a.q, false);
         load_operands(S.LF, S.Ls, a.fc, FCP, 0, a.p, a.q, true);
-        // eta micro-tile: rows 4ty..4ty+3, columns 4tx..4tx+3
-        const int tx = tid & 15, ty = tid >> 4;
         float acc[4][4];
 #pragma unroll
         for (int u = 0; u < 4; u++)
@@ -264,33 +239,25 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w) {
 #pragma unroll
                 for (int v = 0; v < 4; v++) acc[u][v] = fmaf(l4[u], r4[v], acc[u][v]);
         }
-        const bool vec = ((a.m & 3) == 0) && ((col0 & 3) == 0);
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const int il = 4 * ty + u;
             const int jl0 = 4 * tx;
-            float y[4], wv[4] = {1.f, 1.f, 1.f, 1.f};
             const int valid = il < nr ? max(0, min(4, nc - jl0)) : 0;
-            const int64_t idx = (row0 + il) * a.m + col0 + jl0;
-            if (valid > 0) {
-                load_y4(a.Y, a.y16, idx, vec, valid, y);
-                if (a.W)
-#pragma unroll
-                    for (int v = 0; v < 4; v++) wv[v] = v < valid ? __ldg(a.W + idx + v) : 0.f;
-            }
             float dd[4], ddd[4];
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 dd[v] = ddd[v] = 0.f;
                 if (v < valid) {
+                    const float y = yv[u][v], w8 = wv[u][v];
                     const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
                     const float mu = expf(e);
                     const float f = nb ? alpha / (alpha + mu) : 1.f;
-                    dd[v] = wv[v] * (y[v] - mu) * f;
-                    ddd[v] = wv[v] * mu * f;
+                    dd[v] = w8 * (y - mu) * f;
+                    ddd[v] = w8 * mu * f;
                     if (moments) {
-                        s1 = fmaf(wv[v] * mu, mu, s1);
-                        s2 += wv[v] * ((y[v] - mu) * (y[v] - mu) - mu);
+                        s1 = fmaf(w8 * mu, mu, s1);
+                        s2 += w8 * ((y - mu) * (y - mu) - mu);
                     }
                 }
             }
@@ -306,108 +273,7 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w) {
         contract_side(S.Ds, S.DDs, 1, LDD, S.LF, FCP, a.fc, nr, nc, pcol);
     }
 
-    // ---- arrivals: elect the last CTA of each row strip and column strip
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        s_flag[0] = s_flag[1] = 0;
-        if (active) {
-            unsigned prev = atomicAdd(&a.ctrR[k * a.TI + ti], 1u);
-            s_flag[0] = prev == (unsigned)(nTJ - 1);
-            prev = atomicAdd(&a.ctrC[k * a.TJ + tj], 1u);
-            s_flag[1] = prev == (unsigned)(nTI - 1);
-        }
-    }
-    __syncthreads();
-
-    if (s_flag[0]) {  // this CTA updates rows [row0, row0 + nr) of block k
-        __threadfence();
-        if (tid < nr) {
-            const int v = a.cntR[row0 + tid] + 1;
-            s_visits[tid] = v;
-            s_rc[tid] = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, v) : rhoc_blk;
-        }
-        __syncthreads();
-        const float scale = (float)a.m / (float)g.mJ;
-        for (int e = tid; e < nr * a.fr; e += GMF_THREADS) {
-            const int il = e / a.fr, c = e - il * a.fr;
-            float sg = 0.f, sh = 0.f;
-            for (int u = 0; u < nTJ; u++) {
-                const float* src = a.partR + ((size_t)((k * a.TI + ti) * a.TJ + u) * T + il) * 2 * a.fr;
-                sg += __ldcg(src + c);
-                sh += __ldcg(src + a.fr + c);
-            }
-            const int64_t row = row0 + il;
-            const float lam = c < a.q ? a.lam[1] : a.lam[2];
-            smoothed_step(a.L + row * a.K + 1 + a.p + c, a.GbR + row * a.fr + c, a.HbR + row * a.fr + c, sg, sh,
-                          scale, lam, a, s_rc[il], a.err);
-        }
-        __syncthreads();
-        if (tid < nr) a.cntR[row0 + tid] = s_visits[tid];
-        if (tid == 0) a.ctrR[k * a.TI + ti] = 0u;
-    }
-    if (s_flag[1]) {  // this CTA updates columns [col0, col0 + nc) of block k
-        __threadfence();
-        __syncthreads();
-        if (tid < nc) {
-            const int v = a.cntC[col0 + tid] + 1;
-            s_visits[tid] = v;
-            s_rc[tid] = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, v) : rhoc_blk;
-        }
-        __syncthreads();
-        const float scale = (float)a.n / (float)g.nI;
-        for (int e = tid; e < nc * a.fc; e += GMF_THREADS) {
-            const int jl = e / a.fc, c = e - jl * a.fc;
-            float sg = 0.f, sh = 0.f;
-            for (int u = 0; u < nTI; u++) {
-                const float* src = a.partC + ((size_t)((k * a.TJ + tj) * a.TI + u) * T + jl) * 2 * a.fc;
-                sg += __ldcg(src + c);
-                sh += __ldcg(src + a.fc + c);
-            }
-            const int64_t col = col0 + jl;
-            const int rcol = c < a.p ? 1 + c : 1 + a.q + c;
-            const float lam = c < a.p ? a.lam[0] : a.lam[3];
-            smoothed_step(a.R + col * a.K + rcol, a.GbC + col * a.fc + c, a.HbC + col * a.fc + c, sg, sh, scale,
-                          lam, a, s_rc[jl], a.err);
-        }
-        __syncthreads();
-        if (tid < nc) a.cntC[col0 + tid] = s_visits[tid];
-        if (tid == 0) a.ctrC[k * a.TJ + tj] = 0u;
-    }
-
-    // ---- NB shape: moment sums pooled over the sweep, one update per sweep (App. B)
-    if (moments) {
-        const float S1 = block_sum_f(s1, red);
-        const float S2 = block_sum_f(s2, red);
-        const int cta = (k * a.TI + ti) * a.TJ + tj;
-        if (tid == 0) {
-            a.nbpart[2 * cta] = (double)S1;
-            a.nbpart[2 * cta + 1] = (double)S2;
-        }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-            s_flag[2] = atomicAdd(a.ctrSweep, 1u) == total - 1;
-        }
-        __syncthreads();
-        if (s_flag[2] && tid == 0) {
-            __threadfence();
-            const int total = gridDim.x * gridDim.y * gridDim.z;
-            double T1 = 0.0, T2 = 0.0;
-            for (int c = 0; c < total; c++) {
-                T1 += __ldcg(a.nbpart + 2 * c);
-                T2 += __ldcg(a.nbpart + 2 * c + 1);
-            }
-            if (T2 > 0.0) {
-                float ahat = (float)(T1 / T2);
-                if (ahat < a.eps) ahat = a.eps;
-                const float rf = a.rho1[w];
-                *a.alpha = (1.f - rf) * alpha + rf * ahat;
-            }
-            *a.ctrSweep = 0u;
-        }
-    }
+    tile_arrive_update<T, GMF_THREADS>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
 }
 
 // Unit deviance 2w[...] of Table S1 / App. B in FP32, written so that no
@@ -429,13 +295,13 @@ __device__ __forceinline__ float unit_deviance(bool nb, float y, float e, float 
 __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, double* part) {
     extern __shared__ __align__(16) float smem[];
     float* Ls = smem;
-    float* Rs = Ls + a.K * LD;
+    float* Rs = Ls + a.KP * LD;
     __shared__ float red[NW];
     const int tid = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.y * T, col0 = (int64_t)blockIdx.x * T;
     const int nr = (int)min((int64_t)T, a.n - row0), nc = (int)min((int64_t)T, a.m - col0);
-    load_factor_T(Ls, a.L, a.K, row0, nr);
-    load_factor_T(Rs, a.R, a.K, col0, nc);
+    load_factor_T(Ls, a.L, a.KP, row0, nr);
+    load_factor_T(Rs, a.R, a.KP, col0, nc);
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;
     float acc[4][4];
@@ -477,7 +343,7 @@ __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, doubl
             }
         }
     }
-    const float s = block_sum_f(sum, red);
+    const float s = block_sum_f<GMF_THREADS>(sum, red);
     if (tid == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = (double)s;
 }
 
@@ -508,6 +374,7 @@ __global__ void permute_kernel(const Ty* __restrict__ src, Ty* __restrict__ dst,
 
 size_t sweep_smem(int K, int fr, int fc) {
     const int FRP = (fr + 3) & ~3, FCP = (fc + 3) & ~3;
+    K = (K + 3) & ~3;
     return sizeof(float) * (2 * (size_t)K * LD + (size_t)T * 2 * FRP + (size_t)T * 2 * FCP + 2 * (size_t)T * LDD);
 }
 
@@ -522,6 +389,7 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.q = h->q;
     a.d = h->d;
     a.K = h->K;
+    a.KP = h->KP;
     a.fr = h->fr;
     a.fc = h->fc;
     a.nb_row = c.nb_row;
@@ -566,12 +434,14 @@ StepArgs gmf_make_args(gmf_model* h) {
     return a;
 }
 
+cudaError_t gmf_sweep_simt_attr(gmf_model* h) {
+    const size_t smem = sweep_smem(h->K, h->fr, h->fc);
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaStream_t st) {
     const size_t smem = sweep_smem(h->K, h->fr, h->fc);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     dim3 grid(h->TJ, h->TI, h->per);
     sweep_kernel<<<grid, GMF_THREADS, smem, st>>>(a, w);
     return cudaGetLastError();
@@ -580,7 +450,7 @@ cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaSt
 cudaError_t gmf_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st) {
     StepArgs a = gmf_make_args(h);
     dim3 grid((unsigned)((h->m + T - 1) / T), (unsigned)((h->n + T - 1) / T));
-    const size_t smem = sizeof(float) * 2 * (size_t)h->K * LD;
+    const size_t smem = sizeof(float) * 2 * (size_t)h->KP * LD;
     deviance_kernel<<<grid, GMF_THREADS, smem, st>>>(a, h->devpart);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

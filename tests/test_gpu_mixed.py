@@ -1,0 +1,123 @@
+"""Parity of the tensor-core (tcgen05) path with the FP64 oracle.
+
+Tolerances from the arithmetic of the mixed path: eta is a split-BF16 product
+(three BF16 products, FP32 accumulate: relative error ~1e-5 of |L||R|); Ddot,
+Dddot and the contraction operands are BF16 (unit roundoff 2^-9 ~ 2e-3), so
+each block gradient / curvature sum carries up to ~1e-2 relative error against
+the scale of its terms. Hence, after one teacher-forced sweep: the parameter
+step within 3e-2 (max-norm relative), the parameters within 1e-4; after a
+fixed number of epochs: the deviance within 1e-3 of the oracle's (the stated
+target for the mixed path).
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests.test_gpu_parity import Pair, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gmf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def oracle_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+MIXED = {
+    # K = 1+p+q+d <= 16: one 128-byte atom per eta operand row
+    "poisson_cfg1": (1000, 500, 2, 1, 5, "poisson", 100, 100, dict(offset=False)),
+    # 2 atoms (K = 25), uint16 counts, ragged 128-tiles, NB shape updates
+    "nb_d20_uint16": (900, 640, 3, 1, 20, "negbin", 300, 256,
+                      dict(y_dtype="uint16", zero_frac=0.85, alpha_mode=1)),
+    # 3 atoms (K = 55), contraction widths 51 / 53 -> 64
+    "nb_d50": (640, 384, 3, 1, 50, "negbin", 256, 128, dict(y_dtype="uint16", zero_frac=0.8)),
+    # blocks smaller than a tile, r < s role swap, per-visit bias correction, weights
+    "nb_swap_small_blocks": (200, 960, 2, 2, 4, "negbin", 100, 96,
+                             dict(zero_frac=0.7, bias_corr=1, weights=True)),
+}
+
+
+@pytest.mark.parametrize("case", list(MIXED))
+def test_mixed_one_sweep_teacher_forced(gmf, oracle_mod, case):
+    n, m, p, q, d, fam, nbr, nbc, extra = MIXED[case]
+    P = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision="mixed", **extra)
+    for e in range(2):
+        P.ref.epoch(P.sigmas[e])
+    P.teacher_force()
+    before = P.ref_params()
+    sig = P.sigmas[5]
+    w = int(np.random.default_rng(2).integers(P.nsw))
+    P.ref.sweeps(sig, w, w + 1)
+    P.gpu.sweeps(sig, w, w + 1)
+    got, ref = P.gpu.get_params(), P.ref_params()
+    for k in ("U", "V", "B", "Gamma"):
+        if ref[k].size == 0:
+            continue
+        assert rel(got[k], ref[k]) <= 1e-4, (k, rel(got[k], ref[k]))
+        step_ref = ref[k] - before[k]
+        if np.abs(step_ref).max() > 0:
+            step_gpu = got[k] - before[k].astype(np.float32).astype(np.float64)
+            assert rel(step_gpu, step_ref) <= 3e-2, (k, "step", rel(step_gpu, step_ref))
+    ema, rema = P.gpu.get_ema(), P.ref_ema()
+    np.testing.assert_array_equal(ema["cnt_row"], rema["cnt_row"])
+    np.testing.assert_array_equal(ema["cnt_col"], rema["cnt_col"])
+    assert got["alpha"] == pytest.approx(ref["alpha"], rel=1e-3)
+
+
+@pytest.mark.parametrize("case,epochs", [("poisson_cfg1", 50), ("nb_d20_uint16", 6), ("nb_d50", 4)])
+def test_mixed_final_deviance_within_1e3(gmf, oracle_mod, case, epochs):
+    n, m, p, q, d, fam, nbr, nbc, extra = MIXED[case]
+    P = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision="mixed", **extra)
+    d0 = P.ref.deviance()
+    for e in range(epochs):
+        P.ref.epoch(P.sigmas[e])
+        P.gpu.epoch(P.sigmas[e])
+    dr, dg = P.ref.deviance(), P.gpu.deviance()
+    assert dr < d0
+    assert abs(dg - dr) / dr <= 1e-3, (dg, dr)
+
+
+def test_mixed_full_size_nb_medium(gmf, oracle_mod):
+    """The benchmarked workload on the tensor-core path: one epoch, deviance within 1e-3."""
+    w = synth.WORKLOADS["nb_medium"]
+    P = Pair(gmf, oracle_mod, w.n, w.m, w.p, w.q, w.d, w.family, w.nb_row, w.nb_col, zero_frac=w.zero_frac,
+             precision="mixed")
+    P.ref.epoch(P.sigmas[0])
+    P.gpu.epoch(P.sigmas[0])
+    assert P.gpu.deviance() == pytest.approx(P.ref.deviance(), rel=1e-3)
+    got, ref = P.gpu.get_params(), P.ref_params()
+    for k in ("U", "V"):
+        assert rel(got[k], ref[k]) <= 1e-3
+
+
+def test_mixed_is_deterministic(gmf, oracle_mod):
+    n, m, p, q, d, fam, nbr, nbc, extra = MIXED["nb_d20_uint16"]
+    P = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision="mixed", **extra)
+    Q = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision="mixed", **extra)
+    for e in range(2):
+        P.gpu.epoch(P.sigmas[e])
+        Q.gpu.epoch(Q.sigmas[e])
+    a, b = P.gpu.get_params(), Q.gpu.get_params()
+    for k in ("U", "V", "B", "Gamma"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_mixed_rejects_unaligned_layouts(gmf, oracle_mod):
+    with pytest.raises(gmf.GmfError) as e:
+        Pair(gmf, oracle_mod, 100, 50, 2, 1, 3, "poisson", 20, 10, precision="mixed")   # 50 * 4 bytes % 16 != 0
+    assert e.value.code == gmf.GMF_ERR_ARG and "16 bytes" in str(e.value)
+    with pytest.raises(gmf.GmfError):
+        Pair(gmf, oracle_mod, 100, 64, 2, 1, 3, "poisson", 20, 10, precision="mixed")   # nb_col * 4 % 16 != 0
