@@ -5,7 +5,8 @@ Tolerances from the arithmetic of the mixed path: eta is a split-BF16 product
 Dddot and the contraction operands are BF16 (unit roundoff 2^-9 ~ 2e-3), so
 each block gradient / curvature sum carries up to ~1e-2 relative error against
 the scale of its terms. Hence, after one teacher-forced sweep: the parameter
-step within 3e-2 (max-norm relative), the parameters within 1e-4; after a
+step within 3e-2 (max-norm relative); a sweep moves the parameters by about 1%
+of their scale, so the parameters stay within 5e-4; after a
 fixed number of epochs: the deviance within 1e-3 of the oracle's (the stated
 target for the mixed path).
 """
@@ -66,7 +67,7 @@ def test_mixed_one_sweep_teacher_forced(gmf, oracle_mod, case):
     for k in ("U", "V", "B", "Gamma"):
         if ref[k].size == 0:
             continue
-        assert rel(got[k], ref[k]) <= 1e-4, (k, rel(got[k], ref[k]))
+        assert rel(got[k], ref[k]) <= 5e-4, (k, rel(got[k], ref[k]))
         step_ref = ref[k] - before[k]
         if np.abs(step_ref).max() > 0:
             step_gpu = got[k] - before[k].astype(np.float32).astype(np.float64)
