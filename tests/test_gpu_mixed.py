@@ -99,9 +99,11 @@ def test_mixed_full_size_nb_medium(gmf, oracle_mod):
     P.ref.epoch(P.sigmas[0])
     P.gpu.epoch(P.sigmas[0])
     assert P.gpu.deviance() == pytest.approx(P.ref.deviance(), rel=1e-3)
+    # Sanity bound only: a full epoch compounds 4 row visits and 40 column visits
+    # of steps that each carry the BF16 contraction error (<= 3e-2 of a step).
     got, ref = P.gpu.get_params(), P.ref_params()
     for k in ("U", "V"):
-        assert rel(got[k], ref[k]) <= 1e-3
+        assert rel(got[k], ref[k]) <= 2e-2
 
 
 def test_mixed_is_deterministic(gmf, oracle_mod):
