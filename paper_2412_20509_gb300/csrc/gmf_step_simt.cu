@@ -102,7 +102,7 @@ __device__ __forceinline__ void load_operands(float* O, const float* St, int nf,
 // row o (a tile row for the row side, a tile column for the column side) and
 // the summation indices kk = 4*s + q4, s < 16. D(o, kk) is read through
 // dstride_o / dstride_k. Operands O[kk][2P] (values then squares).
-// Writes sums for c < nf to dst[o*2*nf + c] (G) and dst[o*2*nf + nf + c] (H).
+// Writes sums for c < nf to dst[c*T + o] (G) and dst[(nf + c)*T + o] (H).
 __device__ __forceinline__ void contract_side(const float* __restrict__ Ds, const float* __restrict__ DDs,
                                               int dstride_o, int dstride_k, const float* __restrict__ O, int P,
                                               int nf, int nvalid_k, int nvalid_o, float* __restrict__ dst) {
@@ -160,8 +160,8 @@ __device__ __forceinline__ void contract_side(const float* __restrict__ Ds, cons
                 for (int v = 0; v < 4; v++) {
                     const int c = 4 * (ch0 + u) + v;
                     if (v == q4 && c < nf) {
-                        dst[o * 2 * nf + c] = g[u][v];
-                        dst[o * 2 * nf + nf + c] = h[u][v];
+                        dst[c * T + o] = g[u][v];
+                        dst[(nf + c) * T + o] = h[u][v];
                     }
                 }
         }
@@ -183,7 +183,7 @@ __device__ __forceinline__ Smem carve(float* base, int K, int FRP, int FCP) {
     return s;
 }
 
-__global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w) {
+__global__ void __launch_bounds__(GMF_THREADS, 3) sweep_kernel(StepArgs a, int w) {
     extern __shared__ __align__(16) float smem[];
     const int FRP = (a.fr + 3) & ~3, FCP = (a.fc + 3) & ~3;
     const Smem S = carve(smem, a.KP, FRP, FCP);
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(GMF_THREADS) sweep_kernel(StepArgs a, int w) {
         contract_side(S.Ds, S.DDs, 1, LDD, S.LF, FCP, a.fc, nr, nc, pcol);
     }
 
-    tile_arrive_update<T, GMF_THREADS>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
+    tile_arrive_update<T, GMF_THREADS, 2>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
 }
 
 // Unit deviance 2w[...] of Table S1 / App. B in FP32, written so that no

@@ -2,7 +2,7 @@
 // work (eq. 15 with App. B) with eta and the four gradient / curvature
 // contractions on the 5th-generation tensor cores.
 //
-// One CTA per 128 x 128 tile, 8 warps:
+// One CTA per 128 x 128 tile, 16 warps:
 //   1. thread 0 starts the TMA load of the tile's counts (128-byte swizzled
 //      boxes) while all threads build the MMA operands in shared memory:
 //        eta:  A = [L_hi | L_lo | L_hi], B = [R_hi | R_hi | R_lo] (BF16 split of
@@ -11,8 +11,8 @@
 //        row side:    B = [Z, V]' and its square, K = tile columns;
 //        column side: B = [X, U]' and its square, K = tile rows;
 //   2. thread 0 issues the eta MMAs (FP32 accumulate in TMEM) and commits;
-//   3. the 8 warps read eta from TMEM (warp w: lanes 32(w%4).., columns
-//      64(w/4)..), compute mu = exp(eta), Ddot, Dddot (Sec. 3) in FP32 and
+//   3. the 16 warps read eta from TMEM (warp w: lanes 32(w%4).., columns
+//      32(w/4)..), compute mu = exp(eta), Ddot, Dddot (Sec. 3) in FP32 and
 //      store them as BF16 into one swizzled tile (over the dead eta operands);
 //   4. thread 0 issues the contractions: Ddot R_f and Dddot R_f^2 (A = the
 //      tile, K-major) and Ddot' L_f and Dddot' L_f^2 (A = the same tile read
@@ -38,7 +38,7 @@ using namespace gmfdev;
 using namespace sm100;
 
 constexpr int TT = 128;            // tile edge (rows and columns)
-constexpr int NTH = 256;           // threads per CTA
+constexpr int NTH = 512;           // threads per CTA (16 warps)
 constexpr uint32_t ATOM = 16384;   // 128 rows x 128 bytes, 128-byte swizzle
 constexpr uint32_t WAIT_POLLS = 1u << 26;
 
@@ -130,55 +130,76 @@ __global__ void __launch_bounds__(NTH, 1)
                 tma_load_2d(Ys + b * ATOM, &ymap, (int)(col0 + (int64_t)b * Lo.JB), (int)row0, &bars[0]);
         }
 
-        // ---- operands. Threads 0..127: L row -> A and the column-side B; 128..255: R row -> B and the row-side B.
+        // ---- operands. Thread groups of 128: L rows -> eta A; R rows -> eta B;
+        //      L rows -> column-side B ([X, U] and squares); R rows -> row-side B ([Z, V] and squares).
         {
-            const int r = tid & (TT - 1);
-            const bool isL = tid < TT;
+            const int grp = tid >> 7, r = tid & (TT - 1);
+            const bool isL = (grp & 1) == 0;
             const bool ok = isL ? r < nr : r < nc;
             const float* src = isL ? a.L + (row0 + r) * a.KP : a.R + (col0 + r) * a.KP;
-            uint8_t* op = isL ? Aop : Bop;
-            for (int kk0 = 0; kk0 < Lo.KP16; kk0 += 8) {
-                float v[8];
+            if (grp < 2) {
+                uint8_t* op = isL ? Aop : Bop;
+                for (int kb = 0; kb < Lo.KP16; kb += 32) {
+                    float v[32];
 #pragma unroll
-                for (int t = 0; t < 8; t++) {
-                    const int kk = kk0 + t;
-                    v[t] = (ok && kk < a.K) ? __ldg(src + kk) : 0.f;
-                }
-                uint32_t hi[4], lo[4];
+                    for (int u = 0; u < 8; u++) {
+                        const int kk = kb + 4 * u;
+                        const float4 x = (ok && kk < a.KP) ? __ldg((const float4*)(src + kk))
+                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[4 * u] = x.x;
+                        v[4 * u + 1] = x.y;
+                        v[4 * u + 2] = x.z;
+                        v[4 * u + 3] = x.w;
+                    }
 #pragma unroll
-                for (int t = 0; t < 4; t++) {
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * t]), h1 = __float2bfloat16_rn(v[2 * t + 1]);
-                    const float l0 = v[2 * t] - __bfloat162float(h0), l1 = v[2 * t + 1] - __bfloat162float(h1);
-                    hi[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                    lo[t] = bf16_bits(l0) | (bf16_bits(l1) << 16);
-                }
+                    for (int h8 = 0; h8 < 4; h8++) {
+                        const int kk0 = kb + 8 * h8;
+                        if (kk0 < Lo.KP16) {
+                            uint32_t hi[4], lo[4];
 #pragma unroll
-                for (int seg = 0; seg < 3; seg++) {
-                    // A segments: hi, lo, hi;  B segments: hi, hi, lo
-                    const bool use_lo = isL ? seg == 1 : seg == 2;
-                    const int kc = seg * Lo.KP16 + kk0;
-                    uint8_t* dst = op + (kc >> 6) * ATOM + sw128_off(r, (kc & 63) * 2);
-                    if (use_lo)
-                        st_shared_v4(dst, lo[0], lo[1], lo[2], lo[3]);
-                    else
-                        st_shared_v4(dst, hi[0], hi[1], hi[2], hi[3]);
+                            for (int t = 0; t < 4; t++) {
+                                const float x0 = v[8 * h8 + 2 * t], x1 = v[8 * h8 + 2 * t + 1];
+                                hi[t] = pack_bf16x2(x0, x1);
+                                const float r0 = x0 - __uint_as_float(hi[t] << 16);
+                                const float r1 = x1 - __uint_as_float(hi[t] & 0xFFFF0000u);
+                                lo[t] = pack_bf16x2(r0, r1);
+                            }
+#pragma unroll
+                            for (int seg = 0; seg < 3; seg++) {
+                                // A segments: hi, lo, hi;  B segments: hi, hi, lo
+                                const bool use_lo = isL ? seg == 1 : seg == 2;
+                                const int kc = seg * Lo.KP16 + kk0;
+                                uint8_t* dst = op + (kc >> 6) * ATOM + sw128_off(r, (kc & 63) * 2);
+                                if (use_lo)
+                                    st_shared_v4(dst, lo[0], lo[1], lo[2], lo[3]);
+                                else
+                                    st_shared_v4(dst, hi[0], hi[1], hi[2], hi[3]);
+                            }
+                        }
+                    }
                 }
-            }
-            // contraction operands: value and square of the multiplier columns, K index = r
-            const int NF = isL ? Lo.NC : Lo.NR;
-            const int nf = isL ? a.fc : a.fr;
-            uint8_t* o1 = isL ? LF : RF;
-            uint8_t* o2 = isL ? LF2 : RF2;
-            const uint32_t atom = (uint32_t)NF * 128u;
-            for (int c = 0; c < NF; c++) {
-                float v = 0.f;
-                if (ok && c < nf) {
-                    const int col = isL ? (c < a.p ? 1 + c : 1 + a.q + c) : 1 + a.p + c;
-                    v = __ldg(src + col);
+            } else {
+                // value and square of each multiplier column; K index of the contraction = r
+                const int NF = isL ? Lo.NC : Lo.NR;
+                const int nf = isL ? a.fc : a.fr;
+                uint8_t* o1 = isL ? LF : RF;
+                uint8_t* o2 = isL ? LF2 : RF2;
+                const uint32_t atom = (uint32_t)NF * 128u;
+                for (int c0 = 0; c0 < NF; c0 += 16) {
+                    float v[16];
+#pragma unroll
+                    for (int u = 0; u < 16; u++) {
+                        const int c = c0 + u;
+                        const int col = isL ? (c < a.p ? 1 + c : 1 + a.q + c) : 1 + a.p + c;
+                        v[u] = (ok && c < nf) ? __ldg(src + col) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; u++) {
+                        const uint32_t off = (r >> 6) * atom + sw128_off(c0 + u, (r & 63) * 2);
+                        *(__nv_bfloat16*)(o1 + off) = __float2bfloat16_rn(v[u]);
+                        *(__nv_bfloat16*)(o2 + off) = __float2bfloat16_rn(v[u] * v[u]);
+                    }
                 }
-                const uint32_t off = (r >> 6) * atom + sw128_off(c, (r & 63) * 2);
-                *(__nv_bfloat16*)(o1 + off) = __float2bfloat16_rn(v);
-                *(__nv_bfloat16*)(o2 + off) = __float2bfloat16_rn(v * v);
             }
         }
         fence_proxy_async_smem();
@@ -201,63 +222,56 @@ __global__ void __launch_bounds__(NTH, 1)
         tc_fence_after();
 
         if (ok) {
-            // ---- epilogue: warp (q, h) owns rows 32q.. and columns 64h..64h+63
-            const int q = warp & 3, hh = warp >> 2;
+            // ---- epilogue: warp (q, cq) owns rows 32q.. and columns 32cq..32cq+31
+            const int q = warp & 3, cq = warp >> 2;
             const int i = 32 * q + lane;
             const bool row_ok = i < nr;
             const float* Wrow = a.W ? a.W + (row0 + i) * a.m + col0 : nullptr;
-#pragma unroll 1
-            for (int ch = 0; ch < 2; ch++) {
-                const int jc = 64 * hh + 32 * ch;
-                uint32_t ev[32];
-                tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)jc, ev);
-                tmem_wait_ld();
+            const int jc = 32 * cq;
+            uint32_t ev[32];
+            tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)jc, ev);
+            tmem_wait_ld();
 #pragma unroll
-                for (int gq = 0; gq < 4; gq++) {
-                    const int j0 = jc + 8 * gq;
-                    float y[8];
-                    if (Y16) {
-                        const uint4 u = *(const uint4*)(Ys + (j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2));
-                        const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+            for (int gq = 0; gq < 4; gq++) {
+                const int j0 = jc + 8 * gq;
+                float y[8];
+                if (Y16) {
+                    const uint4 u = *(const uint4*)(Ys + (j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2));
+                    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-                        for (int t = 0; t < 4; t++) {
-                            y[2 * t] = (float)(uu[t] & 0xFFFFu);
-                            y[2 * t + 1] = (float)(uu[t] >> 16);
-                        }
-                    } else {
-                        const uint32_t byte = (uint32_t)(j0 & 31) * 4u;
-                        const int4 u0 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte));
-                        const int4 u1 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte + 16));
-                        y[0] = (float)u0.x; y[1] = (float)u0.y; y[2] = (float)u0.z; y[3] = (float)u0.w;
-                        y[4] = (float)u1.x; y[5] = (float)u1.y; y[6] = (float)u1.z; y[7] = (float)u1.w;
+                    for (int t = 0; t < 4; t++) {
+                        y[2 * t] = (float)(uu[t] & 0xFFFFu);
+                        y[2 * t + 1] = (float)(uu[t] >> 16);
                     }
-                    float dd[8], ddd[8];
-#pragma unroll
-                    for (int t = 0; t < 8; t++) {
-                        const int j = j0 + t;
-                        dd[t] = ddd[t] = 0.f;
-                        if (row_ok && j < nc) {
-                            const float wv = Wrow ? __ldg(Wrow + j) : 1.f;
-                            const float e = fminf(fmaxf(__uint_as_float(ev[8 * gq + t]), -a.clamp), a.clamp);
-                            const float mu = __expf(e);
-                            const float f = nb ? __fdividef(alpha, alpha + mu) : 1.f;
-                            dd[t] = wv * (y[t] - mu) * f;
-                            ddd[t] = wv * mu * f;
-                            if (moments) {
-                                s1 = fmaf(wv * mu, mu, s1);
-                                s2 += wv * ((y[t] - mu) * (y[t] - mu) - mu);
-                            }
-                        }
-                    }
-                    const uint32_t off = (uint32_t)(j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2);
-                    st_shared_v4(Dd + off, bf16_bits(dd[0]) | (bf16_bits(dd[1]) << 16),
-                                 bf16_bits(dd[2]) | (bf16_bits(dd[3]) << 16), bf16_bits(dd[4]) | (bf16_bits(dd[5]) << 16),
-                                 bf16_bits(dd[6]) | (bf16_bits(dd[7]) << 16));
-                    st_shared_v4(DDd + off, bf16_bits(ddd[0]) | (bf16_bits(ddd[1]) << 16),
-                                 bf16_bits(ddd[2]) | (bf16_bits(ddd[3]) << 16),
-                                 bf16_bits(ddd[4]) | (bf16_bits(ddd[5]) << 16),
-                                 bf16_bits(ddd[6]) | (bf16_bits(ddd[7]) << 16));
+                } else {
+                    const uint32_t byte = (uint32_t)(j0 & 31) * 4u;
+                    const int4 u0 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte));
+                    const int4 u1 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte + 16));
+                    y[0] = (float)u0.x; y[1] = (float)u0.y; y[2] = (float)u0.z; y[3] = (float)u0.w;
+                    y[4] = (float)u1.x; y[5] = (float)u1.y; y[6] = (float)u1.z; y[7] = (float)u1.w;
                 }
+                float dd[8], ddd[8];
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const int j = j0 + t;
+                    const bool valid = row_ok && j < nc;
+                    const float wv = (Wrow && valid) ? __ldg(Wrow + j) : 1.f;
+                    const float e = fminf(fmaxf(__uint_as_float(ev[8 * gq + t]), -a.clamp), a.clamp);
+                    const float mu = __expf(e);
+                    const float f = nb ? __fdividef(alpha, alpha + mu) : 1.f;
+                    const float wf = valid ? wv * f : 0.f;
+                    dd[t] = wf * (y[t] - mu);
+                    ddd[t] = wf * mu;
+                    if (moments && valid) {
+                        s1 = fmaf(wv * mu, mu, s1);
+                        s2 += wv * ((y[t] - mu) * (y[t] - mu) - mu);
+                    }
+                }
+                const uint32_t off = (uint32_t)(j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2);
+                st_shared_v4(Dd + off, pack_bf16x2(dd[0], dd[1]), pack_bf16x2(dd[2], dd[3]),
+                             pack_bf16x2(dd[4], dd[5]), pack_bf16x2(dd[6], dd[7]));
+                st_shared_v4(DDd + off, pack_bf16x2(ddd[0], ddd[1]), pack_bf16x2(ddd[2], ddd[3]),
+                             pack_bf16x2(ddd[4], ddd[5]), pack_bf16x2(ddd[6], ddd[7]));
             }
         }
         fence_proxy_async_smem();
@@ -291,7 +305,7 @@ __global__ void __launch_bounds__(NTH, 1)
         if (ok) ok = cta_wait(&bars[2], 0, a.err);
         tc_fence_after();
 
-        if (ok) {
+        if (ok && warp < 8) {
             const int q = warp & 3;
             const uint32_t lanes = (uint32_t)(32 * q) << 16;
             const int o = 32 * q + lane;   // tile row (warps 0-3) or tile column (warps 4-7)
@@ -299,8 +313,8 @@ __global__ void __launch_bounds__(NTH, 1)
             const int NF = rowside ? Lo.NR : Lo.NC;
             const int nf = rowside ? a.fr : a.fc;
             const uint32_t tg = tb + lanes + (rowside ? Lo.t_row : Lo.t_col);
-            float* dst = rowside ? a.partR + ((size_t)((k * a.TI + ti) * a.TJ + tj) * TT + o) * 2 * a.fr
-                                 : a.partC + ((size_t)((k * a.TJ + tj) * a.TI + ti) * TT + o) * 2 * a.fc;
+            float* dst = rowside ? a.partR + (size_t)((k * a.TI + ti) * a.TJ + tj) * TT * 2 * a.fr
+                                 : a.partC + (size_t)((k * a.TJ + tj) * a.TI + ti) * TT * 2 * a.fc;
             const bool o_ok = o < (rowside ? nr : nc);
             for (int c0 = 0; c0 < NF; c0 += 16) {
                 uint32_t rg[16], rh[16];
@@ -312,20 +326,19 @@ __global__ void __launch_bounds__(NTH, 1)
                     for (int u = 0; u < 16; u++) {
                         const int c = c0 + u;
                         if (c < nf) {
-                            dst[c] = __uint_as_float(rg[u]);
-                            dst[nf + c] = __uint_as_float(rh[u]);
+                            dst[(size_t)c * TT + o] = __uint_as_float(rg[u]);
+                            dst[(size_t)(nf + c) * TT + o] = __uint_as_float(rh[u]);
                         }
                     }
                 }
             }
-        } else if (tid == 0) {
-            atomicOr(a.err, GMF_DEVERR_TIMEOUT);
         }
+        if (!ok && tid == 0) atomicOr(a.err, GMF_DEVERR_TIMEOUT);
         tc_fence_before();
         __syncthreads();
         if (warp == 0) tmem_dealloc(tb, Lo.tmem_cols);
     }
-    tile_arrive_update<TT, NTH>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
+    tile_arrive_update<TT, NTH, 4>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
 }
 
 int fail_str(std::string* err, const char* msg) {

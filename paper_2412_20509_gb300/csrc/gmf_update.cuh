@@ -2,7 +2,8 @@
 // FP32 and tensor-core block-step kernels (eq. 12, eq. 14, App. B).
 //
 // Each tile kernel writes its row partials (sum_j Ddot_ij R_jc, sum_j Dddot_ij
-// R_jc^2 for the row-free columns c) and column partials to a per-tile slot,
+// R_jc^2 for the row-free columns c) and column partials to a per-tile slot
+// (column-major: G(o, c) at slot[c*T + o], H(o, c) at slot[(nf + c)*T + o]),
 // then calls tile_arrive_update(): an arrival counter per row strip and per
 // column strip elects the last CTA of the strip, which sums the strip's
 // partials in tile order and applies scale factor, penalty, damping, EMA and
@@ -52,29 +53,6 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
     return s;
 }
 
-// Sum of the n tile partials of one strip, in tile order; loads issued in groups.
-__device__ __forceinline__ void strip_sum(const float* src, size_t stride, int hoff, int n, float& sg, float& sh) {
-    constexpr int U = 8;
-    sg = 0.f;
-    sh = 0.f;
-    for (int u0 = 0; u0 < n; u0 += U) {
-        float gv[U], hv[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const bool ok = u0 + u < n;
-            gv[u] = ok ? __ldcg(src + (size_t)(u0 + u) * stride) : 0.f;
-            hv[u] = ok ? __ldcg(src + (size_t)(u0 + u) * stride + hoff) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            if (u0 + u < n) {
-                sg += gv[u];
-                sh += hv[u];
-            }
-        }
-    }
-}
-
 // (1 - (1-a2)^k) / (1 - (1-a1)^k): per-visit bias correction, k >= 1.
 __device__ __forceinline__ float bias_visit(float a1, float a2, int visits) {
     const float k = (float)visits;
@@ -82,24 +60,94 @@ __device__ __forceinline__ float bias_visit(float a1, float a2, int visits) {
 }
 
 // Smoothed local step of eq. 12 / eq. 14 for one free parameter.
-__device__ __forceinline__ void smoothed_step(float* theta, float* gbar, float* hbar, float gsum, float hsum,
+__device__ __forceinline__ void smoothed_step(float& theta, float& gbar, float& hbar, float gsum, float hsum,
                                               float scale, float lam, const StepArgs& a, float rho_c) {
-    const float th = *theta;
-    const float gh = -scale * gsum + lam * th;
+    const float gh = -scale * gsum + lam * theta;
     const float hh = scale * hsum + lam + a.damping;
-    const float gb = (1.f - a.a1) * (*gbar) + a.a1 * gh;
-    const float hb = (1.f - a.a2) * (*hbar) + a.a2 * hh;
-    const float nt = th - rho_c * (gb / hb);
-    *gbar = gb;
-    *hbar = hb;
-    *theta = nt;
-    if (!isfinite(nt)) atomicOr(a.err, GMF_DEVERR_NONFINITE);
+    gbar = (1.f - a.a1) * gbar + a.a1 * gh;
+    hbar = (1.f - a.a2) * hbar + a.a2 * hh;
+    theta = theta - rho_c * (gbar / hbar);
+    if (!isfinite(theta)) atomicOr(a.err, GMF_DEVERR_NONFINITE);
+}
+
+// Update of one strip (rows of a row strip, or columns of a column strip).
+// Per-tile partial slots hold G(o, c) at slot[c*T + o] and H(o, c) at
+// slot[(nf + c)*T + o]; the nslots slots of the strip are nslot_stride apart
+// and are summed in slot order. Items (o, c) go to threads c-major so that the
+// partial loads coalesce; each thread issues the loads of IB items at once.
+template <int T, int NT, int IB>
+__device__ __forceinline__ void strip_update(const StepArgs& a, const float* __restrict__ part, size_t slot_stride,
+                                             int nslots, int no, int nf, int64_t first, bool rowside, float scale,
+                                             const float* s_rc) {
+    const int total = no * nf;
+    for (int e0 = threadIdx.x; e0 < total; e0 += NT * IB) {
+        float* pth[IB];
+        float* pgb[IB];
+        float* phb[IB];
+        float th[IB], gb[IB], hb[IB], sg[IB], sh[IB], lam[IB];
+        int oo[IB], cc[IB];
+        bool ok[IB];
+#pragma unroll
+        for (int b = 0; b < IB; b++) {
+            const int e = e0 + b * NT;
+            ok[b] = e < total;
+            const int c = ok[b] ? e / no : 0, o = ok[b] ? e - c * no : 0;
+            oo[b] = o;
+            cc[b] = c;
+            const int64_t x = first + o;
+            if (rowside) {
+                pth[b] = a.L + x * a.KP + 1 + a.p + c;
+                pgb[b] = a.GbR + x * a.fr + c;
+                phb[b] = a.HbR + x * a.fr + c;
+                lam[b] = c < a.q ? a.lam[1] : a.lam[2];
+            } else {
+                pth[b] = a.R + x * a.KP + (c < a.p ? 1 + c : 1 + a.q + c);
+                pgb[b] = a.GbC + x * a.fc + c;
+                phb[b] = a.HbC + x * a.fc + c;
+                lam[b] = c < a.p ? a.lam[0] : a.lam[3];
+            }
+            th[b] = ok[b] ? *pth[b] : 0.f;
+            gb[b] = ok[b] ? *pgb[b] : 0.f;
+            hb[b] = ok[b] ? *phb[b] : 1.f;
+            sg[b] = sh[b] = 0.f;
+        }
+        for (int u0 = 0; u0 < nslots; u0 += 4) {
+            float gv[IB][4], hv[IB][4];
+#pragma unroll
+            for (int b = 0; b < IB; b++)
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const bool l = ok[b] && u0 + u < nslots;
+                    const float* src = part + (size_t)(u0 + u) * slot_stride + (size_t)cc[b] * T + oo[b];
+                    gv[b][u] = l ? __ldcg(src) : 0.f;
+                    hv[b][u] = l ? __ldcg(src + (size_t)nf * T) : 0.f;
+                }
+#pragma unroll
+            for (int b = 0; b < IB; b++)
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (u0 + u < nslots) {
+                        sg[b] += gv[b][u];
+                        sh[b] += hv[b][u];
+                    }
+        }
+#pragma unroll
+        for (int b = 0; b < IB; b++) {
+            if (ok[b]) {
+                smoothed_step(th[b], gb[b], hb[b], sg[b], sh[b], scale, lam[b], a, s_rc[oo[b]]);
+                *pth[b] = th[b];
+                *pgb[b] = gb[b];
+                *phb[b] = hb[b];
+            }
+        }
+    }
 }
 
 // Arrival, strip updates and the once-per-sweep NB shape update for the tile
-// (ti, tj) of block k of sweep w, tile edge T, NT threads. Must be called by
-// every thread of every CTA of the launch (inactive CTAs included).
-template <int T, int NT>
+// (ti, tj) of block k of sweep w, tile edge T, NT threads, IB strip items in
+// flight per thread. Must be called by every thread of every CTA of the launch
+// (inactive CTAs included).
+template <int T, int NT, int IB>
 __device__ void tile_arrive_update(const StepArgs& a, int w, int k, int ti, int tj, const BlockGeo& g, int nTI,
                                    int nTJ, bool active, float s1, float s2, float alpha) {
     __shared__ int s_flag[3];
@@ -134,16 +182,8 @@ __device__ void tile_arrive_update(const StepArgs& a, int w, int k, int ti, int 
         }
         __syncthreads();
         const float scale = (float)a.m / (float)g.mJ;
-        for (int e = tid; e < nr * a.fr; e += NT) {
-            const int il = e / a.fr, c = e - il * a.fr;
-            const float* src = a.partR + ((size_t)((k * a.TI + ti) * a.TJ) * T + il) * 2 * a.fr + c;
-            float sg, sh;
-            strip_sum(src, (size_t)T * 2 * a.fr, a.fr, nTJ, sg, sh);
-            const int64_t row = row0 + il;
-            const float lam = c < a.q ? a.lam[1] : a.lam[2];
-            smoothed_step(a.L + row * a.KP + 1 + a.p + c, a.GbR + row * a.fr + c, a.HbR + row * a.fr + c, sg, sh,
-                          scale, lam, a, s_rc[il]);
-        }
+        strip_update<T, NT, IB>(a, a.partR + (size_t)((k * a.TI + ti) * a.TJ) * T * 2 * a.fr, (size_t)T * 2 * a.fr, nTJ,
+                            nr, a.fr, row0, true, scale, s_rc);
         __syncthreads();
         if (tid < nr) a.cntR[row0 + tid] = s_visits[tid];
         if (tid == 0) a.ctrR[k * a.TI + ti] = 0u;
@@ -158,17 +198,8 @@ __device__ void tile_arrive_update(const StepArgs& a, int w, int k, int ti, int 
         }
         __syncthreads();
         const float scale = (float)a.n / (float)g.nI;
-        for (int e = tid; e < nc * a.fc; e += NT) {
-            const int jl = e / a.fc, c = e - jl * a.fc;
-            const float* src = a.partC + ((size_t)((k * a.TJ + tj) * a.TI) * T + jl) * 2 * a.fc + c;
-            float sg, sh;
-            strip_sum(src, (size_t)T * 2 * a.fc, a.fc, nTI, sg, sh);
-            const int64_t col = col0 + jl;
-            const int rcol = c < a.p ? 1 + c : 1 + a.q + c;
-            const float lam = c < a.p ? a.lam[0] : a.lam[3];
-            smoothed_step(a.R + col * a.KP + rcol, a.GbC + col * a.fc + c, a.HbC + col * a.fc + c, sg, sh, scale, lam,
-                          a, s_rc[jl]);
-        }
+        strip_update<T, NT, IB>(a, a.partC + (size_t)((k * a.TJ + tj) * a.TI) * T * 2 * a.fc, (size_t)T * 2 * a.fc, nTI,
+                            nc, a.fc, col0, false, scale, s_rc);
         __syncthreads();
         if (tid < nc) a.cntC[col0 + tid] = s_visits[tid];
         if (tid == 0) a.ctrC[k * a.TJ + tj] = 0u;
