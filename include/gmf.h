@@ -214,6 +214,34 @@ int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n
 int gmf_trace(gmf_model* h, int32_t enable);
 int gmf_trace_read(gmf_model* h, double* total_ms, int64_t* launches, void* stream);
 
+/*
+ * gmf_deviance_noalloc -- the total deviance of gmf_deviance, for callers that
+ * cannot allocate device memory: code enqueued while a stream is captured into
+ * a CUDA graph (an allocation there breaks or serializes the capture), or a
+ * plug-in running inside a framework that owns all device memory through its
+ * own pool. The paper has no counterpart; this is a deployment variant of
+ * gmf_deviance that needs no handle and allocates nothing.
+ *
+ *   Y       device, n x m counts (y_dtype GMF_Y_INT32 or GMF_Y_UINT16)
+ *   W       device float32 n x m weights, or NULL (all 1)
+ *   L       device float32 n x ld, row i = [o_i, x_i', gamma_i', u_i', padding]
+ *   R       device float32 m x ld, row j = [1, beta_j', z_j', v_j', padding]
+ *   K       1 + p + q + d columns used (1..64), ld >= K
+ *   family  GMF_POISSON or GMF_NEGBIN (shape alpha > 0), eta_clamp > 0
+ *   d_out   device double: receives sum_ij D(y_ij, mu_ij), eta = L R'
+ * Asynchronous on the stream. Its scratch is a library-owned static device
+ * array of 262144 FP64 partial sums (2 MiB, held by every GPU that loads the
+ * library until the process exits), so ceil(n/64) * ceil(m/64) must not exceed
+ * 262144; larger sizes return GMF_ERR_ARG. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. All calls share the array (each call overwrites
+ * every slot it reads before reading it): calls that may overlap on the GPU
+ * race and must be ordered by the caller (same stream, or events).
+ */
+int gmf_deviance_noalloc(const void* Y, int32_t y_dtype, const float* W, int64_t n, int64_t m, const float* L,
+                         const float* R, int32_t K, int32_t ld, int32_t family, float alpha, float eta_clamp,
+                         double* d_out, void* stream);
+
 /* Release the handle and all of its device memory (NULL is allowed). */
 void gmf_free(gmf_model* h);
 

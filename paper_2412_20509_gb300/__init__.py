@@ -29,8 +29,8 @@ ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
 # Every function declared in include/gmf.h.
 EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_num_sweeps", "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
-           "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_free", "gmf_last_error",
-           "gmf_version")
+           "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
+           "gmf_free", "gmf_last_error", "gmf_version")
 
 
 class GmfError(RuntimeError):
@@ -79,6 +79,8 @@ def lib():
         "gmf_project_cells": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, VP, VP, C.c_int32, VP, VP, VP, VP]),
         "gmf_trace": (C.c_int, [VP, C.c_int32]),
         "gmf_trace_read": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), VP]),
+        "gmf_deviance_noalloc": (C.c_int, [VP, C.c_int32, VP, C.c_int64, C.c_int64, VP, VP, C.c_int32, C.c_int32,
+                                          C.c_int32, C.c_float, C.c_float, VP, VP]),
         "gmf_free": (None, [VP]),
         "gmf_last_error": (C.c_char_p, []),
         "gmf_version": (C.c_char_p, []),

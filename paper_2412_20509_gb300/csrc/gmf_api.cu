@@ -33,6 +33,9 @@ static int fail(int code, const char* fmt, ...) {
     } while (0)
 
 extern "C" const char* gmf_last_error(void) { return g_err.c_str(); }
+
+// Error reporting for gmf_noalloc.cu (same thread-local message as the ABI).
+int gmf_noalloc_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 extern "C" const char* gmf_version(void) { return "gmf-gb300 0.1 (sm_103a)"; }
 
 // tensor-core path hooks (gmf_step_tc.cu)
