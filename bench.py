@@ -127,31 +127,6 @@ def sweep_algorithmic(w, K, fr, fc):
     return entries, entries * flops_entry, entries * ybytes + pbytes
 
 
-def cpu_baseline(w, prob, start, rp, cp, sigmas, budget_s=12.0):
-    import oracle
-    settings = synth.fit_settings()
-    f = oracle.OracleFit(prob.Y, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row,
-                         nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=settings)
-    nsw = synth.n_sweeps(w.n, w.m, w.nb_row, w.nb_col)
-    per = min(-(-w.n // w.nb_row), -(-w.m // w.nb_col))
-    done = 0
-    t0 = time.perf_counter()
-    e = 0
-    while time.perf_counter() - t0 < budget_s:
-        chunk = 5
-        w0 = done % nsw
-        w1 = min(nsw, w0 + chunk)
-        f.sweeps(sigmas[e % len(sigmas)], w0, w1)
-        done += w1 - w0
-        if w1 == nsw:
-            e += 1
-    el = time.perf_counter() - t0
-    entries = done * per * w.nb_row * w.nb_col
-    return {"value": entries / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} sweeps ({done * per} blocks of {w.nb_row}x{w.nb_col}) of the same workload, "
-                      f"FP64 single-threaded C, {el:.1f} s"}
-
-
 def run_reference(args, w):
     """--impl reference: the FP64 oracle on the host cores, bounded sample per step."""
     ws, rank, _ = dist_env()
@@ -194,6 +169,48 @@ def run_reference(args, w):
     return 0
 
 
+def oracle_trajectory(wname, seed, q):
+    """Spawned process: the FP64 oracle on the same fit (same start, partitions,
+    sweep orders); returns per-epoch times and the final deviance."""
+    import oracle
+    w = synth.WORKLOADS[wname]
+    prob = synth.workload_problem(w.name, seed=seed)
+    start = synth.crude_start(prob, w.d, seed=seed)
+    rp, cp = synth.partitions(w.n, w.m, seed)
+    sig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, w.epochs, seed)
+    f = oracle.OracleFit(prob.Y, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row,
+                         nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=synth.fit_settings())
+    times = []
+    t0 = time.perf_counter()
+    for e in range(w.epochs):
+        f.epoch(sig[e])
+        times.append(time.perf_counter() - t0)
+    q.put({"final_deviance": f.deviance(), "epoch_times": times, "entries_per_epoch": w.n * w.m,
+           "epochs": w.epochs})
+
+
+def source_hash(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def committed_traffic(kernel_file, workload):
+    """dram read+write bytes per launch from the committed ncu summary of this
+    kernel and workload, if it was captured on the current kernel source."""
+    prof = os.path.join(ROOT, "profiles", f"{os.path.splitext(os.path.basename(kernel_file))[0]}_{workload}.md")
+    if not os.path.exists(prof):
+        return None
+    want = source_hash(kernel_file)
+    got, traffic = None, None
+    for line in open(prof):
+        if line.startswith("source_sha256_16:"):
+            got = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if got == want else None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,18 +218,30 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nb_medium")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttd", action="store_true", help="skip the time-to-deviance comparison")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
     if args.warmup < 3:
         raise SystemExit("warm-up must be >= 3 steps")
+    ws, rank, local = dist_env()
+    extras = rank == 0 and ws == 1
+
+    # The oracle's trajectory runs on a host core beside the GPU work; spawned
+    # before the first CUDA call.
+    oq = oproc = None
+    if extras and not (args.no_cpu_baseline and args.no_ttd):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        oq = ctx.Queue()
+        oproc = ctx.Process(target=oracle_trajectory, args=(w.name, args.seed, oq), daemon=True)
+        oproc.start()
 
     import torch
-    ws, rank, local = dist_env()
     dist = None
     if ws > 1:
         import torch.distributed as dist
@@ -232,9 +261,13 @@ def main():
     sig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, max(nsteps, 8), args.seed)
     settings = synth.fit_settings()
     Yd = torch.from_numpy(prob.Y).cuda()
-    model = gmf.Model(Yd, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row, nb_col=w.nb_col,
-                      row_perm=rp, col_perm=cp, settings=settings, precision=args.precision)
     stream = torch.cuda.current_stream()
+
+    def make(precision):
+        return gmf.Model(Yd, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row,
+                         nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=settings, precision=precision)
+
+    model = make(args.precision)
     nsw = model.num_sweeps
     n, m, p, q, d = model.dims
     K, fr, fc = 1 + p + q + d, q + d, p + d
@@ -244,21 +277,31 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---------------- device-resident throughput
+    def timed_epochs(mdl, first, count):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for s in range(count):
+            mdl.epoch(sig[first + s])
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1)
+
+    # ---------------- device-resident throughput (the headline value)
     for s in range(args.warmup):
         model.epoch(sig[s])
     dev0 = model.deviance()
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for s in range(args.steps):
-        model.epoch(sig[args.warmup + s])
-    ev1.record(stream)
-    barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms = timed_epochs(model, args.warmup, args.steps)
     clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    entries_step = n * m
+    value = ws * entries_step * args.steps / (elapsed_ms / 1e3)
+    dev1 = model.deviance()
     # Kernel-level timing of the dominant kernel: the same steps again, each
     # block-step launch bracketed by CUDA events on its stream.
     model.trace(True)
@@ -267,13 +310,6 @@ def main():
         model.epoch(sig[args.warmup + s])
     kern_ms, launches = model.trace_read()
     model.trace(False)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    entries_step = n * m
-    value = ws * entries_step * args.steps / (elapsed_ms / 1e3)
-    dev1 = model.deviance()
 
     # ---------------- end to end through the public API from pinned host memory
     Yh = torch.from_numpy(prob.Y).pin_memory()
@@ -295,43 +331,95 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = ws * entries_step * e2e_steps / e2e_s
+    del model
 
-    # ---------------- roofline of the dominant kernel (the block-step launch)
+    # ---------------- roofline of the dominant kernel (one block-step launch = one sweep)
     peaks, peak_src = measured_peaks()
     ent_sweep, flops_sweep, bytes_sweep = sweep_algorithmic(w, K, fr, fc)
     avg_kernel_s = (kern_ms / max(launches, 1)) / 1e3
+    algo = {"entries": ent_sweep, "flops": flops_sweep, "bytes": bytes_sweep}
     if args.precision == "fp32":
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = fp32_simt_peak_tflops(sm_mhz)
         achieved = flops_sweep / avg_kernel_s / 1e12
+        kfile = os.path.join(ROOT, "paper_2412_20509_gb300", "csrc", "gmf_step_simt.cu")
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "sweep_kernel (FP32 CUDA cores)",
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
-                "hbm_gbs": bytes_sweep / avg_kernel_s / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
-                "hbm_frac": bytes_sweep / avg_kernel_s / 1e9 / peaks["hbm_gbs"],
-                "avg_launch_us": avg_kernel_s * 1e6, "launches": launches,
-                "algorithmic_per_launch": {"entries": ent_sweep, "flops": flops_sweep, "bytes": bytes_sweep}}
+                "traffic": committed_traffic(kfile, w.name), "kernel": "sweep_kernel (FP32 CUDA cores)",
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
+                "hbm_gbs": bytes_sweep / avg_kernel_s / 1e9, "hbm_frac_of_measured": bytes_sweep / avg_kernel_s / 1e9 / peaks["hbm_gbs"]}
     else:
-        achieved = flops_sweep / avg_kernel_s / 1e12
-        peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "tcgen05 block step", "peak_source": f"{peak_src} bf16 (sustained)",
-                "hbm_gbs": bytes_sweep / avg_kernel_s / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
-                "hbm_frac": bytes_sweep / avg_kernel_s / 1e9 / peaks["hbm_gbs"],
-                "avg_launch_us": avg_kernel_s * 1e6, "launches": launches,
-                "algorithmic_per_launch": {"entries": ent_sweep, "flops": flops_sweep, "bytes": bytes_sweep}}
+        achieved = bytes_sweep / avg_kernel_s / 1e9
+        peak = float(peaks["hbm_gbs"])
+        kfile = os.path.join(ROOT, "paper_2412_20509_gb300", "csrc", "gmf_step_tc.cu")
+        tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": committed_traffic(kfile, w.name), "kernel": "sweep_tc_kernel (tcgen05)",
+                "peak_source": f"{peak_src} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
+                "tensor_tflops": flops_sweep / avg_kernel_s / 1e12, "tensor_peak_tflops": tc_peak,
+                "tensor_frac_of_measured": flops_sweep / avg_kernel_s / 1e12 / tc_peak}
+    roof.update({"avg_launch_us": avg_kernel_s * 1e6, "launches_timed": launches, "algorithmic_per_launch": algo})
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3+bf16/f32",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if args.precision == "fp32" else "bf16x3 eta + bf16 contractions, f32 accumulate/epilogue",
            "data": "synthetic (seeded NB GMF law; stands in for scRNA-seq counts)",
            "config": describe(w, args.precision), "roofline": roof,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(prob.Y.nbytes + 4 * nsw),
                    "d2h_bytes_per_step": 8 + 4},
            "gpu_launches": int(nsw * args.steps), "clocks": clk,
            "deviance": {"after_warmup": dev0, "after_timed_steps": dev1}}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, prob, start, rp, cp, sig)
+
+    if extras:
+        # ---------------- the other precision on the same workload
+        other = "fp32" if args.precision == "mixed" else "mixed"
+        mo = make(other)
+        for s in range(args.warmup):
+            mo.epoch(sig[s])
+        oms = timed_epochs(mo, args.warmup, args.steps)
+        out[f"{other}_path"] = {"value": entries_step * args.steps / (oms / 1e3), "ms_per_step": oms / args.steps}
+        del mo
+        # ---------------- time to the oracle's deviance (within 1e-3), both paths, fresh starts
+        traj = {}
+        if not args.no_ttd:
+            tsig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, w.epochs, args.seed)
+            for prec in ("mixed", "fp32"):
+                mdl = make(prec)
+                devbuf = torch.zeros(w.epochs, dtype=torch.float64, device="cuda")
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(w.epochs + 1)]
+                barrier()
+                evs[0].record(stream)
+                for e in range(w.epochs):
+                    mdl.epoch(tsig[e])
+                    mdl.deviance_async(devbuf[e:e + 1])
+                    evs[e + 1].record(stream)
+                barrier()
+                cum = [evs[0].elapsed_time(evs[e + 1]) / 1e3 for e in range(w.epochs)]
+                traj[prec] = (devbuf.cpu().numpy().tolist(), cum)
+                del mdl
+        ores = None
+        if oproc is not None:
+            ores = oq.get(timeout=900)
+            oproc.join(timeout=60)
+        if ores is not None and not args.no_ttd:
+            target = ores["final_deviance"] * (1 + 1e-3)
+            ttd = {"oracle_final_deviance": ores["final_deviance"], "target": target, "epochs": w.epochs,
+                   "includes_per_epoch_deviance": True, "start": "crude start (synth.crude_start), same sweep orders"}
+            for prec, (devs, cum) in traj.items():
+                hit = next((e for e, dv in enumerate(devs) if dv <= target), None)
+                ttd[prec] = {"seconds": None if hit is None else cum[hit], "epochs": None if hit is None else hit + 1,
+                             "final_deviance": devs[-1],
+                             "final_rel_gap_to_oracle": devs[-1] / ores["final_deviance"] - 1.0}
+            if ttd["mixed"]["seconds"] and ttd["fp32"]["seconds"]:
+                ttd["fp32_over_mixed"] = ttd["fp32"]["seconds"] / ttd["mixed"]["seconds"]
+            out["time_to_deviance"] = ttd
+        if ores is not None and not args.no_cpu_baseline:
+            times = ores["epoch_times"]
+            k = next((i + 1 for i, t in enumerate(times) if t >= 12.0), len(times))
+            out["cpu_baseline"] = {"value": k * ores["entries_per_epoch"] / times[k - 1], "unit": UNIT, "cores": 1,
+                                   "kind": "oracle",
+                                   "sample": f"first {k} epochs ({k * ores['entries_per_epoch']:.3g} entries) of the "
+                                             f"same fit, FP64 single-threaded C on one host core, {times[k - 1]:.1f} s"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
