@@ -189,26 +189,38 @@ def oracle_trajectory(wname, seed, q):
            "epochs": w.epochs})
 
 
-def source_hash(path):
+def source_hash(paths):
     import hashlib
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel_file, workload):
+KERNEL_SOURCES = {
+    "sweep_tc_kernel": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
+    "sweep_kernel": ["gmf_step_simt.cu", "gmf_update.cuh", "gmf_internal.cuh"],
+}
+
+
+def kernel_hash(kernel):
+    return source_hash([os.path.join(ROOT, "paper_2412_20509_gb300", "csrc", f) for f in KERNEL_SOURCES[kernel]])
+
+
+def committed_traffic(kernel, workload):
     """dram read+write bytes per launch from the committed ncu summary of this
-    kernel and workload, if it was captured on the current kernel source."""
-    prof = os.path.join(ROOT, "profiles", f"{os.path.splitext(os.path.basename(kernel_file))[0]}_{workload}.md")
+    kernel and workload, if it was captured on the current kernel sources."""
+    prof = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(prof):
         return None
-    want = source_hash(kernel_file)
     got, traffic = None, None
     for line in open(prof):
         if line.startswith("source_sha256_16:"):
             got = line.split(":", 1)[1].strip()
         if line.startswith("dram_bytes_per_launch:"):
             traffic = float(line.split(":", 1)[1].strip())
-    return traffic if got == want else None
+    return traffic if got == kernel_hash(kernel) else None
 
 
 def main():
@@ -342,18 +354,16 @@ def main():
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = fp32_simt_peak_tflops(sm_mhz)
         achieved = flops_sweep / avg_kernel_s / 1e12
-        kfile = os.path.join(ROOT, "paper_2412_20509_gb300", "csrc", "gmf_step_simt.cu")
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": committed_traffic(kfile, w.name), "kernel": "sweep_kernel (FP32 CUDA cores)",
+                "traffic": committed_traffic("sweep_kernel", w.name), "kernel": "sweep_kernel (FP32 CUDA cores)",
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
                 "hbm_gbs": bytes_sweep / avg_kernel_s / 1e9, "hbm_frac_of_measured": bytes_sweep / avg_kernel_s / 1e9 / peaks["hbm_gbs"]}
     else:
         achieved = bytes_sweep / avg_kernel_s / 1e9
         peak = float(peaks["hbm_gbs"])
-        kfile = os.path.join(ROOT, "paper_2412_20509_gb300", "csrc", "gmf_step_tc.cu")
         tc_peak = float(peaks.get("bf16_tflops", 1900.0))
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": committed_traffic(kfile, w.name), "kernel": "sweep_tc_kernel (tcgen05)",
+                "traffic": committed_traffic("sweep_tc_kernel", w.name), "kernel": "sweep_tc_kernel (tcgen05)",
                 "peak_source": f"{peak_src} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
                 "tensor_tflops": flops_sweep / avg_kernel_s / 1e12, "tensor_peak_tflops": tc_peak,
                 "tensor_frac_of_measured": flops_sweep / avg_kernel_s / 1e12 / tc_peak}
