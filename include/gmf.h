@@ -191,8 +191,10 @@ int gmf_orthogonalize(gmf_model* h, int32_t mode, void* stream);
  * problem of Sec. 3 (rows separate given V) by n_steps exact Fisher-scoring
  * steps on theta_i = [gamma_i, u_i] (the row step of AIRWLS, Sec. 3.1):
  *   theta <- theta + (R' diag(Dddot_i) R + Lambda)^-1 (R' Ddot_i - Lambda theta),  R = [Z, V].
- * Start: u_i = U_start row (NULL: zeros), gamma_i (q = 1 only) in closed form
- * log(sum_j y_ij / sum_j exp(eta_ij without gamma)); for q != 1, gamma = 0.
+ * Start: u_i = U_start row (NULL: zeros); gamma_i0 (the first Z column, exact
+ * when it is the intercept) in closed form log(max(sum_j y_ij, 0.5) /
+ * sum_j exp(eta_ij without gamma)), the other gamma 0. Requires 1 <= q + d <= 32.
+ * Ynew columns are genes in the caller's original order.
  *   Ynew      device, n_new x m counts (y_dtype)
  *   Xnew      device float32, n_new x p;  offset_new: device float32 n_new or NULL
  *   U_start   device float32 n_new x d or NULL

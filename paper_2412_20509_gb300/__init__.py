@@ -281,9 +281,11 @@ class Model:
         U = torch.empty((n_new, d), dtype=torch.float32, device=dev)
         G = torch.empty((n_new, q), dtype=torch.float32, device=dev)
         D = torch.empty((n_new,), dtype=torch.float32, device=dev) if with_dev else None
+        Yc = Ynew.contiguous()
         Xf = Xnew.to(torch.float32).contiguous()
         of = None if offset_new is None else offset_new.to(torch.float32).contiguous()
         us = None if U_start is None else U_start.to(torch.float32).contiguous()
-        check(lib().gmf_project_cells(self._h, _ptr(Ynew.contiguous()), ydt, n_new, _ptr(Xf), _ptr(of), _ptr(us),
+        check(lib().gmf_project_cells(self._h, _ptr(Yc), ydt, n_new, _ptr(Xf), _ptr(of), _ptr(us),
                                       int(n_steps), _ptr(U), _ptr(G), _ptr(D), _stream(stream)))
+        self._keep_proj = (Yc, Xf, of, us)
         return U, G, D

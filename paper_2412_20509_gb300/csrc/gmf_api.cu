@@ -111,7 +111,7 @@ static void release(gmf_model* h) {
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->tc) gmf_tc_free(h);
     void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
-                    h->rperm, h->cperm, h->ystage, h->partR, h->partC, h->ctrR, h->ctrC, h->ctrSweep,
+                    h->rperm, h->cperm, h->ystage, h->Rorig, h->partR, h->partC, h->ctrR, h->ctrC, h->ctrSweep,
                     h->nbpart, h->sigma, h->rhoc, h->rho1, h->err, h->devpart, h->devtot};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -85,6 +85,7 @@ struct gmf_model {
     int* rperm;
     int* cperm;
     void* ystage;               // staging for counts uploaded from the host
+    float* Rorig;               // m x KP: R in the caller's gene order (per-cell projection)
     float* partR;
     float* partC;
     unsigned* ctrR;
