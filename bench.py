@@ -223,6 +223,59 @@ def committed_traffic(kernel, workload):
     return traffic if got == kernel_hash(kernel) else None
 
 
+RANKS = [2, 5, 10, 15, 20, 30, 40, 50]
+
+
+def run_rank_sweep(args, w):
+    """--workload nb_sweep: 8 ranks on one 50000 x 3000 NB matrix, batched (one
+    launch per sweep for all models) vs the same 8 fits one after another."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as gmf
+    prob = synth.workload_problem(w.name, seed=args.seed)
+    rp, cp = synth.partitions(w.n, w.m, args.seed)
+    starts = [synth.crude_start(prob, d, seed=args.seed) for d in RANKS]
+    sig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, args.warmup + args.steps, args.seed)
+    kw = dict(family=w.family, nb_row=w.nb_row, nb_col=w.nb_col, row_perm=rp, col_perm=cp,
+              settings=synth.fit_settings(), precision=args.precision)
+    Yd = torch.from_numpy(prob.Y.view(np.int16)).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(run):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    sw = gmf.Sweep(prob.Y, prob.X, prob.Z, prob.offset, starts, RANKS, **kw)
+    for s in range(args.warmup):
+        sw.epoch(sig[s])
+    ms_b = timed(lambda: [sw.epoch(sig[args.warmup + s]) for s in range(args.steps)])
+    devs_b = [mdl.deviance() for mdl in sw.models]
+    del sw
+    solo = [gmf.Model(prob.Y, prob.X, prob.Z, prob.offset, st, **kw) for st in starts]
+    for mdl in solo:
+        for s in range(args.warmup):
+            mdl.epoch(sig[s])
+    ms_s = timed(lambda: [mdl.epoch(sig[args.warmup + s]) for mdl in solo for s in range(args.steps)])
+    devs_s = [mdl.deviance() for mdl in solo]
+    work = len(RANKS) * w.n * w.m * args.steps
+    out = {"metric": "rank sweep: model x matrix entries/s, 8 ranks d in {2,5,10,15,20,30,40,50}",
+           "value": work / (ms_b / 1e3), "unit": "model-entries/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
+           "config": {"workload": f"{w.name}: NB {w.n}x{w.m} uint16, blocks {w.nb_row}x{w.nb_col}, step = one epoch "
+                                  f"of all 8 models", "precision": args.precision},
+           "sequential": {"value": work / (ms_s / 1e3), "ms_per_step": ms_s / args.steps},
+           "batched_over_sequential": ms_s / ms_b,
+           "deviance_batched_equals_sequential": devs_b == devs_s}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -238,6 +291,8 @@ def main():
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.workload == "nb_sweep":
+        return run_rank_sweep(args, w)
     if args.warmup < 3:
         raise SystemExit("warm-up must be >= 3 steps")
     ws, rank, local = dist_env()

@@ -207,6 +207,33 @@ int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n
                       int32_t n_steps, float* U_out, float* G_out, float* dev_out, void* stream);
 
 /*
+ * Batched rank sweep: fits of the same model with different latent ranks on one
+ * count matrix (the grid of fits that rank selection by information criteria or
+ * held-out deviance needs, Sec. 4.2).
+ *
+ * gmf_sweep_init -- arguments as gmf_init, for n_models models of ranks
+ * d_list[0..n_models-1] (cfg->d is ignored). The starting values are arrays of
+ * n_models host pointers: B0[i] m x p, G0[i] n x q, U0[i] n x d_list[i],
+ * V0[i] m x d_list[i], alpha0[i]. The counts, weights and partitions are stored
+ * once and read by every model. Synchronous.
+ * gmf_sweep_epoch -- one epoch of every model (same sigma semantics as
+ * gmf_sgd_epoch): one launch per sweep covers all models, heaviest first.
+ * Results equal running each model's own gmf_sgd_epoch.
+ * gmf_sweep_model -- the i-th model's handle, owned by the sweep and valid until
+ * gmf_sweep_free, for gmf_deviance, gmf_get_params, gmf_orthogonalize, ...
+ * (NULL if i is out of range). gmf_update_y is not allowed on models i > 0.
+ */
+typedef struct gmf_sweep gmf_sweep;
+int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int32_t* d_list, int32_t n_models, const void* Y,
+                   int32_t y_dtype, int32_t y_on_device, const float* W, const double* X, const double* Z,
+                   const double* offset, const int32_t* row_perm, const int32_t* col_perm, const double* const* B0,
+                   const double* const* G0, const double* const* U0, const double* const* V0, const double* alpha0,
+                   void* stream);
+int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream);
+gmf_model* gmf_sweep_model(gmf_sweep* s, int32_t i);
+void gmf_sweep_free(gmf_sweep* s);
+
+/*
  * gmf_trace -- enable (1) or disable (0) timing of the block-step kernels:
  * while enabled, every block-step launch is bracketed by CUDA events recorded
  * on the launching stream. gmf_trace_read synchronizes the stream, returns the

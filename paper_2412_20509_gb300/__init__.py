@@ -30,7 +30,8 @@ ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
 EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_num_sweeps", "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
-           "gmf_free", "gmf_last_error", "gmf_version")
+           "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_model", "gmf_sweep_free", "gmf_free", "gmf_last_error",
+           "gmf_version")
 
 
 class GmfError(RuntimeError):
@@ -81,6 +82,11 @@ def lib():
         "gmf_trace_read": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), VP]),
         "gmf_deviance_noalloc": (C.c_int, [VP, C.c_int32, VP, C.c_int64, C.c_int64, VP, VP, C.c_int32, C.c_int32,
                                           C.c_int32, C.c_float, C.c_float, VP, VP]),
+        "gmf_sweep_init": (C.c_int, [C.POINTER(VP), C.POINTER(gmf_config), VP, C.c_int32, VP, C.c_int32, C.c_int32, VP,
+                                     VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP]),
+        "gmf_sweep_epoch": (C.c_int, [VP, VP, VP]),
+        "gmf_sweep_model": (VP, [VP, C.c_int32]),
+        "gmf_sweep_free": (None, [VP]),
         "gmf_free": (None, [VP]),
         "gmf_last_error": (C.c_char_p, []),
         "gmf_version": (C.c_char_p, []),
@@ -177,8 +183,20 @@ class Model:
         self._keep = None
         self.y_dtype = ydt
 
+    @classmethod
+    def _borrow(cls, handle, dims, owner):
+        """A view of a handle owned by someone else (e.g. one model of a Sweep)."""
+        obj = cls.__new__(cls)
+        obj._h = VP(handle)
+        obj.dims = dims
+        obj._owner = owner
+        obj._borrowed = True
+        return obj
+
     def __del__(self):
         h = getattr(self, "_h", None)
+        if getattr(self, "_borrowed", False):
+            return
         if h is not None and h.value and _lib is not None:
             _lib.gmf_free(h)
             self._h = VP()
@@ -289,3 +307,55 @@ class Model:
                                       int(n_steps), _ptr(U), _ptr(G), _ptr(D), _stream(stream)))
         self._keep_proj = (Yc, Xf, of, us)
         return U, G, D
+
+
+class Sweep:
+    """Fits of several latent ranks on one count matrix, advanced together by
+    one launch per sweep (a ``gmf_sweep`` handle)."""
+
+    def __init__(self, Y, X, Z, offset, starts, d_list, *, family, nb_row, nb_col, row_perm, col_perm, settings,
+                 precision="fp32", W=None, stream=None):
+        import torch
+        self._h = VP()
+        on_dev = isinstance(Y, torch.Tensor) and Y.is_cuda
+        if isinstance(Y, torch.Tensor):
+            n, m = Y.shape
+            ydt = GMF_Y_INT32 if Y.dtype == torch.int32 else GMF_Y_UINT16
+            Y = Y.contiguous()
+        else:
+            Y = np.ascontiguousarray(Y)
+            n, m = Y.shape
+            ydt = GMF_Y_INT32 if Y.dtype == np.int32 else GMF_Y_UINT16
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        p, q = X.shape[1], Z.shape[1]
+        d_list = [int(d) for d in d_list]
+        nm = len(d_list)
+        cfg = make_config(n, m, p, q, 0, family, nb_row, nb_col, settings, precision)
+        off = None if offset is None else np.ascontiguousarray(offset, dtype=np.float64)
+        arrs = [dict(B=_f64(st["B"], (m, p)), G=_f64(st["Gamma"], (n, q)), U=_f64(st["U"], (n, d)),
+                     V=_f64(st["V"], (m, d))) for st, d in zip(starts, d_list)]
+        ptrs = {k: (C.c_void_p * nm)(*[a[k].ctypes.data for a in arrs]) for k in ("B", "G", "U", "V")}
+        alph = np.array([float(st.get("alpha", 1.0)) for st in starts])
+        dl = np.array(d_list, dtype=np.int32)
+        rp = np.ascontiguousarray(row_perm, dtype=np.int32)
+        cp = np.ascontiguousarray(col_perm, dtype=np.int32)
+        if W is not None:
+            W = W.to(torch.float32).contiguous() if on_dev else np.ascontiguousarray(W, dtype=np.float32)
+        check(lib().gmf_sweep_init(C.byref(self._h), C.byref(cfg), dl.ctypes.data, nm, _ptr(Y), ydt, int(on_dev),
+                                   _ptr(W), _ptr(X), _ptr(Z), _ptr(off), _ptr(rp), _ptr(cp), C.addressof(ptrs["B"]),
+                                   C.addressof(ptrs["G"]), C.addressof(ptrs["U"]), C.addressof(ptrs["V"]),
+                                   alph.ctypes.data, _stream(stream)))
+        self.models = [Model._borrow(lib().gmf_sweep_model(self._h, i), (n, m, p, q, d), self)
+                       for i, d in enumerate(d_list)]
+        self.d_list = d_list
+
+    def epoch(self, sigma, stream=None):
+        sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+        check(lib().gmf_sweep_epoch(self._h, sigma.ctypes.data, _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.gmf_sweep_free(h)
+            self._h = VP()

@@ -110,6 +110,11 @@ static void release(gmf_model* h) {
     if (h->epoch_graph) cudaGraphExecDestroy(h->epoch_graph);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->tc) gmf_tc_free(h);
+    if (h->y_shared) {  // owned by another handle
+        h->Yp = nullptr;
+        h->Wp = nullptr;
+        h->ystage = nullptr;
+    }
     void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
                     h->rperm, h->cperm, h->ystage, h->Rorig, h->partR, h->partC, h->ctrR, h->ctrC, h->ctrSweep,
                     h->nbpart, h->sigma, h->rhoc, h->rho1, h->err, h->devpart, h->devtot};
@@ -159,10 +164,23 @@ static int upload_y(gmf_model* h, const void* Y, int on_device, cudaStream_t st)
     return GMF_OK;
 }
 
-extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, int32_t y_dtype, int32_t y_on_device,
-                        const float* W, const double* X, const double* Z, const double* offset,
-                        const int32_t* row_perm, const int32_t* col_perm, const double* B0, const double* G0,
-                        const double* U0, const double* V0, double alpha0, void* stream) {
+// gmf_init, or (share != nullptr) a handle that reads the count matrix, the
+// weights and the partitions of `share` instead of owning copies.
+static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int32_t y_dtype, int32_t y_on_device,
+                     const float* W, const double* X, const double* Z, const double* offset,
+                     const int32_t* row_perm, const int32_t* col_perm, const double* B0, const double* G0,
+                     const double* U0, const double* V0, double alpha0, void* stream, const gmf_model* share) {
+    if (share) {
+        Y = share->Yp;
+        y_dtype = share->y16 ? GMF_Y_UINT16 : GMF_Y_INT32;
+        y_on_device = 1;
+        W = share->Wp;
+        row_perm = share->h_rperm;
+        col_perm = share->h_cperm;
+        if (cfg && (cfg->n != share->n || cfg->m != share->m || cfg->nb_row != share->cfg.nb_row ||
+                    cfg->nb_col != share->cfg.nb_col))
+            return fail(GMF_ERR_ARG, "gmf_init: a shared count matrix needs the same n, m and minibatch sizes");
+    }
     if (!out) return fail(GMF_ERR_ARG, "gmf_init: out is NULL");
     *out = nullptr;
     if (!cfg) return fail(GMF_ERR_ARG, "gmf_init: cfg is NULL");
@@ -231,8 +249,14 @@ extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, i
 #define INIT_CUDA(expr) INIT_TRY(([&]() -> int { CUDA_TRY(expr); return GMF_OK; })())
 
     const size_t nm = (size_t)c.n * c.m;
-    INIT_CUDA(cudaMalloc(&h->Yp, nm * (h->y16 ? 2 : 4)));
-    if (W) INIT_CUDA(dalloc(&h->Wp, nm));
+    if (share) {
+        h->Yp = share->Yp;
+        h->Wp = share->Wp;
+        h->y_shared = 1;
+    } else {
+        INIT_CUDA(cudaMalloc(&h->Yp, nm * (h->y16 ? 2 : 4)));
+        if (W) INIT_CUDA(dalloc(&h->Wp, nm));
+    }
     INIT_CUDA(dalloc(&h->L, (size_t)c.n * h->KP));
     INIT_CUDA(dalloc(&h->R, (size_t)c.m * h->KP));
     INIT_CUDA(dalloc(&h->GbR, (size_t)c.n * h->fr));
@@ -279,8 +303,8 @@ extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, i
         INIT_CUDA(cudaMemcpyAsync(h->R, R.data(), sizeof(float) * R.size(), cudaMemcpyHostToDevice, st));
         INIT_CUDA(cudaStreamSynchronize(st));
     }
-    INIT_TRY(upload_y(h, Y, y_on_device, st));
-    if (W) {
+    if (!share) INIT_TRY(upload_y(h, Y, y_on_device, st));
+    if (W && !share) {
         float* wsrc = (float*)W;
         float* wtmp = nullptr;
         if (!y_on_device) {
@@ -306,8 +330,26 @@ extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, i
     return GMF_OK;
 }
 
+extern "C" int gmf_init(gmf_model** out, const gmf_config* cfg, const void* Y, int32_t y_dtype, int32_t y_on_device,
+                        const float* W, const double* X, const double* Z, const double* offset,
+                        const int32_t* row_perm, const int32_t* col_perm, const double* B0, const double* G0,
+                        const double* U0, const double* V0, double alpha0, void* stream) {
+    return init_impl(out, cfg, Y, y_dtype, y_on_device, W, X, Z, offset, row_perm, col_perm, B0, G0, U0, V0, alpha0,
+                     stream, nullptr);
+}
+
+int gmf_init_shared(gmf_model** out, const gmf_config* cfg, const gmf_model* owner, const double* X, const double* Z,
+                    const double* offset, const double* B0, const double* G0, const double* U0, const double* V0,
+                    double alpha0, void* stream) {
+    return init_impl(out, cfg, nullptr, 0, 1, nullptr, X, Z, offset, nullptr, nullptr, B0, G0, U0, V0, alpha0, stream,
+                     owner);
+}
+
+int gmf_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, void* stream) {
     if (!h || !Y) return fail(GMF_ERR_ARG, "gmf_update_y: NULL argument");
+    if (h->y_shared) return fail(GMF_ERR_STATE, "gmf_update_y: this handle reads another handle's counts");
     cudaStream_t st = (cudaStream_t)stream;
     int rc = upload_y(h, Y, y_on_device, st);
     if (rc) return rc;
@@ -331,30 +373,37 @@ static int trace_collect(gmf_model* h, cudaStream_t st) {
     return GMF_OK;
 }
 
+// Copy the epoch's sweep offsets and the step factors of every block of the
+// range [w_begin, w_end) to the device, in FP64 on the host: block k of sweep w
+// has t = t_now + (w - w_begin) * per + k + 1.
+int gmf_stage_schedule(gmf_model* h, const int32_t* sigma, int w_begin, int w_end, cudaStream_t st) {
+    const gmf_config& c = h->cfg;
+    std::vector<float> rc((size_t)h->nsw * h->per, 0.f), r1((size_t)h->nsw, 0.f);
+    for (int w = w_begin; w < w_end; w++) {
+        for (int k = 0; k < h->per; k++) {
+            const double t = (double)(h->t + (int64_t)(w - w_begin) * h->per + k + 1);
+            const double rho = c.k0 / pow(1.0 + c.k0 * c.k1 * t, c.tau);
+            const double ct = c.bias_corr == 0 ? (1.0 - pow(c.a2, t)) / (1.0 - pow(c.a1, t)) : 1.0;
+            rc[(size_t)w * h->per + k] = (float)(rho * ct);
+            if (k == 0) r1[w] = (float)rho;
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->rhoc, rc.data(), sizeof(float) * rc.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->rho1, r1.data(), sizeof(float) * r1.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->sigma, sigma, sizeof(int32_t) * h->nsw, cudaMemcpyHostToDevice, st));
+    return GMF_OK;
+}
+
 extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begin, int32_t w_end, void* stream) {
     if (!h || !sigma) return fail(GMF_ERR_ARG, "gmf_sgd_sweeps: NULL argument");
     if (w_begin < 0 || w_end > h->nsw || w_begin > w_end)
         return fail(GMF_ERR_ARG, "gmf_sgd_sweeps: sweep range [%d, %d) outside [0, %d)", w_begin, w_end, h->nsw);
     if (!is_perm(sigma, h->nsw)) return fail(GMF_ERR_ARG, "gmf_sgd_sweeps: sigma is not a permutation of 0..%d", h->nsw - 1);
     cudaStream_t st = (cudaStream_t)stream;
-    // Step factors of every block of the range, in FP64 on the host: block k of
-    // sweep w has t = t_now + (w - w_begin) * per + k + 1.
     {
-        const gmf_config& c = h->cfg;
-        std::vector<float> rc((size_t)h->nsw * h->per, 0.f), r1((size_t)h->nsw, 0.f);
-        for (int w = w_begin; w < w_end; w++) {
-            for (int k = 0; k < h->per; k++) {
-                const double t = (double)(h->t + (int64_t)(w - w_begin) * h->per + k + 1);
-                const double rho = c.k0 / pow(1.0 + c.k0 * c.k1 * t, c.tau);
-                const double ct = c.bias_corr == 0 ? (1.0 - pow(c.a2, t)) / (1.0 - pow(c.a1, t)) : 1.0;
-                rc[(size_t)w * h->per + k] = (float)(rho * ct);
-                if (k == 0) r1[w] = (float)rho;
-            }
-        }
-        CUDA_TRY(cudaMemcpyAsync(h->rhoc, rc.data(), sizeof(float) * rc.size(), cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaMemcpyAsync(h->rho1, r1.data(), sizeof(float) * r1.size(), cudaMemcpyHostToDevice, st));
+        const int rc = gmf_stage_schedule(h, sigma, w_begin, w_end, st);
+        if (rc) return rc;
     }
-    CUDA_TRY(cudaMemcpyAsync(h->sigma, sigma, sizeof(int32_t) * h->nsw, cudaMemcpyHostToDevice, st));
     const StepArgs a = gmf_make_args(h);
     // A whole epoch replays one captured graph of its sweep launches (the
     // launches read sigma and the step factors from the buffers filled above).

@@ -86,6 +86,7 @@ struct gmf_model {
     int* cperm;
     void* ystage;               // staging for counts uploaded from the host
     float* Rorig;               // m x KP: R in the caller's gene order (per-cell projection)
+    int y_shared;               // Yp / Wp belong to another handle (rank sweep)
     float* partR;
     float* partC;
     unsigned* ctrR;
@@ -116,6 +117,13 @@ struct gmf_model {
 };
 
 #define GMF_TRACE_POOL 512
+
+// gmf_api.cu
+int gmf_stage_schedule(gmf_model* h, const int32_t* sigma, int w_begin, int w_end, cudaStream_t st);
+int gmf_init_shared(gmf_model** out, const gmf_config* cfg, const gmf_model* owner, const double* X, const double* Z,
+                    const double* offset, const double* B0, const double* G0, const double* U0, const double* V0,
+                    double alpha0, void* stream);
+int gmf_fail(int code, const char* msg);
 
 // gmf_step_simt.cu
 StepArgs gmf_make_args(gmf_model* h);

@@ -183,12 +183,11 @@ __device__ __forceinline__ Smem carve(float* base, int K, int FRP, int FCP) {
     return s;
 }
 
-__global__ void __launch_bounds__(GMF_THREADS, 3) sweep_kernel(StepArgs a, int w) {
-    extern __shared__ __align__(16) float smem[];
+__device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float* smem) {
     const int FRP = (a.fr + 3) & ~3, FCP = (a.fc + 3) & ~3;
     const Smem S = carve(smem, a.KP, FRP, FCP);
     const int tid = threadIdx.x;
-    const int tj = blockIdx.x, ti = blockIdx.y, k = blockIdx.z;
+    const int tj = blockIdx.x, ti = blockIdx.y;
     const BlockGeo g = block_geo(a, w, k);
     const int nTI = (int)((g.nI + T - 1) / T), nTJ = (int)((g.mJ + T - 1) / T);
     const bool active = ti < nTI && tj < nTJ;
@@ -274,6 +273,21 @@ __global__ void __launch_bounds__(GMF_THREADS, 3) sweep_kernel(StepArgs a, int w
     }
 
     tile_arrive_update<T, GMF_THREADS, 2>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
+}
+
+__global__ void __launch_bounds__(GMF_THREADS, 3) sweep_kernel(StepArgs a, int w) {
+    extern __shared__ __align__(16) float smem[];
+    simt_tile(a, w, blockIdx.z, smem);
+}
+
+// Several models sharing the count matrix: blockIdx.z = slot * per + k (see sweep_tc_multi).
+__global__ void __launch_bounds__(GMF_THREADS, 2) sweep_multi(const StepArgs* __restrict__ av,
+                                                             const int* __restrict__ order, int per, int w) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ StepArgs s_a;
+    if (threadIdx.x == 0) s_a = av[order[blockIdx.z / per]];
+    __syncthreads();
+    simt_tile(s_a, w, blockIdx.z % per, smem);
 }
 
 // Unit deviance 2w[...] of Table S1 / App. B in FP32, written so that no
@@ -438,6 +452,20 @@ cudaError_t gmf_sweep_simt_attr(gmf_model* h) {
     const size_t smem = sweep_smem(h->K, h->fr, h->fc);
     if (smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+size_t gmf_sweep_simt_smem(const gmf_model* h) { return sweep_smem(h->K, h->fr, h->fc); }
+
+cudaError_t gmf_simt_multi_attr(size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(sweep_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t gmf_simt_launch_multi(const gmf_model* h0, const StepArgs* d_args, const int* d_order, int nmodels,
+                                  size_t smem, int w, cudaStream_t st) {
+    dim3 grid(h0->TJ, h0->TI, h0->per * nmodels);
+    sweep_multi<<<grid, GMF_THREADS, smem, st>>>(d_args, d_order, h0->per, w);
+    return cudaGetLastError();
 }
 
 cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaStream_t st) {

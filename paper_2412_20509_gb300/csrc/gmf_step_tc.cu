@@ -79,15 +79,16 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, unsigne
     return __syncthreads_and(ok) != 0;
 }
 
+// One tile (blockIdx.x, blockIdx.y) of block k of sweep w for the model whose
+// arguments are a / Lo.
 template <bool Y16>
-__global__ void __launch_bounds__(NTH, 1)
-    sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
-    extern __shared__ __align__(1024) uint8_t smraw[];
+__device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, const CUtensorMap* ymap_p, int w,
+                                        int k, uint8_t* smraw) {
     __shared__ uint64_t bars[3];
     __shared__ uint32_t tmem_base;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tj = blockIdx.x, ti = blockIdx.y, k = blockIdx.z;
+    const int tj = blockIdx.x, ti = blockIdx.y;
     const BlockGeo g = block_geo(a, w, k);
     const int nTI = (int)((g.nI + TT - 1) / TT), nTJ = (int)((g.mJ + TT - 1) / TT);
     const bool active = ti < nTI && tj < nTJ;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(NTH, 1)
             mbar_arrive_expect_tx(&bars[0], Lo.y_bytes);
             const int nbox = TT / Lo.JB;
             for (int b = 0; b < nbox; b++)
-                tma_load_2d(Ys + b * ATOM, &ymap, (int)(col0 + (int64_t)b * Lo.JB), (int)row0, &bars[0]);
+                tma_load_2d(Ys + b * ATOM, ymap_p, (int)(col0 + (int64_t)b * Lo.JB), (int)row0, &bars[0]);
         }
 
         // ---- operands. Thread groups of 128: L rows -> eta A; R rows -> eta B;
@@ -341,6 +342,31 @@ __global__ void __launch_bounds__(NTH, 1)
     tile_arrive_update<TT, NTH, 4>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
 }
 
+template <bool Y16>
+__global__ void __launch_bounds__(NTH, 1)
+    sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    tc_tile<Y16>(a, Lo, &ymap, w, blockIdx.z, smraw);
+}
+
+// Several models (ranks) sharing the count matrix and the partitions: blockIdx.z
+// = slot * per + k, slot -> model through `order` (heaviest models first).
+template <bool Y16>
+__global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restrict__ av, const TcLayout* __restrict__ lv,
+                                                         const int* __restrict__ order, int per,
+                                                         const __grid_constant__ CUtensorMap ymap, int w) {
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    __shared__ StepArgs s_a;
+    __shared__ TcLayout s_l;
+    if (threadIdx.x == 0) {
+        const int model = order[blockIdx.z / per];
+        s_a = av[model];
+        s_l = lv[model];
+    }
+    __syncthreads();
+    tc_tile<Y16>(s_a, s_l, &ymap, w, blockIdx.z % per, smraw);
+}
+
 int fail_str(std::string* err, const char* msg) {
     if (err) *err = msg;
     return GMF_ERR_ARG;
@@ -436,6 +462,31 @@ cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
         sweep_tc_kernel<true><<<grid, NTH, tc->lay.smem, st>>>(a, tc->lay, tc->ymap, w);
     else
         sweep_tc_kernel<false><<<grid, NTH, tc->lay.smem, st>>>(a, tc->lay, tc->ymap, w);
+    return cudaGetLastError();
+}
+
+size_t gmf_tc_layout_size() { return sizeof(TcLayout); }
+const void* gmf_tc_layout(const gmf_model* h) { return &((const TcState*)h->tc)->lay; }
+uint32_t gmf_tc_smem(const gmf_model* h) { return ((const TcState*)h->tc)->lay.smem; }
+void gmf_tc_grid(const gmf_model* h, int* TI, int* TJ) {
+    *TI = ((const TcState*)h->tc)->TI;
+    *TJ = ((const TcState*)h->tc)->TJ;
+}
+
+cudaError_t gmf_tc_multi_attr(int y16, uint32_t smem) {
+    return y16 ? cudaFuncSetAttribute(sweep_tc_multi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+               : cudaFuncSetAttribute(sweep_tc_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// One sweep of nmodels models: grid (TJ, TI, nmodels * per).
+cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, const void* d_lays, const int* d_order,
+                                int nmodels, uint32_t smem, int w, cudaStream_t st) {
+    const TcState* tc = (const TcState*)h0->tc;
+    dim3 grid(tc->TJ, tc->TI, h0->per * nmodels);
+    if (h0->y16)
+        sweep_tc_multi<true><<<grid, NTH, smem, st>>>(d_args, (const TcLayout*)d_lays, d_order, h0->per, tc->ymap, w);
+    else
+        sweep_tc_multi<false><<<grid, NTH, smem, st>>>(d_args, (const TcLayout*)d_lays, d_order, h0->per, tc->ymap, w);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,160 @@
+// Batched rank sweep: several GMF fits of different latent rank d on the same
+// count matrix (the model-selection use of Sec. 4.2, where d must be chosen
+// from a grid of fits). Model 0 owns the permuted counts; the others read them.
+// One launch per sweep covers every model (grid z = model slot x block; the
+// heaviest models get the lowest slots so their CTAs start first), and a whole
+// epoch of these launches is captured once into a CUDA graph.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "gmf_internal.cuh"
+
+// gmf_step_tc.cu / gmf_step_simt.cu
+size_t gmf_tc_layout_size();
+const void* gmf_tc_layout(const gmf_model* h);
+uint32_t gmf_tc_smem(const gmf_model* h);
+void gmf_tc_grid(const gmf_model* h, int* TI, int* TJ);
+cudaError_t gmf_tc_multi_attr(int y16, uint32_t smem);
+cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, const void* d_lays, const int* d_order,
+                                int nmodels, uint32_t smem, int w, cudaStream_t st);
+size_t gmf_sweep_simt_smem(const gmf_model* h);
+cudaError_t gmf_simt_multi_attr(size_t smem);
+cudaError_t gmf_simt_launch_multi(const gmf_model* h0, const StepArgs* d_args, const int* d_order, int nmodels,
+                                  size_t smem, int w, cudaStream_t st);
+
+struct gmf_sweep {
+    std::vector<gmf_model*> models;
+    StepArgs* d_args = nullptr;
+    void* d_lays = nullptr;
+    int* d_order = nullptr;
+    size_t smem = 0;
+    int mixed = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t cap = nullptr;
+};
+
+static void sweep_release(gmf_sweep* s) {
+    if (!s) return;
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->d_args) cudaFree(s->d_args);
+    if (s->d_lays) cudaFree(s->d_lays);
+    if (s->d_order) cudaFree(s->d_order);
+    for (size_t i = s->models.size(); i-- > 0;) gmf_free(s->models[i]);  // the owner of the counts last
+    delete s;
+}
+
+extern "C" void gmf_sweep_free(gmf_sweep* s) { sweep_release(s); }
+
+static int sweep_fail(gmf_sweep* s, int code, const std::string& msg) {
+    sweep_release(s);
+    return gmf_fail(code, msg.c_str());
+}
+
+extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int32_t* d_list, int32_t n_models,
+                              const void* Y, int32_t y_dtype, int32_t y_on_device, const float* W, const double* X,
+                              const double* Z, const double* offset, const int32_t* row_perm, const int32_t* col_perm,
+                              const double* const* B0, const double* const* G0, const double* const* U0,
+                              const double* const* V0, const double* alpha0, void* stream) {
+    if (!out || !cfg || !d_list || !B0 || !G0 || !U0 || !V0 || !alpha0)
+        return gmf_fail(GMF_ERR_ARG, "gmf_sweep_init: NULL argument");
+    *out = nullptr;
+    if (n_models < 1 || n_models > 64) return gmf_fail(GMF_ERR_ARG, "gmf_sweep_init: 1 <= n_models <= 64");
+    gmf_sweep* s = new gmf_sweep();
+    s->mixed = cfg->precision == GMF_PREC_MIXED;
+    for (int i = 0; i < n_models; i++) {
+        gmf_config c = *cfg;
+        c.d = d_list[i];
+        gmf_model* h = nullptr;
+        const int rc = i == 0 ? gmf_init(&h, &c, Y, y_dtype, y_on_device, W, X, Z, offset, row_perm, col_perm, B0[i],
+                                         G0[i], U0[i], V0[i], alpha0[i], stream)
+                              : gmf_init_shared(&h, &c, s->models[0], X, Z, offset, B0[i], G0[i], U0[i], V0[i],
+                                                alpha0[i], stream);
+        if (rc != GMF_OK) {
+            const std::string keep = gmf_last_error();
+            return sweep_fail(s, rc, "gmf_sweep_init: model " + std::to_string(i) + ": " + keep);
+        }
+        s->models.push_back(h);
+    }
+    // heaviest models first (per-entry work grows with K = 1+p+q+d)
+    std::vector<int> order(n_models);
+    for (int i = 0; i < n_models; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s->models[a]->K > s->models[b]->K; });
+    std::vector<StepArgs> args(n_models);
+    std::vector<char> lays;
+    for (int i = 0; i < n_models; i++) {
+        gmf_model* h = s->models[i];
+        args[i] = gmf_make_args(h);
+        if (s->mixed) {
+            gmf_tc_grid(h, &args[i].TI, &args[i].TJ);
+            const char* l = (const char*)gmf_tc_layout(h);
+            lays.insert(lays.end(), l, l + gmf_tc_layout_size());
+            s->smem = std::max<size_t>(s->smem, gmf_tc_smem(h));
+        } else {
+            s->smem = std::max(s->smem, gmf_sweep_simt_smem(h));
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMalloc(&s->d_args, sizeof(StepArgs) * n_models) != cudaSuccess ||
+        cudaMalloc(&s->d_order, sizeof(int) * n_models) != cudaSuccess ||
+        (s->mixed && cudaMalloc(&s->d_lays, lays.size()) != cudaSuccess))
+        return sweep_fail(s, GMF_ERR_OOM, "gmf_sweep_init: device allocation failed");
+    cudaMemcpyAsync(s->d_args, args.data(), sizeof(StepArgs) * n_models, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->d_order, order.data(), sizeof(int) * n_models, cudaMemcpyHostToDevice, st);
+    if (s->mixed) cudaMemcpyAsync(s->d_lays, lays.data(), lays.size(), cudaMemcpyHostToDevice, st);
+    const cudaError_t e =
+        s->mixed ? gmf_tc_multi_attr(s->models[0]->y16, (uint32_t)s->smem) : gmf_simt_multi_attr(s->smem);
+    if (e != cudaSuccess)
+        return sweep_fail(s, GMF_ERR_ARG, std::string("gmf_sweep_init: the largest model's tile does not fit: ") +
+                                               cudaGetErrorString(e));
+    if (cudaStreamSynchronize(st) != cudaSuccess) return sweep_fail(s, GMF_ERR_CUDA, "gmf_sweep_init: copy failed");
+    *out = s;
+    return GMF_OK;
+}
+
+static cudaError_t launch(gmf_sweep* s, int w, cudaStream_t st) {
+    const int nm = (int)s->models.size();
+    if (s->mixed) return gmf_tc_launch_multi(s->models[0], s->d_args, s->d_lays, s->d_order, nm, (uint32_t)s->smem, w, st);
+    return gmf_simt_launch_multi(s->models[0], s->d_args, s->d_order, nm, s->smem, w, st);
+}
+
+extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream) {
+    if (!s || !sigma) return gmf_fail(GMF_ERR_ARG, "gmf_sweep_epoch: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    gmf_model* h0 = s->models[0];
+    std::vector<char> seen(h0->nsw, 0);
+    for (int w = 0; w < h0->nsw; w++) {
+        if (sigma[w] < 0 || sigma[w] >= h0->nsw || seen[sigma[w]])
+            return gmf_fail(GMF_ERR_ARG, "gmf_sweep_epoch: sigma is not a permutation");
+        seen[sigma[w]] = 1;
+    }
+    for (gmf_model* h : s->models) {
+        const int rc = gmf_stage_schedule(h, sigma, 0, h->nsw, st);
+        if (rc) return rc;
+    }
+    if (!s->graph) {
+        if (!s->cap && cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess)
+            return gmf_fail(GMF_ERR_CUDA, "gmf_sweep_epoch: stream creation failed");
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return gmf_fail(GMF_ERR_CUDA, "gmf_sweep_epoch: capture failed");
+        cudaError_t e = cudaSuccess;
+        for (int w = 0; w < h0->nsw && e == cudaSuccess; w++) e = launch(s, w, s->cap);
+        const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&s->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            s->graph = nullptr;
+            return gmf_fail(GMF_ERR_CUDA, "gmf_sweep_epoch: graph capture of the sweep launches failed");
+        }
+    }
+    if (cudaGraphLaunch(s->graph, st) != cudaSuccess) return gmf_fail(GMF_ERR_CUDA, "gmf_sweep_epoch: launch failed");
+    for (gmf_model* h : s->models) h->t += (int64_t)h->nsw * h->per;
+    return GMF_OK;
+}
+
+extern "C" gmf_model* gmf_sweep_model(gmf_sweep* s, int32_t i) {
+    if (!s || i < 0 || i >= (int32_t)s->models.size()) return nullptr;
+    return s->models[i];
+}

@@ -217,13 +217,13 @@ __device__ void tile_arrive_update(const StepArgs& a, int w, int k, int ti, int 
         __threadfence();
         __syncthreads();
         if (tid == 0) {
-            const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+            const unsigned total = (unsigned)(a.TJ * a.TI * a.per);  // CTAs of this model's sweep
             s_flag[2] = atomicAdd(a.ctrSweep, 1u) == total - 1;
         }
         __syncthreads();
         if (s_flag[2] && tid == 0) {
             __threadfence();
-            const int total = gridDim.x * gridDim.y * gridDim.z;
+            const int total = a.TJ * a.TI * a.per;
             double T1 = 0.0, T2 = 0.0;
             for (int c = 0; c < total; c++) {
                 T1 += __ldcg(a.nbpart + 2 * c);

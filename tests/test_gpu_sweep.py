@@ -1,0 +1,65 @@
+"""Batched rank sweep: every model of a gmf_sweep advances exactly as the same
+model fitted alone (same kernels, same arithmetic, deterministic reductions),
+so the comparison is bitwise; one model is also checked against the oracle."""
+import numpy as np
+import pytest
+
+import synth
+from tests.test_gpu_parity import rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gmf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as g
+    return g
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_sweep_equals_independent_fits(gmf, precision):
+    n, m, nbr, nbc = 900, 640, 300, 256
+    d_list = [2, 12, 5, 30]
+    prob = synth.make_problem(n, m, 3, 1, 8, "negbin", seed=9, y_dtype="uint16", zero_frac=0.85, offset=True)
+    starts = [synth.crude_start(prob, d, seed=9 + d) for d in d_list]
+    rp, cp = synth.partitions(n, m, 9)
+    st = synth.fit_settings(alpha_mode=1)
+    sig = synth.sweep_orders(n, m, nbr, nbc, 3, 9)
+    kw = dict(family="negbin", nb_row=nbr, nb_col=nbc, row_perm=rp, col_perm=cp, settings=st, precision=precision)
+    sw = gmf.Sweep(prob.Y, prob.X, prob.Z, prob.offset, starts, d_list, **kw)
+    solo = [gmf.Model(prob.Y, prob.X, prob.Z, prob.offset, s0, **kw) for s0 in starts]
+    for e in range(3):
+        sw.epoch(sig[e])
+        for mdl in solo:
+            mdl.epoch(sig[e])
+    for i in range(len(d_list)):
+        a, b = sw.models[i].get_params(), solo[i].get_params()
+        for k in ("U", "V", "B", "Gamma"):
+            np.testing.assert_array_equal(a[k], b[k])
+        assert a["alpha"] == b["alpha"]
+        assert sw.models[i].deviance() == solo[i].deviance()
+
+
+def test_sweep_model_matches_oracle(gmf):
+    import oracle
+    n, m, nbr, nbc = 700, 480, 256, 128
+    d_list = [3, 7]
+    prob = synth.make_problem(n, m, 2, 1, 5, "poisson", seed=4, offset=True)
+    starts = [synth.crude_start(prob, d, seed=4) for d in d_list]
+    rp, cp = synth.partitions(n, m, 4)
+    st = synth.fit_settings()
+    sig = synth.sweep_orders(n, m, nbr, nbc, 4, 4)
+    sw = gmf.Sweep(torch.from_numpy(prob.Y).cuda(), prob.X, prob.Z, prob.offset, starts, d_list, family="poisson",
+                   nb_row=nbr, nb_col=nbc, row_perm=rp, col_perm=cp, settings=st)
+    ref = oracle.OracleFit(prob.Y, prob.X, prob.Z, prob.offset, starts[1], family="poisson", nb_row=nbr, nb_col=nbc,
+                           row_perm=rp, col_perm=cp, settings=st)
+    for e in range(4):
+        sw.epoch(sig[e])
+        ref.epoch(sig[e])
+    assert sw.models[1].deviance() == pytest.approx(ref.deviance(), rel=1e-4)
+    assert rel(sw.models[1].get_params()["U"], ref.U) <= 1e-3
