@@ -234,6 +234,43 @@ gmf_model* gmf_sweep_model(gmf_sweep* s, int32_t i);
 void gmf_sweep_free(gmf_sweep* s);
 
 /*
+ * Warm-start encoder for gmf_project_cells (the paper has no network; it
+ * supplies the training targets -- the fitted, orthogonalised scores U -- and
+ * the per-cell projection the network warms up):
+ *   x = log(1 + y);  h1 = gelu(W1 x + b1);  h2 = gelu(W2 h1 + b2);  o = W3 h2 + b3
+ * with gelu(t) = t Phi(t), trained by minimising mean (o - target)^2 with Adam.
+ * Parameters are FP32: W1 n_h1 x n_in, W2 n_h2 x n_h1, W3 n_out x n_h2 (row-major),
+ * biases vectors. All products run on the library's FP32 tiled GEMM kernel.
+ *
+ * gmf_mlp_create     -- zero parameters; max_batch bounds the rows of one
+ *                       forward chunk / training batch (activations are sized for it).
+ * gmf_mlp_set_params / gmf_mlp_get_params / gmf_mlp_get_grads -- host FP32 copies
+ *                       (NULL pointers are skipped); set_params also resets Adam.
+ * gmf_mlp_forward    -- o for `rows` cells: Y device rows x n_in counts
+ *                       (y_dtype), out device rows x n_out. Asynchronous.
+ * gmf_mlp_loss_grad  -- loss (device float, may be NULL) and the gradients of one
+ *                       batch (rows <= max_batch) into the network. Asynchronous.
+ * gmf_mlp_adam       -- one Adam step with the stored gradients. Asynchronous.
+ * gmf_mlp_train      -- `epochs` passes of minibatches of `batch` rows in an order
+ *                       drawn from `seed` (SplitMix64 on the host); losses (host,
+ *                       may be NULL) receives the mean loss of each epoch. Synchronous.
+ */
+typedef struct gmf_mlp gmf_mlp;
+int gmf_mlp_create(gmf_mlp** out, int32_t n_in, int32_t n_h1, int32_t n_h2, int32_t n_out, int32_t max_batch,
+                   void* stream);
+int gmf_mlp_set_params(gmf_mlp* net, const float* W1, const float* b1, const float* W2, const float* b2,
+                       const float* W3, const float* b3, void* stream);
+int gmf_mlp_get_params(gmf_mlp* net, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3, void* stream);
+int gmf_mlp_get_grads(gmf_mlp* net, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3, void* stream);
+int gmf_mlp_forward(gmf_mlp* net, const void* Y, int32_t y_dtype, int64_t rows, float* out, void* stream);
+int gmf_mlp_loss_grad(gmf_mlp* net, const void* Y, int32_t y_dtype, int64_t rows, const float* target, float* loss,
+                      void* stream);
+int gmf_mlp_adam(gmf_mlp* net, float lr, float beta1, float beta2, float eps, void* stream);
+int gmf_mlp_train(gmf_mlp* net, const void* Y, int32_t y_dtype, int64_t rows, const float* target, int32_t epochs,
+                  int32_t batch, float lr, uint64_t seed, float* losses, void* stream);
+void gmf_mlp_free(gmf_mlp* net);
+
+/*
  * gmf_trace -- enable (1) or disable (0) timing of the block-step kernels:
  * while enabled, every block-step launch is bracketed by CUDA events recorded
  * on the launching stream. gmf_trace_read synchronizes the stream, returns the

@@ -30,8 +30,9 @@ ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
 EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_num_sweeps", "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
-           "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_model", "gmf_sweep_free", "gmf_free", "gmf_last_error",
-           "gmf_version")
+           "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
+           "gmf_mlp_set_params", "gmf_mlp_get_params", "gmf_mlp_get_grads", "gmf_mlp_forward", "gmf_mlp_loss_grad",
+           "gmf_mlp_adam", "gmf_mlp_train", "gmf_mlp_free", "gmf_free", "gmf_last_error", "gmf_version")
 
 
 class GmfError(RuntimeError):
@@ -87,6 +88,16 @@ def lib():
         "gmf_sweep_epoch": (C.c_int, [VP, VP, VP]),
         "gmf_sweep_model": (VP, [VP, C.c_int32]),
         "gmf_sweep_free": (None, [VP]),
+        "gmf_mlp_create": (C.c_int, [C.POINTER(VP), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, VP]),
+        "gmf_mlp_set_params": (C.c_int, [VP] * 8),
+        "gmf_mlp_get_params": (C.c_int, [VP] * 8),
+        "gmf_mlp_get_grads": (C.c_int, [VP] * 8),
+        "gmf_mlp_forward": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, VP]),
+        "gmf_mlp_loss_grad": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, VP, VP]),
+        "gmf_mlp_adam": (C.c_int, [VP, C.c_float, C.c_float, C.c_float, C.c_float, VP]),
+        "gmf_mlp_train": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, C.c_int32, C.c_int32, C.c_float, C.c_uint64, VP,
+                                    VP]),
+        "gmf_mlp_free": (None, [VP]),
         "gmf_free": (None, [VP]),
         "gmf_last_error": (C.c_char_p, []),
         "gmf_version": (C.c_char_p, []),
@@ -359,3 +370,68 @@ class Sweep:
         if h is not None and h.value and _lib is not None:
             _lib.gmf_sweep_free(h)
             self._h = VP()
+
+
+MLP_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+class MLP:
+    """The warm-start encoder (a ``gmf_mlp`` handle): log1p(counts) -> scores."""
+
+    def __init__(self, n_in, n_h1, n_h2, n_out, max_batch=1024, stream=None):
+        self._h = VP()
+        self.shapes = dict(W1=(n_h1, n_in), b1=(n_h1,), W2=(n_h2, n_h1), b2=(n_h2,), W3=(n_out, n_h2), b3=(n_out,))
+        self.n_in, self.n_out, self.max_batch = n_in, n_out, max_batch
+        check(lib().gmf_mlp_create(C.byref(self._h), n_in, n_h1, n_h2, n_out, max_batch, _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.gmf_mlp_free(h)
+            self._h = VP()
+
+    def set_params(self, P, stream=None):
+        arrs = [np.ascontiguousarray(P[k], dtype=np.float32).reshape(self.shapes[k]) for k in MLP_NAMES]
+        check(lib().gmf_mlp_set_params(self._h, *[a.ctypes.data for a in arrs], _stream(stream)))
+
+    def _get(self, fn, stream):
+        out = {k: np.empty(self.shapes[k], dtype=np.float32) for k in MLP_NAMES}
+        check(fn(self._h, *[out[k].ctypes.data for k in MLP_NAMES], _stream(stream)))
+        return out
+
+    def get_params(self, stream=None):
+        return self._get(lib().gmf_mlp_get_params, stream)
+
+    def get_grads(self, stream=None):
+        return self._get(lib().gmf_mlp_get_grads, stream)
+
+    @staticmethod
+    def _ydt(Y):
+        import torch
+        return GMF_Y_INT32 if Y.dtype == torch.int32 else GMF_Y_UINT16
+
+    def forward(self, Y, stream=None):
+        import torch
+        Yc = Y.contiguous()
+        out = torch.empty((Y.shape[0], self.n_out), dtype=torch.float32, device=Y.device)
+        check(lib().gmf_mlp_forward(self._h, Yc.data_ptr(), self._ydt(Y), Y.shape[0], out.data_ptr(), _stream(stream)))
+        return out
+
+    def loss_grad(self, Y, target, stream=None):
+        import torch
+        Yc, Tc = Y.contiguous(), target.to(torch.float32).contiguous()
+        loss = torch.zeros(1, dtype=torch.float32, device=Y.device)
+        check(lib().gmf_mlp_loss_grad(self._h, Yc.data_ptr(), self._ydt(Y), Y.shape[0], Tc.data_ptr(),
+                                      loss.data_ptr(), _stream(stream)))
+        return loss
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        check(lib().gmf_mlp_adam(self._h, lr, beta1, beta2, eps, _stream(stream)))
+
+    def train(self, Y, target, epochs, batch, lr, seed=0, stream=None):
+        import torch
+        Yc, Tc = Y.contiguous(), target.to(torch.float32).contiguous()
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        check(lib().gmf_mlp_train(self._h, Yc.data_ptr(), self._ydt(Y), Y.shape[0], Tc.data_ptr(), epochs, batch,
+                                  lr, seed, losses.ctypes.data, _stream(stream)))
+        return losses[:epochs]

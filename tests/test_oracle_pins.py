@@ -412,3 +412,47 @@ def test_projection_gamma_closed_form_is_fixed_point():
                                  gamma_closed_form=False)
     np.testing.assert_allclose(G_1, G_cf, atol=1e-12)
     np.testing.assert_allclose(G_cold, G_cf, atol=1e-10)
+
+
+# ---------------------------------------------------------------- warm-start encoder (oracle/mlp.py)
+
+def test_mlp_gradients_match_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(30)
+    P = mlp.init_params(7, 5, 4, 3, seed=1)
+    for n in ("b1", "b2", "b3"):
+        P[n] = 0.3 * rng.standard_normal(P[n].shape)
+    Y = rng.poisson(3.0, size=(6, 7))
+    T = rng.standard_normal((6, 3))
+    _, g = mlp.loss_grad(P, Y, T)
+    h = 1e-6
+    for n in mlp.NAMES:
+        flat = P[n].reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 6)):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = mlp.loss(P, Y, T)
+            flat[idx] = old - h
+            lm = mlp.loss(P, Y, T)
+            flat[idx] = old
+            assert g[n].reshape(-1)[idx] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-9), n
+
+
+def test_mlp_gelu_is_x_times_normal_cdf():
+    from scipy import stats
+    from oracle import mlp
+    t = np.linspace(-6, 6, 101)
+    np.testing.assert_allclose(mlp.gelu(t), t * stats.norm.cdf(t), rtol=1e-12, atol=1e-14)
+    h = 1e-6
+    np.testing.assert_allclose(mlp.gelu_prime(t), (mlp.gelu(t + h) - mlp.gelu(t - h)) / (2 * h), rtol=1e-7, atol=1e-9)
+
+
+def test_mlp_adam_first_step_is_signed_learning_rate():
+    """At k = 1 the bias-corrected Adam step is lr * g/(|g| + eps): -lr sign(g)."""
+    from oracle import mlp
+    P = mlp.init_params(4, 3, 3, 2, seed=2)
+    P0 = {k: v.copy() for k, v in P.items()}
+    g = {k: np.random.default_rng(3).standard_normal(v.shape) for k, v in P.items()}
+    mlp.adam_step(P, g, {}, lr=0.01, eps=0.0)
+    for k in P:
+        np.testing.assert_allclose(P[k], P0[k] - 0.01 * np.sign(g[k]), rtol=1e-12)
