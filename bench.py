@@ -226,6 +226,81 @@ def committed_traffic(kernel, workload):
 RANKS = [2, 5, 10, 15, 20, 30, 40, 50]
 
 
+def run_projection(args, w):
+    """--workload nb_project: fit d = 20 on 100000 cells x 3000 genes, orthogonalise,
+    train the warm-start encoder on the training cells' projected scores, then
+    project 100000 held-out cells with 3 Fisher steps from the encoder's scores
+    and from zero; gaps to a 30-step cold fit on the penalised per-cell objective
+    and on the deviance, and cells/s of each."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as gmf
+    n_fit = n_new = w.n // 2
+    prob = synth.make_problem_device(w.n, w.m, w.p, w.q, w.d, w.family, seed=args.seed, zero_frac=w.zero_frac,
+                                     offset=w.offset)
+    Yfit, Ynew = prob.Y[:n_fit].contiguous(), prob.Y[n_fit:].contiguous()
+    fitp = synth.Problem(Y=Yfit.cpu().numpy().view(np.uint16), X=prob.X[:n_fit], Z=prob.Z, offset=prob.offset[:n_fit],
+                         B=prob.B, Gamma=prob.Gamma[:n_fit], U=prob.U[:n_fit], V=prob.V, nb_size=prob.nb_size,
+                         family=w.family)
+    start = synth.crude_start(fitp, w.d, seed=args.seed)
+    rp, cp = synth.partitions(n_fit, w.m, args.seed)
+    settings = synth.fit_settings(alpha_mode=1)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, r
+
+    model = gmf.Model(Yfit.view(torch.int16), fitp.X, fitp.Z, fitp.offset, start, family=w.family, nb_row=w.nb_row,
+                      nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=settings, precision="mixed")
+    sig = synth.sweep_orders(n_fit, w.m, w.nb_row, w.nb_col, w.epochs, args.seed)
+    t_fit, _ = timed(lambda: [model.epoch(s) for s in sig])
+    model.orthogonalize("B1")
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    Xf, of = dev(fitp.X), dev(fitp.offset)
+    Xn, on = dev(prob.X[n_fit:]), dev(prob.offset[n_fit:])
+    Utr, _, _ = model.project_cells(Yfit, Xf, of, None, n_steps=10, with_dev=False)
+    net = gmf.MLP(w.m, 256, 256, w.d, max_batch=1024)
+    net.set_params({k: np.asarray(v, dtype=np.float32) for k, v in synth.mlp_init(w.m, 256, 256, w.d, 2).items()})
+    t_train, losses = timed(lambda: net.train(Yfit, Utr, epochs=10, batch=1024, lr=1e-3, seed=5))
+    lam_u = settings["lambda_"][2]
+
+    def objective(U, G, D):
+        return 0.5 * D.double() + 0.5 * lam_u * (U.double() ** 2).sum(1)
+
+    for _ in range(2):   # warm-up of the projection and forward kernels
+        model.project_cells(Ynew, Xn, on, net.forward(Ynew), n_steps=3)
+    t_ref, ref = timed(lambda: model.project_cells(Ynew, Xn, on, None, n_steps=30))
+    t_cold, cold = timed(lambda: model.project_cells(Ynew, Xn, on, None, n_steps=3))
+    t_warm, warm = timed(lambda: model.project_cells(Ynew, Xn, on, net.forward(Ynew), n_steps=3))
+    oref = objective(*ref)
+    out = {"metric": "per-cell projection of new cells: cells/s and gap to a converged cold fit",
+           "value": n_new / t_warm, "unit": "cells/s", "n_gpus": 1, "higher_is_better": True,
+           "config": {"workload": f"{w.name}: fit {n_fit} + project {n_new} cells x {w.m} genes, NB, d={w.d}, "
+                                  f"GMF fit {w.epochs} epochs (tensor cores), encoder {w.m}-256-256-{w.d} trained 10 "
+                                  f"epochs on the training cells' projected scores", "data": "synthetic (GPU-drawn)"},
+           "warm_start": {"cells_per_s": n_new / t_warm, "steps": 3,
+                          "objective_gap": float((objective(*warm) - oref).mean()),
+                          "deviance_gap": float((warm[2].double() - ref[2].double()).mean())},
+           "cold_start": {"cells_per_s": n_new / t_cold, "steps": 3,
+                          "objective_gap": float((objective(*cold) - oref).mean()),
+                          "deviance_gap": float((cold[2].double() - ref[2].double()).mean())},
+           "reference_cold_fit": {"steps": 30, "cells_per_s": n_new / t_ref,
+                                  "mean_objective": float(oref.mean()), "mean_deviance": float(ref[2].double().mean())},
+           "encoder_training": {"samples_per_s": 10 * n_fit / t_train, "loss_first_epoch": float(losses[0]),
+                                "loss_last_epoch": float(losses[-1])},
+           "gmf_fit_entries_per_s": n_fit * w.m * w.epochs / t_fit}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_rank_sweep(args, w):
     """--workload nb_sweep: 8 ranks on one 50000 x 3000 NB matrix, batched (one
     launch per sweep for all models) vs the same 8 fits one after another."""
@@ -293,6 +368,8 @@ def main():
         return run_reference(args, w)
     if args.workload == "nb_sweep":
         return run_rank_sweep(args, w)
+    if args.workload == "nb_project":
+        return run_projection(args, w)
     if args.warmup < 3:
         raise SystemExit("warm-up must be >= 3 steps")
     ws, rank, local = dist_env()

@@ -29,11 +29,9 @@ def gelu_prime(t):
 
 
 def init_params(n_in, n_h1, n_h2, n_out, seed):
-    """Scaled normal weights, zero biases (a starting point shared by both sides)."""
-    rng = np.random.default_rng([seed, 7])
-    return dict(W1=rng.standard_normal((n_h1, n_in)) / np.sqrt(n_in), b1=np.zeros(n_h1),
-                W2=rng.standard_normal((n_h2, n_h1)) / np.sqrt(n_h1), b2=np.zeros(n_h2),
-                W3=rng.standard_normal((n_out, n_h2)) / np.sqrt(n_h2), b3=np.zeros(n_out))
+    """The seeded starting weights (drawn by the shared input module)."""
+    import synth
+    return synth.mlp_init(n_in, n_h1, n_h2, n_out, seed)
 
 
 def forward(P, Y):

@@ -130,6 +130,16 @@ def _stream(stream):
     return s.cuda_stream
 
 
+def _torch_ydt(Y):
+    """Count type of a torch tensor: int32, or 16-bit counts (uint16, or their int16 view)."""
+    import torch
+    if Y.dtype == torch.int32:
+        return GMF_Y_INT32
+    if Y.dtype == torch.int16 or (hasattr(torch, "uint16") and Y.dtype == torch.uint16):
+        return GMF_Y_UINT16
+    raise TypeError("counts must be int32 or 16-bit (uint16 / int16 view)")
+
+
 def make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision="fp32"):
     cfg = gmf_config()
     lib().gmf_config_default(C.byref(cfg), n, m, p, q, d, FAMILIES[family], nb_row, nb_col)
@@ -160,10 +170,7 @@ class Model:
         on_dev = isinstance(Y, torch.Tensor) and Y.is_cuda
         if isinstance(Y, torch.Tensor):
             n, m = Y.shape
-            ydt = {torch.int32: GMF_Y_INT32, torch.uint16: GMF_Y_UINT16}.get(Y.dtype) if hasattr(torch, "uint16") \
-                else {torch.int32: GMF_Y_INT32}.get(Y.dtype)
-            if ydt is None:
-                raise TypeError("Y must be int32 or uint16")
+            ydt = _torch_ydt(Y)
             Y = Y.contiguous()
         else:
             Y = np.ascontiguousarray(Y)
@@ -305,7 +312,7 @@ class Model:
         import torch
         n_new = Ynew.shape[0]
         _, m, p, q, d = self.dims
-        ydt = GMF_Y_INT32 if Ynew.dtype == torch.int32 else GMF_Y_UINT16
+        ydt = _torch_ydt(Ynew)
         dev = Ynew.device
         U = torch.empty((n_new, d), dtype=torch.float32, device=dev)
         G = torch.empty((n_new, q), dtype=torch.float32, device=dev)
@@ -331,7 +338,7 @@ class Sweep:
         on_dev = isinstance(Y, torch.Tensor) and Y.is_cuda
         if isinstance(Y, torch.Tensor):
             n, m = Y.shape
-            ydt = GMF_Y_INT32 if Y.dtype == torch.int32 else GMF_Y_UINT16
+            ydt = _torch_ydt(Y)
             Y = Y.contiguous()
         else:
             Y = np.ascontiguousarray(Y)
@@ -407,8 +414,7 @@ class MLP:
 
     @staticmethod
     def _ydt(Y):
-        import torch
-        return GMF_Y_INT32 if Y.dtype == torch.int32 else GMF_Y_UINT16
+        return _torch_ydt(Y)
 
     def forward(self, Y, stream=None):
         import torch

@@ -212,3 +212,67 @@ def fit_settings(**over):
              damping=1e-3, eps=1e-8, eta_clamp=30.0, bias_corr=0, alpha_mode=0)
     s.update(over)
     return s
+
+
+def make_problem_device(n, m, p, q, d, family="negbin", *, seed=0, zero_frac=None, offset=True, scale=0.5,
+                        device="cuda"):
+    """The law of make_problem drawn on a CUDA device with torch's generator
+    (for matrices too large to draw with numpy in reasonable time). Returns a
+    Problem whose Y is a CUDA uint16-bit tensor (int16 view of the counts,
+    saturated at 65535) and whose parameters are numpy arrays. Same law as
+    make_problem, different random stream."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    rng = np.random.default_rng([seed, 9])
+    X = np.empty((n, p))
+    X[:, 0] = 1.0
+    if p > 1:
+        X[:, 1:] = rng.standard_normal((n, p - 1))
+    Z = np.ones((m, q))
+    B = scale * rng.standard_normal((m, p))
+    Gamma = scale * rng.standard_normal((n, q))
+    U = scale * rng.standard_normal((n, d))
+    V = scale * rng.standard_normal((m, d))
+    off = rng.normal(0.0, 0.5, size=n) if offset else np.zeros(n)
+    size = rng.gamma(2.0, 0.5, size=m) if family == "negbin" else None
+    if zero_frac is not None:
+        sub = np.sort(rng.choice(n, size=min(n, 2000), replace=False))
+        base = _eta(X, B, Gamma, Z, U, V, off, sub)
+        lo, hi = -15.0, 15.0
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if _zero_frac(base + mid, family, size) > zero_frac:
+                lo = mid
+            else:
+                hi = mid
+        B[:, 0] = B[:, 0] + 0.5 * (lo + hi)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device)
+    Xt, Bt, Gt, Zt, Ut, Vt, ot = map(t, (X, B, Gamma, Z, U, V, off))
+    Y = torch.empty((n, m), dtype=torch.int16, device=device)
+    st = t(size) if size is not None else None
+    chunk = max(1, 20_000_000 // m)
+    saturated = 0
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        eta = Xt[r0:r1] @ Bt.T + Gt[r0:r1] @ Zt.T + Ut[r0:r1] @ Vt.T + ot[r0:r1, None]
+        mu = torch.exp(eta.clamp(-30, 30))
+        if family == "negbin":
+            lam = torch._standard_gamma(st.expand_as(mu).contiguous(), generator=g) * (mu / st)
+        else:
+            lam = mu
+        c = torch.poisson(lam, generator=g)
+        saturated += int((c > 65535).sum())
+        c = c.clamp_(max=65535).to(torch.int32)
+        Y[r0:r1] = torch.where(c > 32767, c - 65536, c).to(torch.int16)
+    return Problem(Y=Y, X=X, Z=Z, offset=off, B=B, Gamma=Gamma, U=U, V=V, nb_size=size, family=family,
+                   saturated=saturated)
+
+
+def mlp_init(n_in, n_h1, n_h2, n_out, seed):
+    """Seeded starting weights of the warm-start encoder: scaled normal weights,
+    zero biases (an input shared by the library and the oracle)."""
+    rng = np.random.default_rng([seed, 7])
+    return dict(W1=rng.standard_normal((n_h1, n_in)) / np.sqrt(n_in), b1=np.zeros(n_h1),
+                W2=rng.standard_normal((n_h2, n_h1)) / np.sqrt(n_h1), b2=np.zeros(n_h2),
+                W3=rng.standard_normal((n_out, n_h2)) / np.sqrt(n_h2), b3=np.zeros(n_out))
