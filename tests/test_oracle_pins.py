@@ -414,6 +414,81 @@ def test_projection_gamma_closed_form_is_fixed_point():
     np.testing.assert_allclose(G_cold, G_cf, atol=1e-10)
 
 
+
+def _far_start_case(seed):
+    """A few NB cells and a warm start far from their optimum, where plain
+    Fisher scoring overshoots."""
+    rng = np.random.default_rng(seed)
+    n, m, p, d = 4, 60, 2, 3
+    X = np.hstack([np.ones((n, 1)), rng.standard_normal((n, 1))])
+    Z = np.ones((m, 1))
+    B = 0.3 * rng.standard_normal((m, p))
+    V = rng.standard_normal((m, d)) * rng.uniform(0.3, 1.5)
+    Ut = rng.standard_normal((n, d)) * rng.uniform(0.5, 2)
+    a = rng.uniform(0.5, 5)
+    Y = rng.poisson(rng.gamma(a, np.exp(X @ B.T + Ut @ V.T) / a))
+    U0 = rng.standard_normal((n, d)) * rng.uniform(1, 3)
+    return Y, X, Z, B, V, a, U0
+
+
+def _row_objective(Y, X, B, Z, V, a, G, U):
+    """Penalised per-cell objective from the likelihood itself (lambda_U = 1)."""
+    eta = X @ B.T + G @ Z.T + U @ V.T
+    return -loglik("negbin", Y, np.exp(eta), a).sum(axis=1) + 0.5 * (U ** 2).sum(axis=1)
+
+
+def test_projection_step_control_never_raises_the_objective_and_converges():
+    """Plain Fisher scoring from a far start overshoots (some cell ends far above
+    its best iterate); with step halving the objective of the returned point
+    never rises from one pass count to the next, and 40 passes reach the
+    stationary point."""
+    from oracle.project import project_cells
+    overshoot = 0
+    for seed in range(8):
+        Y, X, Z, B, V, a, U0 = _far_start_case(seed)
+        kw = dict(family="negbin", alpha=a, U_start=U0, lam_u=1.0)
+        plain = []
+        for k in range(12):
+            U, G, _ = project_cells(Y, X, None, B, Z, V, n_steps=k, halving=False, **kw)
+            plain.append(_row_objective(Y, X, B, Z, V, a, G, U))
+        overshoot += int(np.any(plain[-1] > np.min(plain, axis=0) + 1.0))
+        prev = None
+        for k in range(12):
+            U, G, _ = project_cells(Y, X, None, B, Z, V, n_steps=k, **kw)
+            f = _row_objective(Y, X, B, Z, V, a, G, U)
+            if prev is not None:
+                assert np.all(f <= prev + 1e-4 * (1 + np.abs(prev))), (seed, k)
+            prev = f
+        U, G, _ = project_cells(Y, X, None, B, Z, V, n_steps=40, **kw)
+        h = 1e-6
+        for i in range(len(Y)):
+            th = np.concatenate([G[i], U[i]])
+
+            def fi(t):
+                return _row_objective(Y[i:i + 1], X[i:i + 1], B, Z, V, a, t[None, :1], t[None, 1:])[0]
+
+            for c in range(len(th)):
+                e = np.zeros_like(th); e[c] = h
+                assert abs((fi(th + e) - fi(th - e)) / (2 * h)) < 1e-5 * max(1.0, abs(fi(th))), (seed, i, c)
+    assert overshoot >= 2
+
+
+def test_projection_step_control_is_plain_fisher_when_steps_descend():
+    """From the closed-form start on well-scaled cells every Fisher step lowers
+    the objective, so step halving changes nothing."""
+    from oracle.project import project_cells
+    rng = np.random.default_rng(21)
+    n, m, p, d = 6, 50, 2, 3
+    X = np.hstack([np.ones((n, 1)), rng.standard_normal((n, 1))])
+    Z = np.ones((m, 1))
+    B, V = 0.3 * rng.standard_normal((m, p)), 0.4 * rng.standard_normal((m, d))
+    Y = rng.poisson(np.exp(X @ B.T + 0.5 * rng.standard_normal((n, d)) @ V.T))
+    for fam in ("poisson", "negbin"):
+        a = project_cells(Y, X, None, B, Z, V, family=fam, alpha=4.0, n_steps=6)
+        b = project_cells(Y, X, None, B, Z, V, family=fam, alpha=4.0, n_steps=6, halving=False)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+
 # ---------------------------------------------------------------- warm-start encoder (oracle/mlp.py)
 
 def test_mlp_gradients_match_finite_differences():
