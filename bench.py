@@ -229,9 +229,9 @@ RANKS = [2, 5, 10, 15, 20, 30, 40, 50]
 def run_projection(args, w):
     """--workload nb_project: fit d = 20 on 100000 cells x 3000 genes, orthogonalise,
     train the warm-start encoder on the training cells' projected scores, then
-    project 100000 held-out cells with 3 Fisher steps from the encoder's scores
-    and from zero; gaps to a 30-step cold fit on the penalised per-cell objective
-    and on the deviance, and cells/s of each."""
+    project 100000 held-out cells by 1, 2 and 3 safeguarded Fisher steps from
+    the encoder's scores and from zero. Gaps (mean, median, 99th percentile) are
+    to a 60-step cold fit on the penalised per-cell objective; cells/s of each."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -267,35 +267,50 @@ def run_projection(args, w):
     Xf, of = dev(fitp.X), dev(fitp.offset)
     Xn, on = dev(prob.X[n_fit:]), dev(prob.offset[n_fit:])
     Utr, _, _ = model.project_cells(Yfit, Xf, of, None, n_steps=10, with_dev=False)
+    epochs = 10
     net = gmf.MLP(w.m, 256, 256, w.d, max_batch=1024)
     net.set_params({k: np.asarray(v, dtype=np.float32) for k, v in synth.mlp_init(w.m, 256, 256, w.d, 2).items()})
-    t_train, losses = timed(lambda: net.train(Yfit, Utr, epochs=10, batch=1024, lr=1e-3, seed=5))
-    lam_u = settings["lambda_"][2]
+    t_train, losses = timed(lambda: net.train(Yfit, Utr, epochs=epochs, batch=1024, lr=1e-3, seed=5))
+    lam_u, lam_g = settings["lambda_"][2], settings["lambda_"][1]
 
     def objective(U, G, D):
-        return 0.5 * D.double() + 0.5 * lam_u * (U.double() ** 2).sum(1)
+        return 0.5 * D.double() + 0.5 * lam_u * (U.double() ** 2).sum(1) + 0.5 * lam_g * (G.double() ** 2).sum(1)
 
     for _ in range(2):   # warm-up of the projection and forward kernels
         model.project_cells(Ynew, Xn, on, net.forward(Ynew), n_steps=3)
-    t_ref, ref = timed(lambda: model.project_cells(Ynew, Xn, on, None, n_steps=30))
-    t_cold, cold = timed(lambda: model.project_cells(Ynew, Xn, on, None, n_steps=3))
-    t_warm, warm = timed(lambda: model.project_cells(Ynew, Xn, on, net.forward(Ynew), n_steps=3))
+    t_ref, ref = timed(lambda: model.project_cells(Ynew, Xn, on, None, n_steps=60))
     oref = objective(*ref)
+    conv = objective(*model.project_cells(Ynew, Xn, on, None, n_steps=30)) - oref
+
+    def gap_stats(res):
+        g = objective(*res) - oref
+        return {"mean": float(g.mean()), "median": float(g.median()), "p99": float(g.quantile(0.99)),
+                "max": float(g.max())}
+
+    t_fwd, Uw = timed(lambda: net.forward(Ynew))
+    heldout_mse = float(((Uw.double() - ref[0].double()) ** 2).mean())
+    starts = {"warm_start": lambda k: model.project_cells(Ynew, Xn, on, net.forward(Ynew), n_steps=k),
+              "cold_start": lambda k: model.project_cells(Ynew, Xn, on, None, n_steps=k)}
+    res = {}
+    for name, run in starts.items():
+        res[name] = {}
+        for k in (1, 2, 3):
+            t, r = timed(lambda: run(k))
+            res[name][f"steps_{k}"] = {"cells_per_s": n_new / t, "objective_gap": gap_stats(r)}
     out = {"metric": "per-cell projection of new cells: cells/s and gap to a converged cold fit",
-           "value": n_new / t_warm, "unit": "cells/s", "n_gpus": 1, "higher_is_better": True,
+           "value": res["warm_start"]["steps_3"]["cells_per_s"], "unit": "cells/s", "n_gpus": 1,
+           "higher_is_better": True,
            "config": {"workload": f"{w.name}: fit {n_fit} + project {n_new} cells x {w.m} genes, NB, d={w.d}, "
-                                  f"GMF fit {w.epochs} epochs (tensor cores), encoder {w.m}-256-256-{w.d} trained 10 "
-                                  f"epochs on the training cells' projected scores", "data": "synthetic (GPU-drawn)"},
-           "warm_start": {"cells_per_s": n_new / t_warm, "steps": 3,
-                          "objective_gap": float((objective(*warm) - oref).mean()),
-                          "deviance_gap": float((warm[2].double() - ref[2].double()).mean())},
-           "cold_start": {"cells_per_s": n_new / t_cold, "steps": 3,
-                          "objective_gap": float((objective(*cold) - oref).mean()),
-                          "deviance_gap": float((cold[2].double() - ref[2].double()).mean())},
-           "reference_cold_fit": {"steps": 30, "cells_per_s": n_new / t_ref,
-                                  "mean_objective": float(oref.mean()), "mean_deviance": float(ref[2].double().mean())},
-           "encoder_training": {"samples_per_s": 10 * n_fit / t_train, "loss_first_epoch": float(losses[0]),
-                                "loss_last_epoch": float(losses[-1])},
+                                  f"GMF fit {w.epochs} epochs (tensor cores), encoder {w.m}-256-256-{w.d} trained "
+                                  f"{epochs} epochs on the training cells' projected scores; value = warm start, "
+                                  f"3 Fisher steps, encoder forward included", "data": "synthetic (GPU-drawn)"},
+           **res,
+           "reference_cold_fit": {"steps": 60, "cells_per_s": n_new / t_ref, "mean_objective": float(oref.mean()),
+                                  "max_gap_30_steps": float(conv.max()), "mean_gap_30_steps": float(conv.mean())},
+           "encoder": {"train_samples_per_s": epochs * n_fit / t_train, "loss_first_epoch": float(losses[0]),
+                       "loss_last_epoch": float(losses[-1]), "forward_cells_per_s": n_new / t_fwd,
+                       "heldout_mse_to_converged_scores": heldout_mse,
+                       "converged_score_second_moment": float((ref[0].double() ** 2).mean())},
            "gmf_fit_entries_per_s": n_fit * w.m * w.epochs / t_fit}
     print(json.dumps(out), flush=True)
     return 0

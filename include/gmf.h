@@ -194,6 +194,11 @@ int gmf_orthogonalize(gmf_model* h, int32_t mode, void* stream);
  * Start: u_i = U_start row (NULL: zeros); gamma_i0 (the first Z column, exact
  * when it is the intercept) in closed form log(max(sum_j y_ij, 0.5) /
  * sum_j exp(eta_ij without gamma)), the other gamma 0. Requires 1 <= q + d <= 32.
+ * Step control (the paper states none for this problem): each of the n_steps + 1
+ * passes over the genes evaluates f = 0.5 dev_i + 0.5 theta' Lambda theta at
+ * the current point; a point with f <= f_best + 1e-5 (1 + |f_best|) is taken
+ * and stepped from, otherwise the last step is halved from the best point.
+ * The outputs are the best point and its deviance. n_steps = 0 returns the start.
  * Ynew columns are genes in the caller's original order.
  *   Ynew      device, n_new x m counts (y_dtype)
  *   Xnew      device float32, n_new x p;  offset_new: device float32 n_new or NULL
@@ -253,7 +258,9 @@ void gmf_sweep_free(gmf_sweep* s);
  * gmf_mlp_adam       -- one Adam step with the stored gradients. Asynchronous.
  * gmf_mlp_train      -- `epochs` passes of minibatches of `batch` rows in an order
  *                       drawn from `seed` (SplitMix64 on the host); losses (host,
- *                       may be NULL) receives the mean loss of each epoch. Synchronous.
+ *                       may be NULL) receives the mean loss of each epoch. Allocates
+ *                       rows int64 + epochs doubles of workspace for the call; the
+ *                       host waits only once per epoch. Synchronous.
  */
 typedef struct gmf_mlp gmf_mlp;
 int gmf_mlp_create(gmf_mlp** out, int32_t n_in, int32_t n_h1, int32_t n_h2, int32_t n_out, int32_t max_batch,

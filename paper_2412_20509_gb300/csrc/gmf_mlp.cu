@@ -424,43 +424,68 @@ static uint64_t splitmix(uint64_t& s) {
     return z ^ (z >> 31);
 }
 
+// acc += loss * w  (one thread; the batches of an epoch add in order)
+static __global__ void loss_acc_kernel(const float* loss, double w, double* acc) { *acc += (double)*loss * w; }
+
 extern "C" int gmf_mlp_train(gmf_mlp* n, const void* Y, int32_t y_dtype, int64_t rows, const float* target,
                              int32_t epochs, int32_t batch, float lr, uint64_t seed, float* losses, void* stream) {
     if (!n || !Y || !target || rows < 1 || epochs < 0 || batch < 1 || batch > n->max_batch || !(lr > 0.f))
         return gmf_fail(GMF_ERR_ARG, "gmf_mlp_train: bad argument (batch must be <= max_batch)");
+    if (epochs == 0) return GMF_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int y16 = y_dtype == GMF_Y_UINT16;
+    // One shuffled order per epoch, drawn on the host while the device trains
+    // on the previous one; the epoch losses accumulate on the device and are
+    // read once at the end.
+    int64_t* d_perm = nullptr;
+    double* d_acc = nullptr;
+    if (cudaMalloc(&d_perm, sizeof(int64_t) * rows) != cudaSuccess ||
+        cudaMalloc(&d_acc, sizeof(double) * epochs) != cudaSuccess) {
+        cudaFree(d_perm);
+        return gmf_fail(GMF_ERR_OOM, "gmf_mlp_train: device allocation failed");
+    }
+    auto done = [&](int rc) {
+        cudaStreamSynchronize(st);
+        cudaFree(d_perm);
+        cudaFree(d_acc);
+        return rc;
+    };
     std::vector<int64_t> perm(rows);
     uint64_t s = seed;
-    std::vector<float> bl;
-    for (int ep = 0; ep < epochs; ep++) {
+    auto shuffle = [&]() {
         for (int64_t i = 0; i < rows; i++) perm[i] = i;
         for (int64_t i = rows - 1; i > 0; i--) std::swap(perm[i], perm[splitmix(s) % (uint64_t)(i + 1)]);
-        double total = 0.0;
-        int64_t seen = 0;
+    };
+    if (cudaMemsetAsync(d_acc, 0, sizeof(double) * epochs, st) != cudaSuccess)
+        return done(gmf_fail(GMF_ERR_CUDA, "gmf_mlp_train: memset failed"));
+    shuffle();
+    for (int ep = 0; ep < epochs; ep++) {
+        // pageable source: the copy waits for the stream, so the previous epoch is done with d_perm
+        if (cudaMemcpyAsync(d_perm, perm.data(), sizeof(int64_t) * rows, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return done(gmf_fail(GMF_ERR_CUDA, "gmf_mlp_train: copy failed"));
         for (int64_t b0 = 0; b0 < rows; b0 += batch) {
             const int64_t nb = std::min<int64_t>(batch, rows - b0);
-            if (cudaMemcpyAsync(n->idx, perm.data() + b0, sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess)
-                return gmf_fail(GMF_ERR_CUDA, "gmf_mlp_train: copy failed");
+            const int64_t* idx = d_perm + b0;
             if (y16)
                 gather_rows<unsigned short><<<grid1(nb * n->n_in), NT, 0, st>>>(
-                    (const unsigned short*)Y, n->n_in, n->idx, nb, n->n_in, (unsigned short*)n->yb);
+                    (const unsigned short*)Y, n->n_in, idx, nb, n->n_in, (unsigned short*)n->yb);
             else
-                gather_rows<int><<<grid1(nb * n->n_in), NT, 0, st>>>((const int*)Y, n->n_in, n->idx, nb, n->n_in,
+                gather_rows<int><<<grid1(nb * n->n_in), NT, 0, st>>>((const int*)Y, n->n_in, idx, nb, n->n_in,
                                                                      (int*)n->yb);
-            gather_rows<float><<<grid1(nb * n->n_out), NT, 0, st>>>(target, n->n_out, n->idx, nb, n->n_out, n->tb);
+            gather_rows<float><<<grid1(nb * n->n_out), NT, 0, st>>>(target, n->n_out, idx, nb, n->n_out, n->tb);
             cudaError_t e = backward(n, n->yb, y16, n->n_in, nb, n->tb, st);
-            if (e != cudaSuccess) return gmf_fail(GMF_ERR_CUDA, cudaGetErrorString(e));
+            if (e != cudaSuccess) return done(gmf_fail(GMF_ERR_CUDA, cudaGetErrorString(e)));
             const int rc = gmf_mlp_adam(n, lr, 0.9f, 0.999f, 1e-8f, stream);
-            if (rc) return rc;
-            float lb = 0.f;
-            if (cudaMemcpyAsync(&lb, n->loss, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                return gmf_fail(GMF_ERR_CUDA, "gmf_mlp_train: loss read failed");
-            total += (double)lb * (double)nb;
-            seen += nb;
+            if (rc) return done(rc);
+            loss_acc_kernel<<<1, 1, 0, st>>>(n->loss, (double)nb, d_acc + ep);
         }
-        if (losses) losses[ep] = (float)(total / (double)seen);
+        if (ep + 1 < epochs) shuffle();
     }
-    return GMF_OK;
+    std::vector<double> acc(epochs);
+    if (cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * epochs, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return done(gmf_fail(GMF_ERR_CUDA, "gmf_mlp_train: loss read failed"));
+    if (losses)
+        for (int ep = 0; ep < epochs; ep++) losses[ep] = (float)(acc[ep] / (double)rows);
+    return done(GMF_OK);
 }

@@ -12,6 +12,14 @@
 // an in-place packed Cholesky. Start: u from the caller (or 0); gamma_0 (the
 // first Z column) in closed form log(max(sum_j y_ij, 0.5) / sum_j exp(eta_ij
 // without gamma)), other gamma 0. FP32 throughout.
+//
+// Step control: every pass also sums the cell's unit deviances, giving the
+// penalised objective f = 0.5 dev + 0.5 theta' Lambda theta at the current
+// point. A point with f <= f_best + 1e-5 (1 + |f_best|) is accepted and the
+// Fisher step is taken from it; otherwise the last step is halved and tried
+// from the best point. The best point and its deviance are the output. Plain
+// Fisher scoring overshoots from far starts; accepted steps are exact Fisher
+// steps, so cells whose steps descend take the same path as without control.
 #include <math.h>
 
 #include <algorithm>
@@ -26,6 +34,7 @@ constexpr int CC = 32;     // cells per CTA
 constexpr int GC = 32;     // genes per chunk
 constexpr int FMAX = 32;   // largest q + d
 constexpr int NPMAX = FMAX * (FMAX + 1) / 2;
+constexpr float SLACK = 1e-5f;  // relative slack of the acceptance test
 
 struct ProjArgs {
     const void* Y;
@@ -60,6 +69,11 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
     float* BASE = GR + CC * FMAX;                // CC x (GC+1)  o_i + x_i'beta_j
     float* S1 = BASE + CC * (GC + 1);            // CC: sum y (init) / deviance
     float* S2 = S1 + CC;                         // CC: sum exp(rest) (init)
+    float* DV = S2 + CC;                         // CC x (GC+1)  unit deviances of the chunk
+    float* BEST = DV + CC * (GC + 1);            // CC x f  best accepted theta
+    float* DEL = BEST + CC * FMAX;               // CC x f  last step
+    float* FB = DEL + CC * FMAX;                 // CC: best objective
+    float* DB = FB + CC;                         // CC: deviance at the best point
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t cell0 = (int64_t)blockIdx.x * CC;
@@ -72,14 +86,16 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
         if (c < ncell && k >= a.q && a.Ustart) v = a.Ustart[(cell0 + c) * a.d + (k - a.q)];
         TH[c * FMAX + k] = v;
     }
-    // passes: 0 = closed-form gamma, 1..n_steps = Fisher steps, n_steps+1 = deviance
+    if (tid < CC) FB[tid] = DB[tid] = 0.f;
+    // passes: 0 = closed-form gamma; 1..n_steps+1 evaluate the objective at the
+    // current point, and 1..n_steps also form the Fisher system there
     for (int pass = 0; pass <= a.n_steps + 1; pass++) {
-        const bool init = pass == 0, fisher = pass >= 1 && pass <= a.n_steps, devpass = pass == a.n_steps + 1;
+        const bool init = pass == 0, fisher = pass >= 1 && pass <= a.n_steps;
         if (init && a.q == 0) continue;
-        float facc[4][PP], gacc[4];
+        float facc[4][PP], gacc[4], dacc[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-            gacc[c] = 0.f;
+            gacc[c] = dacc[c] = 0.f;
 #pragma unroll
             for (int t = 0; t < PP; t++) facc[c][t] = 0.f;
         }
@@ -104,7 +120,7 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
             // eta, mu and the per-entry quantities of the 32 x 32 chunk
             for (int e = tid; e < CC * GC; e += NT) {
                 const int c = e / GC, g = e - c * GC;
-                float dd = 0.f, ddd = 0.f;
+                float dd = 0.f, ddd = 0.f, dvu = 0.f;
                 if (c < ncell && g < ng) {
                     const int64_t cell = cell0 + c;
                     float base = a.off ? a.off[cell] : 0.f;
@@ -122,7 +138,7 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
                     } else {
                         const float ec = fminf(fmaxf(eta, -a.clamp), a.clamp);
                         const float mu = expf(ec);
-                        if (devpass) {
+                        {
                             float dv;
                             if (y > 0.f) {
                                 const float r1 = (y - mu) / mu;
@@ -138,8 +154,9 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
                             } else {
                                 dv = a.nb ? alpha * log1pf(mu / alpha) : mu;
                             }
-                            dd = 2.f * dv;
-                        } else {
+                            dvu = 2.f * dv;
+                        }
+                        if (fisher) {
                             const float fct = a.nb ? alpha / (alpha + mu) : 1.f;
                             dd = (y - mu) * fct;
                             ddd = mu * fct;
@@ -148,8 +165,14 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
                 }
                 Dd[c * (GC + 1) + g] = dd;
                 DDd[c * (GC + 1) + g] = ddd;
+                DV[c * (GC + 1) + g] = dvu;
             }
             __syncthreads();
+            if (!init) {
+                // warp w: cells 4w..4w+3; lane: gene lane of the chunk for the deviance
+#pragma unroll
+                for (int c = 0; c < 4; c++) dacc[c] += DV[(4 * warp + c) * (GC + 1) + lane];
+            }
             if (fisher) {
                 // warp w: cells 4w..4w+3; lane: pairs lane + 32t, score component lane
                 for (int g = 0; g < ng; g++) {
@@ -170,8 +193,8 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
                         for (int c = 0; c < 4; c++) facc[c][t] = fmaf(w4[c], rr, facc[c][t]);
                     }
                 }
-            } else if (tid < CC) {
-                // init: S1 = sum y, S2 = sum exp(rest);  deviance: S1 = sum of unit deviances
+            } else if (init && tid < CC) {
+                // S1 = sum y, S2 = sum exp(rest)
                 float s1 = S1[tid], s2 = S2[tid];
                 for (int g = 0; g < ng; g++) {
                     s1 += Dd[tid * (GC + 1) + g];
@@ -185,8 +208,17 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
         if (init) {
             if (tid < ncell) TH[tid * FMAX + 0] = logf(fmaxf(S1[tid], 0.5f) / S2[tid]);
             __syncthreads();
-        } else if (fisher) {
-            float* F = RR;  // CC x np
+            continue;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            float v = dacc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) S1[4 * warp + c] = v;
+        }
+        float* F = RR;  // CC x np
+        if (fisher) {
 #pragma unroll
             for (int c = 0; c < 4; c++) {
                 const int cell = 4 * warp + c;
@@ -197,54 +229,74 @@ __global__ void __launch_bounds__(NT) project_kernel(ProjArgs a) {
                 }
                 if (lane < f) GR[cell * FMAX + lane] = gacc[c];
             }
-            __syncthreads();
-            if (tid < ncell) {
-                float* A = F + tid * np;
-                float* th = TH + tid * FMAX;
-                float* b = GR + tid * FMAX;
+        }
+        __syncthreads();
+        if (tid < ncell) {
+            float* th = TH + tid * FMAX;
+            float* be = BEST + tid * FMAX;
+            float* de = DEL + tid * FMAX;
+            float pen = 0.f;
+            for (int k = 0; k < f; k++) pen += (k < a.q ? a.lam_g : a.lam_u) * th[k] * th[k];
+            const float obj = 0.5f * S1[tid] + 0.5f * pen;
+            const float fb = FB[tid];
+            if (pass == 1 || obj <= fb + SLACK * (1.f + fabsf(fb))) {
+                for (int k = 0; k < f; k++) be[k] = th[k];
+                FB[tid] = obj;
+                DB[tid] = S1[tid];
+                if (fisher) {
+                    float* A = F + tid * np;
+                    float* b = GR + tid * FMAX;
+                    for (int k = 0; k < f; k++) {
+                        const float lam = k < a.q ? a.lam_g : a.lam_u;
+                        A[pidx(k, k)] += lam;
+                        b[k] -= lam * th[k];
+                    }
+                    bool ok = true;
+                    for (int j = 0; j < f; j++) {  // packed lower Cholesky in place
+                        float s = A[pidx(j, j)];
+                        for (int k = 0; k < j; k++) s -= A[pidx(j, k)] * A[pidx(j, k)];
+                        if (!(s > 0.f)) {
+                            ok = false;
+                            break;
+                        }
+                        const float ljj = sqrtf(s);
+                        A[pidx(j, j)] = ljj;
+                        for (int i = j + 1; i < f; i++) {
+                            float t = A[pidx(i, j)];
+                            for (int k = 0; k < j; k++) t -= A[pidx(i, k)] * A[pidx(j, k)];
+                            A[pidx(i, j)] = t / ljj;
+                        }
+                    }
+                    if (ok) {
+                        for (int i = 0; i < f; i++) {  // L z = b
+                            float s = b[i];
+                            for (int k = 0; k < i; k++) s -= A[pidx(i, k)] * b[k];
+                            b[i] = s / A[pidx(i, i)];
+                        }
+                        for (int i = f - 1; i >= 0; i--) {  // L' x = z
+                            float s = b[i];
+                            for (int k = i + 1; k < f; k++) s -= A[pidx(k, i)] * b[k];
+                            b[i] = s / A[pidx(i, i)];
+                        }
+                    }
+                    for (int k = 0; k < f; k++) {
+                        de[k] = ok ? b[k] : 0.f;
+                        th[k] = be[k] + de[k];
+                    }
+                }
+            } else {
                 for (int k = 0; k < f; k++) {
-                    const float lam = k < a.q ? a.lam_g : a.lam_u;
-                    A[pidx(k, k)] += lam;
-                    b[k] -= lam * th[k];
-                }
-                bool ok = true;
-                for (int j = 0; j < f; j++) {  // packed lower Cholesky in place
-                    float s = A[pidx(j, j)];
-                    for (int k = 0; k < j; k++) s -= A[pidx(j, k)] * A[pidx(j, k)];
-                    if (!(s > 0.f)) {
-                        ok = false;
-                        break;
-                    }
-                    const float ljj = sqrtf(s);
-                    A[pidx(j, j)] = ljj;
-                    for (int i = j + 1; i < f; i++) {
-                        float t = A[pidx(i, j)];
-                        for (int k = 0; k < j; k++) t -= A[pidx(i, k)] * A[pidx(j, k)];
-                        A[pidx(i, j)] = t / ljj;
-                    }
-                }
-                if (ok) {
-                    for (int i = 0; i < f; i++) {  // L z = b
-                        float s = b[i];
-                        for (int k = 0; k < i; k++) s -= A[pidx(i, k)] * b[k];
-                        b[i] = s / A[pidx(i, i)];
-                    }
-                    for (int i = f - 1; i >= 0; i--) {  // L' x = z
-                        float s = b[i];
-                        for (int k = i + 1; k < f; k++) s -= A[pidx(k, i)] * b[k];
-                        b[i] = s / A[pidx(i, i)];
-                    }
-                    for (int k = 0; k < f; k++) th[k] += b[k];
+                    de[k] *= 0.5f;
+                    th[k] = be[k] + de[k];
                 }
             }
-            __syncthreads();
-        } else if (devpass) {
-            if (tid < ncell && a.dev) a.dev[cell0 + tid] = S1[tid];
         }
+        __syncthreads();
     }
+    if (tid < ncell && a.dev) a.dev[cell0 + tid] = DB[tid];
     for (int e = tid; e < ncell * f; e += NT) {
         const int c = e / f, k = e - c * f;
-        const float v = TH[c * FMAX + k];
+        const float v = BEST[c * FMAX + k];
         if (k < a.q)
             a.Gout[(cell0 + c) * a.q + k] = v;
         else
@@ -262,8 +314,8 @@ __global__ void unpermute_rows(const float* R, const int* cperm, int64_t m, int 
 
 size_t project_smem(int KP, int f) {
     const int np = f * (f + 1) / 2;
-    return sizeof(float) * ((size_t)GC * KP + (size_t)std::max(GC, CC) * np + 3 * (size_t)CC * (GC + 1) +
-                            2 * (size_t)CC * FMAX + 2 * (size_t)CC);
+    return sizeof(float) * ((size_t)GC * KP + (size_t)std::max(GC, CC) * np + 4 * (size_t)CC * (GC + 1) +
+                            4 * (size_t)CC * FMAX + 4 * (size_t)CC);
 }
 
 }  // namespace

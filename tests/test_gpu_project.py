@@ -83,3 +83,47 @@ def test_projection_zero_steps_is_closed_form_start(gmf, oracle_mod):
     np.testing.assert_allclose(Gg.cpu().numpy(), Gr, rtol=1e-5, atol=1e-6)
     assert not Ug.cpu().numpy().any()
     np.testing.assert_allclose(Dg.cpu().numpy(), Dr, rtol=1e-5)
+
+
+def test_projection_step_control_matches_oracle_from_far_start(gmf, oracle_mod):
+    """A start three noise units away from the truth: plain Fisher scoring
+    overshoots on some cells, so step halving acts. Decisions that differ only
+    by FP32 rounding would need an objective change within 1e-5 of the slack
+    threshold, so the kernel follows the oracle's path; 10 passes leave the
+    scores within 1e-3 and the deviances within 1e-4."""
+    from oracle.project import project_cells
+    P = Pair(gmf, oracle_mod, 700, 480, 3, 1, 6, "negbin", 256, 128, zero_frac=0.8)
+    for e in range(3):
+        P.gpu.epoch(P.sigmas[e])
+    params = P.gpu.get_params()
+    Y, X, off, Utrue = new_cells(P, params, 200, seed=31)
+    U0 = (Utrue + 3.0 * np.random.default_rng(2).standard_normal(Utrue.shape)).astype(np.float32).astype(np.float64)
+    Z32 = P.prob.Z.astype(np.float32).astype(np.float64)
+    st = P.settings
+    kw = dict(family="negbin", alpha=params["alpha"], U_start=U0, lam_gamma=st["lambda_"][1], lam_u=st["lambda_"][2])
+    Ur, Gr, Dr = project_cells(Y, X, off, params["B"], Z32, params["V"], n_steps=10, **kw)
+    Up, _, _ = project_cells(Y, X, off, params["B"], Z32, params["V"], n_steps=10, halving=False, **kw)
+    assert rel(Up, Ur) > 1e-2   # the case exercises the step control
+    Ug, Gg, Dg = P.gpu.project_cells(torch.from_numpy(Y).cuda(), torch.from_numpy(X).cuda(),
+                                     torch.from_numpy(off).cuda(), torch.from_numpy(U0).cuda(), n_steps=10)
+    assert rel(Ug.cpu().numpy(), Ur) <= 1e-3
+    assert rel(Gg.cpu().numpy(), Gr) <= 1e-3
+    np.testing.assert_allclose(Dg.cpu().numpy(), Dr, rtol=1e-4)
+
+
+def test_projection_objective_never_rises_with_passes(gmf, oracle_mod):
+    P = Pair(gmf, oracle_mod, 700, 480, 3, 1, 6, "negbin", 256, 128, zero_frac=0.8)
+    for e in range(3):
+        P.gpu.epoch(P.sigmas[e])
+    params = P.gpu.get_params()
+    Y, X, off, Utrue = new_cells(P, params, 300, seed=32)
+    U0 = torch.from_numpy(Utrue + 3.0 * np.random.default_rng(3).standard_normal(Utrue.shape)).float().cuda()
+    Yd, Xd, od = torch.from_numpy(Y).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(off).cuda()
+    lam_u = P.settings["lambda_"][2]
+    prev = None
+    for k in range(0, 9):
+        U, G, D = P.gpu.project_cells(Yd, Xd, od, U0, n_steps=k)
+        f = 0.5 * D.double() + 0.5 * lam_u * (U.double() ** 2).sum(1)
+        if prev is not None:
+            assert bool((f <= prev + 1e-5 * (1 + prev.abs()) + 1e-6).all()), k
+        prev = f
