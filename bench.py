@@ -201,6 +201,7 @@ def source_hash(paths):
 KERNEL_SOURCES = {
     "sweep_tc_kernel": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
     "sweep_kernel": ["gmf_step_simt.cu", "gmf_update.cuh", "gmf_internal.cuh"],
+    "update_kernel": ["gmf_update.cu", "gmf_update.cuh", "gmf_internal.cuh"],
 }
 
 
@@ -524,7 +525,7 @@ def main():
            "config": describe(w, args.precision), "roofline": roof,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(prob.Y.nbytes + 4 * nsw),
                    "d2h_bytes_per_step": 8 + 4},
-           "gpu_launches": int(nsw * args.steps), "clocks": clk,
+           "gpu_launches": int(2 * nsw * args.steps), "clocks": clk,
            "deviance": {"after_warmup": dev0, "after_timed_steps": dev1}}
 
     if extras:

@@ -132,6 +132,8 @@ int32_t gmf_num_sweeps(const gmf_model* h);
  * theta <- theta - rho_t c_t Gbar/Hbar, with both sides using the block's
  * pre-step parameters. NB with alpha_mode 1: the shape is updated once per
  * sweep from moment sums pooled over the sweep. t advances by one per block.
+ * Each sweep is two kernel launches (the tiles, then the strip updates), with
+ * programmatic stream serialization between them.
  * Asynchronous on the stream (sigma is copied before return).
  */
 int gmf_sgd_epoch(gmf_model* h, const int32_t* sigma, void* stream);
@@ -222,7 +224,8 @@ int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n
  * V0[i] m x d_list[i], alpha0[i]. The counts, weights and partitions are stored
  * once and read by every model. Synchronous.
  * gmf_sweep_epoch -- one epoch of every model (same sigma semantics as
- * gmf_sgd_epoch): one launch per sweep covers all models, heaviest first.
+ * gmf_sgd_epoch): one tile launch per sweep covers all models, heaviest first,
+ * and one update launch all their strips.
  * Results equal running each model's own gmf_sgd_epoch.
  * gmf_sweep_model -- the i-th model's handle, owned by the sweep and valid until
  * gmf_sweep_free, for gmf_deviance, gmf_get_params, gmf_orthogonalize, ...
@@ -278,11 +281,12 @@ int gmf_mlp_train(gmf_mlp* net, const void* Y, int32_t y_dtype, int64_t rows, co
 void gmf_mlp_free(gmf_mlp* net);
 
 /*
- * gmf_trace -- enable (1) or disable (0) timing of the block-step kernels:
- * while enabled, every block-step launch is bracketed by CUDA events recorded
- * on the launching stream. gmf_trace_read synchronizes the stream, returns the
- * summed kernel time in milliseconds and the number of timed launches since
- * the last read, and resets both. Costs one event pair per launch.
+ * gmf_trace -- enable (1) or disable (0) timing of the block-step tile kernels:
+ * while enabled, every sweep's tile launch is bracketed by CUDA events recorded
+ * on the launching stream (the strip-update launch that follows is not timed).
+ * gmf_trace_read synchronizes the stream, returns the summed kernel time in
+ * milliseconds and the number of timed launches since the last read, and
+ * resets both. Costs one event pair per sweep.
  */
 int gmf_trace(gmf_model* h, int32_t enable);
 int gmf_trace_read(gmf_model* h, double* total_ms, int64_t* launches, void* stream);

@@ -41,12 +41,20 @@ extern "C" const char* gmf_version(void) { return "gmf-gb300 0.1 (sm_103a)"; }
 // tensor-core path hooks (gmf_step_tc.cu)
 int gmf_tc_prepare_checked(gmf_model* h, std::string* err);
 cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st);
+cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st);
 void gmf_tc_free(gmf_model* h);
 
 // One sweep launch of the configured path.
-static cudaError_t launch_sweep(gmf_model* h, const StepArgs& a, int w, cudaStream_t st) {
-    if (h->cfg.precision == GMF_PREC_MIXED) return gmf_tc_launch(h, w, st);
-    return gmf_launch_sweep_simt(h, a, w, st);
+// A sweep is a tile launch and an update launch; t0/t1 (or null) are recorded
+// around the tile launch.
+static cudaError_t launch_sweep(gmf_model* h, const StepArgs& a, int w, cudaStream_t st, cudaEvent_t t0 = nullptr,
+                                cudaEvent_t t1 = nullptr) {
+    const bool mixed = h->cfg.precision == GMF_PREC_MIXED;
+    cudaError_t e = t0 ? cudaEventRecord(t0, st) : cudaSuccess;
+    if (e == cudaSuccess) e = mixed ? gmf_tc_launch(h, w, st) : gmf_launch_sweep_simt(h, a, w, st);
+    if (e == cudaSuccess && t1) e = cudaEventRecord(t1, st);
+    if (e == cudaSuccess) e = mixed ? gmf_tc_launch_update(h, w, st) : gmf_launch_update(a, w, GMF_TILE, st);
+    return e;
 }
 // Algorithm 2 (gmf_orth.cu), per-cell projection (gmf_project.cu)
 int gmf_orth_run(gmf_model* h, int mode, cudaStream_t st, std::string* err);
@@ -116,8 +124,8 @@ static void release(gmf_model* h) {
         h->ystage = nullptr;
     }
     void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
-                    h->rperm, h->cperm, h->ystage, h->Rorig, h->partR, h->partC, h->ctrR, h->ctrC, h->ctrSweep,
-                    h->nbpart, h->sigma, h->rhoc, h->rho1, h->err, h->devpart, h->devtot};
+                    h->rperm, h->cperm, h->ystage, h->Rorig, h->partR, h->partC, h->nbpart, h->sigma, h->rhoc,
+                    h->rho1, h->err, h->devpart, h->devtot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] h->h_rperm;
@@ -270,9 +278,6 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     INIT_CUDA(dalloc(&h->cperm, (size_t)c.m));
     INIT_CUDA(dalloc(&h->partR, (size_t)h->per * h->TI * h->TJ * GMF_TILE * 2 * std::max(h->fr, 1)));
     INIT_CUDA(dalloc(&h->partC, (size_t)h->per * h->TI * h->TJ * GMF_TILE * 2 * std::max(h->fc, 1)));
-    INIT_CUDA(dalloc(&h->ctrR, (size_t)h->per * h->TI));
-    INIT_CUDA(dalloc(&h->ctrC, (size_t)h->per * h->TJ));
-    INIT_CUDA(dalloc(&h->ctrSweep, 1));
     INIT_CUDA(dalloc(&h->nbpart, (size_t)2 * h->per * h->TI * h->TJ));
     INIT_CUDA(dalloc(&h->sigma, (size_t)h->nsw));
     INIT_CUDA(dalloc(&h->rhoc, (size_t)h->nsw * h->per));
@@ -290,9 +295,6 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     INIT_CUDA(cudaMemsetAsync(h->HbC, 0, sizeof(float) * c.m * h->fc, st));
     INIT_CUDA(cudaMemsetAsync(h->cntR, 0, sizeof(int) * c.n, st));
     INIT_CUDA(cudaMemsetAsync(h->cntC, 0, sizeof(int) * c.m, st));
-    INIT_CUDA(cudaMemsetAsync(h->ctrR, 0, sizeof(unsigned) * h->per * h->TI, st));
-    INIT_CUDA(cudaMemsetAsync(h->ctrC, 0, sizeof(unsigned) * h->per * h->TJ, st));
-    INIT_CUDA(cudaMemsetAsync(h->ctrSweep, 0, sizeof(unsigned), st));
     INIT_CUDA(cudaMemsetAsync(h->err, 0, sizeof(unsigned), st));
     float a0 = (float)alpha0;
     INIT_CUDA(cudaMemcpyAsync(h->alpha, &a0, sizeof(float), cudaMemcpyHostToDevice, st));
@@ -438,12 +440,10 @@ extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begi
                 int rc = trace_collect(h, st);
                 if (rc) return rc;
             }
-            CUDA_TRY(cudaEventRecord(h->trace_ev[2 * h->trace_used], st));
-        }
-        CUDA_TRY(launch_sweep(h, a, w, st));
-        if (h->trace_on) {
-            CUDA_TRY(cudaEventRecord(h->trace_ev[2 * h->trace_used + 1], st));
+            CUDA_TRY(launch_sweep(h, a, w, st, h->trace_ev[2 * h->trace_used], h->trace_ev[2 * h->trace_used + 1]));
             h->trace_used++;
+        } else {
+            CUDA_TRY(launch_sweep(h, a, w, st));
         }
         h->t += h->per;
     }

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "gmf.h"
 
 #define GMF_TILE 64          // SIMT tile edge (rows and columns)
@@ -51,10 +53,7 @@ struct StepArgs {
     float* alpha;               // device scalar (NB shape)
     float* partR;               // [per][TI][TJ][TILE][2*fr]: row partials of tile (ti, tj)
     float* partC;               // [per][TJ][TI][TILE][2*fc]: column partials of tile (ti, tj)
-    unsigned* ctrR;             // [per][TI]
-    unsigned* ctrC;             // [per][TJ]
-    unsigned* ctrSweep;         // [1]
-    double* nbpart;             // [per*TI*TJ][2]
+    double* nbpart;             // [per*TI*TJ][2]: NB moment sums of each tile
     const int* sigma;           // device copy of the epoch's sweep offsets
     const float* rhoc;          // [nsw][per]: rho_t * c_t per block (rho_t alone when bias_corr = 1)
     const float* rho1;          // [nsw]: rho at the first block of each sweep (NB shape update)
@@ -89,9 +88,6 @@ struct gmf_model {
     int y_shared;               // Yp / Wp belong to another handle (rank sweep)
     float* partR;
     float* partC;
-    unsigned* ctrR;
-    unsigned* ctrC;
-    unsigned* ctrSweep;
     double* nbpart;
     int* sigma;
     float* rhoc;
@@ -117,6 +113,33 @@ struct gmf_model {
 };
 
 #define GMF_TRACE_POOL 512
+
+// Launch with programmatic stream serialization: the kernel may start before
+// the preceding kernel in the stream has finished and waits for it with
+// griddepcontrol.wait before it touches state that kernel writes.
+template <typename... Params, typename... Args>
+cudaError_t gmf_launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                           Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// gmf_update.cu: the strip-update launch that follows each tile launch of a
+// sweep (tile edge T); the multi-model form takes one StepArgs per model.
+cudaError_t gmf_launch_update(const StepArgs& a, int w, int T, cudaStream_t st);
+cudaError_t gmf_launch_update_multi(const StepArgs* d_args, int nmodels, int units, size_t smem, int w, int T,
+                                    cudaStream_t st);
+int gmf_update_units(const StepArgs& a, int T);
+size_t gmf_update_smem(const StepArgs& a);
 
 // gmf_api.cu
 int gmf_stage_schedule(gmf_model* h, const int32_t* sigma, int w_begin, int w_end, cudaStream_t st);

@@ -193,6 +193,7 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
     const bool active = ti < nTI && tj < nTJ;
     const bool nb = a.family == GMF_NEGBIN;
     const bool moments = nb && a.alpha_mode == 1;
+    grid_dependency_wait();  // the previous sweep's update launch writes the model state
     const float alpha = *a.alpha;
     float s1 = 0.f, s2 = 0.f;
 
@@ -272,11 +273,12 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
         contract_side(S.Ds, S.DDs, 1, LDD, S.LF, FCP, a.fc, nr, nc, pcol);
     }
 
-    tile_arrive_update<T, GMF_THREADS, 2>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
+    tile_moments<GMF_THREADS>(a, k, ti, tj, s1, s2);
 }
 
 __global__ void __launch_bounds__(GMF_THREADS, 3) sweep_kernel(StepArgs a, int w) {
     extern __shared__ __align__(16) float smem[];
+    grid_launch_dependents();
     simt_tile(a, w, blockIdx.z, smem);
 }
 
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(GMF_THREADS, 2) sweep_multi(const StepArgs* __
                                                              const int* __restrict__ order, int per, int w) {
     extern __shared__ __align__(16) float smem[];
     __shared__ StepArgs s_a;
+    grid_launch_dependents();
     if (threadIdx.x == 0) s_a = av[order[blockIdx.z / per]];
     __syncthreads();
     simt_tile(s_a, w, blockIdx.z % per, smem);
@@ -437,9 +440,6 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.alpha = h->alpha;
     a.partR = h->partR;
     a.partC = h->partC;
-    a.ctrR = h->ctrR;
-    a.ctrC = h->ctrC;
-    a.ctrSweep = h->ctrSweep;
     a.nbpart = h->nbpart;
     a.sigma = h->sigma;
     a.rhoc = h->rhoc;
@@ -464,15 +464,14 @@ cudaError_t gmf_simt_multi_attr(size_t smem) {
 cudaError_t gmf_simt_launch_multi(const gmf_model* h0, const StepArgs* d_args, const int* d_order, int nmodels,
                                   size_t smem, int w, cudaStream_t st) {
     dim3 grid(h0->TJ, h0->TI, h0->per * nmodels);
-    sweep_multi<<<grid, GMF_THREADS, smem, st>>>(d_args, d_order, h0->per, w);
-    return cudaGetLastError();
+    return gmf_launch_pdl(sweep_multi, grid, dim3(GMF_THREADS), smem, st, d_args, d_order, h0->per, w);
 }
 
 cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaStream_t st) {
     const size_t smem = sweep_smem(h->K, h->fr, h->fc);
     dim3 grid(h->TJ, h->TI, h->per);
-    sweep_kernel<<<grid, GMF_THREADS, smem, st>>>(a, w);
-    return cudaGetLastError();
+    const cudaError_t e = gmf_launch_pdl(sweep_kernel, grid, dim3(GMF_THREADS), smem, st, a, w);
+    return e;
 }
 
 cudaError_t gmf_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st) {

@@ -94,11 +94,11 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
     const bool active = ti < nTI && tj < nTJ;
     const bool nb = a.family == GMF_NEGBIN;
     const bool moments = nb && a.alpha_mode == 1;
-    const float alpha = *a.alpha;
+    float alpha = 0.f;
     float s1 = 0.f, s2 = 0.f;
 
+    uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
     if (active) {
-        uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
         uint8_t* Ys = sm;
         uint8_t* Aop = sm + Lo.off_u;
         uint8_t* Bop = Aop + Lo.KA * ATOM;
@@ -130,6 +130,10 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
             for (int b = 0; b < nbox; b++)
                 tma_load_2d(Ys + b * ATOM, ymap_p, (int)(col0 + (int64_t)b * Lo.JB), (int)row0, &bars[0]);
         }
+        // the counts are read-only; everything below reads or writes model state
+        // that the previous sweep's update launch may still be writing
+        grid_dependency_wait();
+        alpha = *a.alpha;
 
         // ---- operands. Thread groups of 128: L rows -> eta A; R rows -> eta B;
         //      L rows -> column-side B ([X, U] and squares); R rows -> row-side B ([Z, V] and squares).
@@ -338,14 +342,17 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
         tc_fence_before();
         __syncthreads();
         if (warp == 0) tmem_dealloc(tb, Lo.tmem_cols);
+    } else {
+        grid_dependency_wait();  // before writing this sweep's moment slot
     }
-    tile_arrive_update<TT, NTH, 4>(a, w, k, ti, tj, g, nTI, nTJ, active, s1, s2, alpha);
+    tile_moments<NTH>(a, k, ti, tj, s1, s2);
 }
 
 template <bool Y16>
 __global__ void __launch_bounds__(NTH, 1)
     sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
+    grid_launch_dependents();
     tc_tile<Y16>(a, Lo, &ymap, w, blockIdx.z, smraw);
 }
 
@@ -358,6 +365,7 @@ __global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restr
     extern __shared__ __align__(1024) uint8_t smraw[];
     __shared__ StepArgs s_a;
     __shared__ TcLayout s_l;
+    grid_launch_dependents();
     if (threadIdx.x == 0) {
         const int model = order[blockIdx.z / per];
         s_a = av[model];
@@ -458,11 +466,18 @@ cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
     a.TI = tc->TI;
     a.TJ = tc->TJ;
     dim3 grid(tc->TJ, tc->TI, h->per);
-    if (h->y16)
-        sweep_tc_kernel<true><<<grid, NTH, tc->lay.smem, st>>>(a, tc->lay, tc->ymap, w);
-    else
-        sweep_tc_kernel<false><<<grid, NTH, tc->lay.smem, st>>>(a, tc->lay, tc->ymap, w);
-    return cudaGetLastError();
+    const cudaError_t e =
+        h->y16 ? gmf_launch_pdl(sweep_tc_kernel<true>, grid, dim3(NTH), tc->lay.smem, st, a, tc->lay, tc->ymap, w)
+               : gmf_launch_pdl(sweep_tc_kernel<false>, grid, dim3(NTH), tc->lay.smem, st, a, tc->lay, tc->ymap, w);
+    return e;
+}
+
+cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st) {
+    const TcState* tc = (const TcState*)h->tc;
+    StepArgs a = gmf_make_args(h);
+    a.TI = tc->TI;
+    a.TJ = tc->TJ;
+    return gmf_launch_update(a, w, TT, st);
 }
 
 size_t gmf_tc_layout_size() { return sizeof(TcLayout); }
@@ -483,11 +498,11 @@ cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, con
                                 int nmodels, uint32_t smem, int w, cudaStream_t st) {
     const TcState* tc = (const TcState*)h0->tc;
     dim3 grid(tc->TJ, tc->TI, h0->per * nmodels);
-    if (h0->y16)
-        sweep_tc_multi<true><<<grid, NTH, smem, st>>>(d_args, (const TcLayout*)d_lays, d_order, h0->per, tc->ymap, w);
-    else
-        sweep_tc_multi<false><<<grid, NTH, smem, st>>>(d_args, (const TcLayout*)d_lays, d_order, h0->per, tc->ymap, w);
-    return cudaGetLastError();
+    const TcLayout* lays = (const TcLayout*)d_lays;
+    return h0->y16 ? gmf_launch_pdl(sweep_tc_multi<true>, grid, dim3(NTH), smem, st, d_args, lays, d_order, h0->per,
+                                    tc->ymap, w)
+                   : gmf_launch_pdl(sweep_tc_multi<false>, grid, dim3(NTH), smem, st, d_args, lays, d_order, h0->per,
+                                    tc->ymap, w);
 }
 
 void gmf_tc_free(gmf_model* h) {

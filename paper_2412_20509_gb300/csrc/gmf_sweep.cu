@@ -1,9 +1,10 @@
 // Batched rank sweep: several GMF fits of different latent rank d on the same
 // count matrix (the model-selection use of Sec. 4.2, where d must be chosen
 // from a grid of fits). Model 0 owns the permuted counts; the others read them.
-// One launch per sweep covers every model (grid z = model slot x block; the
-// heaviest models get the lowest slots so their CTAs start first), and a whole
-// epoch of these launches is captured once into a CUDA graph.
+// One tile launch per sweep covers every model (grid z = model slot x block;
+// the heaviest models get the lowest slots so their CTAs start first), then one
+// update launch covers every model's strips; a whole epoch of these launches
+// is captured once into a CUDA graph.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -29,6 +30,8 @@ struct gmf_sweep {
     void* d_lays = nullptr;
     int* d_order = nullptr;
     size_t smem = 0;
+    size_t upd_smem = 0;   // update launch: the largest model's staging
+    int upd_units = 0;     // update launch: CTAs per model
     int mixed = 0;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t cap = nullptr;
@@ -94,7 +97,9 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
         } else {
             s->smem = std::max(s->smem, gmf_sweep_simt_smem(h));
         }
+        s->upd_smem = std::max(s->upd_smem, gmf_update_smem(args[i]));
     }
+    s->upd_units = gmf_update_units(args[0], s->mixed ? 128 : GMF_TILE);
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMalloc(&s->d_args, sizeof(StepArgs) * n_models) != cudaSuccess ||
         cudaMalloc(&s->d_order, sizeof(int) * n_models) != cudaSuccess ||
@@ -115,8 +120,11 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
 
 static cudaError_t launch(gmf_sweep* s, int w, cudaStream_t st) {
     const int nm = (int)s->models.size();
-    if (s->mixed) return gmf_tc_launch_multi(s->models[0], s->d_args, s->d_lays, s->d_order, nm, (uint32_t)s->smem, w, st);
-    return gmf_simt_launch_multi(s->models[0], s->d_args, s->d_order, nm, s->smem, w, st);
+    const cudaError_t e =
+        s->mixed ? gmf_tc_launch_multi(s->models[0], s->d_args, s->d_lays, s->d_order, nm, (uint32_t)s->smem, w, st)
+                 : gmf_simt_launch_multi(s->models[0], s->d_args, s->d_order, nm, s->smem, w, st);
+    if (e != cudaSuccess) return e;
+    return gmf_launch_update_multi(s->d_args, nm, s->upd_units, s->upd_smem, w, s->mixed ? 128 : GMF_TILE, st);
 }
 
 extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream) {

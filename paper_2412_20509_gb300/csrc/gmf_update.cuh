@@ -1,15 +1,17 @@
-// Block geometry, arrival counting and the smoothed local update shared by the
-// FP32 and tensor-core block-step kernels (eq. 12, eq. 14, App. B).
+// Block geometry and the smoothed local update shared by the FP32 and
+// tensor-core block-step kernels (eq. 12, eq. 14, App. B).
 //
-// Each tile kernel writes its row partials (sum_j Ddot_ij R_jc, sum_j Dddot_ij
-// R_jc^2 for the row-free columns c) and column partials to a per-tile slot
-// (column-major: G(o, c) at slot[c*T + o], H(o, c) at slot[(nf + c)*T + o]),
-// then calls tile_arrive_update(): an arrival counter per row strip and per
-// column strip elects the last CTA of the strip, which sums the strip's
-// partials in tile order and applies scale factor, penalty, damping, EMA and
-// step to its rows (columns). Every reader of those parameters in this sweep
-// has arrived before the update starts, so it cannot race with a reader, and
-// no CTA ever waits on another.
+// A sweep is two launches. The tile kernel writes, per tile, its row partials
+// (sum_j Ddot_ij R_jc, sum_j Dddot_ij R_jc^2 for the row-free columns c) and
+// column partials to a per-tile slot (column-major: G(o, c) at slot[c*T + o],
+// H(o, c) at slot[(nf + c)*T + o]) and the tile's NB moment sums. The update
+// kernel then gives every 32-row slice of every row strip and column strip its
+// own CTA: it sums the strip's slots in tile order and applies scale factor,
+// penalty, damping, EMA and step to its rows (columns); its block 0 also
+// updates the NB shape from the moment sums. Both kernels are launched with
+// programmatic stream serialization: each waits (griddepcontrol.wait) for the
+// launch before it to complete before it reads or writes the model state, so
+// the next tile kernel's prologue and count-tile loads overlap the update.
 #pragma once
 
 #include "gmf_internal.cuh"
@@ -70,45 +72,83 @@ __device__ __forceinline__ void smoothed_step(float& theta, float& gbar, float& 
     if (!isfinite(theta)) atomicOr(a.err, GMF_DEVERR_NONFINITE);
 }
 
-// Update of one strip (rows of a row strip, or columns of a column strip).
-// Per-tile partial slots hold G(o, c) at slot[c*T + o] and H(o, c) at
-// slot[(nf + c)*T + o]; the nslots slots of the strip are nslot_stride apart
-// and are summed in slot order. Items (o, c) go to threads c-major so that the
-// partial loads coalesce; each thread issues the loads of IB items at once.
-template <int T, int NT, int IB>
-__device__ __forceinline__ void strip_update(const StepArgs& a, const float* __restrict__ part, size_t slot_stride,
-                                             int nslots, int no, int nf, int64_t first, bool rowside, float scale,
-                                             const float* s_rc) {
-    const int total = no * nf;
-    for (int e0 = threadIdx.x; e0 < total; e0 += NT * IB) {
-        float* pth[IB];
-        float* pgb[IB];
-        float* phb[IB];
-        float th[IB], gb[IB], hb[IB], sg[IB], sh[IB], lam[IB];
+// Programmatic dependent launch: wait for the preceding launch in the stream
+// to complete (a no-op without one), and let the next launch start early.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Asynchronous 4-byte global -> shared copy (sm_80 cp.async).
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Moment sums of one tile for the NB shape update (App. B), written to the
+// tile's slot of nbpart. Every thread of the CTA calls this.
+template <int NT>
+__device__ __forceinline__ void tile_moments(const StepArgs& a, int k, int ti, int tj, float s1, float s2) {
+    __shared__ float red[NT / 32];
+    if (a.family == GMF_NEGBIN && a.alpha_mode == 1) {
+        const float S1 = block_sum_f<NT>(s1, red);
+        const float S2 = block_sum_f<NT>(s2, red);
+        if (threadIdx.x == 0) {
+            const int cta = (k * a.TI + ti) * a.TJ + tj;
+            a.nbpart[2 * cta] = (double)S1;
+            a.nbpart[2 * cta + 1] = (double)S2;
+        }
+    }
+}
+
+// Update of one slice: the rows [first, first + nr) of L (row side) or of R
+// (column side), nf free values each, which are rows [o_begin, o_begin + nr)
+// of their strip's tiles. The slice's parameter rows, smoothed derivatives and
+// visit counts are contiguous in global memory; they are staged into shared
+// memory with coalesced asynchronous copies while the partials are summed,
+// updated there, and written back with coalesced stores (whole parameter rows:
+// the fixed columns are written back unchanged). The nslots partial slots of
+// the strip are slot_stride apart and are summed in slot order. Items (o, c)
+// go to threads c-major so that the partial loads coalesce; each thread issues
+// the loads of IB items at once. Every thread of the CTA calls this.
+template <int NT, int IB>
+__device__ __forceinline__ void slice_update(const StepArgs& a, const float* __restrict__ part, size_t slot_stride,
+                                             int nslots, int T, int o_begin, int nr, int nf, int64_t first,
+                                             bool rowside, float scale, float rhoc_blk, float* stage) {
+    const int tid = threadIdx.x;
+    const int KP = a.KP, KS = a.KP + 1;  // staged row stride (odd: no bank conflicts)
+    const int NS = nf | 1;               // staged derivative stride
+    float* P = rowside ? a.L : a.R;
+    float* Gb = rowside ? a.GbR : a.GbC;
+    float* Hb = rowside ? a.HbR : a.HbC;
+    int* cnt = rowside ? a.cntR : a.cntC;
+    float* sP = stage;
+    float* sG = sP + nr * KS;
+    float* sH = sG + nr * NS;
+    int* sC = (int*)(sH + nr * NS);
+    for (int e = tid; e < nr * KP; e += NT) {
+        const int r = e / KP;
+        cp_async4(sP + r * KS + (e - r * KP), P + first * KP + e);
+    }
+    for (int e = tid; e < nr * nf; e += NT) {
+        const int r = e / nf;
+        cp_async4(sG + r * NS + (e - r * nf), Gb + first * nf + e);
+        cp_async4(sH + r * NS + (e - r * nf), Hb + first * nf + e);
+    }
+    for (int e = tid; e < nr; e += NT) cp_async4(sC + e, cnt + first + e);
+
+    const int total = nr * nf;
+    const int iters = (total + NT * IB - 1) / (NT * IB);  // the same for every thread
+    for (int it = 0; it < iters; it++) {
+        float sg[IB], sh[IB];
         int oo[IB], cc[IB];
         bool ok[IB];
 #pragma unroll
         for (int b = 0; b < IB; b++) {
-            const int e = e0 + b * NT;
+            const int e = it * NT * IB + b * NT + tid;
             ok[b] = e < total;
-            const int c = ok[b] ? e / no : 0, o = ok[b] ? e - c * no : 0;
-            oo[b] = o;
-            cc[b] = c;
-            const int64_t x = first + o;
-            if (rowside) {
-                pth[b] = a.L + x * a.KP + 1 + a.p + c;
-                pgb[b] = a.GbR + x * a.fr + c;
-                phb[b] = a.HbR + x * a.fr + c;
-                lam[b] = c < a.q ? a.lam[1] : a.lam[2];
-            } else {
-                pth[b] = a.R + x * a.KP + (c < a.p ? 1 + c : 1 + a.q + c);
-                pgb[b] = a.GbC + x * a.fc + c;
-                phb[b] = a.HbC + x * a.fc + c;
-                lam[b] = c < a.p ? a.lam[0] : a.lam[3];
-            }
-            th[b] = ok[b] ? *pth[b] : 0.f;
-            gb[b] = ok[b] ? *pgb[b] : 0.f;
-            hb[b] = ok[b] ? *phb[b] : 1.f;
+            cc[b] = ok[b] ? e / nr : 0;
+            oo[b] = ok[b] ? e - cc[b] * nr : 0;
             sg[b] = sh[b] = 0.f;
         }
         for (int u0 = 0; u0 < nslots; u0 += 4) {
@@ -118,7 +158,7 @@ __device__ __forceinline__ void strip_update(const StepArgs& a, const float* __r
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const bool l = ok[b] && u0 + u < nslots;
-                    const float* src = part + (size_t)(u0 + u) * slot_stride + (size_t)cc[b] * T + oo[b];
+                    const float* src = part + (size_t)(u0 + u) * slot_stride + (size_t)cc[b] * T + o_begin + oo[b];
                     gv[b][u] = l ? __ldcg(src) : 0.f;
                     hv[b][u] = l ? __ldcg(src + (size_t)nf * T) : 0.f;
                 }
@@ -131,112 +171,93 @@ __device__ __forceinline__ void strip_update(const StepArgs& a, const float* __r
                         sh[b] += hv[b][u];
                     }
         }
+        if (it == 0) {
+            cp_async_wait_all();
+            __syncthreads();
+        }
 #pragma unroll
         for (int b = 0; b < IB; b++) {
             if (ok[b]) {
-                smoothed_step(th[b], gb[b], hb[b], sg[b], sh[b], scale, lam[b], a, s_rc[oo[b]]);
-                *pth[b] = th[b];
-                *pgb[b] = gb[b];
-                *phb[b] = hb[b];
+                const int o = oo[b], c = cc[b];
+                const int col = rowside ? 1 + a.p + c : (c < a.p ? 1 + c : 1 + a.q + c);
+                const float lam = rowside ? (c < a.q ? a.lam[1] : a.lam[2]) : (c < a.p ? a.lam[0] : a.lam[3]);
+                const float rc = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, sC[o] + 1) : rhoc_blk;
+                smoothed_step(sP[o * KS + col], sG[o * NS + c], sH[o * NS + c], sg[b], sh[b], scale, lam, a, rc);
             }
         }
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * KP; e += NT) {
+        const int r = e / KP;
+        P[first * KP + e] = sP[r * KS + (e - r * KP)];
+    }
+    for (int e = tid; e < nr * nf; e += NT) {
+        const int r = e / nf;
+        Gb[first * nf + e] = sG[r * NS + (e - r * nf)];
+        Hb[first * nf + e] = sH[r * NS + (e - r * nf)];
+    }
+    for (int e = tid; e < nr; e += NT) cnt[first + e] = sC[e] + 1;
+}
+
+// Work units of the update kernel for one model: per block k of the sweep, the
+// TI row strips and the TJ column strips of tile edge T, each in slices of SR
+// rows (columns).
+constexpr int UPD_NT = 128;  // threads per update CTA
+constexpr int UPD_SR = 32;   // rows (columns) per slice
+
+__host__ __device__ __forceinline__ int update_units(int per, int TI, int TJ, int T) {
+    return per * (TI + TJ) * ((T + UPD_SR - 1) / UPD_SR);
+}
+
+// Floats of shared memory one update CTA stages: UPD_SR rows of the widest side.
+__host__ __device__ __forceinline__ int update_stage_floats(int KP, int fr, int fc) {
+    const int nf = fr > fc ? fr : fc;
+    return UPD_SR * (KP + 1 + 2 * (nf | 1) + 1);
+}
+
+__device__ __forceinline__ void update_unit(const StepArgs& a, int w, int T, int unit, float* stage) {
+    const int nsl = (T + UPD_SR - 1) / UPD_SR;
+    const int per_block = (a.TI + a.TJ) * nsl;
+    const int k = unit / per_block;
+    const int rem = unit - k * per_block;
+    const BlockGeo g = block_geo(a, w, k);
+    const int nTI = (int)((g.nI + T - 1) / T), nTJ = (int)((g.mJ + T - 1) / T);
+    const float rhoc_blk = a.rhoc[w * a.per + k];
+    if (rem < a.TI * nsl) {  // row strip ti of block k
+        const int ti = rem / nsl, o_begin = (rem - ti * nsl) * UPD_SR;
+        if (ti >= nTI) return;
+        const int nstrip = (int)min((int64_t)T, g.nI - (int64_t)ti * T);
+        if (o_begin >= nstrip) return;
+        slice_update<UPD_NT, 4>(a, a.partR + (size_t)((k * a.TI + ti) * a.TJ) * T * 2 * a.fr, (size_t)T * 2 * a.fr,
+                                nTJ, T, o_begin, min(UPD_SR, nstrip - o_begin), a.fr,
+                                g.r0 + (int64_t)ti * T + o_begin, true, (float)a.m / (float)g.mJ, rhoc_blk, stage);
+    } else {  // column strip tj of block k
+        const int r2 = rem - a.TI * nsl;
+        const int tj = r2 / nsl, o_begin = (r2 - tj * nsl) * UPD_SR;
+        if (tj >= nTJ) return;
+        const int nstrip = (int)min((int64_t)T, g.mJ - (int64_t)tj * T);
+        if (o_begin >= nstrip) return;
+        slice_update<UPD_NT, 4>(a, a.partC + (size_t)((k * a.TJ + tj) * a.TI) * T * 2 * a.fc, (size_t)T * 2 * a.fc,
+                                nTI, T, o_begin, min(UPD_SR, nstrip - o_begin), a.fc,
+                                g.c0 + (int64_t)tj * T + o_begin, false, (float)a.n / (float)g.nI, rhoc_blk, stage);
     }
 }
 
-// Arrival, strip updates and the once-per-sweep NB shape update for the tile
-// (ti, tj) of block k of sweep w, tile edge T, NT threads, IB strip items in
-// flight per thread. Must be called by every thread of every CTA of the launch
-// (inactive CTAs included).
-template <int T, int NT, int IB>
-__device__ void tile_arrive_update(const StepArgs& a, int w, int k, int ti, int tj, const BlockGeo& g, int nTI,
-                                   int nTJ, bool active, float s1, float s2, float alpha) {
-    __shared__ int s_flag[3];
-    __shared__ int s_visits[T];
-    __shared__ float s_rc[T];
-    __shared__ float red[NT / 32];
-    const int tid = threadIdx.x;
-    const float rhoc_blk = a.rhoc[w * a.per + k];
-    const int64_t row0 = g.r0 + (int64_t)ti * T, col0 = g.c0 + (int64_t)tj * T;
-    const int nr = active ? (int)min((int64_t)T, g.nI - (int64_t)ti * T) : 0;
-    const int nc = active ? (int)min((int64_t)T, g.mJ - (int64_t)tj * T) : 0;
-
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        s_flag[0] = s_flag[1] = 0;
-        if (active) {
-            unsigned prev = atomicAdd(&a.ctrR[k * a.TI + ti], 1u);
-            s_flag[0] = prev == (unsigned)(nTJ - 1);
-            prev = atomicAdd(&a.ctrC[k * a.TJ + tj], 1u);
-            s_flag[1] = prev == (unsigned)(nTI - 1);
-        }
+// NB shape: moment sums of all tiles of the sweep, in tile order, then one
+// smoothed update per sweep (App. B). One thread.
+__device__ __forceinline__ void nb_shape_update(const StepArgs& a, int w) {
+    if (a.family != GMF_NEGBIN || a.alpha_mode != 1) return;
+    const int total = a.TJ * a.TI * a.per;
+    double T1 = 0.0, T2 = 0.0;
+    for (int c = 0; c < total; c++) {
+        T1 += a.nbpart[2 * c];
+        T2 += a.nbpart[2 * c + 1];
     }
-    __syncthreads();
-
-    if (s_flag[0]) {  // rows [row0, row0 + nr) of block k
-        __threadfence();
-        if (tid < nr) {
-            const int v = a.cntR[row0 + tid] + 1;
-            s_visits[tid] = v;
-            s_rc[tid] = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, v) : rhoc_blk;
-        }
-        __syncthreads();
-        const float scale = (float)a.m / (float)g.mJ;
-        strip_update<T, NT, IB>(a, a.partR + (size_t)((k * a.TI + ti) * a.TJ) * T * 2 * a.fr, (size_t)T * 2 * a.fr, nTJ,
-                            nr, a.fr, row0, true, scale, s_rc);
-        __syncthreads();
-        if (tid < nr) a.cntR[row0 + tid] = s_visits[tid];
-        if (tid == 0) a.ctrR[k * a.TI + ti] = 0u;
-    }
-    if (s_flag[1]) {  // columns [col0, col0 + nc) of block k
-        __threadfence();
-        __syncthreads();
-        if (tid < nc) {
-            const int v = a.cntC[col0 + tid] + 1;
-            s_visits[tid] = v;
-            s_rc[tid] = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, v) : rhoc_blk;
-        }
-        __syncthreads();
-        const float scale = (float)a.n / (float)g.nI;
-        strip_update<T, NT, IB>(a, a.partC + (size_t)((k * a.TJ + tj) * a.TI) * T * 2 * a.fc, (size_t)T * 2 * a.fc, nTI,
-                            nc, a.fc, col0, false, scale, s_rc);
-        __syncthreads();
-        if (tid < nc) a.cntC[col0 + tid] = s_visits[tid];
-        if (tid == 0) a.ctrC[k * a.TJ + tj] = 0u;
-    }
-
-    // NB shape: moment sums pooled over the sweep, one update per sweep (App. B)
-    if (a.family == GMF_NEGBIN && a.alpha_mode == 1) {
-        const float S1 = block_sum_f<NT>(s1, red);
-        const float S2 = block_sum_f<NT>(s2, red);
-        const int cta = (k * a.TI + ti) * a.TJ + tj;
-        if (tid == 0) {
-            a.nbpart[2 * cta] = (double)S1;
-            a.nbpart[2 * cta + 1] = (double)S2;
-        }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const unsigned total = (unsigned)(a.TJ * a.TI * a.per);  // CTAs of this model's sweep
-            s_flag[2] = atomicAdd(a.ctrSweep, 1u) == total - 1;
-        }
-        __syncthreads();
-        if (s_flag[2] && tid == 0) {
-            __threadfence();
-            const int total = a.TJ * a.TI * a.per;
-            double T1 = 0.0, T2 = 0.0;
-            for (int c = 0; c < total; c++) {
-                T1 += __ldcg(a.nbpart + 2 * c);
-                T2 += __ldcg(a.nbpart + 2 * c + 1);
-            }
-            if (T2 > 0.0) {
-                float ahat = (float)(T1 / T2);
-                if (ahat < a.eps) ahat = a.eps;
-                const float rf = a.rho1[w];
-                *a.alpha = (1.f - rf) * alpha + rf * ahat;
-            }
-            *a.ctrSweep = 0u;
-        }
+    if (T2 > 0.0) {
+        float ahat = (float)(T1 / T2);
+        if (ahat < a.eps) ahat = a.eps;
+        const float rf = a.rho1[w];
+        *a.alpha = (1.f - rf) * (*a.alpha) + rf * ahat;
     }
 }
 
