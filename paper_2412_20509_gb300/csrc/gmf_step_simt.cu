@@ -194,6 +194,7 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
     const bool nb = a.family == GMF_NEGBIN;
     const bool moments = nb && a.alpha_mode == 1;
     grid_dependency_wait();  // the previous sweep's update launch writes the model state
+    grid_launch_dependents();  // this sweep's update may start: the previous one has completed
     const float alpha = *a.alpha;
     float s1 = 0.f, s2 = 0.f;
 
@@ -278,7 +279,6 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
 
 __global__ void __launch_bounds__(GMF_THREADS, 3) sweep_kernel(StepArgs a, int w) {
     extern __shared__ __align__(16) float smem[];
-    grid_launch_dependents();
     simt_tile(a, w, blockIdx.z, smem);
 }
 
@@ -287,7 +287,6 @@ __global__ void __launch_bounds__(GMF_THREADS, 2) sweep_multi(const StepArgs* __
                                                              const int* __restrict__ order, int per, int w) {
     extern __shared__ __align__(16) float smem[];
     __shared__ StepArgs s_a;
-    grid_launch_dependents();
     if (threadIdx.x == 0) s_a = av[order[blockIdx.z / per]];
     __syncthreads();
     simt_tile(s_a, w, blockIdx.z % per, smem);

@@ -131,8 +131,11 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
                 tma_load_2d(Ys + b * ATOM, ymap_p, (int)(col0 + (int64_t)b * Lo.JB), (int)row0, &bars[0]);
         }
         // the counts are read-only; everything below reads or writes model state
-        // that the previous sweep's update launch may still be writing
+        // that the previous sweep's update launch may still be writing. The
+        // next launch (this sweep's update) may start once every CTA is here,
+        // i.e. once the previous update has completed.
         grid_dependency_wait();
+        grid_launch_dependents();
         alpha = *a.alpha;
 
         // ---- operands. Thread groups of 128: L rows -> eta A; R rows -> eta B;
@@ -344,6 +347,7 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
         if (warp == 0) tmem_dealloc(tb, Lo.tmem_cols);
     } else {
         grid_dependency_wait();  // before writing this sweep's moment slot
+        grid_launch_dependents();
     }
     tile_moments<NTH>(a, k, ti, tj, s1, s2);
 }
@@ -352,7 +356,6 @@ template <bool Y16>
 __global__ void __launch_bounds__(NTH, 1)
     sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    grid_launch_dependents();
     tc_tile<Y16>(a, Lo, &ymap, w, blockIdx.z, smraw);
 }
 
@@ -365,7 +368,6 @@ __global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restr
     extern __shared__ __align__(1024) uint8_t smraw[];
     __shared__ StepArgs s_a;
     __shared__ TcLayout s_l;
-    grid_launch_dependents();
     if (threadIdx.x == 0) {
         const int model = order[blockIdx.z / per];
         s_a = av[model];

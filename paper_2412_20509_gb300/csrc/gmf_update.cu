@@ -1,7 +1,9 @@
 // The update launch of a sweep: one CTA per 32-row slice of every row strip and
 // column strip of the sweep's blocks (eq. 12, eq. 14), and the once-per-sweep
 // NB shape update (App. B) in block 0. It waits for the sweep's tile launch to
-// complete (griddepcontrol.wait), so it sees every tile's partials.
+// complete (griddepcontrol.wait) before it reads the tiles' partials and moment
+// sums; the slice state it loads before that wait is not written by the tile
+// launch.
 #include "gmf_internal.cuh"
 #include "gmf_update.cuh"
 
@@ -12,8 +14,7 @@ namespace {
 __global__ void __launch_bounds__(UPD_NT) update_kernel(StepArgs a, int w, int T) {
     extern __shared__ __align__(16) float stage[];
     grid_launch_dependents();
-    grid_dependency_wait();
-    update_unit(a, w, T, blockIdx.x, stage);
+    update_unit(a, w, T, blockIdx.x, stage);  // waits for the tile launch inside
     if (blockIdx.x == 0 && threadIdx.x == 0) nb_shape_update(a, w);
 }
 
@@ -24,8 +25,7 @@ __global__ void __launch_bounds__(UPD_NT) update_multi(const StepArgs* __restric
     grid_launch_dependents();
     if (threadIdx.x == 0) s_a = av[blockIdx.y];
     __syncthreads();
-    grid_dependency_wait();
-    update_unit(s_a, w, T, blockIdx.x, stage);
+    update_unit(s_a, w, T, blockIdx.x, stage);  // waits for the tile launch inside
     if (blockIdx.x == 0 && threadIdx.x == 0) nb_shape_update(s_a, w);
 }
 

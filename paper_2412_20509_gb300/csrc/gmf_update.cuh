@@ -9,9 +9,13 @@
 // own CTA: it sums the strip's slots in tile order and applies scale factor,
 // penalty, damping, EMA and step to its rows (columns); its block 0 also
 // updates the NB shape from the moment sums. Both kernels are launched with
-// programmatic stream serialization: each waits (griddepcontrol.wait) for the
-// launch before it to complete before it reads or writes the model state, so
-// the next tile kernel's prologue and count-tile loads overlap the update.
+// programmatic stream serialization and wait (griddepcontrol.wait) for the
+// launch before them to complete before they touch what it writes: the tile
+// kernel before it reads the parameters (its prologue and count-tile loads
+// overlap the previous update), the update kernel before it reads the
+// partials (its slice state is loaded before). A tile kernel lets its update
+// launch start (griddepcontrol.launch_dependents) only after its own wait, so
+// an update never starts while the previous update is still writing.
 #pragma once
 
 #include "gmf_internal.cuh"
@@ -73,7 +77,8 @@ __device__ __forceinline__ void smoothed_step(float& theta, float& gbar, float& 
 }
 
 // Programmatic dependent launch: wait for the preceding launch in the stream
-// to complete (a no-op without one), and let the next launch start early.
+// to complete and its writes to be visible (a no-op without one), and let the
+// next launch start early.
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -104,14 +109,16 @@ __device__ __forceinline__ void tile_moments(const StepArgs& a, int k, int ti, i
 // Update of one slice: the rows [first, first + nr) of L (row side) or of R
 // (column side), nf free values each, which are rows [o_begin, o_begin + nr)
 // of their strip's tiles. The slice's parameter rows, smoothed derivatives and
-// visit counts are contiguous in global memory; they are staged into shared
-// memory with coalesced asynchronous copies while the partials are summed,
-// updated there, and written back with coalesced stores (whole parameter rows:
-// the fixed columns are written back unchanged). The nslots partial slots of
-// the strip are slot_stride apart and are summed in slot order. Items (o, c)
-// go to threads c-major so that the partial loads coalesce; each thread issues
-// the loads of IB items at once. Every thread of the CTA calls this.
-template <int NT, int IB>
+// visit counts are contiguous in global memory: they are loaded (L2, coalesced)
+// BEFORE griddepcontrol.wait, since the tile launch this update follows only
+// reads them and the update launch before it has completed (the tile launch
+// lets this launch start only after its own wait). The partial slots written
+// by that tile launch are read after the wait and summed in slot order. The
+// update runs in shared memory (stage); results go back with coalesced stores
+// (whole parameter rows: the fixed columns are written back unchanged). Items
+// (o, c) go to threads c-major so that the partial loads coalesce. Every
+// thread of the CTA calls this.
+template <int NT, int IB, int PF>
 __device__ __forceinline__ void slice_update(const StepArgs& a, const float* __restrict__ part, size_t slot_stride,
                                              int nslots, int T, int o_begin, int nr, int nf, int64_t first,
                                              bool rowside, float scale, float rhoc_blk, float* stage) {
@@ -126,16 +133,20 @@ __device__ __forceinline__ void slice_update(const StepArgs& a, const float* __r
     float* sG = sP + nr * KS;
     float* sH = sG + nr * NS;
     int* sC = (int*)(sH + nr * NS);
-    for (int e = tid; e < nr * KP; e += NT) {
-        const int r = e / KP;
-        cp_async4(sP + r * KS + (e - r * KP), P + first * KP + e);
+    // slice state -> registers (PF values of each array per thread, the rest later)
+    const int nP = nr * KP, nG = nr * nf;
+    float rp[PF], rg[PF], rh[PF];
+    int rcn = 0;
+#pragma unroll
+    for (int u = 0; u < PF; u++) {
+        const int e = tid + u * NT;
+        rp[u] = e < nP ? __ldcg(P + first * KP + e) : 0.f;
+        rg[u] = e < nG ? __ldcg(Gb + first * nf + e) : 0.f;
+        rh[u] = e < nG ? __ldcg(Hb + first * nf + e) : 0.f;
     }
-    for (int e = tid; e < nr * nf; e += NT) {
-        const int r = e / nf;
-        cp_async4(sG + r * NS + (e - r * nf), Gb + first * nf + e);
-        cp_async4(sH + r * NS + (e - r * nf), Hb + first * nf + e);
-    }
-    for (int e = tid; e < nr; e += NT) cp_async4(sC + e, cnt + first + e);
+    if (tid < nr) rcn = __ldcg(cnt + first + tid);
+
+    grid_dependency_wait();
 
     const int total = nr * nf;
     const int iters = (total + NT * IB - 1) / (NT * IB);  // the same for every thread
@@ -172,7 +183,22 @@ __device__ __forceinline__ void slice_update(const StepArgs& a, const float* __r
                     }
         }
         if (it == 0) {
-            cp_async_wait_all();
+            // slice state: registers, then whatever did not fit, into shared memory
+#pragma unroll
+            for (int u = 0; u < PF; u++) {
+                const int e = tid + u * NT;
+                if (e < nP) sP[(e / KP) * KS + e % KP] = rp[u];
+                if (e < nG) {
+                    sG[(e / nf) * NS + e % nf] = rg[u];
+                    sH[(e / nf) * NS + e % nf] = rh[u];
+                }
+            }
+            for (int e = tid + PF * NT; e < nP; e += NT) sP[(e / KP) * KS + e % KP] = __ldcg(P + first * KP + e);
+            for (int e = tid + PF * NT; e < nG; e += NT) {
+                sG[(e / nf) * NS + e % nf] = __ldcg(Gb + first * nf + e);
+                sH[(e / nf) * NS + e % nf] = __ldcg(Hb + first * nf + e);
+            }
+            if (tid < nr) sC[tid] = rcn;
             __syncthreads();
         }
 #pragma unroll
@@ -187,11 +213,11 @@ __device__ __forceinline__ void slice_update(const StepArgs& a, const float* __r
         }
     }
     __syncthreads();
-    for (int e = tid; e < nr * KP; e += NT) {
+    for (int e = tid; e < nP; e += NT) {
         const int r = e / KP;
         P[first * KP + e] = sP[r * KS + (e - r * KP)];
     }
-    for (int e = tid; e < nr * nf; e += NT) {
+    for (int e = tid; e < nG; e += NT) {
         const int r = e / nf;
         Gb[first * nf + e] = sG[r * NS + (e - r * nf)];
         Hb[first * nf + e] = sH[r * NS + (e - r * nf)];
@@ -215,6 +241,8 @@ __host__ __device__ __forceinline__ int update_stage_floats(int KP, int fr, int 
     return UPD_SR * (KP + 1 + 2 * (nf | 1) + 1);
 }
 
+// One unit of the update launch. Everything before grid_dependency_wait()
+// reads only data that the preceding tile launch does not write.
 __device__ __forceinline__ void update_unit(const StepArgs& a, int w, int T, int unit, float* stage) {
     const int nsl = (T + UPD_SR - 1) / UPD_SR;
     const int per_block = (a.TI + a.TJ) * nsl;
@@ -223,23 +251,30 @@ __device__ __forceinline__ void update_unit(const StepArgs& a, int w, int T, int
     const BlockGeo g = block_geo(a, w, k);
     const int nTI = (int)((g.nI + T - 1) / T), nTJ = (int)((g.mJ + T - 1) / T);
     const float rhoc_blk = a.rhoc[w * a.per + k];
+    constexpr int PF = 4;  // prefetched values per thread and array (UPD_SR x 16 of P with 128 threads)
     if (rem < a.TI * nsl) {  // row strip ti of block k
         const int ti = rem / nsl, o_begin = (rem - ti * nsl) * UPD_SR;
-        if (ti >= nTI) return;
-        const int nstrip = (int)min((int64_t)T, g.nI - (int64_t)ti * T);
-        if (o_begin >= nstrip) return;
-        slice_update<UPD_NT, 4>(a, a.partR + (size_t)((k * a.TI + ti) * a.TJ) * T * 2 * a.fr, (size_t)T * 2 * a.fr,
-                                nTJ, T, o_begin, min(UPD_SR, nstrip - o_begin), a.fr,
-                                g.r0 + (int64_t)ti * T + o_begin, true, (float)a.m / (float)g.mJ, rhoc_blk, stage);
+        const int nstrip = ti < nTI ? (int)min((int64_t)T, g.nI - (int64_t)ti * T) : 0;
+        if (o_begin >= nstrip) {
+            grid_dependency_wait();
+            return;
+        }
+        slice_update<UPD_NT, 4, PF>(a, a.partR + (size_t)((k * a.TI + ti) * a.TJ) * T * 2 * a.fr,
+                                    (size_t)T * 2 * a.fr, nTJ, T, o_begin, min(UPD_SR, nstrip - o_begin), a.fr,
+                                    g.r0 + (int64_t)ti * T + o_begin, true, (float)a.m / (float)g.mJ, rhoc_blk,
+                                    stage);
     } else {  // column strip tj of block k
         const int r2 = rem - a.TI * nsl;
         const int tj = r2 / nsl, o_begin = (r2 - tj * nsl) * UPD_SR;
-        if (tj >= nTJ) return;
-        const int nstrip = (int)min((int64_t)T, g.mJ - (int64_t)tj * T);
-        if (o_begin >= nstrip) return;
-        slice_update<UPD_NT, 4>(a, a.partC + (size_t)((k * a.TJ + tj) * a.TI) * T * 2 * a.fc, (size_t)T * 2 * a.fc,
-                                nTI, T, o_begin, min(UPD_SR, nstrip - o_begin), a.fc,
-                                g.c0 + (int64_t)tj * T + o_begin, false, (float)a.n / (float)g.nI, rhoc_blk, stage);
+        const int nstrip = tj < nTJ ? (int)min((int64_t)T, g.mJ - (int64_t)tj * T) : 0;
+        if (o_begin >= nstrip) {
+            grid_dependency_wait();
+            return;
+        }
+        slice_update<UPD_NT, 4, PF>(a, a.partC + (size_t)((k * a.TJ + tj) * a.TI) * T * 2 * a.fc,
+                                    (size_t)T * 2 * a.fc, nTI, T, o_begin, min(UPD_SR, nstrip - o_begin), a.fc,
+                                    g.c0 + (int64_t)tj * T + o_begin, false, (float)a.n / (float)g.nI, rhoc_blk,
+                                    stage);
     }
 }
 
