@@ -50,6 +50,14 @@ enum {
                             gradient/curvature contractions in BF16, FP32 accumulate */
 };
 enum { GMF_ORTH_B1 = 1, GMF_ORTH_B2 = 2, GMF_ORTH_B3 = 3 };  /* Sec. 2.1 */
+enum {
+    /* Mixed precision: where the tiles of a block fit one thread-block cluster
+       (at most 16 tiles of 128 x 128, with room for the clusters of a sweep on
+       the device), the strip updates run inside the tile launch and the tiles
+       exchange their partial sums through distributed shared memory. This flag
+       keeps them in their own launch instead. Both give bitwise equal results. */
+    GMF_FLAG_NO_CLUSTER = 1
+};
 
 typedef struct gmf_model gmf_model;  /* opaque, library-owned */
 
@@ -68,7 +76,7 @@ typedef struct {
     int32_t alpha_mode;  /* NB only. 0: shape fixed; 1: stochastic moment estimator (App. B),
                             pooled per sweep */
     int32_t precision;   /* GMF_PREC_FP32 or GMF_PREC_MIXED */
-    int32_t reserved0;   /* must be 0 */
+    int32_t flags;       /* GMF_FLAG_* bits; 0 for the defaults */
     double lambda[4];    /* ridge penalties on (B, Gamma, U, V), eq. 6 [0, 0, 1, 0] */
     double a1, a2;       /* EMA weights of eq. 12 [0.1, 0.01] */
     double k0, k1, tau;  /* rho_t = k0 / (1 + k0 k1 t)^tau (Sec. 3.2) [0.01, 1e-3, 0.75] */
@@ -118,6 +126,11 @@ int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, void* stream)
 
 /* Number of sweeps per epoch: max(r, s) with r = ceil(n/nb_row), s = ceil(m/nb_col). */
 int32_t gmf_num_sweeps(const gmf_model* h);
+
+/* Kernel launches per sweep of gmf_sgd_epoch / gmf_sgd_sweeps: 1 when the
+ * strip updates run inside the tile launch (cluster mode, see
+ * GMF_FLAG_NO_CLUSTER), else 2 (tiles, then updates). -1 for a NULL handle. */
+int32_t gmf_launches_per_sweep(const gmf_model* h);
 
 /*
  * gmf_sgd_epoch -- one epoch of Algorithm 1: every block (I_a, J_b) once.

@@ -21,13 +21,15 @@ GMF_POISSON, GMF_NEGBIN = 0, 1
 GMF_Y_INT32, GMF_Y_UINT16 = 0, 1
 GMF_PREC_FP32, GMF_PREC_MIXED = 0, 1
 GMF_ORTH_B1, GMF_ORTH_B2, GMF_ORTH_B3 = 1, 2, 3
+GMF_FLAG_NO_CLUSTER = 1
 
 FAMILIES = {"poisson": GMF_POISSON, "negbin": GMF_NEGBIN}
 PRECISIONS = {"fp32": GMF_PREC_FP32, "mixed": GMF_PREC_MIXED}
 ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
 
 # Every function declared in include/gmf.h.
-EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_num_sweeps", "gmf_sgd_epoch", "gmf_sgd_sweeps",
+EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_num_sweeps", "gmf_launches_per_sweep",
+           "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
            "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
@@ -44,7 +46,7 @@ class GmfError(RuntimeError):
 class gmf_config(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("p", C.c_int32), ("q", C.c_int32), ("d", C.c_int32),
                 ("family", C.c_int32), ("nb_row", C.c_int32), ("nb_col", C.c_int32), ("bias_corr", C.c_int32),
-                ("alpha_mode", C.c_int32), ("precision", C.c_int32), ("reserved0", C.c_int32),
+                ("alpha_mode", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32),
                 ("lambda_", C.c_double * 4), ("a1", C.c_double), ("a2", C.c_double), ("k0", C.c_double),
                 ("k1", C.c_double), ("tau", C.c_double), ("damping", C.c_double), ("eps", C.c_double),
                 ("eta_clamp", C.c_double)]
@@ -69,6 +71,7 @@ def lib():
                                VP, VP, VP, VP, C.c_double, VP]),
         "gmf_update_y": (C.c_int, [VP, VP, C.c_int32, VP]),
         "gmf_num_sweeps": (C.c_int32, [VP]),
+        "gmf_launches_per_sweep": (C.c_int32, [VP]),
         "gmf_sgd_epoch": (C.c_int, [VP, VP, VP]),
         "gmf_sgd_sweeps": (C.c_int, [VP, VP, C.c_int32, C.c_int32, VP]),
         "gmf_deviance": (C.c_int, [VP, C.POINTER(C.c_double), VP]),
@@ -140,7 +143,7 @@ def _torch_ydt(Y):
     raise TypeError("counts must be int32 or 16-bit (uint16 / int16 view)")
 
 
-def make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision="fp32"):
+def make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision="fp32", flags=0):
     cfg = gmf_config()
     lib().gmf_config_default(C.byref(cfg), n, m, p, q, d, FAMILIES[family], nb_row, nb_col)
     s = settings
@@ -150,6 +153,7 @@ def make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision="fp32
     cfg.bias_corr = int(s["bias_corr"])
     cfg.alpha_mode = int(s["alpha_mode"])
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.flags = int(flags)
     return cfg
 
 
@@ -164,7 +168,7 @@ class Model:
     """One GMF fit held on the GPU (a ``gmf_model`` handle)."""
 
     def __init__(self, Y, X, Z, offset, start, *, family, nb_row, nb_col, row_perm, col_perm, settings,
-                 precision="fp32", W=None, stream=None):
+                 precision="fp32", W=None, stream=None, flags=0):
         import torch
         self._h = VP()
         on_dev = isinstance(Y, torch.Tensor) and Y.is_cuda
@@ -183,7 +187,7 @@ class Model:
         p, q = X.shape[1], Z.shape[1]
         d = np.asarray(start["U"]).shape[1]
         self.dims = (n, m, p, q, d)
-        self.cfg = make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision)
+        self.cfg = make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision, flags)
         off = None if offset is None else np.ascontiguousarray(offset, dtype=np.float64)
         B0 = _f64(start["B"], (m, p)); G0 = _f64(start["Gamma"], (n, q))
         U0 = _f64(start["U"], (n, d)); V0 = _f64(start["V"], (m, d))
@@ -224,6 +228,11 @@ class Model:
     @property
     def num_sweeps(self):
         return lib().gmf_num_sweeps(self._h)
+
+    @property
+    def launches_per_sweep(self):
+        """Kernel launches per sweep: 1 in cluster mode, else 2."""
+        return lib().gmf_launches_per_sweep(self._h)
 
     def epoch(self, sigma, stream=None):
         sigma = np.ascontiguousarray(sigma, dtype=np.int32)

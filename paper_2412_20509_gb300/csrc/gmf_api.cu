@@ -42,6 +42,7 @@ extern "C" const char* gmf_version(void) { return "gmf-gb300 0.1 (sm_103a)"; }
 int gmf_tc_prepare_checked(gmf_model* h, std::string* err);
 cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st);
 cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st);
+int gmf_tc_cluster(const gmf_model* h);
 void gmf_tc_free(gmf_model* h);
 
 // One sweep launch of the configured path.
@@ -124,7 +125,7 @@ static void release(gmf_model* h) {
         h->ystage = nullptr;
     }
     void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
-                    h->rperm, h->cperm, h->ystage, h->Rorig, h->partR, h->partC, h->nbpart, h->sigma, h->rhoc,
+                    h->rperm, h->cperm, h->ystage, h->Rorig, h->partR, h->partC, h->nbpart, h->nbctr, h->sigma, h->rhoc,
                     h->rho1, h->err, h->devpart, h->devtot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -206,7 +207,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     if (c.alpha_mode != 0 && c.alpha_mode != 1) return fail(GMF_ERR_ARG, "gmf_init: alpha_mode must be 0 or 1");
     if (c.precision != GMF_PREC_FP32 && c.precision != GMF_PREC_MIXED)
         return fail(GMF_ERR_ARG, "gmf_init: unknown precision");
-    if (c.reserved0 != 0) return fail(GMF_ERR_ARG, "gmf_init: reserved0 must be 0");
+    if (c.flags & ~GMF_FLAG_NO_CLUSTER) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
     if (!(c.a1 > 0 && c.a1 <= 1 && c.a2 > 0 && c.a2 <= 1)) return fail(GMF_ERR_ARG, "gmf_init: a1, a2 in (0, 1]");
     if (!(c.k0 > 0) || c.k1 < 0 || !(c.tau > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad learning-rate schedule");
     if (c.damping < 0 || !(c.eta_clamp > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad damping or eta_clamp");
@@ -279,6 +280,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     INIT_CUDA(dalloc(&h->partR, (size_t)h->per * h->TI * h->TJ * GMF_TILE * 2 * std::max(h->fr, 1)));
     INIT_CUDA(dalloc(&h->partC, (size_t)h->per * h->TI * h->TJ * GMF_TILE * 2 * std::max(h->fc, 1)));
     INIT_CUDA(dalloc(&h->nbpart, (size_t)2 * h->per * h->TI * h->TJ));
+    INIT_CUDA(dalloc(&h->nbctr, 1));
     INIT_CUDA(dalloc(&h->sigma, (size_t)h->nsw));
     INIT_CUDA(dalloc(&h->rhoc, (size_t)h->nsw * h->per));
     INIT_CUDA(dalloc(&h->rho1, (size_t)h->nsw));
@@ -296,6 +298,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     INIT_CUDA(cudaMemsetAsync(h->cntR, 0, sizeof(int) * c.n, st));
     INIT_CUDA(cudaMemsetAsync(h->cntC, 0, sizeof(int) * c.m, st));
     INIT_CUDA(cudaMemsetAsync(h->err, 0, sizeof(unsigned), st));
+    INIT_CUDA(cudaMemsetAsync(h->nbctr, 0, sizeof(unsigned), st));
     float a0 = (float)alpha0;
     INIT_CUDA(cudaMemcpyAsync(h->alpha, &a0, sizeof(float), cudaMemcpyHostToDevice, st));
     {
@@ -360,6 +363,11 @@ extern "C" int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, vo
 }
 
 extern "C" int32_t gmf_num_sweeps(const gmf_model* h) { return h ? h->nsw : -1; }
+
+extern "C" int32_t gmf_launches_per_sweep(const gmf_model* h) {
+    if (!h) return -1;
+    return h->cfg.precision == GMF_PREC_MIXED && gmf_tc_cluster(h) ? 1 : 2;
+}
 
 // Wait for the recorded event pairs and add their durations to the running total.
 static int trace_collect(gmf_model* h, cudaStream_t st) {

@@ -54,6 +54,7 @@ struct StepArgs {
     float* partR;               // [per][TI][TJ][TILE][2*fr]: row partials of tile (ti, tj)
     float* partC;               // [per][TJ][TI][TILE][2*fc]: column partials of tile (ti, tj)
     double* nbpart;             // [per*TI*TJ][2]: NB moment sums of each tile
+    unsigned* nbctr;            // [1]: tiles of the sweep done (cluster mode's NB shape update)
     const int* sigma;           // device copy of the epoch's sweep offsets
     const float* rhoc;          // [nsw][per]: rho_t * c_t per block (rho_t alone when bias_corr = 1)
     const float* rho1;          // [nsw]: rho at the first block of each sweep (NB shape update)
@@ -89,6 +90,7 @@ struct gmf_model {
     float* partR;
     float* partC;
     double* nbpart;
+    unsigned* nbctr;
     int* sigma;
     float* rhoc;
     float* rho1;
@@ -131,6 +133,22 @@ cudaError_t gmf_launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, siz
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Raise `kernel`'s dynamic shared-memory limit to what the device allows, after
+// checking that `need` bytes fit (cudaErrorInvalidValue if not). The limit
+// belongs to the function, not to a handle: every handle sets the same value,
+// so creating one model never lowers the limit another model's launches need.
+inline cudaError_t gmf_smem_limit(const void* kernel, size_t need) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if (need > (size_t)lim) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 // gmf_update.cu: the strip-update launch that follows each tile launch of a

@@ -363,10 +363,10 @@ int gmf_project_run(gmf_model* h, const void* Ynew, int y16, int64_t n_new, cons
     const dim3 grid((unsigned)((n_new + CC - 1) / CC));
     cudaError_t e;
     if (np <= 32 * 8) {
-        e = cudaFuncSetAttribute(project_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = gmf_smem_limit((const void*)project_kernel<8>, smem);
         if (e == cudaSuccess) project_kernel<8><<<grid, NT, smem, st>>>(a);
     } else {
-        e = cudaFuncSetAttribute(project_kernel<17>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = gmf_smem_limit((const void*)project_kernel<17>, smem);
         if (e == cudaSuccess) project_kernel<17><<<grid, NT, smem, st>>>(a);
     }
     if (e == cudaSuccess) e = cudaGetLastError();

@@ -440,6 +440,7 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.partR = h->partR;
     a.partC = h->partC;
     a.nbpart = h->nbpart;
+    a.nbctr = h->nbctr;
     a.sigma = h->sigma;
     a.rhoc = h->rhoc;
     a.rho1 = h->rho1;
@@ -448,17 +449,12 @@ StepArgs gmf_make_args(gmf_model* h) {
 }
 
 cudaError_t gmf_sweep_simt_attr(gmf_model* h) {
-    const size_t smem = sweep_smem(h->K, h->fr, h->fc);
-    if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return gmf_smem_limit((const void*)sweep_kernel, sweep_smem(h->K, h->fr, h->fc));
 }
 
 size_t gmf_sweep_simt_smem(const gmf_model* h) { return sweep_smem(h->K, h->fr, h->fc); }
 
-cudaError_t gmf_simt_multi_attr(size_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(sweep_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
+cudaError_t gmf_simt_multi_attr(size_t smem) { return gmf_smem_limit((const void*)sweep_multi, smem); }
 
 cudaError_t gmf_simt_launch_multi(const gmf_model* h0, const StepArgs* d_args, const int* d_order, int nmodels,
                                   size_t smem, int w, cudaStream_t st) {

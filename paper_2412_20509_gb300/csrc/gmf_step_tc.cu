@@ -52,12 +52,18 @@ struct TcLayout {
     uint32_t off_rf, off_rf2, off_lf, off_lf2;
     uint32_t smem;         // dynamic shared memory including alignment slack
     uint32_t tmem_cols, t_row, t_col;
+    // cluster mode (one thread-block cluster per block of the sweep)
+    int SRr, SCc;          // rows of a row strip / columns of a column strip each CTA updates
+    uint32_t off_cp;       // slots of this CTA's slices: row partials [TJ][2 fr][SRr], column [TI][2 fc][SCc]
+    uint32_t off_st;       // the CTA's update slices: parameter rows, smoothed derivatives, visit counts
+    uint32_t smem_cl;      // dynamic shared memory of the cluster kernel
 };
 
 struct TcState {
     TcLayout lay;
     CUtensorMap ymap;
     int TI, TJ;
+    int cluster;           // 1: the strip updates run inside the tile launch (cluster mode)
 };
 
 __device__ __forceinline__ void st_shared_v4(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -79,9 +85,131 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, unsigne
     return __syncthreads_and(ok) != 0;
 }
 
+// ---- cluster mode. The TI x TJ tiles of a block form one thread-block
+// cluster. CTA (ti, tj) owns rows [tj*SRr, (tj+1)*SRr) of row strip ti and
+// columns [ti*SCc, (ti+1)*SCc) of column strip tj. Each tile stores its row
+// (column) partials straight from TMEM into the owners' shared memory, one
+// slot per source tile (distributed shared memory stores, coalesced along the
+// rows); after one cluster barrier each owner sums its slots in tile order
+// (the order of the update launch, so both modes give the same bits) and
+// applies the smoothed step. Nothing touches a peer's shared memory after that
+// barrier, so no second barrier is needed before a CTA exits.
+
+struct ClSlice {
+    int nrs, ncs;              // rows / columns of this CTA's slices (0: none)
+    int64_t first_r, first_c;  // their first global row of L / row of R
+    int or0, oc0;              // their first index within the strip's tiles
+};
+
+__device__ __forceinline__ ClSlice cl_slice(const StepArgs& a, const TcLayout& Lo, const BlockGeo& g, int ti, int tj,
+                                            int nTI, int nTJ) {
+    ClSlice c;
+    c.or0 = tj * Lo.SRr;
+    c.oc0 = ti * Lo.SCc;
+    const int nstr = ti < nTI ? (int)min((int64_t)TT, g.nI - (int64_t)ti * TT) : 0;
+    const int nstc = tj < nTJ ? (int)min((int64_t)TT, g.mJ - (int64_t)tj * TT) : 0;
+    c.nrs = max(0, min(Lo.SRr, nstr - c.or0));
+    c.ncs = max(0, min(Lo.SCc, nstc - c.oc0));
+    c.first_r = g.r0 + (int64_t)ti * TT + c.or0;
+    c.first_c = g.c0 + (int64_t)tj * TT + c.oc0;
+    return c;
+}
+
+// Shared-memory pieces of one side's slice (rows of P, Gb, Hb, counts).
+struct ClStage {
+    float *P, *G, *H;
+    int* C;
+};
+
+__device__ __forceinline__ ClStage cl_stage_ptrs(float* base, int rows, int KS, int NS) {
+    ClStage t;
+    t.P = base;
+    t.G = t.P + rows * KS;
+    t.H = t.G + rows * NS;
+    t.C = (int*)(t.H + rows * NS);
+    return t;
+}
+
+// Start the copies of this CTA's slices with threads [t0, t0 + nt) (after the
+// dependency wait: the previous sweep wrote these rows). Each thread waits for
+// its own copies (cp.async.wait_all) before the cluster barrier.
+__device__ __forceinline__ void cl_stage_issue(const StepArgs& a, const TcLayout& Lo, uint8_t* sm, const ClSlice& c,
+                                               int t0, int nt) {
+    const int KS = a.KP + 1;
+    const int tid = (int)threadIdx.x - t0;
+    if (tid < 0 || tid >= nt) return;
+    const ClStage r = cl_stage_ptrs((float*)(sm + Lo.off_st), Lo.SRr, KS, a.fr | 1);
+    const ClStage q = cl_stage_ptrs(r.P + (size_t)Lo.SRr * (KS + 2 * (a.fr | 1) + 1), Lo.SCc, KS, a.fc | 1);
+    for (int e = tid; e < c.nrs * a.KP; e += nt)
+        cp_async4(r.P + (e / a.KP) * KS + e % a.KP, a.L + c.first_r * a.KP + e);
+    for (int e = tid; e < c.ncs * a.KP; e += nt)
+        cp_async4(q.P + (e / a.KP) * KS + e % a.KP, a.R + c.first_c * a.KP + e);
+    for (int e = tid; e < c.nrs * a.fr; e += nt) {
+        cp_async4(r.G + (e / a.fr) * (a.fr | 1) + e % a.fr, a.GbR + c.first_r * a.fr + e);
+        cp_async4(r.H + (e / a.fr) * (a.fr | 1) + e % a.fr, a.HbR + c.first_r * a.fr + e);
+    }
+    for (int e = tid; e < c.ncs * a.fc; e += nt) {
+        cp_async4(q.G + (e / a.fc) * (a.fc | 1) + e % a.fc, a.GbC + c.first_c * a.fc + e);
+        cp_async4(q.H + (e / a.fc) * (a.fc | 1) + e % a.fc, a.HbC + c.first_c * a.fc + e);
+    }
+    for (int e = tid; e < c.nrs; e += nt) cp_async4(r.C + e, a.cntR + c.first_r + e);
+    for (int e = tid; e < c.ncs; e += nt) cp_async4(q.C + e, a.cntC + c.first_c + e);
+}
+
+// The strip updates of cluster mode. Every thread of every CTA of the cluster
+// calls this (one cluster barrier).
+__device__ __forceinline__ void cl_update(const StepArgs& a, const TcLayout& Lo, uint8_t* sm, const ClSlice& c,
+                                          const BlockGeo& g, float rhoc_blk, int nTI, int nTJ) {
+    const int KS = a.KP + 1, NSr = a.fr | 1, NSc = a.fc | 1;
+    const ClStage r = cl_stage_ptrs((float*)(sm + Lo.off_st), Lo.SRr, KS, NSr);
+    const ClStage q = cl_stage_ptrs(r.P + (size_t)Lo.SRr * (KS + 2 * NSr + 1), Lo.SCc, KS, NSc);
+    cp_async_wait_all();
+    cluster_sync();  // every tile's partials are in their owners' slots; the slices are staged
+    const float* prow = (const float*)(sm + Lo.off_cp);
+    const float* pcol = prow + (size_t)a.TJ * 2 * a.fr * Lo.SRr;
+    const float scale_r = (float)a.m / (float)g.mJ, scale_c = (float)a.n / (float)g.nI;
+    const int tot_r = c.nrs * a.fr, total = tot_r + c.ncs * a.fc;
+    for (int e = threadIdx.x; e < total; e += NTH) {
+        const bool rowside = e < tot_r;
+        const int nf = rowside ? a.fr : a.fc;
+        const int no = rowside ? c.nrs : c.ncs;
+        const int SR = rowside ? Lo.SRr : Lo.SCc;
+        const int e2 = rowside ? e : e - tot_r;
+        const int cc = e2 / no, o = e2 - cc * no;
+        const int nsl = rowside ? nTJ : nTI;
+        const float* slot = (rowside ? prow : pcol) + (size_t)cc * SR + o;
+        const size_t sstride = (size_t)2 * nf * SR, hofs = (size_t)nf * SR;
+        float gs = 0.f, hs = 0.f;
+        for (int t = 0; t < nsl; t++) {
+            gs += slot[t * sstride];
+            hs += slot[t * sstride + hofs];
+        }
+        const ClStage& st = rowside ? r : q;
+        const int NS = rowside ? NSr : NSc;
+        const int col = rowside ? 1 + a.p + cc : (cc < a.p ? 1 + cc : 1 + a.q + cc);
+        const float lam = rowside ? (cc < a.q ? a.lam[1] : a.lam[2]) : (cc < a.p ? a.lam[0] : a.lam[3]);
+        const float rc = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, st.C[o] + 1) : rhoc_blk;
+        smoothed_step(st.P[o * KS + col], st.G[o * NS + cc], st.H[o * NS + cc], gs, hs, rowside ? scale_r : scale_c,
+                      lam, a, rc);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < c.nrs * a.KP; e += NTH) a.L[c.first_r * a.KP + e] = r.P[(e / a.KP) * KS + e % a.KP];
+    for (int e = threadIdx.x; e < c.ncs * a.KP; e += NTH) a.R[c.first_c * a.KP + e] = q.P[(e / a.KP) * KS + e % a.KP];
+    for (int e = threadIdx.x; e < c.nrs * a.fr; e += NTH) {
+        a.GbR[c.first_r * a.fr + e] = r.G[(e / a.fr) * NSr + e % a.fr];
+        a.HbR[c.first_r * a.fr + e] = r.H[(e / a.fr) * NSr + e % a.fr];
+    }
+    for (int e = threadIdx.x; e < c.ncs * a.fc; e += NTH) {
+        a.GbC[c.first_c * a.fc + e] = q.G[(e / a.fc) * NSc + e % a.fc];
+        a.HbC[c.first_c * a.fc + e] = q.H[(e / a.fc) * NSc + e % a.fc];
+    }
+    for (int e = threadIdx.x; e < c.nrs; e += NTH) a.cntR[c.first_r + e] = r.C[e] + 1;
+    for (int e = threadIdx.x; e < c.ncs; e += NTH) a.cntC[c.first_c + e] = q.C[e] + 1;
+}
+
 // One tile (blockIdx.x, blockIdx.y) of block k of sweep w for the model whose
-// arguments are a / Lo.
-template <bool Y16>
+// arguments are a / Lo. CL: cluster mode (the strip updates run here).
+template <bool Y16, bool CL>
 __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, const CUtensorMap* ymap_p, int w,
                                         int k, uint8_t* smraw) {
     __shared__ uint64_t bars[3];
@@ -98,6 +226,13 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
     float s1 = 0.f, s2 = 0.f;
 
     uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+    ClSlice cls{};
+    float rhoc_blk = 0.f;  // the block's step factor, fixed for the epoch
+    if (CL) {
+        rhoc_blk = a.rhoc[w * a.per + k];
+        cls = cl_slice(a, Lo, g, ti, tj, nTI, nTJ);
+        cluster_arrive_relaxed();  // waited for before the first store into a peer (all peers have started)
+    }
     if (active) {
         uint8_t* Ys = sm;
         uint8_t* Aop = sm + Lo.off_u;
@@ -310,8 +445,11 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
             }
             umma_commit(&bars[2]);
         }
+        // warps 8-15 have no partials to read: they start the update slices' copies
+        if (CL) cl_stage_issue(a, Lo, sm, cls, NTH / 2, NTH / 2);
         if (ok) ok = cta_wait(&bars[2], 0, a.err);
         tc_fence_after();
+        if (CL) cluster_wait();
 
         if (ok && warp < 8) {
             const int q = warp & 3;
@@ -323,6 +461,13 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
             const uint32_t tg = tb + lanes + (rowside ? Lo.t_row : Lo.t_col);
             float* dst = rowside ? a.partR + (size_t)((k * a.TI + ti) * a.TJ + tj) * TT * 2 * a.fr
                                  : a.partC + (size_t)((k * a.TJ + tj) * a.TI + ti) * TT * 2 * a.fc;
+            // cluster mode: slot `src` of the owner of row (column) o, at index o - own * SR
+            const int SR = rowside ? Lo.SRr : Lo.SCc;
+            const int own = CL ? o / SR : 0, ol = o - own * SR, src = rowside ? tj : ti;
+            const uint32_t slots = CL ? mapa_shared(smem_u32(sm + Lo.off_cp) +
+                                                        (rowside ? 0u : (uint32_t)(4 * a.TJ * 2 * a.fr * Lo.SRr)),
+                                                    rowside ? (uint32_t)(own + ti * a.TJ) : (uint32_t)(tj + own * a.TJ))
+                                      : 0u;
             const bool o_ok = o < (rowside ? nr : nc);
             for (int c0 = 0; c0 < NF; c0 += 16) {
                 uint32_t rg[16], rh[16];
@@ -334,8 +479,14 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
                     for (int u = 0; u < 16; u++) {
                         const int c = c0 + u;
                         if (c < nf) {
-                            dst[(size_t)c * TT + o] = __uint_as_float(rg[u]);
-                            dst[(size_t)(nf + c) * TT + o] = __uint_as_float(rh[u]);
+                            if (CL) {
+                                st_dsmem_f32(slots + 4u * (uint32_t)((src * 2 * nf + c) * SR + ol), __uint_as_float(rg[u]));
+                                st_dsmem_f32(slots + 4u * (uint32_t)((src * 2 * nf + nf + c) * SR + ol),
+                                             __uint_as_float(rh[u]));
+                            } else {
+                                dst[(size_t)c * TT + o] = __uint_as_float(rg[u]);
+                                dst[(size_t)(nf + c) * TT + o] = __uint_as_float(rh[u]);
+                            }
                         }
                     }
                 }
@@ -348,15 +499,43 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
     } else {
         grid_dependency_wait();  // before writing this sweep's moment slot
         grid_launch_dependents();
+        if (CL) {
+            cl_stage_issue(a, Lo, sm, cls, 0, NTH);
+            cluster_wait();
+        }
     }
     tile_moments<NTH>(a, k, ti, tj, s1, s2);
+    if (CL) {
+        cl_update(a, Lo, sm, cls, g, rhoc_blk, nTI, nTJ);
+        // NB shape: the last CTA of the sweep pools the moment sums (App. B)
+        if (a.family == GMF_NEGBIN && a.alpha_mode == 1) {
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                const unsigned total = (unsigned)(a.TJ * a.TI * a.per);
+                if (atomicAdd(a.nbctr, 1u) == total - 1) {
+                    __threadfence();
+                    nb_shape_update(a, w);
+                    *a.nbctr = 0u;
+                }
+            }
+        }
+    }
 }
 
 template <bool Y16>
 __global__ void __launch_bounds__(NTH, 1)
     sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    tc_tile<Y16>(a, Lo, &ymap, w, blockIdx.z, smraw);
+    tc_tile<Y16, false>(a, Lo, &ymap, w, blockIdx.z, smraw);
+}
+
+// Cluster mode: launched with cluster dimensions (TJ, TI, 1), one cluster per block.
+template <bool Y16>
+__global__ void __launch_bounds__(NTH, 1)
+    sweep_tc_cluster(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    tc_tile<Y16, true>(a, Lo, &ymap, w, blockIdx.z, smraw);
 }
 
 // Several models (ranks) sharing the count matrix and the partitions: blockIdx.z
@@ -374,8 +553,10 @@ __global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restr
         s_l = lv[model];
     }
     __syncthreads();
-    tc_tile<Y16>(s_a, s_l, &ymap, w, blockIdx.z % per, smraw);
+    tc_tile<Y16, false>(s_a, s_l, &ymap, w, blockIdx.z % per, smraw);
 }
+
+int tc_cluster_layout(gmf_model* h, TcState* tc);
 
 int fail_str(std::string* err, const char* msg) {
     if (err) *err = msg;
@@ -447,10 +628,8 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
         if (err) *err = "cuTensorMapEncodeTiled failed for the count matrix";
         return GMF_ERR_CUDA;
     }
-    cudaError_t e = h->y16 ? cudaFuncSetAttribute(sweep_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)L.smem)
-                           : cudaFuncSetAttribute(sweep_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)L.smem);
+    cudaError_t e = gmf_smem_limit(h->y16 ? (const void*)sweep_tc_kernel<true> : (const void*)sweep_tc_kernel<false>,
+                                   L.smem);
     if (e != cudaSuccess) {
         delete tc;
         if (err) *err = cudaGetErrorString(e);
@@ -458,9 +637,56 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
     }
     tc->TI = (int)((std::min<int64_t>(h->cfg.nb_row, h->n) + TT - 1) / TT);
     tc->TJ = (int)((std::min<int64_t>(h->cfg.nb_col, h->m) + TT - 1) / TT);
+    tc->cluster = 0;
+    if (!(h->cfg.flags & GMF_FLAG_NO_CLUSTER) && tc->TI * tc->TJ <= 16) tc->cluster = tc_cluster_layout(h, tc);
     h->tc = tc;
     return GMF_OK;
 }
+
+namespace {
+
+// Cluster mode needs the partials and the update slices in shared memory next
+// to the tile, cluster dimensions (TJ, TI) within the device's limit, and room
+// for all clusters of a sweep at once (else the sweep would run in waves).
+int tc_cluster_layout(gmf_model* h, TcState* tc) {
+    TcLayout& L = tc->lay;
+    const int TI = tc->TI, TJ = tc->TJ;
+    L.SRr = (TT + TJ - 1) / TJ;
+    L.SCc = (TT + TI - 1) / TI;
+    L.off_cp = (L.off_lf2 + (uint32_t)L.NC * 256u + 15u) & ~15u;
+    L.off_st = L.off_cp + 4u * (uint32_t)(TJ * 2 * h->fr * L.SRr + TI * 2 * h->fc * L.SCc);
+    const uint32_t st_bytes = 4u * (uint32_t)(L.SRr * (h->KP + 1 + 2 * (h->fr | 1) + 1) +
+                                              L.SCc * (h->KP + 1 + 2 * (h->fc | 1) + 1));
+    L.smem_cl = L.off_st + st_bytes + 1024u;
+    const void* fn = h->y16 ? (const void*)sweep_tc_cluster<true> : (const void*)sweep_tc_cluster<false>;
+    if (gmf_smem_limit(fn, L.smem_cl) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (TI * TJ > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(TJ, TI, h->per);
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = L.smem_cl;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = TJ;
+    at[0].val.clusterDim.y = TI;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nclusters >= h->per ? 1 : 0;
+}
+
+}  // namespace
 
 cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
     TcState* tc = (TcState*)h->tc;
@@ -468,6 +694,24 @@ cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
     a.TI = tc->TI;
     a.TJ = tc->TJ;
     dim3 grid(tc->TJ, tc->TI, h->per);
+    if (tc->cluster) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(NTH);
+        cfg.dynamicSmemBytes = tc->lay.smem_cl;
+        cfg.stream = st;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = tc->TJ;
+        at[0].val.clusterDim.y = tc->TI;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        return h->y16 ? cudaLaunchKernelEx(&cfg, sweep_tc_cluster<true>, a, tc->lay, tc->ymap, w)
+                      : cudaLaunchKernelEx(&cfg, sweep_tc_cluster<false>, a, tc->lay, tc->ymap, w);
+    }
     const cudaError_t e =
         h->y16 ? gmf_launch_pdl(sweep_tc_kernel<true>, grid, dim3(NTH), tc->lay.smem, st, a, tc->lay, tc->ymap, w)
                : gmf_launch_pdl(sweep_tc_kernel<false>, grid, dim3(NTH), tc->lay.smem, st, a, tc->lay, tc->ymap, w);
@@ -476,6 +720,7 @@ cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
 
 cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st) {
     const TcState* tc = (const TcState*)h->tc;
+    if (tc->cluster) return cudaSuccess;  // the tile launch did the updates
     StepArgs a = gmf_make_args(h);
     a.TI = tc->TI;
     a.TJ = tc->TJ;
@@ -491,8 +736,7 @@ void gmf_tc_grid(const gmf_model* h, int* TI, int* TJ) {
 }
 
 cudaError_t gmf_tc_multi_attr(int y16, uint32_t smem) {
-    return y16 ? cudaFuncSetAttribute(sweep_tc_multi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-               : cudaFuncSetAttribute(sweep_tc_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return gmf_smem_limit(y16 ? (const void*)sweep_tc_multi<true> : (const void*)sweep_tc_multi<false>, smem);
 }
 
 // One sweep of nmodels models: grid (TJ, TI, nmodels * per).
@@ -506,6 +750,8 @@ cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, con
                    : gmf_launch_pdl(sweep_tc_multi<false>, grid, dim3(NTH), smem, st, d_args, lays, d_order, h0->per,
                                     tc->ymap, w);
 }
+
+int gmf_tc_cluster(const gmf_model* h) { return h->tc && ((const TcState*)h->tc)->cluster; }
 
 void gmf_tc_free(gmf_model* h) {
     delete (TcState*)h->tc;

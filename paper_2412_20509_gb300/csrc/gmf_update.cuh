@@ -285,8 +285,8 @@ __device__ __forceinline__ void nb_shape_update(const StepArgs& a, int w) {
     const int total = a.TJ * a.TI * a.per;
     double T1 = 0.0, T2 = 0.0;
     for (int c = 0; c < total; c++) {
-        T1 += a.nbpart[2 * c];
-        T2 += a.nbpart[2 * c + 1];
+        T1 += __ldcg(a.nbpart + 2 * c);
+        T2 += __ldcg(a.nbpart + 2 * c + 1);
     }
     if (T2 > 0.0) {
         float ahat = (float)(T1 / T2);

@@ -124,3 +124,49 @@ def test_mixed_rejects_unaligned_layouts(gmf, oracle_mod):
     assert e.value.code == gmf.GMF_ERR_ARG and "16 bytes" in str(e.value)
     with pytest.raises(gmf.GmfError):
         Pair(gmf, oracle_mod, 100, 64, 2, 1, 3, "poisson", 20, 10, precision="mixed")   # nb_col * 4 % 16 != 0
+
+
+CLUSTER_CASES = {
+    # name: (n, m, p, q, d, family, nb_row, nb_col, extra); tiles per block TI x TJ <= 16
+    "nb_ragged_12_tiles": (1100, 704, 3, 1, 6, "negbin", 500, 384,
+                           dict(zero_frac=0.8, weights=True, alpha_mode=1, bias_corr=1)),
+    "poisson_16_tiles_uint16": (2000, 1024, 2, 1, 10, "poisson", 500, 512, dict(y_dtype="uint16")),
+    "nb_6_tiles": (300, 256, 2, 2, 3, "negbin", 300, 256, dict(zero_frac=0.6, alpha_mode=1)),
+}
+
+
+@pytest.mark.parametrize("case", list(CLUSTER_CASES))
+def test_cluster_mode_equals_separate_update_launch(gmf, case):
+    """Where a block's tiles fit one thread-block cluster the strip updates run
+    inside the tile launch and read the partials from the peers' shared memory;
+    the sums follow the same tile order as the separate update launch, so the
+    two modes must agree to the bit."""
+    n, m, p, q, d, fam, nbr, nbc, extra = CLUSTER_CASES[case]
+    extra = dict(extra)
+    y_dtype = extra.pop("y_dtype", "int32")
+    zero_frac = extra.pop("zero_frac", None)
+    weights = extra.pop("weights", False)
+    prob = synth.make_problem(n, m, p, q, d, fam, seed=3, y_dtype=y_dtype, zero_frac=zero_frac, offset=True)
+    start = synth.crude_start(prob, d, seed=3)
+    rp, cp = synth.partitions(n, m, 3)
+    settings = synth.fit_settings(**extra)
+    W = torch.from_numpy(np.random.default_rng(10).uniform(0.5, 1.5, (n, m)).astype(np.float32)).cuda() \
+        if weights else None
+    sig = synth.sweep_orders(n, m, nbr, nbc, 3, 3)
+    fits = []
+    for flags in (0, gmf.GMF_FLAG_NO_CLUSTER):
+        Yd = torch.from_numpy(prob.Y.view(np.int16) if y_dtype == "uint16" else prob.Y).cuda()
+        mdl = gmf.Model(Yd, prob.X, prob.Z, prob.offset, start, family=fam, nb_row=nbr, nb_col=nbc, row_perm=rp,
+                        col_perm=cp, settings=settings, W=W, precision="mixed", flags=flags)
+        for s in sig:
+            mdl.epoch(s)
+        fits.append(mdl)
+    assert fits[0].launches_per_sweep == 1 and fits[1].launches_per_sweep == 2
+    a, b = fits[0].get_params(), fits[1].get_params()
+    for k in ("B", "Gamma", "U", "V"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert a["alpha"] == b["alpha"]
+    ea, eb = fits[0].get_ema(), fits[1].get_ema()
+    for k in ("Gb_row", "Hb_row", "Gb_col", "Hb_col", "cnt_row", "cnt_col"):
+        np.testing.assert_array_equal(ea[k], eb[k], err_msg=k)
+    assert fits[0].deviance() == fits[1].deviance()
