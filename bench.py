@@ -270,7 +270,8 @@ def run_projection(args, w):
     Xn, on = dev(prob.X[n_fit:]), dev(prob.offset[n_fit:])
     Utr, _, _ = model.project_cells(Yfit, Xf, of, None, n_steps=10, with_dev=False)
     epochs = 10
-    net = gmf.MLP(w.m, 256, 256, w.d, max_batch=1024)
+    net = gmf.MLP(w.m, 256, 256, w.d, max_batch=16384)   # forward in chunks of 16384 cells, training batches of 1024
+    net.set_precision(args.encoder_precision)
     net.set_params({k: np.asarray(v, dtype=np.float32) for k, v in synth.mlp_init(w.m, 256, 256, w.d, 2).items()})
     t_train, losses = timed(lambda: net.train(Yfit, Utr, epochs=epochs, batch=1024, lr=1e-3, seed=5))
     lam_u, lam_g = settings["lambda_"][2], settings["lambda_"][1]
@@ -305,7 +306,8 @@ def run_projection(args, w):
            "config": {"workload": f"{w.name}: fit {n_fit} + project {n_new} cells x {w.m} genes, NB, d={w.d}, "
                                   f"GMF fit {w.epochs} epochs (tensor cores), encoder {w.m}-256-256-{w.d} trained "
                                   f"{epochs} epochs on the training cells' projected scores; value = warm start, "
-                                  f"3 Fisher steps, encoder forward included", "data": "synthetic (GPU-drawn)"},
+                                  f"3 Fisher steps, encoder forward included",
+                      "encoder_precision": args.encoder_precision, "data": "synthetic (GPU-drawn)"},
            **res,
            "reference_cold_fit": {"steps": 60, "cells_per_s": n_new / t_ref, "mean_objective": float(oref.mean()),
                                   "max_gap_30_steps": float(conv.max()), "mean_gap_30_steps": float(conv.mean())},
@@ -379,6 +381,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttd", action="store_true", help="skip the time-to-deviance comparison")
+    ap.add_argument("--encoder-precision", default="mixed", choices=["fp32", "mixed"],
+                    help="nb_project: the encoder's first layer on the tensor cores (mixed) or FP32")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -272,6 +272,14 @@ void gmf_sweep_free(gmf_sweep* s);
  * gmf_mlp_loss_grad  -- loss (device float, may be NULL) and the gradients of one
  *                       batch (rows <= max_batch) into the network. Asynchronous.
  * gmf_mlp_adam       -- one Adam step with the stored gradients. Asynchronous.
+ * gmf_mlp_set_precision -- GMF_PREC_FP32 (the default: every product in FP32) or
+ *                       GMF_PREC_MIXED: the first layer, z1 = W1 log(1 + y) + b1, runs on
+ *                       the tcgen05 tensor cores with W1 and log(1 + y) rounded to BF16
+ *                       (round to nearest even) and FP32 accumulation; the other layers and
+ *                       the gradients stay FP32. Needs n_h1 a multiple of 16 in [16, 256];
+ *                       the counts passed later must be 16-byte aligned with n_in * sizeof(count)
+ *                       a multiple of 16 (GMF_ERR_ARG otherwise). Keeps a BF16 copy of W1,
+ *                       refreshed by set_params and every Adam step.
  * gmf_mlp_train      -- `epochs` passes of minibatches of `batch` rows in an order
  *                       drawn from `seed` (SplitMix64 on the host); losses (host,
  *                       may be NULL) receives the mean loss of each epoch. Allocates
@@ -289,6 +297,7 @@ int gmf_mlp_forward(gmf_mlp* net, const void* Y, int32_t y_dtype, int64_t rows, 
 int gmf_mlp_loss_grad(gmf_mlp* net, const void* Y, int32_t y_dtype, int64_t rows, const float* target, float* loss,
                       void* stream);
 int gmf_mlp_adam(gmf_mlp* net, float lr, float beta1, float beta2, float eps, void* stream);
+int gmf_mlp_set_precision(gmf_mlp* net, int32_t precision, void* stream);
 int gmf_mlp_train(gmf_mlp* net, const void* Y, int32_t y_dtype, int64_t rows, const float* target, int32_t epochs,
                   int32_t batch, float lr, uint64_t seed, float* losses, void* stream);
 void gmf_mlp_free(gmf_mlp* net);

@@ -35,7 +35,12 @@ def init_params(n_in, n_h1, n_h2, n_out, seed):
 
 
 def forward(P, Y):
-    X = np.log1p(np.asarray(Y, dtype=np.float64))
+    return forward_x(P, np.log1p(np.asarray(Y, dtype=np.float64)))
+
+
+def forward_x(P, X):
+    """The forward pass from the inputs x = log(1 + y) themselves."""
+    X = np.asarray(X, dtype=np.float64)
     Z1 = X @ P["W1"].T + P["b1"]
     H1 = gelu(Z1)
     Z2 = H1 @ P["W2"].T + P["b2"]

@@ -34,7 +34,8 @@ EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_num_sweeps", "
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
            "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
            "gmf_mlp_set_params", "gmf_mlp_get_params", "gmf_mlp_get_grads", "gmf_mlp_forward", "gmf_mlp_loss_grad",
-           "gmf_mlp_adam", "gmf_mlp_train", "gmf_mlp_free", "gmf_free", "gmf_last_error", "gmf_version")
+           "gmf_mlp_adam", "gmf_mlp_set_precision", "gmf_mlp_train", "gmf_mlp_free", "gmf_free", "gmf_last_error",
+           "gmf_version")
 
 
 class GmfError(RuntimeError):
@@ -98,6 +99,7 @@ def lib():
         "gmf_mlp_forward": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, VP]),
         "gmf_mlp_loss_grad": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, VP, VP]),
         "gmf_mlp_adam": (C.c_int, [VP, C.c_float, C.c_float, C.c_float, C.c_float, VP]),
+        "gmf_mlp_set_precision": (C.c_int, [VP, C.c_int32, VP]),
         "gmf_mlp_train": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, C.c_int32, C.c_int32, C.c_float, C.c_uint64, VP,
                                     VP]),
         "gmf_mlp_free": (None, [VP]),
@@ -442,6 +444,11 @@ class MLP:
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         check(lib().gmf_mlp_adam(self._h, lr, beta1, beta2, eps, _stream(stream)))
+
+    def set_precision(self, precision, stream=None):
+        """"fp32" (default) or "mixed": the first layer on the tensor cores with BF16 W1 and inputs."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        check(lib().gmf_mlp_set_precision(self._h, p, _stream(stream)))
 
     def train(self, Y, target, epochs, batch, lr, seed=0, stream=None):
         import torch

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "gmf_internal.cuh"
+#include "gmf_mlp_tc.cuh"
 
 namespace {
 
@@ -177,12 +178,15 @@ struct gmf_mlp {
     void* yb = nullptr;    // gathered batch counts (int32 bytes)
     float* tb = nullptr;   // gathered batch targets
     int64_t* idx = nullptr;
+    int prec = GMF_PREC_FP32;        // GMF_PREC_MIXED: first layer on the tensor cores (BF16 W1 and inputs)
+    __nv_bfloat16* W1b = nullptr;    // padded BF16 copy of W1 (mixed)
+    unsigned* err = nullptr;         // device status word of the tensor-core layer
 };
 
 static void mlp_release(gmf_mlp* n) {
     if (!n) return;
     void* ptrs[] = {n->P, n->G, n->M, n->V, n->Z1, n->H1, n->Z2, n->H2, n->O, n->dO, n->dZ2, n->dZ1, n->loss,
-                    n->yb, n->tb, n->idx};
+                    n->yb, n->tb, n->idx, n->W1b, n->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete n;
@@ -257,7 +261,30 @@ extern "C" int gmf_mlp_set_params(gmf_mlp* n, const float* W1, const float* b1, 
     n->k = 0;
     cudaMemsetAsync(n->M, 0, sizeof(float) * n->off[6], (cudaStream_t)stream);
     cudaMemsetAsync(n->V, 0, sizeof(float) * n->off[6], (cudaStream_t)stream);
-    return copy_params(n, n->P, h, true, (cudaStream_t)stream);
+    const int rc = copy_params(n, n->P, h, true, (cudaStream_t)stream);
+    if (rc == GMF_OK && n->prec == GMF_PREC_MIXED &&
+        gmf_mlp_tc_weights(n->P + n->off[0], n->h1, n->n_in, n->W1b, (cudaStream_t)stream) != GMF_OK)
+        return gmf_fail(GMF_ERR_CUDA, "gmf_mlp_set_params: BF16 copy of W1 failed");
+    return rc;
+}
+
+extern "C" int gmf_mlp_set_precision(gmf_mlp* n, int32_t precision, void* stream) {
+    if (!n) return gmf_fail(GMF_ERR_ARG, "gmf_mlp_set_precision: NULL handle");
+    if (precision != GMF_PREC_FP32 && precision != GMF_PREC_MIXED)
+        return gmf_fail(GMF_ERR_ARG, "gmf_mlp_set_precision: precision must be GMF_PREC_FP32 or GMF_PREC_MIXED");
+    if (precision == GMF_PREC_MIXED) {
+        std::string msg;
+        if (gmf_mlp_tc_check(n->n_in, n->h1, &msg) != GMF_OK)
+            return gmf_fail(GMF_ERR_ARG, ("gmf_mlp_set_precision: " + msg).c_str());
+        if (!n->W1b && (cudaMalloc(&n->W1b, sizeof(__nv_bfloat16) * gmf_mlp_tc_w1_elems(n->h1, n->n_in)) != cudaSuccess ||
+                        cudaMalloc(&n->err, sizeof(unsigned)) != cudaSuccess))
+            return gmf_fail(GMF_ERR_OOM, "gmf_mlp_set_precision: device allocation failed");
+        cudaMemsetAsync(n->err, 0, sizeof(unsigned), (cudaStream_t)stream);
+        if (gmf_mlp_tc_weights(n->P + n->off[0], n->h1, n->n_in, n->W1b, (cudaStream_t)stream) != GMF_OK)
+            return gmf_fail(GMF_ERR_CUDA, "gmf_mlp_set_precision: BF16 copy of W1 failed");
+    }
+    n->prec = precision;
+    return GMF_OK;
 }
 extern "C" int gmf_mlp_get_params(gmf_mlp* n, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3,
                                   void* stream) {
@@ -279,8 +306,42 @@ static cudaError_t run_gemm(const Gemm& g, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Message of the last failure inside the tensor-core first layer (reported by the ABI call).
+static thread_local std::string tl_layer_msg;
+
+// ABI status for a failed forward / backward pass.
+static int pass_fail(const char* fn, cudaError_t e) {
+    std::string m = std::string(fn) + ": " + (tl_layer_msg.empty() ? cudaGetErrorString(e) : tl_layer_msg);
+    const int code = tl_layer_msg.empty() ? GMF_ERR_CUDA : GMF_ERR_ARG;
+    tl_layer_msg.clear();
+    return gmf_fail(code, m.c_str());
+}
+
+static cudaError_t forward_l1_simt(gmf_mlp* n, const void* Y, int y16, int64_t ldy, int64_t rows, cudaStream_t st);
+static cudaError_t forward_l23(gmf_mlp* n, int64_t rows, float* out, cudaStream_t st);
+
 // Forward pass of `rows` cells whose counts start at Y (row stride ldy); output rows x n_out.
 static cudaError_t forward(gmf_mlp* n, const void* Y, int y16, int64_t ldy, int64_t rows, float* out, cudaStream_t st) {
+    float* P = n->P;
+    cudaError_t e = cudaSuccess;
+    if (n->prec == GMF_PREC_MIXED) {
+        std::string msg;
+        if (ldy != n->n_in) msg = "the tensor-core encoder reads contiguous rows of n_in counts";
+        if (!msg.empty() ||
+            gmf_mlp_tc_layer1(Y, y16, rows, n->n_in, n->h1, n->W1b, P + n->off[1], n->Z1, n->H1, n->err, st, &msg) !=
+                GMF_OK) {
+            tl_layer_msg = msg;
+            return cudaErrorInvalidValue;
+        }
+    } else {
+        e = forward_l1_simt(n, Y, y16, ldy, rows, st);
+        if (e != cudaSuccess) return e;
+    }
+    return forward_l23(n, rows, out, st);
+}
+
+// First layer on the FP32 CUDA-core GEMM.
+static cudaError_t forward_l1_simt(gmf_mlp* n, const void* Y, int y16, int64_t ldy, int64_t rows, cudaStream_t st) {
     float* P = n->P;
     Gemm g{};
     g.M = rows;
@@ -296,9 +357,14 @@ static cudaError_t forward(gmf_mlp* n, const void* Y, int y16, int64_t ldy, int6
     g.ldc = n->h1;
     g.bias = P + n->off[1];
     g.H = n->H1;
-    cudaError_t e = y16 ? run_gemm<SRC_U16, SRC_F32, EPI_BIAS_GELU>(g, st) : run_gemm<SRC_I32, SRC_F32, EPI_BIAS_GELU>(g, st);
-    if (e != cudaSuccess) return e;
-    g = Gemm{};
+    return y16 ? run_gemm<SRC_U16, SRC_F32, EPI_BIAS_GELU>(g, st) : run_gemm<SRC_I32, SRC_F32, EPI_BIAS_GELU>(g, st);
+}
+
+// Layers 2 and 3 (FP32 CUDA-core GEMM) from H1.
+static cudaError_t forward_l23(gmf_mlp* n, int64_t rows, float* out, cudaStream_t st) {
+    float* P = n->P;
+    cudaError_t e = cudaSuccess;
+    Gemm g{};
     g.M = rows;
     g.N = n->h2;
     g.K = n->h1;
@@ -388,7 +454,7 @@ extern "C" int gmf_mlp_forward(gmf_mlp* n, const void* Y, int32_t y_dtype, int64
         const int64_t nr = std::min<int64_t>(n->max_batch, rows - r0);
         const cudaError_t e = forward(n, (const char*)Y + (size_t)r0 * n->n_in * es, y16, n->n_in, nr,
                                       out + r0 * n->n_out, st);
-        if (e != cudaSuccess) return gmf_fail(GMF_ERR_CUDA, cudaGetErrorString(e));
+        if (e != cudaSuccess) return pass_fail("gmf_mlp_forward", e);
     }
     return GMF_OK;
 }
@@ -399,7 +465,7 @@ extern "C" int gmf_mlp_loss_grad(gmf_mlp* n, const void* Y, int32_t y_dtype, int
         return gmf_fail(GMF_ERR_ARG, "gmf_mlp_loss_grad: bad argument (rows must be <= max_batch)");
     cudaStream_t st = (cudaStream_t)stream;
     const cudaError_t e = backward(n, Y, y_dtype == GMF_Y_UINT16, n->n_in, rows, target, st);
-    if (e != cudaSuccess) return gmf_fail(GMF_ERR_CUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return pass_fail("gmf_mlp_loss_grad", e);
     if (loss && cudaMemcpyAsync(loss, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return gmf_fail(GMF_ERR_CUDA, "gmf_mlp_loss_grad: copy failed");
     return GMF_OK;
@@ -413,7 +479,11 @@ extern "C" int gmf_mlp_adam(gmf_mlp* n, float lr, float beta1, float beta2, floa
     adam_kernel<<<grid1(n->off[6]), NT, 0, (cudaStream_t)stream>>>(n->P, n->G, n->M, n->V, n->off[6], lr, beta1, beta2,
                                                                    eps, c1, c2);
     const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? GMF_OK : gmf_fail(GMF_ERR_CUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return gmf_fail(GMF_ERR_CUDA, cudaGetErrorString(e));
+    if (n->prec == GMF_PREC_MIXED &&
+        gmf_mlp_tc_weights(n->P + n->off[0], n->h1, n->n_in, n->W1b, (cudaStream_t)stream) != GMF_OK)
+        return gmf_fail(GMF_ERR_CUDA, "gmf_mlp_adam: BF16 copy of W1 failed");
+    return GMF_OK;
 }
 
 // SplitMix64: the host-side generator of the minibatch order.
@@ -474,7 +544,7 @@ extern "C" int gmf_mlp_train(gmf_mlp* n, const void* Y, int32_t y_dtype, int64_t
                                                                      (int*)n->yb);
             gather_rows<float><<<grid1(nb * n->n_out), NT, 0, st>>>(target, n->n_out, idx, nb, n->n_out, n->tb);
             cudaError_t e = backward(n, n->yb, y16, n->n_in, nb, n->tb, st);
-            if (e != cudaSuccess) return done(gmf_fail(GMF_ERR_CUDA, cudaGetErrorString(e)));
+            if (e != cudaSuccess) return done(pass_fail("gmf_mlp_train", e));
             const int rc = gmf_mlp_adam(n, lr, 0.9f, 0.999f, 1e-8f, stream);
             if (rc) return done(rc);
             loss_acc_kernel<<<1, 1, 0, st>>>(n->loss, (double)nb, d_acc + ep);
@@ -487,5 +557,10 @@ extern "C" int gmf_mlp_train(gmf_mlp* n, const void* Y, int32_t y_dtype, int64_t
         return done(gmf_fail(GMF_ERR_CUDA, "gmf_mlp_train: loss read failed"));
     if (losses)
         for (int ep = 0; ep < epochs; ep++) losses[ep] = (float)(acc[ep] / (double)rows);
+    if (n->err) {
+        unsigned w = 0;
+        if (cudaMemcpy(&w, n->err, sizeof w, cudaMemcpyDeviceToHost) == cudaSuccess && w)
+            return done(gmf_fail(GMF_ERR_TIMEOUT, "gmf_mlp_train: a bounded wait in the tensor-core layer gave up"));
+    }
     return done(GMF_OK);
 }

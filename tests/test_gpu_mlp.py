@@ -30,6 +30,56 @@ def f32(P):
     return {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in P.items()}
 
 
+def bf16(a):
+    """Round to BF16 (nearest even) through FP32, as the tensor-core layer rounds its operands."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("dims,rows,y16", [((3000, 256, 256, 20), 300, True), ((200, 64, 32, 5), 130, False),
+                                           ((64, 16, 16, 3), 1, True)])
+def test_mixed_first_layer_matches_oracle_on_bf16_operands(gmf, dims, rows, y16):
+    """The tensor-core first layer rounds W1 and log(1 + y) to BF16 and accumulates
+    in FP32: against the FP64 oracle fed the same rounded operands only the
+    accumulation order differs (~1e-6 relative), so the outputs agree within
+    1e-4 (max-norm relative), with ragged rows (300, 130, 1 = not multiples of
+    128) and a K tail (200 = 3 x 64 + 8)."""
+    from oracle import mlp
+    rng = np.random.default_rng(40)
+    P = f32(mlp.init_params(*dims, seed=8))
+    for k in ("b1", "b2", "b3"):
+        P[k] = f32({k: 0.1 * rng.standard_normal(P[k].shape)})[k]
+    Y = rng.poisson(rng.gamma(0.5, 4.0, size=(rows, dims[0])))
+    Y[rng.random(Y.shape) < 0.02] += 400   # some counts beyond the 256-entry table
+    Y = Y.astype(np.uint16 if y16 else np.int32)
+    net = gmf.MLP(*dims, max_batch=max(rows, 128))
+    net.set_params(P)
+    net.set_precision("mixed")
+    Yd = torch.from_numpy(Y.view(np.int16) if y16 else Y).cuda()
+    out = net.forward(Yd).cpu().numpy()
+    Pb = dict(P, W1=bf16(P["W1"]))
+    ref, _ = mlp.forward_x(Pb, bf16(np.log1p(Y.astype(np.float64))))
+    assert rel(out, ref) <= 1e-4, rel(out, ref)
+    # and the FP32 path differs from it by the BF16 rounding, not more
+    net.set_precision("fp32")
+    out32 = net.forward(Yd).cpu().numpy()
+    ref32, _ = mlp.forward(P, Y.astype(np.float64))
+    assert rel(out32, ref32) <= 1e-4
+    assert rel(out, ref32) <= 5e-2
+
+
+def test_mixed_encoder_rejects_unsupported_shapes(gmf):
+    net = gmf.MLP(100, 24, 16, 4, max_batch=64)
+    with pytest.raises(gmf.GmfError):
+        net.set_precision("mixed")          # n_h1 = 24 is not a multiple of 16
+    net = gmf.MLP(10, 32, 16, 4, max_batch=64)
+    net.set_precision("mixed")
+    Y = torch.zeros((5, 10), dtype=torch.int32, device="cuda")
+    with pytest.raises(gmf.GmfError):
+        net.forward(Y)                      # 10 int32 counts per row: 40 bytes, not a multiple of 16
+
+
 @pytest.mark.parametrize("dims,rows,y16", [((300, 40, 24, 5), 37, False), ((3000, 256, 256, 20), 256, True)])
 def test_mlp_loss_and_gradients_match_oracle(gmf, dims, rows, y16):
     from oracle import mlp
@@ -71,7 +121,8 @@ def test_mlp_adam_step_matches_oracle(gmf):
         assert rel(got[k], P[k]) <= 1e-5, k
 
 
-def test_mlp_training_is_deterministic_and_learns(gmf):
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_mlp_training_is_deterministic_and_learns(gmf, precision):
     from oracle import mlp
     rng = np.random.default_rng(13)
     dims = (200, 64, 64, 6)
@@ -82,6 +133,7 @@ def test_mlp_training_is_deterministic_and_learns(gmf):
     runs = []
     for _ in range(2):
         net = gmf.MLP(*dims, max_batch=128)
+        net.set_precision(precision)
         net.set_params(P0)
         losses = net.train(torch.from_numpy(Y).cuda(), torch.from_numpy(T).cuda(), epochs=15, batch=128, lr=3e-3,
                            seed=4)
@@ -92,7 +144,8 @@ def test_mlp_training_is_deterministic_and_learns(gmf):
     assert runs[0][0][-1] < 0.5 * runs[0][0][0]
 
 
-def test_warm_start_beats_cold_start(gmf):
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_warm_start_beats_cold_start(gmf, precision):
     """Fit on training cells, orthogonalise (B1), train the encoder on (counts,
     scores), then project held-out cells by Fisher scoring from the network's
     scores and from zero. Fisher scoring minimises the penalised objective
@@ -121,6 +174,7 @@ def test_warm_start_beats_cold_start(gmf):
     Ufit, _, _ = model.project_cells(Yfd, torch.from_numpy(sub.X).cuda(), torch.from_numpy(sub.offset).cuda(), None,
                                      n_steps=15, with_dev=False)
     net = gmf.MLP(m, 256, 256, d, max_batch=256)
+    net.set_precision(precision)
     net.set_params(f32(mlp.init_params(m, 256, 256, d, seed=2)))
     losses = net.train(Yfd, Ufit, epochs=60, batch=256, lr=1e-3, seed=5)
     assert losses[-1] < 0.1 * losses[0]
