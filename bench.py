@@ -52,6 +52,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the job ends when its slowest rank does)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds):
+    """Units of all ranks per second of the slowest rank (replicas: every rank runs the same workload)."""
+    return ws * units_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -460,12 +475,9 @@ def main():
     clocks.start()
     elapsed_ms = timed_epochs(model, args.warmup, args.steps)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
     entries_step = n * m
-    value = ws * entries_step * args.steps / (elapsed_ms / 1e3)
+    value = whole_job_rate(entries_step * args.steps, ws, elapsed_ms / 1e3)
     dev1 = model.deviance()
     # Kernel-level timing of the dominant kernel: the same steps again, each
     # block-step launch bracketed by CUDA events on its stream.
@@ -491,11 +503,8 @@ def main():
         model.deviance()              # D2H: the FP64 deviance (+ status word)
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * entries_step * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e_value = whole_job_rate(entries_step * e2e_steps, ws, e2e_s)
     launches_per_sweep = model.launches_per_sweep
     del model
 
