@@ -214,6 +214,10 @@ int gmf_orthogonalize(gmf_model* h, int32_t mode, void* stream);
  * the current point; a point with f <= f_best + 1e-5 (1 + |f_best|) is taken
  * and stepped from, otherwise the last step is halved from the best point.
  * The outputs are the best point and its deviance. n_steps = 0 returns the start.
+ * Precision: on a GMF_PREC_MIXED handle with q + d <= 22, q >= 1, p <= 8, uint16
+ * counts (16-byte aligned, m a multiple of 8) the Fisher matrices are formed on
+ * the tensor cores from BF16 weights and BF16 products r_ja r_jb (FP32
+ * accumulate); the score, eta and the deviance stay FP32. Otherwise FP32 throughout.
  * Ynew columns are genes in the caller's original order.
  *   Ynew      device, n_new x m counts (y_dtype)
  *   Xnew      device float32, n_new x p;  offset_new: device float32 n_new or NULL

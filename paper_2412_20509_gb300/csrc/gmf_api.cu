@@ -125,8 +125,8 @@ static void release(gmf_model* h) {
         h->ystage = nullptr;
     }
     void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
-                    h->rperm, h->cperm, h->ystage, h->Rorig, h->partR, h->partC, h->nbpart, h->nbctr, h->sigma, h->rhoc,
-                    h->rho1, h->err, h->devpart, h->devtot};
+                    h->rperm, h->cperm, h->ystage, h->Rorig, h->kr_buf, h->partR, h->partC, h->nbpart, h->nbctr,
+                    h->sigma, h->rhoc, h->rho1, h->err, h->devpart, h->devtot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] h->h_rperm;

@@ -86,6 +86,8 @@ struct gmf_model {
     int* cperm;
     void* ystage;               // staging for counts uploaded from the host
     float* Rorig;               // m x KP: R in the caller's gene order (per-cell projection)
+    void* kr_buf;               // BF16 Khatri-Rao product of [Z, V] (tensor-core projection)
+    size_t kr_elems;
     int y_shared;               // Yp / Wp belong to another handle (rank sweep)
     float* partR;
     float* partC;

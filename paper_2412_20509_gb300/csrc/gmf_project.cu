@@ -25,6 +25,8 @@
 #include <algorithm>
 #include <string>
 
+#include <cuda_bf16.h>
+
 #include "gmf_internal.cuh"
 
 namespace {
@@ -320,6 +322,13 @@ size_t project_smem(int KP, int f) {
 
 }  // namespace
 
+// gmf_project_tc.cu
+int gmf_project_tc_run(const float* Rorig, int64_t m, int p, int q, int d, int KP, const void* Ynew, int y16,
+                       int64_t n_new, const float* Xnew, const float* off, const float* Ustart, const float* alpha,
+                       int nb, float clamp, float lam_g, float lam_u, int n_steps, float* Uout, float* Gout, float* dev,
+                       unsigned* err_word, __nv_bfloat16** kr_buf, size_t* kr_elems, cudaStream_t st,
+                       std::string* err);
+
 int gmf_project_run(gmf_model* h, const void* Ynew, int y16, int64_t n_new, const float* Xnew, const float* off,
                     const float* Ustart, int n_steps, float* Uout, float* Gout, float* dev, cudaStream_t st,
                     std::string* err) {
@@ -336,6 +345,14 @@ int gmf_project_run(gmf_model* h, const void* Ynew, int y16, int64_t n_new, cons
     }
     unpermute_rows<<<(int)std::min<int64_t>((h->m * h->KP + 255) / 256, 4096), 256, 0, st>>>(h->R, h->cperm, h->m,
                                                                                              h->KP, h->Rorig);
+    if (h->cfg.precision == GMF_PREC_MIXED) {
+        // Fisher matrices on the tensor cores where the shapes allow (f <= 22, uint16 counts, ...)
+        const int rc = gmf_project_tc_run(h->Rorig, h->m, h->p, h->q, h->d, h->KP, Ynew, y16, n_new, Xnew, off, Ustart,
+                                          h->alpha, h->cfg.family == GMF_NEGBIN, (float)h->cfg.eta_clamp,
+                                          (float)h->cfg.lambda[1], (float)h->cfg.lambda[2], n_steps, Uout, Gout, dev,
+                                          h->err, (__nv_bfloat16**)&h->kr_buf, &h->kr_elems, st, err);
+        if (rc != GMF_ERR_STATE) return rc;
+    }
     ProjArgs a{};
     a.Y = Ynew;
     a.y16 = y16;

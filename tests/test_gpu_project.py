@@ -127,3 +127,69 @@ def test_projection_objective_never_rises_with_passes(gmf, oracle_mod):
         if prev is not None:
             assert bool((f <= prev + 1e-5 * (1 + prev.abs()) + 1e-6).all()), k
         prev = f
+
+
+@pytest.mark.parametrize("m,d,warm", [(488, 6, False), (480, 20, True)])
+def test_tensor_core_projection_matches_oracle(gmf, oracle_mod, m, d, warm):
+    """Mixed-precision handles form the Fisher matrices on the tensor cores from
+    BF16 weights and BF16 products r_ja r_jb. Their rounding errors are
+    independent across the genes and average out (Fisher sums within ~1e-4 of
+    their scale), and the score is exact FP32. So three passes stay within 2e-3
+    of the FP64 oracle (the Fisher matrix only scales the steps) and the
+    deviances within 1e-4. 300 cells make a ragged last CTA; m = 488 a gene
+    tail chunk."""
+    from oracle.project import project_cells
+    P = Pair(gmf, oracle_mod, 700, m, 3, 1, d, "negbin", 256, 128, zero_frac=0.8, precision="mixed")
+    for e in range(3):
+        P.gpu.epoch(P.sigmas[e])
+    params = P.gpu.get_params()
+    Y, X, off, Utrue = new_cells(P, params, 300, seed=d)
+    Y = np.minimum(Y, 65535).astype(np.uint16)
+    U0 = (Utrue + 0.3 * np.random.default_rng(1).standard_normal(Utrue.shape)).astype(np.float32).astype(np.float64) \
+        if warm else None
+    Z32 = P.prob.Z.astype(np.float32).astype(np.float64)
+    st = P.settings
+    kw = dict(family="negbin", alpha=params["alpha"], U_start=U0, lam_gamma=st["lambda_"][1], lam_u=st["lambda_"][2])
+    Ur, Gr, Dr = project_cells(Y, X, off, params["B"], Z32, params["V"], n_steps=3, **kw)
+    Yd = torch.from_numpy(Y.view(np.int16)).cuda()
+    Ug, Gg, Dg = P.gpu.project_cells(Yd, torch.from_numpy(X).cuda(), torch.from_numpy(off).cuda(),
+                                     None if U0 is None else torch.from_numpy(U0).cuda(), n_steps=3)
+    assert rel(Ug.cpu().numpy(), Ur) <= 2e-3, rel(Ug.cpu().numpy(), Ur)
+    assert rel(Gg.cpu().numpy(), Gr) <= 2e-3
+    np.testing.assert_allclose(Dg.cpu().numpy(), Dr, rtol=1e-4)
+    # many passes: the same optimum (fixed by the FP32 score)
+    Ur, Gr, Dr = project_cells(Y, X, off, params["B"], Z32, params["V"], n_steps=25, **kw)
+    Ug, Gg, Dg = P.gpu.project_cells(Yd, torch.from_numpy(X).cuda(), torch.from_numpy(off).cuda(),
+                                     None if U0 is None else torch.from_numpy(U0).cuda(), n_steps=25)
+    assert rel(Ug.cpu().numpy(), Ur) <= 1e-3, rel(Ug.cpu().numpy(), Ur)
+    np.testing.assert_allclose(Dg.cpu().numpy(), Dr, rtol=1e-5)
+
+
+def test_tensor_core_projection_from_far_start(gmf, oracle_mod):
+    """Far start (step halving acts on most cells): the objective of the returned
+    point never rises with the pass count, and 30 passes reach the oracle's
+    optimum."""
+    from oracle.project import project_cells
+    P = Pair(gmf, oracle_mod, 700, 480, 3, 1, 6, "negbin", 256, 128, zero_frac=0.8, precision="mixed")
+    for e in range(3):
+        P.gpu.epoch(P.sigmas[e])
+    params = P.gpu.get_params()
+    Y, X, off, Utrue = new_cells(P, params, 260, seed=33)
+    Y = np.minimum(Y, 65535).astype(np.uint16)
+    U0 = (Utrue + 3.0 * np.random.default_rng(4).standard_normal(Utrue.shape)).astype(np.float32).astype(np.float64)
+    Yd, Xd, od = torch.from_numpy(Y.view(np.int16)).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(off).cuda()
+    U0d = torch.from_numpy(U0).float().cuda()
+    lam_u = P.settings["lambda_"][2]
+    prev = None
+    for k in range(0, 9):
+        U, G, D = P.gpu.project_cells(Yd, Xd, od, U0d, n_steps=k)
+        fk = 0.5 * D.double() + 0.5 * lam_u * (U.double() ** 2).sum(1)
+        if prev is not None:
+            assert bool((fk <= prev + 1e-5 * (1 + prev.abs()) + 1e-6).all()), k
+        prev = fk
+    Z32 = P.prob.Z.astype(np.float32).astype(np.float64)
+    Ur, _, Dr = project_cells(Y, X, off, params["B"], Z32, params["V"], family="negbin", alpha=params["alpha"],
+                              U_start=U0, n_steps=30, lam_gamma=P.settings["lambda_"][1], lam_u=lam_u)
+    Ug, _, Dg = P.gpu.project_cells(Yd, Xd, od, U0d, n_steps=30)
+    assert rel(Ug.cpu().numpy(), Ur) <= 1e-3, rel(Ug.cpu().numpy(), Ur)
+    np.testing.assert_allclose(Dg.cpu().numpy(), Dr, rtol=1e-5)
