@@ -335,6 +335,75 @@ def run_projection(args, w):
     return 0
 
 
+def run_atlas(args, w):
+    """--workload nb_atlas: the precision study at atlas scale. 200000 x 5000 uint16
+    NB counts (~90 % zeros, d = 20, blocks 2048 x 1024), drawn on the GPU; the
+    same start and sweep orders fitted 10 epochs in mixed precision (split-BF16
+    eta, BF16 contractions, FP32 accumulate) and in FP32; FP64 deviance after
+    every epoch and the FP64 orthogonalisation (B1) of each fit."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as gmf
+    prob = synth.make_problem_device(w.n, w.m, w.p, w.q, w.d, w.family, seed=args.seed, zero_frac=w.zero_frac,
+                                     offset=w.offset)
+    hp = synth.Problem(Y=prob.Y.cpu().numpy().view(np.uint16), X=prob.X, Z=prob.Z, offset=prob.offset, B=prob.B,
+                       Gamma=prob.Gamma, U=prob.U, V=prob.V, nb_size=prob.nb_size, family=w.family)
+    start = synth.crude_start(hp, w.d, seed=args.seed)
+    del hp
+    rp, cp = synth.partitions(w.n, w.m, args.seed)
+    sig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, w.epochs, args.seed)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    res = {}
+    for prec in ("mixed", "fp32"):
+        model = gmf.Model(prob.Y, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row,
+                          nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=synth.fit_settings(), precision=prec)
+        ms, devs = [], []
+        for e in range(w.epochs):
+            a, b = ev(), ev()
+            torch.cuda.synchronize()
+            a.record(stream)
+            model.epoch(sig[e])
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            devs.append(model.deviance())
+        a, b = ev(), ev()
+        a.record(stream)
+        model.orthogonalize("B1")
+        b.record(stream)
+        torch.cuda.synchronize()
+        steady = ms[1:]
+        res[prec] = {"entries_per_s": w.n * w.m * len(steady) / (sum(steady) / 1e3),
+                     "ms_per_epoch": float(np.median(steady)), "first_epoch_ms_incl_graph_capture": ms[0],
+                     "deviance_per_epoch": devs, "cumulative_s": list(np.cumsum(ms) / 1e3),
+                     "orthogonalize_b1_ms": a.elapsed_time(b), "deviance_after_b1": model.deviance(),
+                     "launches_per_sweep": model.launches_per_sweep}
+        del model
+        torch.cuda.empty_cache()
+    target = res["fp32"]["deviance_per_epoch"][-1] * (1 + 1e-3)
+
+    def ttd(r):
+        for i, dv in enumerate(r["deviance_per_epoch"]):
+            if dv <= target:
+                return {"seconds": r["cumulative_s"][i], "epochs": i + 1}
+        return None
+    dm, df = res["mixed"]["deviance_per_epoch"][-1], res["fp32"]["deviance_per_epoch"][-1]
+    out = {"metric": "atlas-scale precision study: SGD matrix entries/s, mixed vs FP32, and the final FP64 deviance gap",
+           "value": res["mixed"]["entries_per_s"], "unit": "entries/s", "n_gpus": 1, "higher_is_better": True,
+           "config": {"workload": f"{w.name}: NB GMF {w.n}x{w.m} uint16 (~90% zeros, {prob.saturated} counts "
+                                  f"saturated at 65535), d={w.d}, blocks {w.nb_row}x{w.nb_col}, {w.epochs} epochs, "
+                                  f"same start and sweep orders for both precisions", "data": "synthetic (GPU-drawn)"},
+           "mixed": res["mixed"], "fp32": res["fp32"],
+           "mixed_over_fp32_throughput": res["mixed"]["entries_per_s"] / res["fp32"]["entries_per_s"],
+           "final_deviance_rel_gap_mixed_vs_fp32": (dm - df) / df,
+           "time_to_deviance": {"target": target, "rule": "within 1e-3 of the FP32 fit's final deviance",
+                                "mixed": ttd(res["mixed"]), "fp32": ttd(res["fp32"])}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_rank_sweep(args, w):
     """--workload nb_sweep: 8 ranks on one 50000 x 3000 NB matrix, batched (one
     launch per sweep for all models) vs the same 8 fits one after another."""
@@ -402,6 +471,8 @@ def main():
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.workload == "nb_atlas":
+        return run_atlas(args, w)
     if args.workload == "nb_sweep":
         return run_rank_sweep(args, w)
     if args.workload == "nb_project":

@@ -4,7 +4,7 @@
 // project_kernel (gmf_project.cu); f = q + d <= 22 and uint16 counts.
 //
 // For 128 cells per CTA the genes stream in chunks of 64. Per chunk:
-//   warp 16 (one thread): TMA of the counts (128 x 64), of R's rows (64 x KP,
+//   warp 16 (one thread): TMA of the counts (128 x 64, 128-byte swizzle), of R's rows (64 x KP,
 //     FP32) and, in Fisher passes, of the chunk of the Khatri-Rao product
 //     KR[pair][gene] = r_ga r_gb of [Z, V] (BF16, 128-byte swizzle, 256 pairs);
 //   warps 0-15 (thread -> cell t % 128, genes 16 (t / 128) ..): eta, mu, the
@@ -78,20 +78,27 @@ __device__ __forceinline__ int bar_compute_or(int flag) {
     return r;
 }
 
-// Unit deviance / 2 in FP32, written without differences of large logarithms.
-__device__ __forceinline__ float half_unit_dev(bool nb, float y, float ec, float mu, float alpha) {
-    if (y > 0.f) {
-        const float r1 = (y - mu) / mu;
-        const float l1 = fabsf(r1) < 0.5f ? log1pf(r1) : logf(y) - ec;
-        if (!nb) return y * l1 - (y - mu);
-        const float r2 = (y - mu) / (mu + alpha);
-        const float lma = mu > alpha ? ec + log1pf(alpha / mu) : logf(alpha) + log1pf(mu / alpha);
-        const float l2 = fabsf(r2) < 0.5f ? log1pf(r2) : logf(y + alpha) - lma;
-        return y * l1 - (y + alpha) * l2;
+// Unit deviance / 2, branch-free (every lane of a warp takes the same path):
+//   Poisson  y (log y - eta) - (y - mu),   NB  y (log y - eta) - (y + a)(log(y + a) - log(mu + a)),
+// the y log y term zero at y = 0. log y and log(y + a) come from per-CTA tables for y < 256. Near
+// mu = y the two logarithms of the NB term cancel: the rounding is ~1e-7 of (y + a) log(y + a) per
+// entry, ~1e-6 of a cell's deviance over thousands of genes.
+__device__ __forceinline__ float half_unit_dev(bool nb, float y, float ec, float mu, float alpha, const float* tlog,
+                                               const float* tloga) {
+    const int yi = (int)y;
+    float ly, lya;
+    if (yi < 256) {
+        ly = tlog[yi];
+        lya = tloga[yi];
+    } else {
+        ly = logf(y);
+        lya = logf(y + alpha);
     }
-    return nb ? alpha * log1pf(mu / alpha) : mu;
+    const float t1 = yi > 0 ? y * (ly - ec) : 0.f;
+    return nb ? t1 - (y + alpha) * (lya - __logf(mu + alpha)) : t1 - (y - mu);
 }
 
+// 18 warps: five share one of the four SM sub-partitions, which caps registers at 96 per thread.
 __global__ void __launch_bounds__(NTH, 1)
     project_tc(PArgs a, const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap rmap,
                const __grid_constant__ CUtensorMap krmap) {
@@ -99,6 +106,7 @@ __global__ void __launch_bounds__(NTH, 1)
     __shared__ uint64_t full_tma[2], empty_cmp[2], full_a[2], empty_mma[2], mma_done, pass_gate;
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
+    __shared__ float tlog[256], tloga[256];  // log(v), log(v + alpha), v < 256
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
@@ -137,6 +145,11 @@ __global__ void __launch_bounds__(NTH, 1)
         DEL[e] = 0.f;
     }
     if (tid < BM) FB[tid] = DB[tid] = 0.f;
+    if (tid < 256) {
+        const float al = *a.alpha;
+        tlog[tid] = tid > 0 ? logf((float)tid) : 0.f;
+        tloga[tid] = a.nb ? logf((float)tid + al) : 0.f;
+    }
     if (warp == 17) tmem_alloc(&tmem_base, NPP);
     tc_fence_before();
     __syncthreads();
@@ -228,17 +241,19 @@ __global__ void __launch_bounds__(NTH, 1)
                     s_abort = 1;
                 }
                 const float* sR = (const float*)(st + A_BYTES + KR_BYTES);
-                const unsigned short* sY = (const unsigned short*)(st + A_BYTES + KR_BYTES + a.r_pad);
+                // the count tile has the 128-byte swizzle: a warp (32 cells, one gene) reads 8 banks, not 1
+                const uint8_t* sY = st + A_BYTES + KR_BYTES + a.r_pad;
                 uint32_t pk[8];
-#pragma unroll 2
-                for (int jj = 0; jj < 16; jj += 2) {
+#pragma unroll
+                for (int jj = 0; jj < 16; jj += 2) {  // fully unrolled: pk stays in registers
                     float wv[2];
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         const int j = qg * 16 + jj + h;
                         const float* rj = sR + j * KP;
                         const bool valid = cv && (int64_t)kc * GC + j < a.m;
-                        const float y = (float)sY[cell * GC + j];
+                        const float y =
+                            (float)*(const unsigned short*)(sY + sw128_off((uint32_t)cell, (uint32_t)(2 * j)));
                         float eta = o;
 #pragma unroll
                         for (int k = 0; k < PTC; k++)
@@ -256,10 +271,10 @@ __global__ void __launch_bounds__(NTH, 1)
                             }
                         } else {
                             const float ec = fminf(fmaxf(eta, -a.clamp), a.clamp);
-                            const float mu = expf(ec);
-                            if (valid) dv += half_unit_dev(a.nb, y, ec, mu, alpha);
+                            const float mu = __expf(ec);
+                            if (valid) dv += half_unit_dev(a.nb, y, ec, mu, alpha, tlog, tloga);
                             if (fisher && valid) {
-                                const float fct = a.nb ? alpha / (alpha + mu) : 1.f;
+                                const float fct = a.nb ? __fdividef(alpha, alpha + mu) : 1.f;
                                 const float dd = (y - mu) * fct;
                                 ddd = mu * fct;
 #pragma unroll
@@ -291,8 +306,11 @@ __global__ void __launch_bounds__(NTH, 1)
             S1Q[qg * BM + cell] = s1;
             S2Q[qg * BM + cell] = s2;
             for (int r = 0; r < 4; r++) {
-                if (qg == r && fisher)
-                    for (int k = 0; k < f; k++) GRD[cell * FS + k] = (r == 0 ? 0.f : GRD[cell * FS + k]) + g[k];
+                if (qg == r && fisher) {
+#pragma unroll
+                    for (int k = 0; k < FTC; k++)  // constant indices keep g in registers
+                        if (k < f) GRD[cell * FS + k] = (r == 0 ? 0.f : GRD[cell * FS + k]) + g[k];
+                }
                 bar_compute();
             }
             if (fisher) {
@@ -336,12 +354,13 @@ __global__ void __launch_bounds__(NTH, 1)
                         FB[cell] = obj;
                         DB[cell] = D;
                         if (fisher) {
-                            // F + Lambda = L L' in place (packed, column `cell` of F), b = score - Lambda theta
-                            float b[FTC];
+                            // F + Lambda = L L' in place (packed, column `cell` of F); the right-hand side
+                            // b = score - Lambda theta, then the solution, in place in this cell's GRD row
+                            float* b = GRD + cell * FS;
                             for (int k = 0; k < f; k++) {
                                 const float lam = k < a.q ? a.lam_g : a.lam_u;
                                 F[pidx(k, k) * BM + cell] += lam;
-                                b[k] = GRD[cell * FS + k] - lam * thc[k];
+                                b[k] -= lam * thc[k];
                             }
                             bool okc = true;
                             for (int j = 0; j < f && okc; j++) {
@@ -460,7 +479,7 @@ bool plan(int64_t m, int p, int q, int d, int KP, ProjTcPlan* pl) {
     int optin = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return pl->smem + 2048 <= (size_t)optin;
+    return pl->smem + 4096 <= (size_t)optin;  // static shared memory (barriers, log tables)
 }
 
 }  // namespace
@@ -503,7 +522,7 @@ int gmf_project_tc_run(const float* Rorig, int64_t m, int p, int q, int d, int K
     cuuint64_t kd[2] = {(cuuint64_t)mP, (cuuint64_t)NPP}, ks[1] = {(cuuint64_t)mP * 2};
     cuuint32_t kb[2] = {(cuuint32_t)GC, (cuuint32_t)NPP};
     CUresult cr = enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, (void*)Ynew, yd, ys, yb, one,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr == CUDA_SUCCESS)
         cr = enc(&rmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)Rorig, rd, rs, rb, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
