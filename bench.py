@@ -404,6 +404,60 @@ def run_atlas(args, w):
     return 0
 
 
+def run_case(args):
+    """--case: one-kernel measurement cases of a size an ncu capture handles.
+    project_20000: a d = 20 NB model (2 fit epochs, mixed precision) on 20000 cells x 3000 genes,
+      then the tensor-core projection of 20000 held-out cells with 3 Fisher passes.
+    encoder_16384: the forward pass of a 3000-256-256-20 encoder (first layer on the tensor cores) on 16384
+      cells."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as gmf
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    if args.case == "project_20000":
+        n_fit = n_new = 20000
+        m, d = 3000, 20
+        prob = synth.make_problem_device(n_fit + n_new, m, 3, 1, d, "negbin", seed=1, zero_frac=0.9, offset=True)
+        Yfit, Ynew = prob.Y[:n_fit].contiguous(), prob.Y[n_fit:].contiguous()
+        fitp = synth.Problem(Y=Yfit.cpu().numpy().view(np.uint16), X=prob.X[:n_fit], Z=prob.Z,
+                             offset=prob.offset[:n_fit], B=prob.B, Gamma=prob.Gamma[:n_fit], U=prob.U[:n_fit], V=prob.V,
+                             nb_size=prob.nb_size, family="negbin")
+        start = synth.crude_start(fitp, d, seed=1)
+        rp, cp = synth.partitions(n_fit, m, 1)
+        model = gmf.Model(Yfit, fitp.X, fitp.Z, fitp.offset, start, family="negbin", nb_row=2048, nb_col=1024,
+                          row_perm=rp, col_perm=cp, settings=synth.fit_settings(alpha_mode=1), precision="mixed")
+        for sg in synth.sweep_orders(n_fit, m, 2048, 1024, 2, 1):
+            model.epoch(sg)
+        Xn = torch.from_numpy(np.ascontiguousarray(prob.X[n_fit:])).cuda()
+        on = torch.from_numpy(np.ascontiguousarray(prob.offset[n_fit:])).cuda()
+        run = lambda: model.project_cells(Ynew, Xn, on, None, n_steps=3)
+        units, unit = n_new, "cells/s"
+    else:
+        n, m = 16384, 3000
+        g = torch.Generator(device="cuda")
+        g.manual_seed(3)
+        lam = torch.empty((n, m), device="cuda").exponential_(1.0, generator=g).mul_(0.6)
+        Y = torch.poisson(lam, generator=g).clamp_(max=65535).to(torch.int32)
+        Y16 = torch.where(Y > 32767, Y - 65536, Y).to(torch.int16)
+        net = gmf.MLP(m, 256, 256, 20, max_batch=n)
+        net.set_precision("mixed")
+        net.set_params({k: np.asarray(v, dtype=np.float32) for k, v in synth.mlp_init(m, 256, 256, 20, 2).items()})
+        run = lambda: net.forward(Y16)
+        units, unit = n, "cells/s"
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    run()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    print(json.dumps({"case": args.case, "ms": ms, "value": units / (ms / 1e3), "unit": unit}), flush=True)
+    return 0
+
+
 def run_rank_sweep(args, w):
     """--workload nb_sweep: 8 ranks on one 50000 x 3000 NB matrix, batched (one
     launch per sweep for all models) vs the same 8 fits one after another."""
@@ -467,7 +521,11 @@ def main():
     ap.add_argument("--no-ttd", action="store_true", help="skip the time-to-deviance comparison")
     ap.add_argument("--encoder-precision", default="mixed", choices=["fp32", "mixed"],
                     help="nb_project: the encoder's first layer on the tensor cores (mixed) or FP32")
+    ap.add_argument("--case", default=None, choices=["project_20000", "encoder_16384"],
+                    help="a one-kernel measurement case (the profiles' captures)")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
