@@ -64,6 +64,7 @@ struct TcState {
     CUtensorMap ymap;
     int TI, TJ;
     int cluster;           // 1: the strip updates run inside the tile launch (cluster mode)
+    int epi;               // epilogue variant (EPI_*)
 };
 
 __device__ __forceinline__ void st_shared_v4(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -209,7 +210,11 @@ __device__ __forceinline__ void cl_update(const StepArgs& a, const TcLayout& Lo,
 
 // One tile (blockIdx.x, blockIdx.y) of block k of sweep w for the model whose
 // arguments are a / Lo. CL: cluster mode (the strip updates run here).
-template <bool Y16, bool CL>
+// EPI: 0 = any model (weights, family and moment sums read at run time); EPI_NB / EPI_PO = negative binomial /
+// Poisson without weights and without the NB moment sums, decided at compile time (fewer instructions per entry).
+constexpr int EPI_ANY = 0, EPI_NB = 1, EPI_PO = 2;
+
+template <bool Y16, bool CL, int EPI>
 __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, const CUtensorMap* ymap_p, int w,
                                         int k, uint8_t* smraw) {
     __shared__ uint64_t bars[3];
@@ -220,8 +225,8 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
     const BlockGeo g = block_geo(a, w, k);
     const int nTI = (int)((g.nI + TT - 1) / TT), nTJ = (int)((g.mJ + TT - 1) / TT);
     const bool active = ti < nTI && tj < nTJ;
-    const bool nb = a.family == GMF_NEGBIN;
-    const bool moments = nb && a.alpha_mode == 1;
+    const bool nb = EPI == EPI_ANY ? a.family == GMF_NEGBIN : EPI == EPI_NB;
+    const bool moments = EPI == EPI_ANY && nb && a.alpha_mode == 1;
     float alpha = 0.f;
     float s1 = 0.f, s2 = 0.f;
 
@@ -369,7 +374,7 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
             const int q = warp & 3, cq = warp >> 2;
             const int i = 32 * q + lane;
             const bool row_ok = i < nr;
-            const float* Wrow = a.W ? a.W + (row0 + i) * a.m + col0 : nullptr;
+            const float* Wrow = (EPI == EPI_ANY && a.W) ? a.W + (row0 + i) * a.m + col0 : nullptr;
             const int jc = 32 * cq;
             uint32_t ev[32];
             tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)jc, ev);
@@ -523,19 +528,30 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
     }
 }
 
-template <bool Y16>
+template <bool Y16, int EPI>
 __global__ void __launch_bounds__(NTH, 1)
     sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    tc_tile<Y16, false>(a, Lo, &ymap, w, blockIdx.z, smraw);
+    tc_tile<Y16, false, EPI>(a, Lo, &ymap, w, blockIdx.z, smraw);
 }
 
 // Cluster mode: launched with cluster dimensions (TJ, TI, 1), one cluster per block.
-template <bool Y16>
+template <bool Y16, int EPI>
 __global__ void __launch_bounds__(NTH, 1)
     sweep_tc_cluster(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    tc_tile<Y16, true>(a, Lo, &ymap, w, blockIdx.z, smraw);
+    tc_tile<Y16, true, EPI>(a, Lo, &ymap, w, blockIdx.z, smraw);
+}
+
+// The kernel of a handle: counts type, cluster mode and epilogue variant.
+template <int EPI>
+const void* tc_fn_epi(int y16, int cl) {
+    if (cl) return y16 ? (const void*)sweep_tc_cluster<true, EPI> : (const void*)sweep_tc_cluster<false, EPI>;
+    return y16 ? (const void*)sweep_tc_kernel<true, EPI> : (const void*)sweep_tc_kernel<false, EPI>;
+}
+const void* tc_fn(int y16, int cl, int epi) {
+    return epi == EPI_NB ? tc_fn_epi<EPI_NB>(y16, cl) : epi == EPI_PO ? tc_fn_epi<EPI_PO>(y16, cl)
+                                                                      : tc_fn_epi<EPI_ANY>(y16, cl);
 }
 
 // Several models (ranks) sharing the count matrix and the partitions: blockIdx.z
@@ -553,7 +569,7 @@ __global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restr
         s_l = lv[model];
     }
     __syncthreads();
-    tc_tile<Y16, false>(s_a, s_l, &ymap, w, blockIdx.z % per, smraw);
+    tc_tile<Y16, false, EPI_ANY>(s_a, s_l, &ymap, w, blockIdx.z % per, smraw);
 }
 
 int tc_cluster_layout(gmf_model* h, TcState* tc);
@@ -600,8 +616,7 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncAttributes fa;
-        const cudaError_t fe = h->y16 ? cudaFuncGetAttributes(&fa, sweep_tc_kernel<true>)
-                                      : cudaFuncGetAttributes(&fa, sweep_tc_kernel<false>);
+        const cudaError_t fe = cudaFuncGetAttributes(&fa, tc_fn(h->y16, 0, EPI_ANY));
         if (fe != cudaSuccess || (size_t)L.smem + fa.sharedSizeBytes > (size_t)optin) {
             delete tc;
             return fail_str(err, "mixed precision: the tile does not fit in shared memory (reduce d or use uint16 counts)");
@@ -628,8 +643,10 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
         if (err) *err = "cuTensorMapEncodeTiled failed for the count matrix";
         return GMF_ERR_CUDA;
     }
-    cudaError_t e = gmf_smem_limit(h->y16 ? (const void*)sweep_tc_kernel<true> : (const void*)sweep_tc_kernel<false>,
-                                   L.smem);
+    tc->epi = h->Wp ? EPI_ANY
+              : h->cfg.family == GMF_NEGBIN ? (h->cfg.alpha_mode == 1 ? EPI_ANY : EPI_NB)
+                                            : EPI_PO;
+    cudaError_t e = gmf_smem_limit(tc_fn(h->y16, 0, tc->epi), L.smem);
     if (e != cudaSuccess) {
         delete tc;
         if (err) *err = cudaGetErrorString(e);
@@ -658,7 +675,7 @@ int tc_cluster_layout(gmf_model* h, TcState* tc) {
     const uint32_t st_bytes = 4u * (uint32_t)(L.SRr * (h->KP + 1 + 2 * (h->fr | 1) + 1) +
                                               L.SCc * (h->KP + 1 + 2 * (h->fc | 1) + 1));
     L.smem_cl = L.off_st + st_bytes + 1024u;
-    const void* fn = h->y16 ? (const void*)sweep_tc_cluster<true> : (const void*)sweep_tc_cluster<false>;
+    const void* fn = tc_fn(h->y16, 1, tc->epi);
     if (gmf_smem_limit(fn, L.smem_cl) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -709,13 +726,21 @@ cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
         at[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 2;
-        return h->y16 ? cudaLaunchKernelEx(&cfg, sweep_tc_cluster<true>, a, tc->lay, tc->ymap, w)
-                      : cudaLaunchKernelEx(&cfg, sweep_tc_cluster<false>, a, tc->lay, tc->ymap, w);
+        void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap, &w};
+        return cudaLaunchKernelExC(&cfg, tc_fn(h->y16, 1, tc->epi), args);
     }
-    const cudaError_t e =
-        h->y16 ? gmf_launch_pdl(sweep_tc_kernel<true>, grid, dim3(NTH), tc->lay.smem, st, a, tc->lay, tc->ymap, w)
-               : gmf_launch_pdl(sweep_tc_kernel<false>, grid, dim3(NTH), tc->lay.smem, st, a, tc->lay, tc->ymap, w);
-    return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = tc->lay.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap, &w};
+    return cudaLaunchKernelExC(&cfg, tc_fn(h->y16, 0, tc->epi), args);
 }
 
 cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st) {
