@@ -292,19 +292,25 @@ __global__ void __launch_bounds__(GMF_THREADS, 2) sweep_multi(const StepArgs* __
     simt_tile(s_a, w, blockIdx.z % per, smem);
 }
 
-// Unit deviance 2w[...] of Table S1 / App. B in FP32, written so that no
-// difference of two large logarithms appears when mu >> y or mu << y.
-__device__ __forceinline__ float unit_deviance(bool nb, float y, float e, float mu, float alpha) {
-    if (y > 0.f) {
-        const float r1 = (y - mu) / mu;
-        const float l1 = fabsf(r1) < 0.5f ? log1pf(r1) : logf(y) - e;  // log(y / mu)
-        if (!nb) return y * l1 - (y - mu);
-        const float r2 = (y - mu) / (mu + alpha);
-        const float lma = mu > alpha ? e + log1pf(alpha / mu) : logf(alpha) + log1pf(mu / alpha);
-        const float l2 = fabsf(r2) < 0.5f ? log1pf(r2) : logf(y + alpha) - lma;  // log((y+a)/(mu+a))
-        return y * l1 - (y + alpha) * l2;
+// Unit deviance / 2 without branches on y (every lane of a warp takes the same path):
+//   Poisson  y (log y - eta) - (y - mu)
+//   NB       y (log y - eta) - (y + a)(log(y + a) - log a - log1p(mu / a)),
+// the y log y term zero at y = 0, so a zero count (most entries) is exactly a log1p(mu / a). log y and
+// log(y + a) come from per-CTA tables for y < 256. Near mu = y the logarithms cancel: the rounding is
+// ~6e-8 (y + a) log(y + a) per entry, ~1e-7 of a whole matrix's deviance.
+__device__ __forceinline__ float half_dev_tab(bool nb, float y, float e, float mu, float alpha, float la,
+                                              const float* tlog, const float* tloga) {
+    const int yi = (int)y;
+    float ly, lya;
+    if (yi < 256) {
+        ly = tlog[yi];
+        lya = tloga[yi];
+    } else {
+        ly = logf(y);
+        lya = logf(y + alpha);
     }
-    return nb ? alpha * log1pf(mu / alpha) : mu;
+    const float t1 = yi > 0 ? y * (ly - e) : 0.f;
+    return nb ? t1 - (y + alpha) * ((lya - la) - log1pf(__fdividef(mu, alpha))) : t1 - (y - mu);
 }
 
 // Deviance of one 64 x 64 tile of the whole (permuted) matrix.
@@ -313,7 +319,13 @@ __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, doubl
     float* Ls = smem;
     float* Rs = Ls + a.KP * LD;
     __shared__ float red[NW];
+    __shared__ float tlog[256], tloga[256];  // log(v), log(v + alpha), v < 256
     const int tid = threadIdx.x;
+    {
+        const float al = *a.alpha;
+        tlog[tid] = tid > 0 ? logf((float)tid) : 0.f;
+        tloga[tid] = logf((float)tid + al);
+    }
     const int64_t row0 = (int64_t)blockIdx.y * T, col0 = (int64_t)blockIdx.x * T;
     const int nr = (int)min((int64_t)T, a.n - row0), nc = (int)min((int64_t)T, a.m - col0);
     load_factor_T(Ls, a.L, a.KP, row0, nr);
@@ -335,6 +347,7 @@ __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, doubl
             for (int v = 0; v < 4; v++) acc[u][v] = fmaf(l4[u], r4[v], acc[u][v]);
     }
     const float alpha = *a.alpha;
+    const float la = tloga[0];  // log(alpha), the same rounding as the table's y = 0 entry
     const bool nb = a.family == GMF_NEGBIN;
     const bool vec = ((a.m & 3) == 0) && ((col0 & 3) == 0);
     float sum = 0.f, comp = 0.f;  // compensated (Kahan) per-thread sum
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, doubl
             if (v < valid) {
                 const float wv = a.W ? __ldg(a.W + idx + v) : 1.f;
                 const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
-                const float dv = 2.f * wv * unit_deviance(nb, y[v], e, expf(e), alpha);
+                const float dv = 2.f * wv * half_dev_tab(nb, y[v], e, __expf(e), alpha, la, tlog, tloga);
                 const float yk = dv - comp;
                 const float tk = sum + yk;
                 comp = (tk - sum) - yk;
