@@ -124,6 +124,22 @@ int gmf_init(gmf_model** out, const gmf_config* cfg,
  */
 int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, void* stream);
 
+/*
+ * gmf_update_y_async -- replace the counts from a host buffer without waiting:
+ * for streaming a sequence of count matrices of the same shape. The copy runs
+ * on the library's own copy stream into one of two device staging buffers (so
+ * it overlaps work already enqueued on `stream`); the permutation into the
+ * model's counts is ordered on `stream` after the copy. Work enqueued on
+ * `stream` before this call sees the old counts, work enqueued after it the new
+ * ones. Y: host, n x m counts of the init dtype; page-locked (pinned) memory
+ * for the copy to overlap; it must stay unchanged until `stream` has passed the
+ * work enqueued by this call (e.g. after a later synchronous call on it). At
+ * most two calls may be in flight on one handle. The paper has no counterpart
+ * (a deployment variant of gmf_update_y). Errors: GMF_ERR_ARG, GMF_ERR_STATE
+ * (a handle that reads another handle's counts), GMF_ERR_CUDA.
+ */
+int gmf_update_y_async(gmf_model* h, const void* Y, void* stream);
+
 /* Number of sweeps per epoch: max(r, s) with r = ceil(n/nb_row), s = ceil(m/nb_col). */
 int32_t gmf_num_sweeps(const gmf_model* h);
 

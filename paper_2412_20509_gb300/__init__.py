@@ -28,7 +28,8 @@ PRECISIONS = {"fp32": GMF_PREC_FP32, "mixed": GMF_PREC_MIXED}
 ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
 
 # Every function declared in include/gmf.h.
-EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_num_sweeps", "gmf_launches_per_sweep",
+EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async", "gmf_num_sweeps",
+           "gmf_launches_per_sweep",
            "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
@@ -71,6 +72,7 @@ def lib():
         "gmf_init": (C.c_int, [C.POINTER(VP), C.POINTER(gmf_config), VP, C.c_int32, C.c_int32, VP, VP, VP, VP, VP, VP,
                                VP, VP, VP, VP, C.c_double, VP]),
         "gmf_update_y": (C.c_int, [VP, VP, C.c_int32, VP]),
+        "gmf_update_y_async": (C.c_int, [VP, VP, VP]),
         "gmf_num_sweeps": (C.c_int32, [VP]),
         "gmf_launches_per_sweep": (C.c_int32, [VP]),
         "gmf_sgd_epoch": (C.c_int, [VP, VP, VP]),
@@ -250,6 +252,11 @@ class Model:
         if not on_dev:
             Y = np.ascontiguousarray(Y) if not isinstance(Y, torch.Tensor) else Y.contiguous()
         check(lib().gmf_update_y(self._h, _ptr(Y), int(on_dev), _stream(stream)))
+
+    def update_y_async(self, Y, stream=None):
+        """Counts from a pinned host tensor without waiting (see gmf_update_y_async); keep Y unchanged until the
+        stream has passed this call's work."""
+        check(lib().gmf_update_y_async(self._h, _ptr(Y), _stream(stream)))
 
     def deviance(self, stream=None):
         out = C.c_double()

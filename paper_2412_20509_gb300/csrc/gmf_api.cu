@@ -124,7 +124,15 @@ static void release(gmf_model* h) {
         h->Wp = nullptr;
         h->ystage = nullptr;
     }
-    void* ptrs[] = {h->Yp, h->Wp, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
+    if (h->up_init) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+        for (int i = 0; i < 2; i++) {
+            cudaEventDestroy(h->up_copied[i]);
+            cudaEventDestroy(h->up_free[i]);
+        }
+    }
+    void* ptrs[] = {h->Yp, h->Wp, h->ystage2, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
                     h->rperm, h->cperm, h->ystage, h->Rorig, h->kr_buf, h->partR, h->partC, h->nbpart, h->nbctr,
                     h->sigma, h->rhoc, h->rho1, h->err, h->devpart, h->devtot};
     for (void* p : ptrs)
@@ -359,6 +367,34 @@ extern "C" int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, vo
     int rc = upload_y(h, Y, y_on_device, st);
     if (rc) return rc;
     if (!y_on_device) CUDA_TRY(cudaStreamSynchronize(st));
+    return GMF_OK;
+}
+
+extern "C" int gmf_update_y_async(gmf_model* h, const void* Y, void* stream) {
+    if (!h || !Y) return fail(GMF_ERR_ARG, "gmf_update_y_async: NULL argument");
+    if (h->y_shared) return fail(GMF_ERR_STATE, "gmf_update_y_async: this handle reads another handle's counts");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)h->n * h->m * (h->y16 ? 2 : 4);
+    if (!h->up_init) {
+        if (!h->ystage) CUDA_TRY(cudaMalloc(&h->ystage, bytes));
+        CUDA_TRY(cudaMalloc(&h->ystage2, bytes));
+        CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; i++) {
+            CUDA_TRY(cudaEventCreateWithFlags(&h->up_copied[i], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&h->up_free[i], cudaEventDisableTiming));
+        }
+        h->up_init = 1;
+    }
+    const int i = h->up_idx;
+    h->up_idx ^= 1;
+    void* buf = i ? h->ystage2 : h->ystage;
+    // the copy into buf waits for the permutation that last read buf (no wait before its first use)
+    CUDA_TRY(cudaStreamWaitEvent(h->copy_stream, h->up_free[i], 0));
+    CUDA_TRY(cudaMemcpyAsync(buf, Y, bytes, cudaMemcpyHostToDevice, h->copy_stream));
+    CUDA_TRY(cudaEventRecord(h->up_copied[i], h->copy_stream));
+    CUDA_TRY(cudaStreamWaitEvent(st, h->up_copied[i], 0));
+    CUDA_TRY(gmf_launch_permute_y(buf, h->Yp, h->y16, h->n, h->m, h->rperm, h->cperm, st));
+    CUDA_TRY(cudaEventRecord(h->up_free[i], st));
     return GMF_OK;
 }
 

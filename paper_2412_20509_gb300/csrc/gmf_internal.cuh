@@ -85,6 +85,12 @@ struct gmf_model {
     int* rperm;
     int* cperm;
     void* ystage;               // staging for counts uploaded from the host
+    void* ystage2;              // second staging buffer (gmf_update_y_async)
+    cudaStream_t copy_stream;   // host-to-device copies of gmf_update_y_async
+    cudaEvent_t up_copied[2];   // staging buffer i filled
+    cudaEvent_t up_free[2];     // staging buffer i read by its permutation
+    int up_idx;                 // staging buffer of the next gmf_update_y_async
+    int up_init;
     float* Rorig;               // m x KP: R in the caller's gene order (per-cell projection)
     void* kr_buf;               // BF16 Khatri-Rao product of [Z, V] (tensor-core projection)
     size_t kr_elems;
