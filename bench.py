@@ -131,6 +131,26 @@ def fp32_simt_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def sfu_peak_ops(sm_mhz):
+    # special-function unit (exp2, rcp, lg2): 152 SMs x 16 results per clock (4 per SM sub-partition) x clock
+    return 152 * 16 * sm_mhz * 1e6
+
+
+def host_cpu():
+    """Core count and model of the host that runs the oracle."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model name", "CPU part") and v.strip():
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 def sweep_algorithmic(w, K, fr, fc):
     """Algorithmic flops and HBM bytes of one sweep launch (all blocks of a sweep)."""
     per = min(-(-w.n // w.nb_row), -(-w.m // w.nb_col))
@@ -178,7 +198,7 @@ def run_reference(args, w):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": describe(w, "fp64"),
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, **host_cpu()},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -680,6 +700,12 @@ def main():
                 "peak_source": f"{peak_src} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
                 "tensor_tflops": flops_sweep / avg_kernel_s / 1e12, "tensor_peak_tflops": tc_peak,
                 "tensor_frac_of_measured": flops_sweep / avg_kernel_s / 1e12 / tc_peak}
+        # special-function work of the epilogue: exp per entry, and a reciprocal for the NB weight
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        sfu_ops = ent_sweep * (2 if w.family == "negbin" else 1) / avg_kernel_s
+        roof.update({"sfu_ops_per_s": sfu_ops, "sfu_peak_ops_per_s": sfu_peak_ops(sm_mhz),
+                     "sfu_frac": sfu_ops / sfu_peak_ops(sm_mhz),
+                     "sfu_peak_source": f"derived: 152 SMs x 16 SFU results per clock x {sm_mhz:.0f} MHz"})
     roof.update({"avg_launch_us": avg_kernel_s * 1e6, "launches_timed": launches, "algorithmic_per_launch": algo})
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -743,7 +769,7 @@ def main():
             times = ores["epoch_times"]
             k = next((i + 1 for i, t in enumerate(times) if t >= 12.0), len(times))
             out["cpu_baseline"] = {"value": k * ores["entries_per_epoch"] / times[k - 1], "unit": UNIT, "cores": 1,
-                                   "kind": "oracle",
+                                   "kind": "oracle", **host_cpu(),
                                    "sample": f"first {k} epochs ({k * ores['entries_per_epoch']:.3g} entries) of the "
                                              f"same fit, FP64 single-threaded C on one host core, {times[k - 1]:.1f} s"}
     if rank == 0:
