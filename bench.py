@@ -236,6 +236,7 @@ def source_hash(paths):
 KERNEL_SOURCES = {
     "sweep_tc_kernel": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
     "sweep_tc_cluster": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
+    "sweep_tc_epoch": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
     "sweep_kernel": ["gmf_step_simt.cu", "gmf_update.cuh", "gmf_internal.cuh"],
     "update_kernel": ["gmf_update.cu", "gmf_update.cuh", "gmf_internal.cuh"],
 }
@@ -592,9 +593,10 @@ def main():
     Yd = torch.from_numpy(prob.Y).cuda()
     stream = torch.cuda.current_stream()
 
-    def make(precision):
+    def make(precision, flags=0):
         return gmf.Model(Yd, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row,
-                         nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=settings, precision=precision)
+                         nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=settings, precision=precision,
+                         flags=flags)
 
     model = make(args.precision)
     nsw = model.num_sweeps
@@ -673,11 +675,17 @@ def main():
         e2e[name] = whole_job_rate(entries_step * e2e_steps, ws, e2e_s)
     e2e_value = e2e["streamed"]
     launches_per_sweep = model.launches_per_sweep
+    epoch_mode = model.epoch_mode
     del model
+    # sweeps per traced launch, launches of this library per timed epoch
+    sweeps_per_launch = nsw if epoch_mode == "persistent" else 1
+    launches_per_epoch = 1 if epoch_mode == "persistent" else launches_per_sweep * nsw
 
     # ---------------- roofline of the dominant kernel (the tile launch of a sweep)
     peaks, peak_src = measured_peaks()
     ent_sweep, flops_sweep, bytes_sweep = sweep_algorithmic(w, K, fr, fc)
+    ent_sweep, flops_sweep, bytes_sweep = (sweeps_per_launch * ent_sweep, sweeps_per_launch * flops_sweep,
+                                           sweeps_per_launch * bytes_sweep)
     avg_kernel_s = (kern_ms / max(launches, 1)) / 1e3
     algo = {"entries": ent_sweep, "flops": flops_sweep, "bytes": bytes_sweep}
     if args.precision == "fp32":
@@ -692,11 +700,12 @@ def main():
         achieved = bytes_sweep / avg_kernel_s / 1e9
         peak = float(peaks["hbm_gbs"])
         tc_peak = float(peaks.get("bf16_tflops", 1900.0))
-        tc_kernel = "sweep_tc_cluster" if launches_per_sweep == 1 else "sweep_tc_kernel"
+        tc_kernel = {"persistent": "sweep_tc_epoch", "cluster": "sweep_tc_cluster"}.get(epoch_mode, "sweep_tc_kernel")
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": committed_traffic(tc_kernel, w.name),
-                "kernel": tc_kernel + (" (tcgen05, strip updates in the same launch)" if tc_kernel == "sweep_tc_cluster"
-                                       else " (tcgen05; the strip updates follow in update_kernel)"),
+                "kernel": tc_kernel + {"sweep_tc_epoch": f" (tcgen05, persistent: one launch = {nsw} sweeps)",
+                                       "sweep_tc_cluster": " (tcgen05, strip updates in the same launch)"}.get(
+                                           tc_kernel, " (tcgen05; the strip updates follow in update_kernel)"),
                 "peak_source": f"{peak_src} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
                 "tensor_tflops": flops_sweep / avg_kernel_s / 1e12, "tensor_peak_tflops": tc_peak,
                 "tensor_frac_of_measured": flops_sweep / avg_kernel_s / 1e12 / tc_peak}
@@ -706,7 +715,8 @@ def main():
         roof.update({"sfu_ops_per_s": sfu_ops, "sfu_peak_ops_per_s": sfu_peak_ops(sm_mhz),
                      "sfu_frac": sfu_ops / sfu_peak_ops(sm_mhz),
                      "sfu_peak_source": f"derived: 152 SMs x 16 SFU results per clock x {sm_mhz:.0f} MHz"})
-    roof.update({"avg_launch_us": avg_kernel_s * 1e6, "launches_timed": launches, "algorithmic_per_launch": algo})
+    roof.update({"avg_launch_us": avg_kernel_s * 1e6, "launches_timed": launches, "sweeps_per_launch": sweeps_per_launch,
+                 "algorithmic_per_launch": algo})
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -719,7 +729,7 @@ def main():
                           "gmf_deviance_async; with the synchronous gmf_update_y / gmf_deviance: "
                           f"{e2e['serial']:.4g} {UNIT}",
                    "d2h_bytes_per_step": 8},
-           "gpu_launches": int(launches_per_sweep * nsw * args.steps), "clocks": clk,
+           "gpu_launches": int(launches_per_epoch * args.steps), "epoch_mode": epoch_mode, "clocks": clk,
            "deviance": {"after_warmup": dev0, "after_timed_steps": dev1}}
 
     if extras:
@@ -731,6 +741,16 @@ def main():
         oms = timed_epochs(mo, args.warmup, args.steps)
         out[f"{other}_path"] = {"value": entries_step * args.steps / (oms / 1e3), "ms_per_step": oms / args.steps}
         del mo
+        if epoch_mode == "cluster":
+            # ---------------- the same path as one persistent launch per epoch (GMF_FLAG_PERSIST)
+            mo = make(args.precision, gmf.GMF_FLAG_PERSIST)
+            if mo.epoch_mode == "persistent":
+                for s in range(args.warmup):
+                    mo.epoch(sig[s])
+                oms = timed_epochs(mo, args.warmup, args.steps)
+                out["persistent_epoch"] = {"value": entries_step * args.steps / (oms / 1e3),
+                                           "ms_per_step": oms / args.steps}
+            del mo
         # ---------------- time to the oracle's deviance (within 1e-3), both paths, fresh starts
         traj = {}
         if not args.no_ttd:

@@ -21,7 +21,9 @@ GMF_POISSON, GMF_NEGBIN = 0, 1
 GMF_Y_INT32, GMF_Y_UINT16 = 0, 1
 GMF_PREC_FP32, GMF_PREC_MIXED = 0, 1
 GMF_ORTH_B1, GMF_ORTH_B2, GMF_ORTH_B3 = 1, 2, 3
-GMF_FLAG_NO_CLUSTER = 1
+GMF_FLAG_NO_CLUSTER, GMF_FLAG_PERSIST = 1, 2
+GMF_EPOCH_SEPARATE, GMF_EPOCH_CLUSTER, GMF_EPOCH_PERSISTENT = 0, 1, 2
+EPOCH_MODES = {GMF_EPOCH_SEPARATE: "separate", GMF_EPOCH_CLUSTER: "cluster", GMF_EPOCH_PERSISTENT: "persistent"}
 
 FAMILIES = {"poisson": GMF_POISSON, "negbin": GMF_NEGBIN}
 PRECISIONS = {"fp32": GMF_PREC_FP32, "mixed": GMF_PREC_MIXED}
@@ -29,7 +31,7 @@ ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
 
 # Every function declared in include/gmf.h.
 EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async", "gmf_num_sweeps",
-           "gmf_launches_per_sweep",
+           "gmf_launches_per_sweep", "gmf_epoch_mode", "gmf_strip_schedule",
            "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
@@ -75,6 +77,8 @@ def lib():
         "gmf_update_y_async": (C.c_int, [VP, VP, VP]),
         "gmf_num_sweeps": (C.c_int32, [VP]),
         "gmf_launches_per_sweep": (C.c_int32, [VP]),
+        "gmf_epoch_mode": (C.c_int32, [VP]),
+        "gmf_strip_schedule": (C.c_int, [C.c_int32, C.c_int32, VP, C.c_int32, C.c_int32, VP]),
         "gmf_sgd_epoch": (C.c_int, [VP, VP, VP]),
         "gmf_sgd_sweeps": (C.c_int, [VP, VP, C.c_int32, C.c_int32, VP]),
         "gmf_deviance": (C.c_int, [VP, C.POINTER(C.c_double), VP]),
@@ -145,6 +149,17 @@ def _torch_ydt(Y):
     if Y.dtype == torch.int16 or (hasattr(torch, "uint16") and Y.dtype == torch.uint16):
         return GMF_Y_UINT16
     raise TypeError("counts must be int32 or 16-bit (uint16 / int16 view)")
+
+
+def strip_schedule(r, s, sigma, w_begin=0, w_end=None):
+    """need[w - w_begin, k]: earlier visits (within [w_begin, w)) of the moving
+    strip of block k of sweep w -- the dependency counts of a persistent sweep
+    range (host computation, gmf_strip_schedule)."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+    w_end = len(sigma) if w_end is None else w_end
+    out = np.zeros((max(w_end - w_begin, 0), min(r, s)), dtype=np.int32)
+    check(lib().gmf_strip_schedule(int(r), int(s), sigma.ctypes.data, int(w_begin), int(w_end), out.ctypes.data))
+    return out
 
 
 def make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision="fp32", flags=0):
@@ -235,8 +250,14 @@ class Model:
 
     @property
     def launches_per_sweep(self):
-        """Kernel launches per sweep: 1 in cluster mode, else 2."""
+        """Kernel launches per sweep: 1 in cluster mode, 2 with a separate update
+        launch, 0 when a sweep range is one persistent launch."""
         return lib().gmf_launches_per_sweep(self._h)
+
+    @property
+    def epoch_mode(self):
+        """'separate', 'cluster' or 'persistent' (how gmf_sgd_epoch launches)."""
+        return EPOCH_MODES[lib().gmf_epoch_mode(self._h)]
 
     def epoch(self, sigma, stream=None):
         sigma = np.ascontiguousarray(sigma, dtype=np.int32)

@@ -43,6 +43,8 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err);
 cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st);
 cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st);
 int gmf_tc_cluster(const gmf_model* h);
+int gmf_tc_persistent(const gmf_model* h);
+cudaError_t gmf_tc_launch_epoch(gmf_model* h, int w0, int w1, cudaStream_t st);
 void gmf_tc_free(gmf_model* h);
 
 // One sweep launch of the configured path.
@@ -134,7 +136,7 @@ static void release(gmf_model* h) {
     }
     void* ptrs[] = {h->Yp, h->Wp, h->ystage2, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
                     h->rperm, h->cperm, h->ystage, h->Rorig, h->kr_buf, h->partR, h->partC, h->nbpart, h->nbctr,
-                    h->sigma, h->rhoc, h->rho1, h->err, h->devpart, h->devtot};
+                    h->sigma, h->rhoc, h->rho1, h->need, h->strip_done, h->err, h->devpart, h->devtot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] h->h_rperm;
@@ -215,7 +217,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     if (c.alpha_mode != 0 && c.alpha_mode != 1) return fail(GMF_ERR_ARG, "gmf_init: alpha_mode must be 0 or 1");
     if (c.precision != GMF_PREC_FP32 && c.precision != GMF_PREC_MIXED)
         return fail(GMF_ERR_ARG, "gmf_init: unknown precision");
-    if (c.flags & ~GMF_FLAG_NO_CLUSTER) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
+    if (c.flags & ~(GMF_FLAG_NO_CLUSTER | GMF_FLAG_PERSIST)) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
     if (!(c.a1 > 0 && c.a1 <= 1 && c.a2 > 0 && c.a2 <= 1)) return fail(GMF_ERR_ARG, "gmf_init: a1, a2 in (0, 1]");
     if (!(c.k0 > 0) || c.k1 < 0 || !(c.tau > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad learning-rate schedule");
     if (c.damping < 0 || !(c.eta_clamp > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad damping or eta_clamp");
@@ -292,6 +294,8 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     INIT_CUDA(dalloc(&h->sigma, (size_t)h->nsw));
     INIT_CUDA(dalloc(&h->rhoc, (size_t)h->nsw * h->per));
     INIT_CUDA(dalloc(&h->rho1, (size_t)h->nsw));
+    INIT_CUDA(dalloc(&h->need, (size_t)h->nsw * h->per));
+    INIT_CUDA(dalloc(&h->strip_done, (size_t)std::max(h->r, h->s)));
     INIT_CUDA(dalloc(&h->err, 1));
     h->devparts = (int)(((c.n + GMF_TILE - 1) / GMF_TILE) * ((c.m + GMF_TILE - 1) / GMF_TILE));
     INIT_CUDA(dalloc(&h->devpart, (size_t)h->devparts));
@@ -400,9 +404,40 @@ extern "C" int gmf_update_y_async(gmf_model* h, const void* Y, void* stream) {
 
 extern "C" int32_t gmf_num_sweeps(const gmf_model* h) { return h ? h->nsw : -1; }
 
+extern "C" int32_t gmf_epoch_mode(const gmf_model* h) {
+    if (!h) return -1;
+    if (h->cfg.precision != GMF_PREC_MIXED || !gmf_tc_cluster(h)) return GMF_EPOCH_SEPARATE;
+    return gmf_tc_persistent(h) ? GMF_EPOCH_PERSISTENT : GMF_EPOCH_CLUSTER;
+}
+
 extern "C" int32_t gmf_launches_per_sweep(const gmf_model* h) {
     if (!h) return -1;
-    return h->cfg.precision == GMF_PREC_MIXED && gmf_tc_cluster(h) ? 1 : 2;
+    const int mode = gmf_epoch_mode(h);
+    return mode == GMF_EPOCH_PERSISTENT ? 0 : mode == GMF_EPOCH_CLUSTER ? 1 : 2;
+}
+
+// Visits of each block's moving strip by the earlier sweeps of [w_begin, w_end)
+// (the blocks of one sweep move along disjoint strips).
+static void strip_need(int r, int s, const int32_t* sigma, int w_begin, int w_end, int32_t* need) {
+    const int swap = r < s, per = std::min(r, s), mod = swap ? s : r;
+    std::vector<int32_t> visits((size_t)mod, 0);
+    for (int w = w_begin; w < w_end; w++) {
+        for (int k = 0; k < per; k++) need[(size_t)(w - w_begin) * per + k] = visits[(size_t)((sigma[w] + k) % mod)];
+        for (int k = 0; k < per; k++) visits[(size_t)((sigma[w] + k) % mod)]++;
+    }
+}
+
+extern "C" int gmf_strip_schedule(int32_t r, int32_t s, const int32_t* sigma, int32_t w_begin, int32_t w_end,
+                                  int32_t* need_out) {
+    if (!sigma || !need_out) return fail(GMF_ERR_ARG, "gmf_strip_schedule: NULL argument");
+    if (r < 1 || s < 1) return fail(GMF_ERR_ARG, "gmf_strip_schedule: r = %d, s = %d", r, s);
+    const int S = std::max(r, s);
+    if (w_begin < 0 || w_end > S || w_begin > w_end)
+        return fail(GMF_ERR_ARG, "gmf_strip_schedule: sweep range [%d, %d) outside [0, %d)", w_begin, w_end, S);
+    for (int w = 0; w < S; w++)
+        if (sigma[w] < 0 || sigma[w] >= S) return fail(GMF_ERR_ARG, "gmf_strip_schedule: sigma[%d] = %d", w, sigma[w]);
+    strip_need(r, s, sigma, w_begin, w_end, need_out);
+    return GMF_OK;
 }
 
 // Wait for the recorded event pairs and add their durations to the running total.
@@ -437,6 +472,11 @@ int gmf_stage_schedule(gmf_model* h, const int32_t* sigma, int w_begin, int w_en
     CUDA_TRY(cudaMemcpyAsync(h->rhoc, rc.data(), sizeof(float) * rc.size(), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->rho1, r1.data(), sizeof(float) * r1.size(), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->sigma, sigma, sizeof(int32_t) * h->nsw, cudaMemcpyHostToDevice, st));
+    if (gmf_tc_persistent(h)) {
+        std::vector<int32_t> need((size_t)h->nsw * h->per, 0);
+        strip_need(h->r, h->s, sigma, w_begin, w_end, need.data() + (size_t)w_begin * h->per);
+        CUDA_TRY(cudaMemcpyAsync(h->need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, st));
+    }
     return GMF_OK;
 }
 
@@ -449,6 +489,24 @@ extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begi
     {
         const int rc = gmf_stage_schedule(h, sigma, w_begin, w_end, st);
         if (rc) return rc;
+    }
+    if (gmf_tc_persistent(h)) {  // the range is one launch
+        if (w_begin == w_end) return GMF_OK;
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        if (h->trace_on) {
+            if (h->trace_used == GMF_TRACE_POOL) {
+                int rc = trace_collect(h, st);
+                if (rc) return rc;
+            }
+            t0 = h->trace_ev[2 * h->trace_used];
+            t1 = h->trace_ev[2 * h->trace_used + 1];
+            h->trace_used++;
+        }
+        if (t0) CUDA_TRY(cudaEventRecord(t0, st));
+        CUDA_TRY(gmf_tc_launch_epoch(h, w_begin, w_end, st));
+        if (t1) CUDA_TRY(cudaEventRecord(t1, st));
+        h->t += (int64_t)(w_end - w_begin) * h->per;
+        return GMF_OK;
     }
     const StepArgs a = gmf_make_args(h);
     // A whole epoch replays one captured graph of its sweep launches (the

@@ -58,6 +58,8 @@ struct StepArgs {
     const int* sigma;           // device copy of the epoch's sweep offsets
     const float* rhoc;          // [nsw][per]: rho_t * c_t per block (rho_t alone when bias_corr = 1)
     const float* rho1;          // [nsw]: rho at the first block of each sweep (NB shape update)
+    const int* need;            // [nsw][per]: earlier visits of each block's moving strip (persistent epochs)
+    unsigned* strip_done;       // [max(r, s)]: CTAs done with each moving strip in this launch (persistent epochs)
     unsigned* err;              // device status word
 };
 
@@ -102,6 +104,8 @@ struct gmf_model {
     int* sigma;
     float* rhoc;
     float* rho1;
+    int* need;
+    unsigned* strip_done;
     unsigned* err;
     double* devpart;
     double* devtot;

@@ -457,6 +457,8 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.sigma = h->sigma;
     a.rhoc = h->rhoc;
     a.rho1 = h->rho1;
+    a.need = h->need;
+    a.strip_done = h->strip_done;
     a.err = h->err;
     return a;
 }

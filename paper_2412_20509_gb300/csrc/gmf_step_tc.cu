@@ -56,7 +56,7 @@ struct TcLayout {
     int SRr, SCc;          // rows of a row strip / columns of a column strip each CTA updates
     uint32_t off_cp;       // slots of this CTA's slices: row partials [TJ][2 fr][SRr], column [TI][2 fc][SCc]
     uint32_t off_st;       // the CTA's update slices: parameter rows, smoothed derivatives, visit counts
-    uint32_t smem_cl;      // dynamic shared memory of the cluster kernel
+    uint32_t smem_cl;      // dynamic shared memory of the cluster kernels
 };
 
 struct TcState {
@@ -64,6 +64,7 @@ struct TcState {
     CUtensorMap ymap;
     int TI, TJ;
     int cluster;           // 1: the strip updates run inside the tile launch (cluster mode)
+    int persist;           // 1: a sweep range runs as one persistent launch (sweep_tc_epoch)
     int epi;               // epilogue variant (EPI_*)
 };
 
@@ -133,34 +134,45 @@ __device__ __forceinline__ ClStage cl_stage_ptrs(float* base, int rows, int KS, 
 
 // Start the copies of this CTA's slices with threads [t0, t0 + nt) (after the
 // dependency wait: the previous sweep wrote these rows). Each thread waits for
-// its own copies (cp.async.wait_all) before the cluster barrier.
+// its own copies (cp.async.wait_all) before the cluster barrier. In the
+// persistent kernel the copies are issued after the acquire that orders them
+// behind their writer (the moving strip's count; the CTA's own fixed-strip
+// slice has no other writer), and no stale line can serve them: a cluster
+// visits each moving strip once per launch and reads operands through L2.
+// stage_r / stage_c: copy that side (the persistent kernel keeps its fixed
+// side's slice in shared memory from one block to the next).
 __device__ __forceinline__ void cl_stage_issue(const StepArgs& a, const TcLayout& Lo, uint8_t* sm, const ClSlice& c,
-                                               int t0, int nt) {
+                                               int t0, int nt, bool stage_r = true, bool stage_c = true) {
     const int KS = a.KP + 1;
     const int tid = (int)threadIdx.x - t0;
     if (tid < 0 || tid >= nt) return;
     const ClStage r = cl_stage_ptrs((float*)(sm + Lo.off_st), Lo.SRr, KS, a.fr | 1);
     const ClStage q = cl_stage_ptrs(r.P + (size_t)Lo.SRr * (KS + 2 * (a.fr | 1) + 1), Lo.SCc, KS, a.fc | 1);
-    for (int e = tid; e < c.nrs * a.KP; e += nt)
+    const int nrs = stage_r ? c.nrs : 0, ncs = stage_c ? c.ncs : 0;
+    for (int e = tid; e < nrs * a.KP; e += nt)
         cp_async4(r.P + (e / a.KP) * KS + e % a.KP, a.L + c.first_r * a.KP + e);
-    for (int e = tid; e < c.ncs * a.KP; e += nt)
+    for (int e = tid; e < ncs * a.KP; e += nt)
         cp_async4(q.P + (e / a.KP) * KS + e % a.KP, a.R + c.first_c * a.KP + e);
-    for (int e = tid; e < c.nrs * a.fr; e += nt) {
+    for (int e = tid; e < nrs * a.fr; e += nt) {
         cp_async4(r.G + (e / a.fr) * (a.fr | 1) + e % a.fr, a.GbR + c.first_r * a.fr + e);
         cp_async4(r.H + (e / a.fr) * (a.fr | 1) + e % a.fr, a.HbR + c.first_r * a.fr + e);
     }
-    for (int e = tid; e < c.ncs * a.fc; e += nt) {
+    for (int e = tid; e < ncs * a.fc; e += nt) {
         cp_async4(q.G + (e / a.fc) * (a.fc | 1) + e % a.fc, a.GbC + c.first_c * a.fc + e);
         cp_async4(q.H + (e / a.fc) * (a.fc | 1) + e % a.fc, a.HbC + c.first_c * a.fc + e);
     }
-    for (int e = tid; e < c.nrs; e += nt) cp_async4(r.C + e, a.cntR + c.first_r + e);
-    for (int e = tid; e < c.ncs; e += nt) cp_async4(q.C + e, a.cntC + c.first_c + e);
+    for (int e = tid; e < nrs; e += nt) cp_async4(r.C + e, a.cntR + c.first_r + e);
+    for (int e = tid; e < ncs; e += nt) cp_async4(q.C + e, a.cntC + c.first_c + e);
 }
 
 // The strip updates of cluster mode. Every thread of every CTA of the cluster
-// calls this (one cluster barrier).
+// calls this (one cluster barrier). The parameter rows always go back to
+// global memory; wb_r / wb_c: write back that side's smoothed derivatives and
+// visit counts too (else only the staged counts advance: a side kept resident
+// in shared memory by the persistent kernel).
 __device__ __forceinline__ void cl_update(const StepArgs& a, const TcLayout& Lo, uint8_t* sm, const ClSlice& c,
-                                          const BlockGeo& g, float rhoc_blk, int nTI, int nTJ) {
+                                          const BlockGeo& g, float rhoc_blk, int nTI, int nTJ, bool wb_r = true,
+                                          bool wb_c = true) {
     const int KS = a.KP + 1, NSr = a.fr | 1, NSc = a.fc | 1;
     const ClStage r = cl_stage_ptrs((float*)(sm + Lo.off_st), Lo.SRr, KS, NSr);
     const ClStage q = cl_stage_ptrs(r.P + (size_t)Lo.SRr * (KS + 2 * NSr + 1), Lo.SCc, KS, NSc);
@@ -196,38 +208,301 @@ __device__ __forceinline__ void cl_update(const StepArgs& a, const TcLayout& Lo,
     __syncthreads();
     for (int e = threadIdx.x; e < c.nrs * a.KP; e += NTH) a.L[c.first_r * a.KP + e] = r.P[(e / a.KP) * KS + e % a.KP];
     for (int e = threadIdx.x; e < c.ncs * a.KP; e += NTH) a.R[c.first_c * a.KP + e] = q.P[(e / a.KP) * KS + e % a.KP];
-    for (int e = threadIdx.x; e < c.nrs * a.fr; e += NTH) {
+    for (int e = threadIdx.x; e < (wb_r ? c.nrs * a.fr : 0); e += NTH) {
         a.GbR[c.first_r * a.fr + e] = r.G[(e / a.fr) * NSr + e % a.fr];
         a.HbR[c.first_r * a.fr + e] = r.H[(e / a.fr) * NSr + e % a.fr];
     }
-    for (int e = threadIdx.x; e < c.ncs * a.fc; e += NTH) {
+    for (int e = threadIdx.x; e < (wb_c ? c.ncs * a.fc : 0); e += NTH) {
         a.GbC[c.first_c * a.fc + e] = q.G[(e / a.fc) * NSc + e % a.fc];
         a.HbC[c.first_c * a.fc + e] = q.H[(e / a.fc) * NSc + e % a.fc];
     }
-    for (int e = threadIdx.x; e < c.nrs; e += NTH) a.cntR[c.first_r + e] = r.C[e] + 1;
-    for (int e = threadIdx.x; e < c.ncs; e += NTH) a.cntC[c.first_c + e] = q.C[e] + 1;
+    for (int e = threadIdx.x; e < c.nrs; e += NTH) {
+        const int v = r.C[e] + 1;
+        if (wb_r)
+            a.cntR[c.first_r + e] = v;
+        else
+            r.C[e] = v;
+    }
+    for (int e = threadIdx.x; e < c.ncs; e += NTH) {
+        const int v = q.C[e] + 1;
+        if (wb_c)
+            a.cntC[c.first_c + e] = v;
+        else
+            q.C[e] = v;
+    }
 }
 
-// One tile (blockIdx.x, blockIdx.y) of block k of sweep w for the model whose
-// arguments are a / Lo. CL: cluster mode (the strip updates run here).
 // EPI: 0 = any model (weights, family and moment sums read at run time); EPI_NB / EPI_PO = negative binomial /
 // Poisson without weights and without the NB moment sums, decided at compile time (fewer instructions per entry).
 constexpr int EPI_ANY = 0, EPI_NB = 1, EPI_PO = 2;
 
+// ---- the phases of one tile. COH: model state is read through L2 only (the
+// persistent kernel, where other CTAs wrote it during the same launch).
+template <bool COH>
+__device__ __forceinline__ float4 ld_state4(const float* p) {
+    return COH ? __ldcg((const float4*)p) : __ldg((const float4*)p);
+}
+template <bool COH>
+__device__ __forceinline__ float ld_state(const float* p) {
+    return COH ? __ldcg(p) : __ldg(p);
+}
+
+// Thread 0: the TMA load of the count tile at (row0, col0) into Ys.
+__device__ __forceinline__ void issue_counts(const TcLayout& Lo, const CUtensorMap* ymap_p, uint8_t* Ys, int64_t row0,
+                                             int64_t col0, uint64_t* bar) {
+    mbar_arrive_expect_tx(bar, Lo.y_bytes);
+    const int nbox = TT / Lo.JB;
+    for (int b = 0; b < nbox; b++)
+        tma_load_2d(Ys + b * ATOM, ymap_p, (int)(col0 + (int64_t)b * Lo.JB), (int)row0, bar);
+}
+
+// Operands. Thread groups of 128: L rows -> eta A; R rows -> eta B; L rows ->
+// column-side B ([X, U] and squares); R rows -> row-side B ([Z, V] and squares).
+template <bool COH>
+__device__ __forceinline__ void build_operands(const StepArgs& a, const TcLayout& Lo, uint8_t* sm, int64_t row0,
+                                               int64_t col0, int nr, int nc) {
+    const int tid = threadIdx.x;
+    uint8_t* Aop = sm + Lo.off_u;
+    uint8_t* Bop = Aop + Lo.KA * ATOM;
+    const int grp = tid >> 7, r = tid & (TT - 1);
+    const bool isL = (grp & 1) == 0;
+    const bool ok = isL ? r < nr : r < nc;
+    const float* src = isL ? a.L + (row0 + r) * a.KP : a.R + (col0 + r) * a.KP;
+    if (grp < 2) {
+        uint8_t* op = isL ? Aop : Bop;
+        for (int kb = 0; kb < Lo.KP16; kb += 32) {
+            float v[32];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int kk = kb + 4 * u;
+                const float4 x = (ok && kk < a.KP) ? ld_state4<COH>(src + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[4 * u] = x.x;
+                v[4 * u + 1] = x.y;
+                v[4 * u + 2] = x.z;
+                v[4 * u + 3] = x.w;
+            }
+#pragma unroll
+            for (int h8 = 0; h8 < 4; h8++) {
+                const int kk0 = kb + 8 * h8;
+                if (kk0 < Lo.KP16) {
+                    uint32_t hi[4], lo[4];
+#pragma unroll
+                    for (int t = 0; t < 4; t++) {
+                        const float x0 = v[8 * h8 + 2 * t], x1 = v[8 * h8 + 2 * t + 1];
+                        hi[t] = pack_bf16x2(x0, x1);
+                        const float r0 = x0 - __uint_as_float(hi[t] << 16);
+                        const float r1 = x1 - __uint_as_float(hi[t] & 0xFFFF0000u);
+                        lo[t] = pack_bf16x2(r0, r1);
+                    }
+#pragma unroll
+                    for (int seg = 0; seg < 3; seg++) {
+                        // A segments: hi, lo, hi;  B segments: hi, hi, lo
+                        const bool use_lo = isL ? seg == 1 : seg == 2;
+                        const int kc = seg * Lo.KP16 + kk0;
+                        uint8_t* dst = op + (kc >> 6) * ATOM + sw128_off(r, (kc & 63) * 2);
+                        if (use_lo)
+                            st_shared_v4(dst, lo[0], lo[1], lo[2], lo[3]);
+                        else
+                            st_shared_v4(dst, hi[0], hi[1], hi[2], hi[3]);
+                    }
+                }
+            }
+        }
+    } else {
+        // value and square of each multiplier column; K index of the contraction = r
+        const int NF = isL ? Lo.NC : Lo.NR;
+        const int nf = isL ? a.fc : a.fr;
+        uint8_t* o1 = sm + (isL ? Lo.off_lf : Lo.off_rf);
+        uint8_t* o2 = sm + (isL ? Lo.off_lf2 : Lo.off_rf2);
+        const uint32_t atom = (uint32_t)NF * 128u;
+        for (int c0 = 0; c0 < NF; c0 += 16) {
+            float v[16];
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+                const int c = c0 + u;
+                const int col = isL ? (c < a.p ? 1 + c : 1 + a.q + c) : 1 + a.p + c;
+                v[u] = (ok && c < nf) ? ld_state<COH>(src + col) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+                const uint32_t off = (r >> 6) * atom + sw128_off(c0 + u, (r & 63) * 2);
+                *(__nv_bfloat16*)(o1 + off) = __float2bfloat16_rn(v[u]);
+                *(__nv_bfloat16*)(o2 + off) = __float2bfloat16_rn(v[u] * v[u]);
+            }
+        }
+    }
+}
+
+// Thread 0: eta = [L_hi|L_lo|L_hi] [R_hi|R_hi|R_lo]' into TMEM columns [0, 128).
+__device__ __forceinline__ void issue_eta(const TcLayout& Lo, uint8_t* sm, uint32_t tb, uint64_t* bar) {
+    const uint8_t* Aop = sm + Lo.off_u;
+    const uint8_t* Bop = Aop + Lo.KA * ATOM;
+    const uint32_t id = idesc_bf16(TT, TT, 0, 0);
+    const int nks = 3 * Lo.KP16 / 16;
+    for (int ks = 0; ks < nks; ks++) {
+        const uint32_t off = (uint32_t)(ks >> 2) * ATOM + (uint32_t)(ks & 3) * 32u;
+        umma_bf16(tb, sdesc(smem_u32(Aop) + off, 16, 1024, SWIZZLE_128B),
+                  sdesc(smem_u32(Bop) + off, 16, 1024, SWIZZLE_128B), id, ks > 0);
+    }
+    umma_commit(bar);
+}
+
+// Epilogue: warp (q, cq) owns rows 32q.. and columns 32cq..32cq+31 of the tile;
+// Ddot and Dddot go as BF16 into one swizzled tile over the dead eta operands.
+template <bool Y16, int EPI>
+__device__ __forceinline__ void epilogue(const StepArgs& a, const TcLayout& Lo, uint8_t* sm, uint32_t tb, int64_t row0,
+                                         int64_t col0, int nr, int nc, float alpha, float& s1, float& s2) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool nb = EPI == EPI_ANY ? a.family == GMF_NEGBIN : EPI == EPI_NB;
+    const bool moments = EPI == EPI_ANY && nb && a.alpha_mode == 1;
+    const uint8_t* Ys = sm;
+    uint8_t* Dd = sm + Lo.off_u;
+    uint8_t* DDd = Dd + 2 * ATOM;
+    const int q = warp & 3, cq = warp >> 2;
+    const int i = 32 * q + lane;
+    const bool row_ok = i < nr;
+    const float* Wrow = (EPI == EPI_ANY && a.W) ? a.W + (row0 + i) * a.m + col0 : nullptr;
+    const int jc = 32 * cq;
+    uint32_t ev[32];
+    tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)jc, ev);
+    tmem_wait_ld();
+#pragma unroll
+    for (int gq = 0; gq < 4; gq++) {
+        const int j0 = jc + 8 * gq;
+        float y[8];
+        if (Y16) {
+            const uint4 u = *(const uint4*)(Ys + (j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2));
+            const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                y[2 * t] = (float)(uu[t] & 0xFFFFu);
+                y[2 * t + 1] = (float)(uu[t] >> 16);
+            }
+        } else {
+            const uint32_t byte = (uint32_t)(j0 & 31) * 4u;
+            const int4 u0 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte));
+            const int4 u1 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte + 16));
+            y[0] = (float)u0.x; y[1] = (float)u0.y; y[2] = (float)u0.z; y[3] = (float)u0.w;
+            y[4] = (float)u1.x; y[5] = (float)u1.y; y[6] = (float)u1.z; y[7] = (float)u1.w;
+        }
+        float dd[8], ddd[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            const int j = j0 + t;
+            const bool valid = row_ok && j < nc;
+            const float wv = (Wrow && valid) ? __ldg(Wrow + j) : 1.f;
+            const float e = fminf(fmaxf(__uint_as_float(ev[8 * gq + t]), -a.clamp), a.clamp);
+            const float mu = __expf(e);
+            const float f = nb ? __fdividef(alpha, alpha + mu) : 1.f;
+            const float wf = valid ? wv * f : 0.f;
+            dd[t] = wf * (y[t] - mu);
+            ddd[t] = wf * mu;
+            if (moments && valid) {
+                s1 = fmaf(wv * mu, mu, s1);
+                s2 += wv * ((y[t] - mu) * (y[t] - mu) - mu);
+            }
+        }
+        const uint32_t off = (uint32_t)(j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2);
+        st_shared_v4(Dd + off, pack_bf16x2(dd[0], dd[1]), pack_bf16x2(dd[2], dd[3]), pack_bf16x2(dd[4], dd[5]),
+                     pack_bf16x2(dd[6], dd[7]));
+        st_shared_v4(DDd + off, pack_bf16x2(ddd[0], ddd[1]), pack_bf16x2(ddd[2], ddd[3]), pack_bf16x2(ddd[4], ddd[5]),
+                     pack_bf16x2(ddd[6], ddd[7]));
+    }
+}
+
+// Thread 0: Ddot R_f, Dddot R_f^2 (row side) and Ddot' L_f, Dddot' L_f^2 (column side).
+__device__ __forceinline__ void issue_contractions(const TcLayout& Lo, uint8_t* sm, uint32_t tb, uint64_t* bar) {
+    const uint8_t* Dd = sm + Lo.off_u;
+    const uint8_t* DDd = Dd + 2 * ATOM;
+    const uint8_t* RF = sm + Lo.off_rf;
+    const uint8_t* RF2 = sm + Lo.off_rf2;
+    const uint8_t* LF = sm + Lo.off_lf;
+    const uint8_t* LF2 = sm + Lo.off_lf2;
+    const uint32_t idr = idesc_bf16(TT, Lo.NR, 0, 0);
+    const uint32_t atr = (uint32_t)Lo.NR * 128u;
+    for (int ks = 0; ks < TT / 16; ks++) {
+        const uint32_t aoff = (uint32_t)(ks >> 2) * ATOM + (uint32_t)(ks & 3) * 32u;
+        const uint32_t boff = (uint32_t)(ks >> 2) * atr + (uint32_t)(ks & 3) * 32u;
+        umma_bf16(tb + Lo.t_row, sdesc(smem_u32(Dd) + aoff, 16, 1024, SWIZZLE_128B),
+                  sdesc(smem_u32(RF) + boff, 16, 1024, SWIZZLE_128B), idr, ks > 0);
+        umma_bf16(tb + Lo.t_row + Lo.NR, sdesc(smem_u32(DDd) + aoff, 16, 1024, SWIZZLE_128B),
+                  sdesc(smem_u32(RF2) + boff, 16, 1024, SWIZZLE_128B), idr, ks > 0);
+    }
+    const uint32_t idc = idesc_bf16(TT, Lo.NC, 1, 0);
+    const uint32_t atc = (uint32_t)Lo.NC * 128u;
+    for (int ks = 0; ks < TT / 16; ks++) {
+        const uint32_t aoff = (uint32_t)ks * 2048u;  // 16 tile rows = two 8-row groups
+        const uint32_t boff = (uint32_t)(ks >> 2) * atc + (uint32_t)(ks & 3) * 32u;
+        umma_bf16(tb + Lo.t_col, sdesc(smem_u32(Dd) + aoff, ATOM, 1024, SWIZZLE_128B),
+                  sdesc(smem_u32(LF) + boff, 16, 1024, SWIZZLE_128B), idc, ks > 0);
+        umma_bf16(tb + Lo.t_col + Lo.NC, sdesc(smem_u32(DDd) + aoff, ATOM, 1024, SWIZZLE_128B),
+                  sdesc(smem_u32(LF2) + boff, 16, 1024, SWIZZLE_128B), idc, ks > 0);
+    }
+    umma_commit(bar);
+}
+
+// Warps 0-3 read the row sums, warps 4-7 the column sums, from TMEM into the
+// per-tile partial slots (global memory), or in cluster mode into the owners'
+// slots (distributed shared memory).
+template <bool CL>
+__device__ __forceinline__ void store_partials(const StepArgs& a, const TcLayout& Lo, uint8_t* sm, uint32_t tb, int k,
+                                               int ti, int tj, int nr, int nc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= 8) return;
+    const int q = warp & 3;
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    const int o = 32 * q + lane;   // tile row (warps 0-3) or tile column (warps 4-7)
+    const bool rowside = warp < 4;
+    const int NF = rowside ? Lo.NR : Lo.NC;
+    const int nf = rowside ? a.fr : a.fc;
+    const uint32_t tg = tb + lanes + (rowside ? Lo.t_row : Lo.t_col);
+    float* dst = rowside ? a.partR + (size_t)((k * a.TI + ti) * a.TJ + tj) * TT * 2 * a.fr
+                         : a.partC + (size_t)((k * a.TJ + tj) * a.TI + ti) * TT * 2 * a.fc;
+    // cluster mode: slot `src` of the owner of row (column) o, at index o - own * SR
+    const int SR = rowside ? Lo.SRr : Lo.SCc;
+    const int own = CL ? o / SR : 0, ol = o - own * SR, src = rowside ? tj : ti;
+    const uint32_t slots = CL ? mapa_shared(smem_u32(sm + Lo.off_cp) +
+                                                (rowside ? 0u : (uint32_t)(4 * a.TJ * 2 * a.fr * Lo.SRr)),
+                                            rowside ? (uint32_t)(own + ti * a.TJ) : (uint32_t)(tj + own * a.TJ))
+                              : 0u;
+    const bool o_ok = o < (rowside ? nr : nc);
+    for (int c0 = 0; c0 < NF; c0 += 16) {
+        uint32_t rg[16], rh[16];
+        tmem_ld16(tg + (uint32_t)c0, rg);
+        tmem_ld16(tg + (uint32_t)(NF + c0), rh);
+        tmem_wait_ld();
+        if (o_ok) {
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+                const int c = c0 + u;
+                if (c < nf) {
+                    if (CL) {
+                        st_dsmem_f32(slots + 4u * (uint32_t)((src * 2 * nf + c) * SR + ol), __uint_as_float(rg[u]));
+                        st_dsmem_f32(slots + 4u * (uint32_t)((src * 2 * nf + nf + c) * SR + ol),
+                                     __uint_as_float(rh[u]));
+                    } else {
+                        dst[(size_t)c * TT + o] = __uint_as_float(rg[u]);
+                        dst[(size_t)(nf + c) * TT + o] = __uint_as_float(rh[u]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// One tile (blockIdx.x, blockIdx.y) of block k of sweep w for the model whose
+// arguments are a / Lo. CL: cluster mode (the strip updates run here).
 template <bool Y16, bool CL, int EPI>
 __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, const CUtensorMap* ymap_p, int w,
                                         int k, uint8_t* smraw) {
     __shared__ uint64_t bars[3];
     __shared__ uint32_t tmem_base;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int tj = blockIdx.x, ti = blockIdx.y;
     const BlockGeo g = block_geo(a, w, k);
     const int nTI = (int)((g.nI + TT - 1) / TT), nTJ = (int)((g.mJ + TT - 1) / TT);
     const bool active = ti < nTI && tj < nTJ;
-    const bool nb = EPI == EPI_ANY ? a.family == GMF_NEGBIN : EPI == EPI_NB;
-    const bool moments = EPI == EPI_ANY && nb && a.alpha_mode == 1;
-    float alpha = 0.f;
     float s1 = 0.f, s2 = 0.f;
 
     uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
@@ -239,15 +514,6 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
         cluster_arrive_relaxed();  // waited for before the first store into a peer (all peers have started)
     }
     if (active) {
-        uint8_t* Ys = sm;
-        uint8_t* Aop = sm + Lo.off_u;
-        uint8_t* Bop = Aop + Lo.KA * ATOM;
-        uint8_t* Dd = sm + Lo.off_u;   // overlays the eta operands once the eta MMA has completed
-        uint8_t* DDd = Dd + 2 * ATOM;
-        uint8_t* RF = sm + Lo.off_rf;
-        uint8_t* RF2 = sm + Lo.off_rf2;
-        uint8_t* LF = sm + Lo.off_lf;
-        uint8_t* LF2 = sm + Lo.off_lf2;
         const int64_t row0 = g.r0 + (int64_t)ti * TT, col0 = g.c0 + (int64_t)tj * TT;
         const int nr = (int)min((int64_t)TT, g.nI - (int64_t)ti * TT);
         const int nc = (int)min((int64_t)TT, g.mJ - (int64_t)tj * TT);
@@ -264,239 +530,40 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
         tc_fence_after();
         const uint32_t tb = tmem_base;
 
-        if (tid == 0) {
-            mbar_arrive_expect_tx(&bars[0], Lo.y_bytes);
-            const int nbox = TT / Lo.JB;
-            for (int b = 0; b < nbox; b++)
-                tma_load_2d(Ys + b * ATOM, ymap_p, (int)(col0 + (int64_t)b * Lo.JB), (int)row0, &bars[0]);
-        }
+        if (tid == 0) issue_counts(Lo, ymap_p, sm, row0, col0, &bars[0]);
         // the counts are read-only; everything below reads or writes model state
         // that the previous sweep's update launch may still be writing. The
         // next launch (this sweep's update) may start once every CTA is here,
         // i.e. once the previous update has completed.
         grid_dependency_wait();
         grid_launch_dependents();
-        alpha = *a.alpha;
+        const float alpha = *a.alpha;
 
-        // ---- operands. Thread groups of 128: L rows -> eta A; R rows -> eta B;
-        //      L rows -> column-side B ([X, U] and squares); R rows -> row-side B ([Z, V] and squares).
-        {
-            const int grp = tid >> 7, r = tid & (TT - 1);
-            const bool isL = (grp & 1) == 0;
-            const bool ok = isL ? r < nr : r < nc;
-            const float* src = isL ? a.L + (row0 + r) * a.KP : a.R + (col0 + r) * a.KP;
-            if (grp < 2) {
-                uint8_t* op = isL ? Aop : Bop;
-                for (int kb = 0; kb < Lo.KP16; kb += 32) {
-                    float v[32];
-#pragma unroll
-                    for (int u = 0; u < 8; u++) {
-                        const int kk = kb + 4 * u;
-                        const float4 x = (ok && kk < a.KP) ? __ldg((const float4*)(src + kk))
-                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
-                        v[4 * u] = x.x;
-                        v[4 * u + 1] = x.y;
-                        v[4 * u + 2] = x.z;
-                        v[4 * u + 3] = x.w;
-                    }
-#pragma unroll
-                    for (int h8 = 0; h8 < 4; h8++) {
-                        const int kk0 = kb + 8 * h8;
-                        if (kk0 < Lo.KP16) {
-                            uint32_t hi[4], lo[4];
-#pragma unroll
-                            for (int t = 0; t < 4; t++) {
-                                const float x0 = v[8 * h8 + 2 * t], x1 = v[8 * h8 + 2 * t + 1];
-                                hi[t] = pack_bf16x2(x0, x1);
-                                const float r0 = x0 - __uint_as_float(hi[t] << 16);
-                                const float r1 = x1 - __uint_as_float(hi[t] & 0xFFFF0000u);
-                                lo[t] = pack_bf16x2(r0, r1);
-                            }
-#pragma unroll
-                            for (int seg = 0; seg < 3; seg++) {
-                                // A segments: hi, lo, hi;  B segments: hi, hi, lo
-                                const bool use_lo = isL ? seg == 1 : seg == 2;
-                                const int kc = seg * Lo.KP16 + kk0;
-                                uint8_t* dst = op + (kc >> 6) * ATOM + sw128_off(r, (kc & 63) * 2);
-                                if (use_lo)
-                                    st_shared_v4(dst, lo[0], lo[1], lo[2], lo[3]);
-                                else
-                                    st_shared_v4(dst, hi[0], hi[1], hi[2], hi[3]);
-                            }
-                        }
-                    }
-                }
-            } else {
-                // value and square of each multiplier column; K index of the contraction = r
-                const int NF = isL ? Lo.NC : Lo.NR;
-                const int nf = isL ? a.fc : a.fr;
-                uint8_t* o1 = isL ? LF : RF;
-                uint8_t* o2 = isL ? LF2 : RF2;
-                const uint32_t atom = (uint32_t)NF * 128u;
-                for (int c0 = 0; c0 < NF; c0 += 16) {
-                    float v[16];
-#pragma unroll
-                    for (int u = 0; u < 16; u++) {
-                        const int c = c0 + u;
-                        const int col = isL ? (c < a.p ? 1 + c : 1 + a.q + c) : 1 + a.p + c;
-                        v[u] = (ok && c < nf) ? __ldg(src + col) : 0.f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 16; u++) {
-                        const uint32_t off = (r >> 6) * atom + sw128_off(c0 + u, (r & 63) * 2);
-                        *(__nv_bfloat16*)(o1 + off) = __float2bfloat16_rn(v[u]);
-                        *(__nv_bfloat16*)(o2 + off) = __float2bfloat16_rn(v[u] * v[u]);
-                    }
-                }
-            }
-        }
+        build_operands<false>(a, Lo, sm, row0, col0, nr, nc);
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
 
-        if (tid == 0) {
-            const uint32_t id = idesc_bf16(TT, TT, 0, 0);
-            const int nks = 3 * Lo.KP16 / 16;
-            for (int ks = 0; ks < nks; ks++) {
-                const uint32_t off = (uint32_t)(ks >> 2) * ATOM + (uint32_t)(ks & 3) * 32u;
-                umma_bf16(tb, sdesc(smem_u32(Aop) + off, 16, 1024, SWIZZLE_128B),
-                          sdesc(smem_u32(Bop) + off, 16, 1024, SWIZZLE_128B), id, ks > 0);
-            }
-            umma_commit(&bars[1]);
-        }
+        if (tid == 0) issue_eta(Lo, sm, tb, &bars[1]);
         bool ok = cta_wait(&bars[0], 0, a.err);
         ok = cta_wait(&bars[1], 0, a.err) && ok;
         tc_fence_after();
 
-        if (ok) {
-            // ---- epilogue: warp (q, cq) owns rows 32q.. and columns 32cq..32cq+31
-            const int q = warp & 3, cq = warp >> 2;
-            const int i = 32 * q + lane;
-            const bool row_ok = i < nr;
-            const float* Wrow = (EPI == EPI_ANY && a.W) ? a.W + (row0 + i) * a.m + col0 : nullptr;
-            const int jc = 32 * cq;
-            uint32_t ev[32];
-            tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)jc, ev);
-            tmem_wait_ld();
-#pragma unroll
-            for (int gq = 0; gq < 4; gq++) {
-                const int j0 = jc + 8 * gq;
-                float y[8];
-                if (Y16) {
-                    const uint4 u = *(const uint4*)(Ys + (j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2));
-                    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                    for (int t = 0; t < 4; t++) {
-                        y[2 * t] = (float)(uu[t] & 0xFFFFu);
-                        y[2 * t + 1] = (float)(uu[t] >> 16);
-                    }
-                } else {
-                    const uint32_t byte = (uint32_t)(j0 & 31) * 4u;
-                    const int4 u0 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte));
-                    const int4 u1 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte + 16));
-                    y[0] = (float)u0.x; y[1] = (float)u0.y; y[2] = (float)u0.z; y[3] = (float)u0.w;
-                    y[4] = (float)u1.x; y[5] = (float)u1.y; y[6] = (float)u1.z; y[7] = (float)u1.w;
-                }
-                float dd[8], ddd[8];
-#pragma unroll
-                for (int t = 0; t < 8; t++) {
-                    const int j = j0 + t;
-                    const bool valid = row_ok && j < nc;
-                    const float wv = (Wrow && valid) ? __ldg(Wrow + j) : 1.f;
-                    const float e = fminf(fmaxf(__uint_as_float(ev[8 * gq + t]), -a.clamp), a.clamp);
-                    const float mu = __expf(e);
-                    const float f = nb ? __fdividef(alpha, alpha + mu) : 1.f;
-                    const float wf = valid ? wv * f : 0.f;
-                    dd[t] = wf * (y[t] - mu);
-                    ddd[t] = wf * mu;
-                    if (moments && valid) {
-                        s1 = fmaf(wv * mu, mu, s1);
-                        s2 += wv * ((y[t] - mu) * (y[t] - mu) - mu);
-                    }
-                }
-                const uint32_t off = (uint32_t)(j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2);
-                st_shared_v4(Dd + off, pack_bf16x2(dd[0], dd[1]), pack_bf16x2(dd[2], dd[3]),
-                             pack_bf16x2(dd[4], dd[5]), pack_bf16x2(dd[6], dd[7]));
-                st_shared_v4(DDd + off, pack_bf16x2(ddd[0], ddd[1]), pack_bf16x2(ddd[2], ddd[3]),
-                             pack_bf16x2(ddd[4], ddd[5]), pack_bf16x2(ddd[6], ddd[7]));
-            }
-        }
+        if (ok) epilogue<Y16, EPI>(a, Lo, sm, tb, row0, col0, nr, nc, alpha, s1, s2);
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
 
-        if (ok && tid == 0) {
-            const uint32_t idr = idesc_bf16(TT, Lo.NR, 0, 0);
-            const uint32_t atr = (uint32_t)Lo.NR * 128u;
-            for (int ks = 0; ks < TT / 16; ks++) {
-                const uint32_t aoff = (uint32_t)(ks >> 2) * ATOM + (uint32_t)(ks & 3) * 32u;
-                const uint32_t boff = (uint32_t)(ks >> 2) * atr + (uint32_t)(ks & 3) * 32u;
-                umma_bf16(tb + Lo.t_row, sdesc(smem_u32(Dd) + aoff, 16, 1024, SWIZZLE_128B),
-                          sdesc(smem_u32(RF) + boff, 16, 1024, SWIZZLE_128B), idr, ks > 0);
-                umma_bf16(tb + Lo.t_row + Lo.NR, sdesc(smem_u32(DDd) + aoff, 16, 1024, SWIZZLE_128B),
-                          sdesc(smem_u32(RF2) + boff, 16, 1024, SWIZZLE_128B), idr, ks > 0);
-            }
-            const uint32_t idc = idesc_bf16(TT, Lo.NC, 1, 0);
-            const uint32_t atc = (uint32_t)Lo.NC * 128u;
-            for (int ks = 0; ks < TT / 16; ks++) {
-                const uint32_t aoff = (uint32_t)ks * 2048u;  // 16 tile rows = two 8-row groups
-                const uint32_t boff = (uint32_t)(ks >> 2) * atc + (uint32_t)(ks & 3) * 32u;
-                umma_bf16(tb + Lo.t_col, sdesc(smem_u32(Dd) + aoff, ATOM, 1024, SWIZZLE_128B),
-                          sdesc(smem_u32(LF) + boff, 16, 1024, SWIZZLE_128B), idc, ks > 0);
-                umma_bf16(tb + Lo.t_col + Lo.NC, sdesc(smem_u32(DDd) + aoff, ATOM, 1024, SWIZZLE_128B),
-                          sdesc(smem_u32(LF2) + boff, 16, 1024, SWIZZLE_128B), idc, ks > 0);
-            }
-            umma_commit(&bars[2]);
-        }
+        if (ok && tid == 0) issue_contractions(Lo, sm, tb, &bars[2]);
         // warps 8-15 have no partials to read: they start the update slices' copies
         if (CL) cl_stage_issue(a, Lo, sm, cls, NTH / 2, NTH / 2);
         if (ok) ok = cta_wait(&bars[2], 0, a.err);
         tc_fence_after();
         if (CL) cluster_wait();
 
-        if (ok && warp < 8) {
-            const int q = warp & 3;
-            const uint32_t lanes = (uint32_t)(32 * q) << 16;
-            const int o = 32 * q + lane;   // tile row (warps 0-3) or tile column (warps 4-7)
-            const bool rowside = warp < 4;
-            const int NF = rowside ? Lo.NR : Lo.NC;
-            const int nf = rowside ? a.fr : a.fc;
-            const uint32_t tg = tb + lanes + (rowside ? Lo.t_row : Lo.t_col);
-            float* dst = rowside ? a.partR + (size_t)((k * a.TI + ti) * a.TJ + tj) * TT * 2 * a.fr
-                                 : a.partC + (size_t)((k * a.TJ + tj) * a.TI + ti) * TT * 2 * a.fc;
-            // cluster mode: slot `src` of the owner of row (column) o, at index o - own * SR
-            const int SR = rowside ? Lo.SRr : Lo.SCc;
-            const int own = CL ? o / SR : 0, ol = o - own * SR, src = rowside ? tj : ti;
-            const uint32_t slots = CL ? mapa_shared(smem_u32(sm + Lo.off_cp) +
-                                                        (rowside ? 0u : (uint32_t)(4 * a.TJ * 2 * a.fr * Lo.SRr)),
-                                                    rowside ? (uint32_t)(own + ti * a.TJ) : (uint32_t)(tj + own * a.TJ))
-                                      : 0u;
-            const bool o_ok = o < (rowside ? nr : nc);
-            for (int c0 = 0; c0 < NF; c0 += 16) {
-                uint32_t rg[16], rh[16];
-                tmem_ld16(tg + (uint32_t)c0, rg);
-                tmem_ld16(tg + (uint32_t)(NF + c0), rh);
-                tmem_wait_ld();
-                if (o_ok) {
-#pragma unroll
-                    for (int u = 0; u < 16; u++) {
-                        const int c = c0 + u;
-                        if (c < nf) {
-                            if (CL) {
-                                st_dsmem_f32(slots + 4u * (uint32_t)((src * 2 * nf + c) * SR + ol), __uint_as_float(rg[u]));
-                                st_dsmem_f32(slots + 4u * (uint32_t)((src * 2 * nf + nf + c) * SR + ol),
-                                             __uint_as_float(rh[u]));
-                            } else {
-                                dst[(size_t)c * TT + o] = __uint_as_float(rg[u]);
-                                dst[(size_t)(nf + c) * TT + o] = __uint_as_float(rh[u]);
-                            }
-                        }
-                    }
-                }
-            }
-        }
+        if (ok) store_partials<CL>(a, Lo, sm, tb, k, ti, tj, nr, nc);
         if (!ok && tid == 0) atomicOr(a.err, GMF_DEVERR_TIMEOUT);
         tc_fence_before();
         __syncthreads();
@@ -528,6 +595,200 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
     }
 }
 
+// ---- persistent epoch (cluster mode). One launch runs the sweeps [w0, w1);
+// cluster k takes block k of every sweep. The block's fixed strip (column
+// strip k; row strip k when the roles swap) belongs to cluster k alone: its
+// slices' smoothed derivatives and visit counts stay in shared memory for the
+// whole launch (written back after the last block), its parameter rows go
+// back after every block for the peers' next operands, ordered by the cluster
+// barrier. Only the moving strip passes between clusters. Every CTA adds one
+// to the moving strip's completion count after its write-back (a release
+// reduction; skipped after the launch's last block, which nothing later
+// reads); block k of sweep w waits (acquire) until the count of its moving
+// strip reaches need[w][k] -- the visits of that strip by the earlier sweeps
+// of the launch -- times the cluster size. Every wait therefore points to an earlier sweep, and since all
+// clusters are resident at once (checked with the occupancy query before this
+// mode is chosen) they cannot wait in a cycle. An acquiring look one block
+// ahead, while the contractions run, usually finds the next strip ready. State
+// written during the launch is read through L2 only. The next block's count
+// tile is loaded while the current block finishes. Results equal the
+// per-sweep launches bit for bit (same phases, same sums in the same order).
+constexpr uint64_t WAIT_NS = 2000000000ull;  // limit of one strip wait
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+
+// One thread: spin until *cnt >= target. Gives up, flagging a time-out, after
+// WAIT_NS or as soon as another CTA has flagged one.
+__device__ __forceinline__ void wait_count(const unsigned* cnt, unsigned target, unsigned* err) {
+    if (ld_acquire_u32(cnt) >= target) return;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (ld_acquire_u32(cnt) >= target) return;
+        if (*(volatile unsigned*)err & GMF_DEVERR_TIMEOUT) return;
+        if (global_ns() - t0 > WAIT_NS) {
+            atomicOr(err, GMF_DEVERR_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// Block k of a sweep whose offset sigma[w] is sg (block_geo without the load).
+__device__ __forceinline__ BlockGeo block_geo_sg(const StepArgs& a, int sg, int k) {
+    int rc, cc;
+    if (!a.swap) {
+        rc = (sg + k) % a.r;
+        cc = k;
+    } else {
+        rc = k;
+        cc = (sg + k) % a.s;
+    }
+    BlockGeo g;
+    g.r0 = (int64_t)rc * a.nb_row;
+    g.nI = min((int64_t)a.nb_row, a.n - g.r0);
+    g.c0 = (int64_t)cc * a.nb_col;
+    g.mJ = min((int64_t)a.nb_col, a.m - g.c0);
+    return g;
+}
+
+template <bool Y16, int EPI>
+__global__ void __launch_bounds__(NTH, 1)
+    sweep_tc_epoch(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w0, int w1) {
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    __shared__ uint64_t bars[3];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tj = blockIdx.x, ti = blockIdx.y, k = blockIdx.z;
+    uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+    const bool fix_r = a.swap != 0, fix_c = a.swap == 0;  // the side of the fixed strip
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, Lo.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tb = tmem_base;
+    const float alpha = *a.alpha;  // the shape is not re-estimated inside this launch
+    float s1 = 0.f, s2 = 0.f;      // (no moment sums in this mode)
+    uint32_t ph = 0;               // parity of the mbarrier phases of the next active block
+    bool dead = false;             // a bounded wait of this CTA timed out: no further copies or MMAs
+    bool y_next = false;           // the count tile of the next block is already requested
+    const unsigned ncta = (unsigned)(a.TI * a.TJ);
+    __shared__ int s_ready;        // a block whose moving strip an early look found written back
+    if (tid == 0) s_ready = -1;    // (ordered before its first read by the barrier at the top)
+    // schedule of the current block; the next block's is loaded one block ahead
+    int sg = a.sigma[w0];
+    float rhoc_blk = a.rhoc[w0 * a.per + k];
+    unsigned need = (unsigned)a.need[w0 * a.per + k];
+
+    cluster_arrive_relaxed();  // matched by the wait at the top of the first sweep
+    for (int w = w0; w < w1; w++) {
+        const BlockGeo g = block_geo_sg(a, sg, k);
+        const int nTI = (int)((g.nI + TT - 1) / TT), nTJ = (int)((g.mJ + TT - 1) / TT);
+        const bool active = ti < nTI && tj < nTJ && !dead;
+        const int64_t row0 = g.r0 + (int64_t)ti * TT, col0 = g.c0 + (int64_t)tj * TT;
+        if (active && !y_next && tid == 0) issue_counts(Lo, &ymap, sm, row0, col0, &bars[0]);
+        y_next = false;
+        const ClSlice cls = cl_slice(a, Lo, g, ti, tj, nTI, nTJ);
+        const int strip = a.swap ? (int)(g.c0 / a.nb_col) : (int)(g.r0 / a.nb_row);
+        cluster_wait();  // the peers finished the previous block: fixed strip written, slots free
+        if (tid == 0 && s_ready != w) wait_count(a.strip_done + strip, need * ncta, a.err);
+        __syncthreads();
+        tc_fence_after();
+        const int wn = min(w + 1, w1 - 1);  // (the last block loads its own values again)
+        const int sg_next = a.sigma[wn];
+        const float rhoc_next = a.rhoc[wn * a.per + k];
+        const unsigned need_next = (unsigned)a.need[wn * a.per + k];
+
+        if (active) {
+            const int nr = (int)min((int64_t)TT, g.nI - (int64_t)ti * TT);
+            const int nc = (int)min((int64_t)TT, g.mJ - (int64_t)tj * TT);
+            build_operands<true>(a, Lo, sm, row0, col0, nr, nc);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+
+            if (tid == 0) issue_eta(Lo, sm, tb, &bars[1]);
+            bool ok = cta_wait(&bars[0], ph, a.err);
+            ok = cta_wait(&bars[1], ph, a.err) && ok;
+            tc_fence_after();
+
+            if (ok) epilogue<Y16, EPI>(a, Lo, sm, tb, row0, col0, nr, nc, alpha, s1, s2);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+
+            if (ok && tid == 0) issue_contractions(Lo, sm, tb, &bars[2]);
+            if (ok && w + 1 < w1) {  // the count tile is no longer read: request the next block's
+                const BlockGeo gn = block_geo_sg(a, sg_next, k);
+                if (ti * TT < gn.nI && tj * TT < gn.mJ) {
+                    if (tid == 0)
+                        issue_counts(Lo, &ymap, sm, gn.r0 + (int64_t)ti * TT, gn.c0 + (int64_t)tj * TT, &bars[0]);
+                    y_next = true;
+                }
+            }
+            cl_stage_issue(a, Lo, sm, cls, NTH / 2, NTH / 2, !fix_r || w == w0, !fix_c || w == w0);
+            if (tid == 32 && w + 1 < w1) {
+                // an early look (acquire) at the next block's moving strip by an idle warp
+                // while the contractions run; when it is written back, the next block
+                // does not poll (the barriers in between order the look before its reads)
+                const BlockGeo gn = block_geo_sg(a, sg_next, k);
+                const int sn = a.swap ? (int)(gn.c0 / a.nb_col) : (int)(gn.r0 / a.nb_row);
+                if (ld_acquire_u32(a.strip_done + sn) >= need_next * ncta) s_ready = w + 1;
+            }
+            if (ok) ok = cta_wait(&bars[2], ph, a.err);
+            tc_fence_after();
+            if (ok) store_partials<true>(a, Lo, sm, tb, k, ti, tj, nr, nc);
+            tc_fence_before();
+            if (!ok) {
+                if (tid == 0) atomicOr(a.err, GMF_DEVERR_TIMEOUT);
+                // a requested count tile is drained (bounded) before the CTA stops copying
+                if (y_next) mbar_wait(&bars[0], ph ^ 1u, WAIT_POLLS);
+                y_next = false;
+                dead = true;
+            }
+            ph ^= 1u;
+        } else {
+            cl_stage_issue(a, Lo, sm, cls, 0, NTH, !fix_r || w == w0, !fix_c || w == w0);
+        }
+        cl_update(a, Lo, sm, cls, g, rhoc_blk, nTI, nTJ, !fix_r || w == w1 - 1, !fix_c || w == w1 - 1);
+        __syncthreads();
+        // publish this CTA's rows of the moving strip (release, cumulative over the
+        // CTA through the barrier above) while the cluster barrier's release drains
+        if (tid == 32 && w + 1 < w1) red_release_add_u32(a.strip_done + strip, 1u);
+        cluster_arrive_release();  // this CTA's slices are written back and its partial slots free
+        sg = sg_next;
+        rhoc_blk = rhoc_next;
+        need = need_next;
+    }
+    cluster_wait();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tb, Lo.tmem_cols);
+}
+
 template <bool Y16, int EPI>
 __global__ void __launch_bounds__(NTH, 1)
     sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
@@ -553,6 +814,14 @@ const void* tc_fn(int y16, int cl, int epi) {
     return epi == EPI_NB ? tc_fn_epi<EPI_NB>(y16, cl) : epi == EPI_PO ? tc_fn_epi<EPI_PO>(y16, cl)
                                                                       : tc_fn_epi<EPI_ANY>(y16, cl);
 }
+template <int EPI>
+const void* tc_epoch_fn_epi(int y16) {
+    return y16 ? (const void*)sweep_tc_epoch<true, EPI> : (const void*)sweep_tc_epoch<false, EPI>;
+}
+const void* tc_epoch_fn(int y16, int epi) {
+    return epi == EPI_NB ? tc_epoch_fn_epi<EPI_NB>(y16) : epi == EPI_PO ? tc_epoch_fn_epi<EPI_PO>(y16)
+                                                                        : tc_epoch_fn_epi<EPI_ANY>(y16);
+}
 
 // Several models (ranks) sharing the count matrix and the partitions: blockIdx.z
 // = slot * per + k, slot -> model through `order` (heaviest models first).
@@ -573,6 +842,7 @@ __global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restr
 }
 
 int tc_cluster_layout(gmf_model* h, TcState* tc);
+int tc_persist_check(gmf_model* h, TcState* tc);
 
 int fail_str(std::string* err, const char* msg) {
     if (err) *err = msg;
@@ -655,12 +925,45 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
     tc->TI = (int)((std::min<int64_t>(h->cfg.nb_row, h->n) + TT - 1) / TT);
     tc->TJ = (int)((std::min<int64_t>(h->cfg.nb_col, h->m) + TT - 1) / TT);
     tc->cluster = 0;
+    tc->persist = 0;
     if (!(h->cfg.flags & GMF_FLAG_NO_CLUSTER) && tc->TI * tc->TJ <= 16) tc->cluster = tc_cluster_layout(h, tc);
+    if (tc->cluster && (h->cfg.flags & GMF_FLAG_PERSIST)) tc->persist = tc_persist_check(h, tc);
     h->tc = tc;
     return GMF_OK;
 }
 
 namespace {
+
+// Shared-memory and cluster-size attributes of a cluster kernel, and whether
+// all clusters of one sweep can be resident at once.
+int cluster_fits(gmf_model* h, TcState* tc, const void* fn, uint32_t smem) {
+    const int TI = tc->TI, TJ = tc->TJ;
+    if (gmf_smem_limit(fn, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (TI * TJ > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(TJ, TI, h->per);
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = TJ;
+    at[0].val.clusterDim.y = TI;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nclusters >= h->per ? 1 : 0;
+}
 
 // Cluster mode needs the partials and the update slices in shared memory next
 // to the tile, cluster dimensions (TJ, TI) within the device's limit, and room
@@ -675,32 +978,15 @@ int tc_cluster_layout(gmf_model* h, TcState* tc) {
     const uint32_t st_bytes = 4u * (uint32_t)(L.SRr * (h->KP + 1 + 2 * (h->fr | 1) + 1) +
                                               L.SCc * (h->KP + 1 + 2 * (h->fc | 1) + 1));
     L.smem_cl = L.off_st + st_bytes + 1024u;
-    const void* fn = tc_fn(h->y16, 1, tc->epi);
-    if (gmf_smem_limit(fn, L.smem_cl) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    if (TI * TJ > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(TJ, TI, h->per);
-    cfg.blockDim = dim3(NTH);
-    cfg.dynamicSmemBytes = L.smem_cl;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = TJ;
-    at[0].val.clusterDim.y = TI;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return nclusters >= h->per ? 1 : 0;
+    return cluster_fits(h, tc, tc_fn(h->y16, 1, tc->epi), L.smem_cl);
+}
+
+// The persistent epoch needs every cluster of a sweep resident at once (the
+// same occupancy test) and a fixed NB shape: the per-sweep shape estimate of
+// alpha_mode 1 pools all clusters of a sweep, which this launch never joins.
+int tc_persist_check(gmf_model* h, TcState* tc) {
+    if (h->cfg.family == GMF_NEGBIN && h->cfg.alpha_mode == 1) return 0;
+    return cluster_fits(h, tc, tc_epoch_fn(h->y16, tc->epi), tc->lay.smem_cl);
 }
 
 }  // namespace
@@ -751,6 +1037,33 @@ cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st) {
     a.TJ = tc->TJ;
     return gmf_launch_update(a, w, TT, st);
 }
+
+// The sweeps [w0, w1) as one persistent launch (sweep_tc_epoch): the strip
+// completion counts start from zero.
+cudaError_t gmf_tc_launch_epoch(gmf_model* h, int w0, int w1, cudaStream_t st) {
+    TcState* tc = (TcState*)h->tc;
+    cudaError_t e = cudaMemsetAsync(h->strip_done, 0, sizeof(unsigned) * (size_t)std::max(h->r, h->s), st);
+    if (e != cudaSuccess) return e;
+    StepArgs a = gmf_make_args(h);
+    a.TI = tc->TI;
+    a.TJ = tc->TJ;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tc->TJ, tc->TI, h->per);
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = tc->lay.smem_cl;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = tc->TJ;
+    at[0].val.clusterDim.y = tc->TI;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap, &w0, &w1};
+    return cudaLaunchKernelExC(&cfg, tc_epoch_fn(h->y16, tc->epi), args);
+}
+
+int gmf_tc_persistent(const gmf_model* h) { return h->tc && ((const TcState*)h->tc)->persist; }
 
 size_t gmf_tc_layout_size() { return sizeof(TcLayout); }
 const void* gmf_tc_layout(const gmf_model* h) { return &((const TcState*)h->tc)->lay; }

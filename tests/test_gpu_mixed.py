@@ -132,15 +132,17 @@ CLUSTER_CASES = {
                            dict(zero_frac=0.8, weights=True, alpha_mode=1, bias_corr=1)),
     "poisson_16_tiles_uint16": (2000, 1024, 2, 1, 10, "poisson", 500, 512, dict(y_dtype="uint16")),
     "nb_6_tiles": (300, 256, 2, 2, 3, "negbin", 300, 256, dict(zero_frac=0.6, alpha_mode=1)),
+    # fixed NB shape or Poisson: the epoch is one persistent launch
+    "nb_ragged_weights_fixed_shape": (1100, 704, 3, 1, 6, "negbin", 500, 384,
+                                      dict(zero_frac=0.8, weights=True, bias_corr=1)),
+    "poisson_uint16_roles_swapped": (600, 2048, 2, 2, 5, "poisson", 300, 512, dict(y_dtype="uint16")),
+    "nb_12_sweeps_16_tiles": (6000, 1024, 2, 1, 10, "negbin", 500, 512, dict(zero_frac=0.5)),
 }
 
+MODE_FLAGS = {"persistent": 2, "cluster": 0, "separate": 1}   # gmf.GMF_FLAG_PERSIST, gmf.GMF_FLAG_NO_CLUSTER
 
-@pytest.mark.parametrize("case", list(CLUSTER_CASES))
-def test_cluster_mode_equals_separate_update_launch(gmf, case):
-    """Where a block's tiles fit one thread-block cluster the strip updates run
-    inside the tile launch and read the partials from the peers' shared memory;
-    the sums follow the same tile order as the separate update launch, so the
-    two modes must agree to the bit."""
+
+def _fit_modes(gmf, case, epochs=3, split=None):
     n, m, p, q, d, fam, nbr, nbc, extra = CLUSTER_CASES[case]
     extra = dict(extra)
     y_dtype = extra.pop("y_dtype", "int32")
@@ -152,21 +154,77 @@ def test_cluster_mode_equals_separate_update_launch(gmf, case):
     settings = synth.fit_settings(**extra)
     W = torch.from_numpy(np.random.default_rng(10).uniform(0.5, 1.5, (n, m)).astype(np.float32)).cuda() \
         if weights else None
-    sig = synth.sweep_orders(n, m, nbr, nbc, 3, 3)
-    fits = []
-    for flags in (0, gmf.GMF_FLAG_NO_CLUSTER):
+    sig = synth.sweep_orders(n, m, nbr, nbc, epochs, 3)
+    fits = {}
+    for mode, flags in MODE_FLAGS.items():
         Yd = torch.from_numpy(prob.Y.view(np.int16) if y_dtype == "uint16" else prob.Y).cuda()
         mdl = gmf.Model(Yd, prob.X, prob.Z, prob.offset, start, family=fam, nb_row=nbr, nb_col=nbc, row_perm=rp,
                         col_perm=cp, settings=settings, W=W, precision="mixed", flags=flags)
-        for s in sig:
-            mdl.epoch(s)
-        fits.append(mdl)
-    assert fits[0].launches_per_sweep == 1 and fits[1].launches_per_sweep == 2
-    a, b = fits[0].get_params(), fits[1].get_params()
+        for s_ in sig:
+            if split is None:
+                mdl.epoch(s_)
+            else:   # the epoch as several sweep ranges
+                bounds = [0, *split, mdl.num_sweeps]
+                for b0, b1 in zip(bounds[:-1], bounds[1:]):
+                    mdl.sweeps(s_, b0, b1)
+        fits[mode] = mdl
+    return fits, settings, fam
+
+
+def _assert_same_state(a_mdl, b_mdl, label):
+    a, b = a_mdl.get_params(), b_mdl.get_params()
     for k in ("B", "Gamma", "U", "V"):
-        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
-    assert a["alpha"] == b["alpha"]
-    ea, eb = fits[0].get_ema(), fits[1].get_ema()
-    for k in ("Gb_row", "Hb_row", "Gb_col", "Hb_col", "cnt_row", "cnt_col"):
-        np.testing.assert_array_equal(ea[k], eb[k], err_msg=k)
-    assert fits[0].deviance() == fits[1].deviance()
+        np.testing.assert_array_equal(a[k], b[k], err_msg=f"{label}: {k}")
+    assert a["alpha"] == b["alpha"], label
+    ea, eb = a_mdl.get_ema(), b_mdl.get_ema()
+    for k in ("Gb_row", "Hb_row", "Gb_col", "Hb_col", "cnt_row", "cnt_col", "t"):
+        np.testing.assert_array_equal(ea[k], eb[k], err_msg=f"{label}: {k}")
+    assert a_mdl.deviance() == b_mdl.deviance(), label
+
+
+@pytest.mark.parametrize("case", list(CLUSTER_CASES))
+def test_epoch_modes_agree_bitwise(gmf, case):
+    """The three ways an epoch can launch -- tiles then a separate strip-update
+    launch per sweep; one cluster launch per sweep, the partials exchanged
+    through distributed shared memory; one persistent launch per epoch, each
+    cluster waiting only for the earlier visits of its moving strip -- run the
+    same phases and sum the same partials in the same tile order, so they must
+    agree to the bit. Cases with the per-sweep NB shape estimate (alpha_mode 1)
+    have no persistent mode and run cluster launches with GMF_FLAG_PERSIST."""
+    fits, settings, fam = _fit_modes(gmf, case)
+    moment = fam == "negbin" and settings["alpha_mode"] == 1
+    assert fits["persistent"].epoch_mode == ("cluster" if moment else "persistent")
+    assert fits["cluster"].epoch_mode == "cluster" and fits["separate"].epoch_mode == "separate"
+    assert fits["persistent"].launches_per_sweep == (1 if moment else 0)
+    assert fits["cluster"].launches_per_sweep == 1 and fits["separate"].launches_per_sweep == 2
+    _assert_same_state(fits["persistent"], fits["separate"], "persistent vs separate")
+    _assert_same_state(fits["cluster"], fits["separate"], "cluster vs separate")
+
+
+@pytest.mark.parametrize("case", ["nb_12_sweeps_16_tiles", "poisson_uint16_roles_swapped"])
+def test_persistent_sweep_ranges_equal_whole_epochs(gmf, case):
+    """gmf_sgd_sweeps over a split of the epoch: each range is one persistent
+    launch whose dependency counts start from zero; the result equals the
+    per-sweep launches of whole epochs bit for bit."""
+    fits, _, _ = _fit_modes(gmf, case, epochs=2, split=[1, 4])
+    assert fits["persistent"].epoch_mode == "persistent"
+    _assert_same_state(fits["persistent"], fits["separate"], "ranges: persistent vs separate")
+
+
+def test_persistent_trace_times_one_launch_per_epoch(gmf):
+    n, m, p, q, d, fam, nbr, nbc, extra = CLUSTER_CASES["nb_12_sweeps_16_tiles"]
+    prob = synth.make_problem(n, m, p, q, d, fam, seed=4, zero_frac=0.5, offset=True)
+    start = synth.crude_start(prob, d, seed=4)
+    rp, cp = synth.partitions(n, m, 4)
+    mdl = gmf.Model(torch.from_numpy(prob.Y).cuda(), prob.X, prob.Z, prob.offset, start, family=fam, nb_row=nbr,
+                    nb_col=nbc, row_perm=rp, col_perm=cp, settings=synth.fit_settings(), precision="mixed",
+                    flags=gmf.GMF_FLAG_PERSIST)
+    assert mdl.epoch_mode == "persistent"
+    sig = synth.sweep_orders(n, m, nbr, nbc, 3, 4)
+    mdl.trace(True)
+    for s_ in sig:
+        mdl.epoch(s_)
+    ms, launches = mdl.trace_read()
+    mdl.trace(False)
+    assert launches == 3 and ms > 0.0
+    assert np.isfinite(mdl.deviance())
