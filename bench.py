@@ -151,6 +151,34 @@ def host_cpu():
     return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
+def sweep_entries(n, m, nb_row, nb_col, sg):
+    """Matrix entries of the blocks of one sweep with offset sg (Algorithm 1's schedule)."""
+    r, s = -(-n // nb_row), -(-m // nb_col)
+    tot = 0
+    for k in range(min(r, s)):
+        rc, cc = ((sg + k) % r, k) if r >= s else (k, (sg + k) % s)
+        tot += min(nb_row, n - rc * nb_row) * min(nb_col, m - cc * nb_col)
+    return tot
+
+
+def oracle_sweep_rate(Y, X, Z, offset, start, w, rp, cp, sigma, settings, budget_s):
+    """The FP64 oracle as it stands (single-threaded C, one host core) on the same
+    fit: the sweeps of one epoch in order until budget_s of host time has passed
+    (at least one). Returns (entries/s, sweeps run, entries, seconds)."""
+    import oracle
+    oracle.build()
+    f = oracle.OracleFit(Y, X, Z, offset, start, family=w.family, nb_row=w.nb_row, nb_col=w.nb_col,
+                         row_perm=rp, col_perm=cp, settings=settings)
+    n, m = Y.shape
+    done, entries, t0 = 0, 0, time.perf_counter()
+    while done < len(sigma) and (done == 0 or time.perf_counter() - t0 < budget_s):
+        f.sweeps(sigma, done, done + 1)
+        entries += sweep_entries(n, m, w.nb_row, w.nb_col, int(sigma[done]))
+        done += 1
+    dt = time.perf_counter() - t0
+    return entries / dt, done, entries, dt
+
+
 def sweep_algorithmic(w, K, fr, fc):
     """Algorithmic flops and HBM bytes of one sweep launch (all blocks of a sweep)."""
     per = min(-(-w.n // w.nb_row), -(-w.m // w.nb_col))
@@ -352,6 +380,28 @@ def run_projection(args, w):
                        "heldout_mse_to_converged_scores": heldout_mse,
                        "converged_score_second_moment": float((ref[0].double() ** 2).mean())},
            "gmf_fit_entries_per_s": n_fit * w.m * w.epochs / t_fit}
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on the first 1000 held-out cells: the encoder's forward pass
+        # and 3 safeguarded Fisher steps, and the cold 3-step projection
+        import oracle.mlp as omlp
+        import oracle.project as oproj
+        nc = 1000
+        prm = model.get_params()
+        P = {k: np.asarray(v, dtype=np.float64) for k, v in net.get_params().items()}
+        Yc = Ynew[:nc].cpu().numpy().view(np.uint16)
+        Xc, oc = np.asarray(prob.X[n_fit:n_fit + nc]), np.asarray(prob.offset[n_fit:n_fit + nc])
+        kw = dict(family=w.family, alpha=prm["alpha"], n_steps=3, lam_gamma=lam_g, lam_u=lam_u)
+        t0 = time.perf_counter()
+        Uo = omlp.forward(P, Yc)[0]
+        oproj.project_cells(Yc, Xc, oc, prm["B"], prob.Z, prm["V"], U_start=Uo, **kw)
+        t_warm = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oproj.project_cells(Yc, Xc, oc, prm["B"], prob.Z, prm["V"], U_start=None, **kw)
+        t_cold = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": nc / t_warm, "unit": "cells/s", "cores": 1, "kind": "oracle", **host_cpu(),
+                               "cold_start_3_steps_cells_per_s": nc / t_cold,
+                               "sample": f"first {nc} held-out cells, encoder forward + 3 safeguarded Fisher steps "
+                                         f"(FP64 numpy; {t_warm:.1f} s; the cold 3-step projection {t_cold:.1f} s)"}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -371,7 +421,6 @@ def run_atlas(args, w):
     hp = synth.Problem(Y=prob.Y.cpu().numpy().view(np.uint16), X=prob.X, Z=prob.Z, offset=prob.offset, B=prob.B,
                        Gamma=prob.Gamma, U=prob.U, V=prob.V, nb_size=prob.nb_size, family=w.family)
     start = synth.crude_start(hp, w.d, seed=args.seed)
-    del hp
     rp, cp = synth.partitions(w.n, w.m, args.seed)
     sig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, w.epochs, args.seed)
     stream = torch.cuda.current_stream()
@@ -421,6 +470,12 @@ def run_atlas(args, w):
            "final_deviance_rel_gap_mixed_vs_fp32": (dm - df) / df,
            "time_to_deviance": {"target": target, "rule": "within 1e-3 of the FP32 fit's final deviance",
                                 "mixed": ttd(res["mixed"]), "fp32": ttd(res["fp32"])}}
+    if not args.no_cpu_baseline:
+        rate, done, ent, dt = oracle_sweep_rate(hp.Y, hp.X, hp.Z, hp.offset, start, w, rp, cp, sig[0],
+                                                synth.fit_settings(), budget_s=15.0)
+        out["cpu_baseline"] = {"value": rate, "unit": "entries/s", "cores": 1, "kind": "oracle", **host_cpu(),
+                               "sample": f"first {done} sweeps of epoch 1 ({ent:.3g} entries) of the same fit, "
+                                         f"FP64 single-threaded C on one host core, {dt:.1f} s"}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -525,6 +580,18 @@ def run_rank_sweep(args, w):
            "sequential": {"value": work / (ms_s / 1e3), "ms_per_step": ms_s / args.steps},
            "batched_over_sequential": ms_s / ms_b,
            "deviance_batched_equals_sequential": devs_b == devs_s}
+    if not args.no_cpu_baseline:
+        ent_all, t_all, per_rank = 0, 0.0, {}
+        for d, st in zip(RANKS, starts):
+            rate, done, ent, dt = oracle_sweep_rate(prob.Y, prob.X, prob.Z, prob.offset, st, w, rp, cp, sig[0],
+                                                    synth.fit_settings(), budget_s=2.0)
+            ent_all, t_all = ent_all + ent, t_all + dt
+            per_rank[str(d)] = rate
+        out["cpu_baseline"] = {"value": ent_all / t_all, "unit": "model-entries/s", "cores": 1, "kind": "oracle",
+                               **host_cpu(), "per_rank_entries_per_s": per_rank,
+                               "sample": f"each of the 8 models run alone for the first sweeps of epoch 1 (about "
+                                         f"2 s each, {ent_all:.3g} model-entries), FP64 single-threaded C on one "
+                                         f"host core, {t_all:.1f} s"}
     print(json.dumps(out), flush=True)
     return 0
 

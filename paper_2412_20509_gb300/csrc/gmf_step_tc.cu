@@ -823,9 +823,10 @@ const void* tc_epoch_fn(int y16, int epi) {
                                                                         : tc_epoch_fn_epi<EPI_ANY>(y16);
 }
 
-// Several models (ranks) sharing the count matrix and the partitions: blockIdx.z
-// = slot * per + k, slot -> model through `order` (heaviest models first).
-template <bool Y16>
+// Several models (ranks) sharing the count matrix, the partitions and the
+// settings (so one epilogue variant serves all): blockIdx.z = slot * per + k,
+// slot -> model through `order` (heaviest models first).
+template <bool Y16, int EPI>
 __global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restrict__ av, const TcLayout* __restrict__ lv,
                                                          const int* __restrict__ order, int per,
                                                          const __grid_constant__ CUtensorMap ymap, int w) {
@@ -838,7 +839,16 @@ __global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restr
         s_l = lv[model];
     }
     __syncthreads();
-    tc_tile<Y16, false, EPI_ANY>(s_a, s_l, &ymap, w, blockIdx.z % per, smraw);
+    tc_tile<Y16, false, EPI>(s_a, s_l, &ymap, w, blockIdx.z % per, smraw);
+}
+
+template <int EPI>
+const void* tc_multi_fn_epi(int y16) {
+    return y16 ? (const void*)sweep_tc_multi<true, EPI> : (const void*)sweep_tc_multi<false, EPI>;
+}
+const void* tc_multi_fn(int y16, int epi) {
+    return epi == EPI_NB ? tc_multi_fn_epi<EPI_NB>(y16) : epi == EPI_PO ? tc_multi_fn_epi<EPI_PO>(y16)
+                                                                        : tc_multi_fn_epi<EPI_ANY>(y16);
 }
 
 int tc_cluster_layout(gmf_model* h, TcState* tc);
@@ -1073,20 +1083,29 @@ void gmf_tc_grid(const gmf_model* h, int* TI, int* TJ) {
     *TJ = ((const TcState*)h->tc)->TJ;
 }
 
-cudaError_t gmf_tc_multi_attr(int y16, uint32_t smem) {
-    return gmf_smem_limit(y16 ? (const void*)sweep_tc_multi<true> : (const void*)sweep_tc_multi<false>, smem);
+cudaError_t gmf_tc_multi_attr(const gmf_model* h0, uint32_t smem) {
+    return gmf_smem_limit(tc_multi_fn(h0->y16, ((const TcState*)h0->tc)->epi), smem);
 }
 
-// One sweep of nmodels models: grid (TJ, TI, nmodels * per).
+// One sweep of nmodels models: grid (TJ, TI, nmodels * per), with programmatic
+// stream serialization like the single-model tile launch.
 cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, const void* d_lays, const int* d_order,
                                 int nmodels, uint32_t smem, int w, cudaStream_t st) {
     const TcState* tc = (const TcState*)h0->tc;
-    dim3 grid(tc->TJ, tc->TI, h0->per * nmodels);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tc->TJ, tc->TI, h0->per * nmodels);
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     const TcLayout* lays = (const TcLayout*)d_lays;
-    return h0->y16 ? gmf_launch_pdl(sweep_tc_multi<true>, grid, dim3(NTH), smem, st, d_args, lays, d_order, h0->per,
-                                    tc->ymap, w)
-                   : gmf_launch_pdl(sweep_tc_multi<false>, grid, dim3(NTH), smem, st, d_args, lays, d_order, h0->per,
-                                    tc->ymap, w);
+    int per = h0->per;
+    void* args[] = {(void*)&d_args, (void*)&lays, (void*)&d_order, &per, (void*)&tc->ymap, &w};
+    return cudaLaunchKernelExC(&cfg, tc_multi_fn(h0->y16, tc->epi), args);
 }
 
 int gmf_tc_cluster(const gmf_model* h) { return h->tc && ((const TcState*)h->tc)->cluster; }

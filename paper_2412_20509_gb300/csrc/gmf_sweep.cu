@@ -16,7 +16,7 @@ size_t gmf_tc_layout_size();
 const void* gmf_tc_layout(const gmf_model* h);
 uint32_t gmf_tc_smem(const gmf_model* h);
 void gmf_tc_grid(const gmf_model* h, int* TI, int* TJ);
-cudaError_t gmf_tc_multi_attr(int y16, uint32_t smem);
+cudaError_t gmf_tc_multi_attr(const gmf_model* h0, uint32_t smem);
 cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, const void* d_lays, const int* d_order,
                                 int nmodels, uint32_t smem, int w, cudaStream_t st);
 size_t gmf_sweep_simt_smem(const gmf_model* h);
@@ -109,7 +109,7 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
     cudaMemcpyAsync(s->d_order, order.data(), sizeof(int) * n_models, cudaMemcpyHostToDevice, st);
     if (s->mixed) cudaMemcpyAsync(s->d_lays, lays.data(), lays.size(), cudaMemcpyHostToDevice, st);
     const cudaError_t e =
-        s->mixed ? gmf_tc_multi_attr(s->models[0]->y16, (uint32_t)s->smem) : gmf_simt_multi_attr(s->smem);
+        s->mixed ? gmf_tc_multi_attr(s->models[0], (uint32_t)s->smem) : gmf_simt_multi_attr(s->smem);
     if (e != cudaSuccess)
         return sweep_fail(s, GMF_ERR_ARG, std::string("gmf_sweep_init: the largest model's tile does not fit: ") +
                                                cudaGetErrorString(e));
