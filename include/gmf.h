@@ -136,19 +136,30 @@ int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, void* stream)
 
 /*
  * gmf_update_y_async -- replace the counts from a host buffer without waiting:
- * for streaming a sequence of count matrices of the same shape. The copy runs
- * on the library's own copy stream into one of two device staging buffers (so
- * it overlaps work already enqueued on `stream`); the permutation into the
- * model's counts is ordered on `stream` after the copy. Work enqueued on
- * `stream` before this call sees the old counts, work enqueued after it the new
- * ones. Y: host, n x m counts of the init dtype; page-locked (pinned) memory
- * for the copy to overlap; it must stay unchanged until `stream` has passed the
- * work enqueued by this call (e.g. after a later synchronous call on it). At
- * most two calls may be in flight on one handle. The paper has no counterpart
- * (a deployment variant of gmf_update_y). Errors: GMF_ERR_ARG, GMF_ERR_STATE
- * (a handle that reads another handle's counts), GMF_ERR_CUDA.
+ * for streaming a sequence of count matrices of the same shape. Work enqueued
+ * on `stream` before this call sees the old counts, work enqueued after it the
+ * new ones. When the device can read Y (page-locked, mapped memory:
+ * cudaHostAlloc, cudaHostRegister with mapping, torch's pin_memory; any host
+ * memory where the device reads pageable memory, as on Grace-based systems),
+ * Y is 16-byte aligned, and a row of counts is a multiple of 16 bytes of at
+ * most 48 KiB, one gather kernel on the library's
+ * copy stream reads Y over the host link and writes the permuted counts into
+ * the handle's second count buffer (allocated on first use, n x m counts), and
+ * the handle switches buffers: the upload overlaps work already enqueued on
+ * `stream`, which keeps reading the previous buffer. Otherwise the counts are
+ * copied on the copy stream into one of two device staging buffers and
+ * permuted in place on `stream` after the copy. Y: host, n x m counts of the
+ * init dtype; it must stay unchanged until `stream` has passed the work
+ * enqueued by this call (e.g. after a later synchronous call on it). At most
+ * two calls may be in flight on one handle. The paper has no counterpart (a
+ * deployment variant of gmf_update_y). Errors: GMF_ERR_ARG, GMF_ERR_STATE (a
+ * handle that reads another handle's counts), GMF_ERR_CUDA.
  */
 int gmf_update_y_async(gmf_model* h, const void* Y, void* stream);
+
+/* Count buffers the handle holds on the device: 1, or 2 once gmf_update_y_async
+ * took the direct path. -1 for a NULL handle. */
+int32_t gmf_count_buffers(const gmf_model* h);
 
 /* Number of sweeps per epoch: max(r, s) with r = ceil(n/nb_row), s = ceil(m/nb_col). */
 int32_t gmf_num_sweeps(const gmf_model* h);

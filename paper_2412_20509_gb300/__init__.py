@@ -31,7 +31,7 @@ ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
 
 # Every function declared in include/gmf.h.
 EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async", "gmf_num_sweeps",
-           "gmf_launches_per_sweep", "gmf_epoch_mode", "gmf_strip_schedule",
+           "gmf_launches_per_sweep", "gmf_epoch_mode", "gmf_strip_schedule", "gmf_count_buffers",
            "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
@@ -78,6 +78,7 @@ def lib():
         "gmf_num_sweeps": (C.c_int32, [VP]),
         "gmf_launches_per_sweep": (C.c_int32, [VP]),
         "gmf_epoch_mode": (C.c_int32, [VP]),
+        "gmf_count_buffers": (C.c_int32, [VP]),
         "gmf_strip_schedule": (C.c_int, [C.c_int32, C.c_int32, VP, C.c_int32, C.c_int32, VP]),
         "gmf_sgd_epoch": (C.c_int, [VP, VP, VP]),
         "gmf_sgd_sweeps": (C.c_int, [VP, VP, C.c_int32, C.c_int32, VP]),
@@ -275,9 +276,14 @@ class Model:
         check(lib().gmf_update_y(self._h, _ptr(Y), int(on_dev), _stream(stream)))
 
     def update_y_async(self, Y, stream=None):
-        """Counts from a pinned host tensor without waiting (see gmf_update_y_async); keep Y unchanged until the
-        stream has passed this call's work."""
+        """Counts from a host tensor or array without waiting (see gmf_update_y_async: pinned memory is read
+        directly by the GPU); keep Y unchanged until the stream has passed this call's work."""
         check(lib().gmf_update_y_async(self._h, _ptr(Y), _stream(stream)))
+
+    @property
+    def count_buffers(self):
+        """Count buffers held on the device (2 once gmf_update_y_async took the direct path)."""
+        return lib().gmf_count_buffers(self._h)
 
     def deviance(self, stream=None):
         out = C.c_double()

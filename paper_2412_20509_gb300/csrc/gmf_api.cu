@@ -45,6 +45,7 @@ cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st);
 int gmf_tc_cluster(const gmf_model* h);
 int gmf_tc_persistent(const gmf_model* h);
 cudaError_t gmf_tc_launch_epoch(gmf_model* h, int w0, int w1, cudaStream_t st);
+int gmf_tc_set_ybuf(gmf_model* h, int idx, const void* Y);
 void gmf_tc_free(gmf_model* h);
 
 // One sweep launch of the configured path.
@@ -118,17 +119,27 @@ static void trace_destroy(gmf_model* h) {
 static void release(gmf_model* h) {
     if (!h) return;
     trace_destroy(h);
-    if (h->epoch_graph) cudaGraphExecDestroy(h->epoch_graph);
+    for (int i = 0; i < 2; i++)
+        if (h->epoch_graph[i]) cudaGraphExecDestroy(h->epoch_graph[i]);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->tc) gmf_tc_free(h);
+    if (h->ybuf[1]) {  // the second count buffer: wait for its last gather, free both buffers below
+        if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+        cudaEventDestroy(h->y_ready);
+        for (int i = 0; i < 2; i++) cudaEventDestroy(h->y_free[i]);
+        cudaFree(h->ybuf[h->ycur ^ 1]);
+        h->Yp = h->ybuf[h->ycur];
+    }
     if (h->y_shared) {  // owned by another handle
         h->Yp = nullptr;
         h->Wp = nullptr;
         h->ystage = nullptr;
     }
-    if (h->up_init) {
+    if (h->copy_stream) {
         cudaStreamSynchronize(h->copy_stream);
         cudaStreamDestroy(h->copy_stream);
+    }
+    if (h->up_init) {
         for (int i = 0; i < 2; i++) {
             cudaEventDestroy(h->up_copied[i]);
             cudaEventDestroy(h->up_free[i]);
@@ -276,6 +287,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
         INIT_CUDA(cudaMalloc(&h->Yp, nm * (h->y16 ? 2 : 4)));
         if (W) INIT_CUDA(dalloc(&h->Wp, nm));
     }
+    h->ybuf[0] = h->Yp;
     INIT_CUDA(dalloc(&h->L, (size_t)c.n * h->KP));
     INIT_CUDA(dalloc(&h->R, (size_t)c.m * h->KP));
     INIT_CUDA(dalloc(&h->GbR, (size_t)c.n * h->fr));
@@ -379,10 +391,35 @@ extern "C" int gmf_update_y_async(gmf_model* h, const void* Y, void* stream) {
     if (h->y_shared) return fail(GMF_ERR_STATE, "gmf_update_y_async: this handle reads another handle's counts");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)h->n * h->m * (h->y16 ? 2 : 4);
+    if (!h->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    // Direct path: page-locked, mapped host memory is read by one gather kernel on
+    // the copy stream into the count buffer that is not current; the handle then
+    // switches buffers, so work already enqueued on `st` keeps its counts.
+    void* dsrc = nullptr;
+    const bool mapped = !h->y_fixed && gmf_gather_host_ok(h->y16, h->m) && ((uintptr_t)Y & 15u) == 0 &&
+                        cudaHostGetDevicePointer(&dsrc, (void*)Y, 0) == cudaSuccess && dsrc != nullptr;
+    if (!mapped) cudaGetLastError();  // (not page-locked: the staged copy below)
+    if (mapped) {
+        if (!h->ybuf[1]) {
+            CUDA_TRY(cudaMalloc(&h->ybuf[1], bytes));
+            CUDA_TRY(cudaEventCreateWithFlags(&h->y_ready, cudaEventDisableTiming));
+            for (int i = 0; i < 2; i++) CUDA_TRY(cudaEventCreateWithFlags(&h->y_free[i], cudaEventDisableTiming));
+            if (gmf_tc_set_ybuf(h, 1, h->ybuf[1]) != GMF_OK)
+                return fail(GMF_ERR_CUDA, "gmf_update_y_async: cuTensorMapEncodeTiled failed for the second buffer");
+        }
+        const int nb = h->ycur ^ 1;
+        CUDA_TRY(cudaEventRecord(h->y_free[h->ycur], st));          // the current buffer's readers so far
+        CUDA_TRY(cudaStreamWaitEvent(h->copy_stream, h->y_free[nb], 0));  // nb's last readers (none at first)
+        CUDA_TRY(gmf_launch_gather_host(dsrc, h->ybuf[nb], h->y16, h->n, h->m, h->rperm, h->cperm, h->copy_stream));
+        CUDA_TRY(cudaEventRecord(h->y_ready, h->copy_stream));
+        CUDA_TRY(cudaStreamWaitEvent(st, h->y_ready, 0));
+        h->ycur = nb;
+        h->Yp = h->ybuf[nb];
+        return GMF_OK;
+    }
     if (!h->up_init) {
         if (!h->ystage) CUDA_TRY(cudaMalloc(&h->ystage, bytes));
         CUDA_TRY(cudaMalloc(&h->ystage2, bytes));
-        CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
         for (int i = 0; i < 2; i++) {
             CUDA_TRY(cudaEventCreateWithFlags(&h->up_copied[i], cudaEventDisableTiming));
             CUDA_TRY(cudaEventCreateWithFlags(&h->up_free[i], cudaEventDisableTiming));
@@ -403,6 +440,11 @@ extern "C" int gmf_update_y_async(gmf_model* h, const void* Y, void* stream) {
 }
 
 extern "C" int32_t gmf_num_sweeps(const gmf_model* h) { return h ? h->nsw : -1; }
+
+extern "C" int32_t gmf_count_buffers(const gmf_model* h) {
+    if (!h) return -1;
+    return h->ybuf[1] ? 2 : 1;
+}
 
 extern "C" int32_t gmf_epoch_mode(const gmf_model* h) {
     if (!h) return -1;
@@ -512,7 +554,8 @@ extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begi
     // A whole epoch replays one captured graph of its sweep launches (the
     // launches read sigma and the step factors from the buffers filled above).
     if (!h->trace_on && w_begin == 0 && w_end == h->nsw) {
-        if (!h->epoch_graph) {
+        cudaGraphExec_t& graph = h->epoch_graph[h->ycur];  // the launches hold the count buffer's address
+        if (!graph) {
             if (!h->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
             cudaGraph_t g = nullptr;
             CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
@@ -525,14 +568,14 @@ extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begi
                 }
             }
             CUDA_TRY(cudaStreamEndCapture(h->capture_stream, &g));
-            cudaError_t e = cudaGraphInstantiate(&h->epoch_graph, g, 0);
+            cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) {
-                h->epoch_graph = nullptr;
+                graph = nullptr;
                 return fail(GMF_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
             }
         }
-        CUDA_TRY(cudaGraphLaunch(h->epoch_graph, st));
+        CUDA_TRY(cudaGraphLaunch(graph, st));
         h->t += (int64_t)h->nsw * h->per;
         return GMF_OK;
     }

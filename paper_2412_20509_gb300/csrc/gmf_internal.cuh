@@ -93,6 +93,12 @@ struct gmf_model {
     cudaEvent_t up_free[2];     // staging buffer i read by its permutation
     int up_idx;                 // staging buffer of the next gmf_update_y_async
     int up_init;
+    // counts read straight from mapped host memory into a second count buffer (gmf_update_y_async)
+    void* ybuf[2];              // the two count buffers (ybuf[1] allocated on first use); Yp = ybuf[ycur]
+    int ycur;
+    int y_fixed;                // other handles read Yp: it never moves
+    cudaEvent_t y_free[2];      // last work that read ybuf[i] (recorded when it stops being current)
+    cudaEvent_t y_ready;        // the gather into the new current buffer
     float* Rorig;               // m x KP: R in the caller's gene order (per-cell projection)
     void* kr_buf;               // BF16 Khatri-Rao product of [Z, V] (tensor-core projection)
     size_t kr_elems;
@@ -122,7 +128,7 @@ struct gmf_model {
     double trace_ms;
     int64_t trace_launches;
     // CUDA graph of one full epoch of FP32 sweeps (captured on first use)
-    cudaGraphExec_t epoch_graph;
+    cudaGraphExec_t epoch_graph[2];   // one per count buffer
     cudaStream_t capture_stream;
 };
 
@@ -185,5 +191,11 @@ cudaError_t gmf_sweep_simt_attr(gmf_model* h);
 cudaError_t gmf_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st);
 cudaError_t gmf_launch_permute_y(const void* src, void* dst, int y16, int64_t n, int64_t m,
                                  const int* rperm, const int* cperm, cudaStream_t st);
+// Yp[i][j] = Y[rperm[i]][cperm[j]] with Y in mapped host memory (16-byte
+// aligned, rows of a multiple of 16 bytes); gmf_gather_host_ok says whether a
+// row fits the kernel's shared memory.
+cudaError_t gmf_launch_gather_host(const void* src, void* dst, int y16, int64_t n, int64_t m, const int* rperm,
+                                   const int* cperm, cudaStream_t st);
+int gmf_gather_host_ok(int y16, int64_t m);
 cudaError_t gmf_launch_permute_w(const float* src, float* dst, int64_t n, int64_t m,
                                  const int* rperm, const int* cperm, cudaStream_t st);

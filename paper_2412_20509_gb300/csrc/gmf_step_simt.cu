@@ -22,6 +22,8 @@
 // device does no FP64 arithmetic except the cross-CTA sums of the NB moments.
 #include <math.h>
 
+#include <algorithm>
+
 #include "gmf_internal.cuh"
 #include "gmf_update.cuh"
 
@@ -401,6 +403,34 @@ __global__ void permute_kernel(const Ty* __restrict__ src, Ty* __restrict__ dst,
     }
 }
 
+// Mapped host rows -> permuted device rows. Each CTA takes `rows` destination
+// rows at a time: their source rows come over the host link as 16-byte loads
+// into shared memory (all loads of the group in flight before the first use),
+// then the destination rows are written in column order.
+constexpr int GH_THREADS = 512;
+template <typename Ty>
+__global__ void __launch_bounds__(GH_THREADS)
+    gather_host_kernel(const Ty* __restrict__ src, Ty* __restrict__ dst, int64_t n, int64_t m,
+                       const int* __restrict__ rperm, const int* __restrict__ cperm, int rows) {
+    extern __shared__ uint4 gh_smem[];
+    const Ty* srow = (const Ty*)gh_smem;
+    const int chunks = (int)(m * (int64_t)sizeof(Ty) / 16);  // 16-byte chunks per row
+    for (int64_t i0 = (int64_t)blockIdx.x * rows; i0 < n; i0 += (int64_t)gridDim.x * rows) {
+        const int nr = (int)min((int64_t)rows, n - i0);
+        for (int e = threadIdx.x; e < nr * chunks; e += blockDim.x) {
+            const int r = e / chunks, c = e - r * chunks;
+            gh_smem[e] = ((const uint4*)(src + (int64_t)rperm[i0 + r] * m))[c];
+        }
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < (int64_t)nr * m; e += blockDim.x) {
+            const int r = (int)(e / m);
+            const int64_t j = e - (int64_t)r * m;
+            dst[(i0 + r) * m + j] = srow[(int64_t)r * m + cperm[j]];
+        }
+        __syncthreads();
+    }
+}
+
 size_t sweep_smem(int K, int fr, int fc) {
     const int FRP = (fr + 3) & ~3, FCP = (fc + 3) & ~3;
     K = (K + 3) & ~3;
@@ -503,6 +533,33 @@ cudaError_t gmf_launch_permute_y(const void* src, void* dst, int y16, int64_t n,
                                                                rperm, cperm);
     else
         permute_kernel<int><<<blocks, 256, 0, st>>>((const int*)src, (int*)dst, n, m, rperm, cperm);
+    return cudaGetLastError();
+}
+
+int gmf_gather_host_ok(int y16, int64_t m) {
+    const int64_t rb = m * (y16 ? 2 : 4);
+    return rb % 16 == 0 && rb <= 48 * 1024;
+}
+
+// One CTA per SM (fewer reach only ~80 % of the link's rate), two rows per
+// round: up to 16 KB of shared memory and 26 registers a thread, so that the
+// CTAs share SMs with the block-step kernels running at the same time.
+cudaError_t gmf_launch_gather_host(const void* src, void* dst, int y16, int64_t n, int64_t m, const int* rperm,
+                                   const int* cperm, cudaStream_t st) {
+    const int64_t rb = m * (y16 ? 2 : 4);
+    const int rows = (int)std::max<int64_t>(1, std::min<int64_t>(2, 16384 / rb));
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>((n + rows - 1) / rows, nsm);
+    const size_t smem = (size_t)rows * (size_t)rb;
+    if (y16)
+        gather_host_kernel<unsigned short><<<blocks, GH_THREADS, smem, st>>>(
+            (const unsigned short*)src, (unsigned short*)dst, n, m, rperm, cperm, rows);
+    else
+        gather_host_kernel<int><<<blocks, GH_THREADS, smem, st>>>((const int*)src, (int*)dst, n, m, rperm, cperm,
+                                                                  rows);
     return cudaGetLastError();
 }
 

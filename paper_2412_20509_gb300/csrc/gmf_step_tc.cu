@@ -61,7 +61,7 @@ struct TcLayout {
 
 struct TcState {
     TcLayout lay;
-    CUtensorMap ymap;
+    CUtensorMap ymap[2];   // the count matrix in each of the handle's count buffers (ymap[1] once allocated)
     int TI, TJ;
     int cluster;           // 1: the strip updates run inside the tile launch (cluster mode)
     int persist;           // 1: a sweep range runs as one persistent launch (sweep_tc_epoch)
@@ -861,6 +861,31 @@ int fail_str(std::string* err, const char* msg) {
 
 }  // namespace
 
+// TMA descriptor of an n x m count matrix at Y: 128-byte boxes of TT rows, 128-byte swizzle.
+static int tc_encode_y(const gmf_model* h, CUtensorMap* map, const void* Y) {
+    const int es = h->y16 ? 2 : 4;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        !fn)
+        return GMF_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)h->m, (cuuint64_t)h->n};
+    cuuint64_t strides[1] = {(cuuint64_t)h->m * es};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)TT};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult cr = ((PFN_cuTensorMapEncodeTiled_v12000)fn)(
+        map, h->y16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2, (void*)Y, dims, strides, box,
+        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return cr == CUDA_SUCCESS ? GMF_OK : GMF_ERR_CUDA;
+}
+
+// The tensor map of the handle's second count buffer (gmf_update_y_async).
+int gmf_tc_set_ybuf(gmf_model* h, int idx, const void* Y) {
+    if (!h->tc) return GMF_OK;
+    return tc_encode_y(h, &((TcState*)h->tc)->ymap[idx], Y);
+}
+
 // Set up the tensor-core path of a handle: layout, TMA descriptor, attributes.
 int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
     const int es = h->y16 ? 2 : 4;
@@ -902,23 +927,7 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
             return fail_str(err, "mixed precision: the tile does not fit in shared memory (reduce d or use uint16 counts)");
         }
     }
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult qr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
-        !fn) {
-        delete tc;
-        if (err) *err = "cuTensorMapEncodeTiled is not available";
-        return GMF_ERR_CUDA;
-    }
-    cuuint64_t dims[2] = {(cuuint64_t)h->m, (cuuint64_t)h->n};
-    cuuint64_t strides[1] = {(cuuint64_t)h->m * es};
-    cuuint32_t box[2] = {(cuuint32_t)L.JB, (cuuint32_t)TT};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult cr = ((PFN_cuTensorMapEncodeTiled_v12000)fn)(
-        &tc->ymap, h->y16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2, h->Yp, dims, strides,
-        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) {
+    if (tc_encode_y(h, &tc->ymap[0], h->Yp) != GMF_OK) {
         delete tc;
         if (err) *err = "cuTensorMapEncodeTiled failed for the count matrix";
         return GMF_ERR_CUDA;
@@ -1022,7 +1031,7 @@ cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
         at[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 2;
-        void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap, &w};
+        void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap[h->ycur], &w};
         return cudaLaunchKernelExC(&cfg, tc_fn(h->y16, 1, tc->epi), args);
     }
     cudaLaunchConfig_t cfg = {};
@@ -1035,7 +1044,7 @@ cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap, &w};
+    void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap[h->ycur], &w};
     return cudaLaunchKernelExC(&cfg, tc_fn(h->y16, 0, tc->epi), args);
 }
 
@@ -1069,7 +1078,7 @@ cudaError_t gmf_tc_launch_epoch(gmf_model* h, int w0, int w1, cudaStream_t st) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap, &w0, &w1};
+    void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap[h->ycur], &w0, &w1};
     return cudaLaunchKernelExC(&cfg, tc_epoch_fn(h->y16, tc->epi), args);
 }
 
@@ -1104,7 +1113,7 @@ cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, con
     cfg.numAttrs = 1;
     const TcLayout* lays = (const TcLayout*)d_lays;
     int per = h0->per;
-    void* args[] = {(void*)&d_args, (void*)&lays, (void*)&d_order, &per, (void*)&tc->ymap, &w};
+    void* args[] = {(void*)&d_args, (void*)&lays, (void*)&d_order, &per, (void*)&tc->ymap[h0->ycur], &w};
     return cudaLaunchKernelExC(&cfg, tc_multi_fn(h0->y16, tc->epi), args);
 }
 

@@ -80,6 +80,7 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
         }
         s->models.push_back(h);
     }
+    s->models[0]->y_fixed = 1;  // the other models read its count buffer
     // heaviest models first (per-entry work grows with K = 1+p+q+d)
     std::vector<int> order(n_models);
     for (int i = 0; i < n_models; i++) order[i] = i;
