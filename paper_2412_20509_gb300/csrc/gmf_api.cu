@@ -182,9 +182,26 @@ static void build_factors(const gmf_model* h, const double* X, const double* Z, 
     }
 }
 
+// The device address of host counts the device can read with the gather
+// kernel (16-byte aligned, rows of a multiple of 16 bytes), or null.
+static const void* host_gather_src(const gmf_model* h, const void* Y) {
+    void* d = nullptr;
+    if (!gmf_gather_host_ok(h->y16, h->m) || ((uintptr_t)Y & 15u) != 0) return nullptr;
+    if (cudaHostGetDevicePointer(&d, (void*)Y, 0) != cudaSuccess) {
+        cudaGetLastError();  // (not page-locked)
+        return nullptr;
+    }
+    return d;
+}
+
 static int upload_y(gmf_model* h, const void* Y, int on_device, cudaStream_t st) {
     const size_t bytes = (size_t)h->n * h->m * (h->y16 ? 2 : 4);
     const void* src = Y;
+    const void* dsrc = on_device ? nullptr : host_gather_src(h, Y);
+    if (dsrc) {  // one permuting gather over the host link, ordered on st
+        CUDA_TRY(gmf_launch_gather_host(dsrc, h->Yp, h->y16, h->n, h->m, h->rperm, h->cperm, st));
+        return GMF_OK;
+    }
     if (!on_device) {
         if (!h->ystage) CUDA_TRY(cudaMalloc(&h->ystage, bytes));
         CUDA_TRY(cudaMemcpyAsync(h->ystage, Y, bytes, cudaMemcpyHostToDevice, st));
@@ -395,11 +412,8 @@ extern "C" int gmf_update_y_async(gmf_model* h, const void* Y, void* stream) {
     // Direct path: page-locked, mapped host memory is read by one gather kernel on
     // the copy stream into the count buffer that is not current; the handle then
     // switches buffers, so work already enqueued on `st` keeps its counts.
-    void* dsrc = nullptr;
-    const bool mapped = !h->y_fixed && gmf_gather_host_ok(h->y16, h->m) && ((uintptr_t)Y & 15u) == 0 &&
-                        cudaHostGetDevicePointer(&dsrc, (void*)Y, 0) == cudaSuccess && dsrc != nullptr;
-    if (!mapped) cudaGetLastError();  // (not page-locked: the staged copy below)
-    if (mapped) {
+    const void* dsrc = h->y_fixed ? nullptr : host_gather_src(h, Y);
+    if (dsrc) {
         if (!h->ybuf[1]) {
             CUDA_TRY(cudaMalloc(&h->ybuf[1], bytes));
             CUDA_TRY(cudaEventCreateWithFlags(&h->y_ready, cudaEventDisableTiming));
