@@ -67,8 +67,63 @@ def whole_job_rate(units_per_rank, ws, seconds):
     return ws * units_per_rank / seconds
 
 
+class NvmlClocks:
+    """SM clock and clock-event reasons read through NVML (read-only queries) every
+    ~2 ms on a background thread, so that even a timed region of a few ms has
+    samples; mark(True/False) brackets the timed region."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu_index):
+        import ctypes as C
+        self.C = C
+        self.nvml = C.CDLL("libnvidia-ml.so.1")
+        if self.nvml.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = C.c_void_p()
+        if self.nvml.nvmlDeviceGetHandleByIndex_v2(C.c_uint(gpu_index), C.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn if fn is not None else self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples = []
+        self.inside = False
+        self.run = True
+        self.t = threading.Thread(target=self._poll, daemon=True)
+
+    def _poll(self):
+        C = self.C
+        mhz, mx, mask = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        while self.run:
+            ok = self.nvml.nvmlDeviceGetClockInfo(self.h, 1, C.byref(mhz)) == 0   # NVML_CLOCK_SM
+            ok = ok and self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, C.byref(mx)) == 0
+            ok = ok and self.reasons_fn(self.h, C.byref(mask)) == 0
+            if ok and self.inside:
+                self.samples.append((mhz.value, mx.value, mask.value))
+            time.sleep(0.002)
+
+    def start(self):
+        self.t.start()
+
+    def mark(self, inside):
+        self.inside = inside
+
+    def stop(self):
+        self.run = False
+        self.t.join(timeout=2)
+        try:
+            self.nvml.nvmlShutdown()
+        except Exception:
+            pass
+        sm = [a for a, _, _ in self.samples]
+        reasons = sorted({nm for _, _, m in self.samples for bit, nm in self.REASONS.items() if m & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(b for _, b, _ in self.samples) if self.samples else None,
+                "reasons": reasons, "samples": len(sm), "source": "NVML, every ~2 ms inside the timed region"}
+
+
 class ClockSampler:
-    """nvidia-smi clock / throttle samples while the timed region runs."""
+    """Clock and throttle samples while the timed region runs: NVML when the
+    driver's library loads, else nvidia-smi."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -77,8 +132,15 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        try:
+            self.nv = NvmlClocks(gpu_index)
+        except (OSError, AttributeError):
+            self.nv = None
 
     def start(self):
+        if self.nv is not None:
+            self.nv.start()
+            return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                           "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
@@ -88,11 +150,17 @@ class ClockSampler:
         except (OSError, ValueError):
             self.proc = None
 
+    def mark(self, inside):
+        if self.nv is not None:
+            self.nv.mark(inside)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nv is not None:
+            return self.nv.stop()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -115,7 +183,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, every 100 ms"}
 
 
 def measured_peaks():
@@ -675,14 +743,18 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_epochs(mdl, first, count):
+    def timed_epochs(mdl, first, count, clk=None):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
+        if clk is not None:
+            clk.mark(True)
         e0.record(stream)
         for s in range(count):
             mdl.epoch(sig[first + s])
         e1.record(stream)
         barrier()
+        if clk is not None:
+            clk.mark(False)
         return e0.elapsed_time(e1)
 
     # ---------------- device-resident throughput (the headline value)
@@ -691,7 +763,8 @@ def main():
     dev0 = model.deviance()
     clocks = ClockSampler(local)
     clocks.start()
-    elapsed_ms = timed_epochs(model, args.warmup, args.steps)
+    time.sleep(0.05)  # the sampler is polling before the timed region starts
+    elapsed_ms = timed_epochs(model, args.warmup, args.steps, clocks)
     clk = clocks.stop()
     elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
     entries_step = n * m
