@@ -286,7 +286,10 @@ int gmf_orthogonalize(gmf_model* h, int32_t mode, void* stream);
  *   U_start   device float32 n_new x d or NULL
  *   U_out     device float32 n_new x d;  G_out: device float32 n_new x q
  *   dev_out   device float32 n_new (per-cell deviance at the result) or NULL
+ * n_new = 0 is an empty batch: nothing is read or written (pointers may be NULL).
  * Asynchronous on the stream. Allocates its workspace from the handle.
+ * Errors: GMF_ERR_ARG (n_new < 0, bad y_dtype, n_steps outside [0, 1000], NULL
+ * pointers of a non-empty batch), GMF_ERR_CUDA.
  */
 int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n_new,
                       const float* Xnew, const float* offset_new, const float* U_start,
@@ -335,6 +338,7 @@ void gmf_sweep_free(gmf_sweep* s);
  *                       (NULL pointers are skipped); set_params also resets Adam.
  * gmf_mlp_forward    -- o for `rows` cells: Y device rows x n_in counts
  *                       (y_dtype), out device rows x n_out. Asynchronous.
+ *                       rows = 0: nothing to do (pointers may be NULL).
  * gmf_mlp_loss_grad  -- loss (device float, may be NULL) and the gradients of one
  *                       batch (rows <= max_batch) into the network. Asynchronous.
  * gmf_mlp_adam       -- one Adam step with the stored gradients. Asynchronous.

@@ -816,11 +816,13 @@ extern "C" int gmf_orthogonalize(gmf_model* h, int32_t mode, void* stream) {
 extern "C" int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n_new, const float* Xnew,
                                  const float* offset_new, const float* U_start, int32_t n_steps, float* U_out,
                                  float* G_out, float* dev_out, void* stream) {
-    if (!h || !Ynew || !U_out || !G_out) return fail(GMF_ERR_ARG, "gmf_project_cells: NULL argument");
-    if (h->p > 0 && !Xnew) return fail(GMF_ERR_ARG, "gmf_project_cells: Xnew is NULL");
-    if (n_new <= 0 || n_new > (int64_t)INT32_MAX) return fail(GMF_ERR_ARG, "gmf_project_cells: bad n_new");
+    if (!h) return fail(GMF_ERR_ARG, "gmf_project_cells: NULL handle");
+    if (n_new < 0 || n_new > (int64_t)INT32_MAX) return fail(GMF_ERR_ARG, "gmf_project_cells: bad n_new");
     if (y_dtype != GMF_Y_INT32 && y_dtype != GMF_Y_UINT16) return fail(GMF_ERR_ARG, "gmf_project_cells: bad y_dtype");
     if (n_steps < 0 || n_steps > 1000) return fail(GMF_ERR_ARG, "gmf_project_cells: n_steps in [0, 1000]");
+    if (n_new == 0) return GMF_OK;  // an empty batch (its pointers may be NULL)
+    if (!Ynew || !U_out || !G_out) return fail(GMF_ERR_ARG, "gmf_project_cells: NULL argument");
+    if (h->p > 0 && !Xnew) return fail(GMF_ERR_ARG, "gmf_project_cells: Xnew is NULL");
     std::string err;
     int rc = gmf_project_run(h, Ynew, y_dtype == GMF_Y_UINT16, n_new, Xnew, offset_new, U_start, n_steps, U_out,
                              G_out, dev_out, (cudaStream_t)stream, &err);

@@ -446,7 +446,9 @@ static cudaError_t backward(gmf_mlp* n, const void* Y, int y16, int64_t ldy, int
 }
 
 extern "C" int gmf_mlp_forward(gmf_mlp* n, const void* Y, int32_t y_dtype, int64_t rows, float* out, void* stream) {
-    if (!n || !Y || !out || rows < 1) return gmf_fail(GMF_ERR_ARG, "gmf_mlp_forward: bad argument");
+    if (!n || rows < 0) return gmf_fail(GMF_ERR_ARG, "gmf_mlp_forward: bad argument");
+    if (rows == 0) return GMF_OK;  // an empty batch (its pointers may be NULL)
+    if (!Y || !out) return gmf_fail(GMF_ERR_ARG, "gmf_mlp_forward: bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     const int y16 = y_dtype == GMF_Y_UINT16;
     const size_t es = y16 ? 2 : 4;

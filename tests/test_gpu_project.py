@@ -193,3 +193,34 @@ def test_tensor_core_projection_from_far_start(gmf, oracle_mod):
     Ug, _, Dg = P.gpu.project_cells(Yd, Xd, od, U0d, n_steps=30)
     assert rel(Ug.cpu().numpy(), Ur) <= 1e-3, rel(Ug.cpu().numpy(), Ur)
     np.testing.assert_allclose(Dg.cpu().numpy(), Dr, rtol=1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_projection_empty_batch_and_single_cell(gmf, oracle_mod, precision):
+    """Degenerate batches: 0 cells is a no-op (empty outputs, no error, nothing
+    read); 1 cell (a CTA with 127 empty rows on the tensor-core path) matches the
+    oracle within the path's bar; the encoder's forward pass of 0 rows too."""
+    from oracle.project import project_cells
+    m = 480
+    P = Pair(gmf, oracle_mod, 500, m, 3, 1, 6, "negbin", 256, 128, zero_frac=0.8, precision=precision)
+    for e in range(2):
+        P.gpu.epoch(P.sigmas[e])
+    params = P.gpu.get_params()
+    Y, X, off, _ = new_cells(P, params, 1, seed=7)
+    Y = np.minimum(Y, 65535).astype(np.uint16)
+    Yd = torch.from_numpy(Y.view(np.int16)).cuda()
+    Xd, od = torch.from_numpy(X).cuda(), torch.from_numpy(off).cuda()
+    U0, G0, D0 = P.gpu.project_cells(Yd[:0], Xd[:0], od[:0], None, n_steps=3)
+    assert U0.shape == (0, 6) and G0.shape == (0, 1) and D0.shape == (0,)
+    st = P.settings
+    Ur, Gr, Dr = project_cells(Y, X, off, params["B"], P.prob.Z.astype(np.float32).astype(np.float64), params["V"],
+                               family="negbin", alpha=params["alpha"], n_steps=3, lam_gamma=st["lambda_"][1],
+                               lam_u=st["lambda_"][2])
+    Ug, Gg, Dg = P.gpu.project_cells(Yd, Xd, od, None, n_steps=3)
+    bar = 2e-3 if precision == "mixed" else 3e-4
+    assert rel(Ug.cpu().numpy(), Ur) <= bar, rel(Ug.cpu().numpy(), Ur)
+    assert rel(Gg.cpu().numpy(), Gr) <= bar
+    np.testing.assert_allclose(Dg.cpu().numpy(), Dr, rtol=1e-4)
+    net = gmf.MLP(m, 32, 16, 6, max_batch=64)
+    out = net.forward(Yd[:0])
+    assert out.shape == (0, 6)
