@@ -35,7 +35,6 @@ constexpr int NT = 256;
 constexpr int CC = 32;     // cells per CTA
 constexpr int GC = 32;     // genes per chunk
 constexpr int FMAX = 32;   // largest q + d
-constexpr int NPMAX = FMAX * (FMAX + 1) / 2;
 constexpr float SLACK = 1e-5f;  // relative slack of the acceptance test
 
 struct ProjArgs {
