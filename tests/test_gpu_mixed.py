@@ -228,3 +228,24 @@ def test_persistent_trace_times_one_launch_per_epoch(gmf):
     mdl.trace(False)
     assert launches == 3 and ms > 0.0
     assert np.isfinite(mdl.deviance())
+
+
+def test_persistent_epoch_equals_cluster_launches_full_size(gmf):
+    """The benchmarked workload (20000 x 2000 NB, 4 clusters of 16 CTAs, 40 sweeps
+    per epoch, every strip waited on across clusters): two epochs as one
+    persistent launch each equal the per-sweep cluster launches bit for bit."""
+    w = synth.WORKLOADS["nb_medium"]
+    prob = synth.workload_problem(w.name, seed=5)
+    start = synth.crude_start(prob, w.d, seed=5)
+    rp, cp = synth.partitions(w.n, w.m, 5)
+    sig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, 2, 5)
+    Yd = torch.from_numpy(prob.Y).cuda()
+    fits = []
+    for flags in (gmf.GMF_FLAG_PERSIST, 0):
+        mdl = gmf.Model(Yd, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row, nb_col=w.nb_col,
+                        row_perm=rp, col_perm=cp, settings=synth.fit_settings(), precision="mixed", flags=flags)
+        for s_ in sig:
+            mdl.epoch(s_)
+        fits.append(mdl)
+    assert fits[0].epoch_mode == "persistent" and fits[1].epoch_mode == "cluster"
+    _assert_same_state(fits[0], fits[1], "nb_medium: persistent vs cluster")

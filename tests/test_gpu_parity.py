@@ -204,7 +204,7 @@ def test_update_y_from_host_and_device(gmf, oracle_mod):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
-@pytest.mark.parametrize("source", ["pinned", "pageable", "unaligned_rows"])
+@pytest.mark.parametrize("source", ["pinned", "pageable", "unaligned_rows", "pinned_int32"])
 def test_streamed_counts_equal_synchronous_updates(gmf, oracle_mod, precision, source):
     """gmf_update_y_async with the next matrix's upload issued before the current
     epoch has run gives the same fit, bit for bit, as gmf_update_y between
@@ -219,13 +219,15 @@ def test_streamed_counts_equal_synchronous_updates(gmf, oracle_mod, precision, s
         if precision == "mixed":
             pytest.skip("the tensor-core layout needs 16-byte rows")
         m = 650
-    extra = dict(y_dtype="uint16", zero_frac=0.85)
+    i32 = source == "pinned_int32"
+    extra = dict(y_dtype="int32" if i32 else "uint16", zero_frac=0.85)
     P = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision=precision, **extra)
     Q = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision=precision, **extra)
     rng = np.random.default_rng(44)
     mats = [np.ascontiguousarray(np.minimum(P.prob.Y.astype(np.int64) + rng.poisson(0.3, P.prob.Y.shape), 65535)
-                                 .astype(np.uint16)) for _ in range(4)]
-    srcs = [torch.from_numpy(Y.view(np.int16)).pin_memory() if source == "pinned" else Y for Y in mats]
+                                 .astype(np.int32 if i32 else np.uint16)) for _ in range(4)]
+    srcs = [torch.from_numpy(Y if i32 else Y.view(np.int16)).pin_memory() if source.startswith("pinned") else Y
+            for Y in mats]
     for e, Y in enumerate(mats):
         P.gpu.update_y(Y)
         P.gpu.epoch(P.sigmas[e])
@@ -236,7 +238,7 @@ def test_streamed_counts_equal_synchronous_updates(gmf, oracle_mod, precision, s
             Q.gpu.update_y_async(srcs[e + 1])   # its upload overlaps this epoch
     torch.cuda.synchronize()
     assert P.gpu.count_buffers == 1
-    assert Q.gpu.count_buffers == {"pinned": 2, "unaligned_rows": 1}.get(source, Q.gpu.count_buffers)
+    assert Q.gpu.count_buffers == {"pinned": 2, "pinned_int32": 2, "unaligned_rows": 1}.get(source, Q.gpu.count_buffers)
     a, b = P.gpu.get_params(), Q.gpu.get_params()
     for k in ("B", "Gamma", "U", "V"):
         np.testing.assert_array_equal(a[k], b[k])
