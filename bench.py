@@ -205,17 +205,28 @@ def sfu_peak_ops(sm_mhz):
 
 
 def host_cpu():
-    """Core count and model of the host that runs the oracle."""
+    """Core count and model of the host that runs the oracle (lscpu's model name,
+    which names Arm cores by their part, else /proc/cpuinfo)."""
     model = "unknown"
     try:
-        with open("/proc/cpuinfo") as fh:
-            for line in fh:
-                k, _, v = line.partition(":")
-                if k.strip() in ("model name", "Model name", "CPU part") and v.strip():
-                    model = v.strip()
-                    break
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                model = v.strip()
+                break
+    except (OSError, subprocess.SubprocessError):
         pass
+    if model == "unknown":
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    k, _, v = line.partition(":")
+                    if k.strip() in ("model name", "Model name", "CPU part") and v.strip():
+                        model = v.strip()
+                        break
+        except OSError:
+            pass
     return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
