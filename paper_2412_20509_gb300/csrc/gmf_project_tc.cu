@@ -254,14 +254,18 @@ __global__ void __launch_bounds__(NTH, 1)
                         const bool valid = cv && (int64_t)kc * GC + j < a.m;
                         const float y =
                             (float)*(const unsigned short*)(sY + sw128_off((uint32_t)cell, (uint32_t)(2 * j)));
-                        float eta = o;
+                        // two interleaved partial sums: half the dependent chain
+                        float eta = o, eta2 = 0.f;
 #pragma unroll
                         for (int k = 0; k < PTC; k++)
                             if (k < a.p) eta = fmaf(xr[k], rj[1 + k], eta);
                         const float* rz = rj + 1 + a.p;
 #pragma unroll
-                        for (int k = 0; k < FTC; k++)
-                            if (k < f) eta = fmaf(th[k], rz[k], eta);
+                        for (int k = 0; k < FTC; k += 2) {
+                            if (k < f) eta2 = fmaf(th[k], rz[k], eta2);
+                            if (k + 1 < f) eta = fmaf(th[k + 1], rz[k + 1], eta);
+                        }
+                        eta += eta2;
                         float ddd = 0.f;
                         if (init) {
                             const float rest = eta - th[0] * rz[0];
