@@ -414,12 +414,23 @@ extern "C" int gmf_update_y_async(gmf_model* h, const void* Y, void* stream) {
     // switches buffers, so work already enqueued on `st` keeps its counts.
     const void* dsrc = h->y_fixed ? nullptr : host_gather_src(h, Y);
     if (dsrc) {
-        if (!h->ybuf[1]) {
-            CUDA_TRY(cudaMalloc(&h->ybuf[1], bytes));
-            CUDA_TRY(cudaEventCreateWithFlags(&h->y_ready, cudaEventDisableTiming));
-            for (int i = 0; i < 2; i++) CUDA_TRY(cudaEventCreateWithFlags(&h->y_free[i], cudaEventDisableTiming));
-            if (gmf_tc_set_ybuf(h, 1, h->ybuf[1]) != GMF_OK)
-                return fail(GMF_ERR_CUDA, "gmf_update_y_async: cuTensorMapEncodeTiled failed for the second buffer");
+        if (!h->ybuf[1]) {  // the second buffer, its events and its TMA descriptor, all or nothing
+            void* buf = nullptr;
+            cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+            bool okb = cudaMalloc(&buf, bytes) == cudaSuccess;
+            for (int i = 0; i < 3 && okb; i++) okb = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+            okb = okb && gmf_tc_set_ybuf(h, 1, buf) == GMF_OK;
+            if (!okb) {
+                for (int i = 0; i < 3; i++)
+                    if (ev[i]) cudaEventDestroy(ev[i]);
+                if (buf) cudaFree(buf);
+                cudaGetLastError();
+                return fail(GMF_ERR_CUDA, "gmf_update_y_async: cannot set up the second count buffer");
+            }
+            h->ybuf[1] = buf;
+            h->y_ready = ev[0];
+            h->y_free[0] = ev[1];
+            h->y_free[1] = ev[2];
         }
         const int nb = h->ycur ^ 1;
         CUDA_TRY(cudaEventRecord(h->y_free[h->ycur], st));          // the current buffer's readers so far
