@@ -639,6 +639,9 @@ def run_rank_sweep(args, w):
         return e0.elapsed_time(e1)
 
     sw = gmf.Sweep(prob.Y, prob.X, prob.Z, prob.offset, starts, RANKS, **kw)
+    t0 = time.perf_counter()
+    group, tune_ms = sw.autotune(sig[0])   # launch grouping timed on one epoch's sweeps, state restored
+    tune_s = time.perf_counter() - t0
     for s in range(args.warmup):
         sw.epoch(sig[s])
     ms_b = timed(lambda: [sw.epoch(sig[args.warmup + s]) for s in range(args.steps)])
@@ -658,7 +661,9 @@ def run_rank_sweep(args, w):
                                   f"of all 8 models", "precision": args.precision},
            "sequential": {"value": work / (ms_s / 1e3), "ms_per_step": ms_s / args.steps},
            "batched_over_sequential": ms_s / ms_b,
-           "deviance_batched_equals_sequential": devs_b == devs_s}
+           "deviance_batched_equals_sequential": devs_b == devs_s,
+           "autotune": {"models_per_launch": group, "epoch_ms_by_models_per_launch": tune_ms,
+                        "seconds": tune_s}}
     if not args.no_cpu_baseline:
         ent_all, t_all, per_rank = 0, 0.0, {}
         for d, st in zip(RANKS, starts):

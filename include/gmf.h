@@ -306,9 +306,22 @@ int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n
  * V0[i] m x d_list[i], alpha0[i]. The counts, weights and partitions are stored
  * once and read by every model. Synchronous.
  * gmf_sweep_epoch -- one epoch of every model (same sigma semantics as
- * gmf_sgd_epoch): one tile launch per sweep covers all models, heaviest first,
- * and one update launch all their strips.
- * Results equal running each model's own gmf_sgd_epoch.
+ * gmf_sgd_epoch): per sweep, the models, heaviest first, go in groups (all of
+ * them by default, see gmf_sweep_set_group); one tile launch covers the models
+ * of a group and one update launch their strips.
+ * Results equal running each model's own gmf_sgd_epoch, whatever the grouping.
+ * gmf_sweep_set_group -- models per launch group: 1..n_models, or 0 for all.
+ *   Errors: GMF_ERR_ARG (outside [0, n_models]).
+ * gmf_sweep_group -- the current group size (n_models when all); -1 for NULL.
+ * gmf_sweep_autotune -- times sweeps [0, n_sweeps) of the epoch defined by
+ *   sigma (1 <= n_sweeps <= S) for the group sizes n_models, ceil(n_models/2),
+ *   ..., 1, each from the same state (the models' parameters, smoothed
+ *   derivatives, visit counts and shapes are saved before and restored after,
+ *   t is not advanced), and keeps the fastest. group_out (host, may be NULL):
+ *   the chosen size; ms_out (host, n_models floats, may be NULL): the time of
+ *   each tried size g at ms_out[g - 1], -1 where not tried. Synchronous; needs
+ *   device memory for one copy of the models' state. Errors: GMF_ERR_ARG,
+ *   GMF_ERR_OOM, GMF_ERR_CUDA.
  * gmf_sweep_model -- the i-th model's handle, owned by the sweep and valid until
  * gmf_sweep_free, for gmf_deviance, gmf_get_params, gmf_orthogonalize, ...
  * (NULL if i is out of range). gmf_update_y is not allowed on models i > 0.
@@ -320,6 +333,10 @@ int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int32_t* d_list
                    const double* const* G0, const double* const* U0, const double* const* V0, const double* alpha0,
                    void* stream);
 int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream);
+int gmf_sweep_set_group(gmf_sweep* s, int32_t group);
+int32_t gmf_sweep_group(const gmf_sweep* s);
+int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_sweeps, int32_t* group_out, float* ms_out,
+                       void* stream);
 gmf_model* gmf_sweep_model(gmf_sweep* s, int32_t i);
 void gmf_sweep_free(gmf_sweep* s);
 

@@ -35,7 +35,8 @@ EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async
            "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
-           "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
+           "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_set_group", "gmf_sweep_group", "gmf_sweep_autotune",
+           "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
            "gmf_mlp_set_params", "gmf_mlp_get_params", "gmf_mlp_get_grads", "gmf_mlp_forward", "gmf_mlp_loss_grad",
            "gmf_mlp_adam", "gmf_mlp_set_precision", "gmf_mlp_train", "gmf_mlp_free", "gmf_free", "gmf_last_error",
            "gmf_version")
@@ -97,6 +98,9 @@ def lib():
         "gmf_sweep_init": (C.c_int, [C.POINTER(VP), C.POINTER(gmf_config), VP, C.c_int32, VP, C.c_int32, C.c_int32, VP,
                                      VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP]),
         "gmf_sweep_epoch": (C.c_int, [VP, VP, VP]),
+        "gmf_sweep_set_group": (C.c_int, [VP, C.c_int32]),
+        "gmf_sweep_group": (C.c_int32, [VP]),
+        "gmf_sweep_autotune": (C.c_int, [VP, VP, C.c_int32, VP, VP, VP]),
         "gmf_sweep_model": (VP, [VP, C.c_int32]),
         "gmf_sweep_free": (None, [VP]),
         "gmf_mlp_create": (C.c_int, [C.POINTER(VP), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, VP]),
@@ -416,6 +420,26 @@ class Sweep:
     def epoch(self, sigma, stream=None):
         sigma = np.ascontiguousarray(sigma, dtype=np.int32)
         check(lib().gmf_sweep_epoch(self._h, sigma.ctypes.data, _stream(stream)))
+
+    @property
+    def group(self):
+        """Models per launch group (see gmf_sweep_set_group)."""
+        return lib().gmf_sweep_group(self._h)
+
+    @group.setter
+    def group(self, g):
+        check(lib().gmf_sweep_set_group(self._h, int(g)))
+
+    def autotune(self, sigma, n_sweeps=None, stream=None):
+        """Time the launch groupings on sweeps of the epoch sigma from the models' current state
+        (restored afterwards) and keep the fastest; returns (group, {group: ms})."""
+        sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+        n_sweeps = len(sigma) if n_sweeps is None else int(n_sweeps)
+        g = C.c_int32()
+        ms = np.empty(len(self.models), dtype=np.float32)
+        check(lib().gmf_sweep_autotune(self._h, sigma.ctypes.data, n_sweeps, C.addressof(g), ms.ctypes.data,
+                                       _stream(stream)))
+        return g.value, {i + 1: float(v) for i, v in enumerate(ms) if v >= 0}
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -1,10 +1,13 @@
 // Batched rank sweep: several GMF fits of different latent rank d on the same
 // count matrix (the model-selection use of Sec. 4.2, where d must be chosen
 // from a grid of fits). Model 0 owns the permuted counts; the others read them.
-// One tile launch per sweep covers every model (grid z = model slot x block;
-// the heaviest models get the lowest slots so their CTAs start first), then one
-// update launch covers every model's strips; a whole epoch of these launches
-// is captured once into a CUDA graph.
+// The models, heaviest first, are split into groups of `group`; per sweep, one
+// tile launch covers every model of a group (grid z = model slot x block, the
+// heaviest models in the lowest slots so their CTAs start first) and one update
+// launch covers their strips; a whole epoch of these launches is captured once
+// into a CUDA graph. gmf_sweep_autotune times the groupings on trial sweeps
+// (the models' state is saved before and restored after) and keeps the
+// fastest; every grouping gives the same results bit for bit.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -26,9 +29,11 @@ cudaError_t gmf_simt_launch_multi(const gmf_model* h0, const StepArgs* d_args, c
 
 struct gmf_sweep {
     std::vector<gmf_model*> models;
-    StepArgs* d_args = nullptr;
-    void* d_lays = nullptr;
-    int* d_order = nullptr;
+    std::vector<int> order;        // model of each slot, heaviest first
+    StepArgs* d_args = nullptr;    // per slot
+    void* d_lays = nullptr;        // per slot (tensor-core layouts)
+    int* d_order = nullptr;        // identity: slot -> its own argument entry
+    int group = 0;                 // models per launch (0: all)
     size_t smem = 0;
     size_t upd_smem = 0;   // update launch: the largest model's staging
     int upd_units = 0;     // update launch: CTAs per model
@@ -85,10 +90,11 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
     std::vector<int> order(n_models);
     for (int i = 0; i < n_models; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s->models[a]->K > s->models[b]->K; });
+    s->order = order;
     std::vector<StepArgs> args(n_models);
     std::vector<char> lays;
-    for (int i = 0; i < n_models; i++) {
-        gmf_model* h = s->models[i];
+    for (int i = 0; i < n_models; i++) {  // in slot order
+        gmf_model* h = s->models[order[i]];
         args[i] = gmf_make_args(h);
         if (s->mixed) {
             gmf_tc_grid(h, &args[i].TI, &args[i].TJ);
@@ -107,7 +113,9 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
         (s->mixed && cudaMalloc(&s->d_lays, lays.size()) != cudaSuccess))
         return sweep_fail(s, GMF_ERR_OOM, "gmf_sweep_init: device allocation failed");
     cudaMemcpyAsync(s->d_args, args.data(), sizeof(StepArgs) * n_models, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s->d_order, order.data(), sizeof(int) * n_models, cudaMemcpyHostToDevice, st);
+    std::vector<int> ident(n_models);
+    for (int i = 0; i < n_models; i++) ident[i] = i;
+    cudaMemcpyAsync(s->d_order, ident.data(), sizeof(int) * n_models, cudaMemcpyHostToDevice, st);
     if (s->mixed) cudaMemcpyAsync(s->d_lays, lays.data(), lays.size(), cudaMemcpyHostToDevice, st);
     const cudaError_t e =
         s->mixed ? gmf_tc_multi_attr(s->models[0], (uint32_t)s->smem) : gmf_simt_multi_attr(s->smem);
@@ -119,13 +127,24 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
     return GMF_OK;
 }
 
-static cudaError_t launch(gmf_sweep* s, int w, cudaStream_t st) {
+// One sweep of every model: per group of slots [g0, g0 + gn), a tile launch and an update launch.
+static cudaError_t launch(gmf_sweep* s, int w, cudaStream_t st, int group) {
     const int nm = (int)s->models.size();
-    const cudaError_t e =
-        s->mixed ? gmf_tc_launch_multi(s->models[0], s->d_args, s->d_lays, s->d_order, nm, (uint32_t)s->smem, w, st)
-                 : gmf_simt_launch_multi(s->models[0], s->d_args, s->d_order, nm, s->smem, w, st);
-    if (e != cudaSuccess) return e;
-    return gmf_launch_update_multi(s->d_args, nm, s->upd_units, s->upd_smem, w, s->mixed ? 128 : GMF_TILE, st);
+    const int gsz = group > 0 ? std::min(group, nm) : nm;
+    const size_t lay_bytes = s->mixed ? gmf_tc_layout_size() : 0;
+    for (int g0 = 0; g0 < nm; g0 += gsz) {
+        const int gn = std::min(gsz, nm - g0);
+        const StepArgs* args = s->d_args + g0;
+        const cudaError_t e =
+            s->mixed ? gmf_tc_launch_multi(s->models[0], args, (const char*)s->d_lays + g0 * lay_bytes, s->d_order, gn,
+                                           (uint32_t)s->smem, w, st)
+                     : gmf_simt_launch_multi(s->models[0], args, s->d_order, gn, s->smem, w, st);
+        if (e != cudaSuccess) return e;
+        const cudaError_t e2 =
+            gmf_launch_update_multi(args, gn, s->upd_units, s->upd_smem, w, s->mixed ? 128 : GMF_TILE, st);
+        if (e2 != cudaSuccess) return e2;
+    }
+    return cudaSuccess;
 }
 
 extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream) {
@@ -149,7 +168,7 @@ extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream)
         if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return gmf_fail(GMF_ERR_CUDA, "gmf_sweep_epoch: capture failed");
         cudaError_t e = cudaSuccess;
-        for (int w = 0; w < h0->nsw && e == cudaSuccess; w++) e = launch(s, w, s->cap);
+        for (int w = 0; w < h0->nsw && e == cudaSuccess; w++) e = launch(s, w, s->cap, s->group);
         const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
         if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&s->graph, g, 0);
         if (g) cudaGraphDestroy(g);
@@ -160,6 +179,121 @@ extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream)
     }
     if (cudaGraphLaunch(s->graph, st) != cudaSuccess) return gmf_fail(GMF_ERR_CUDA, "gmf_sweep_epoch: launch failed");
     for (gmf_model* h : s->models) h->t += (int64_t)h->nsw * h->per;
+    return GMF_OK;
+}
+
+extern "C" int gmf_sweep_set_group(gmf_sweep* s, int32_t group) {
+    if (!s || group < 0 || group > (int32_t)s->models.size())
+        return gmf_fail(GMF_ERR_ARG, "gmf_sweep_set_group: group outside [0, n_models]");
+    if (group != s->group && s->graph) {
+        cudaGraphExecDestroy(s->graph);  // recaptured by the next epoch
+        s->graph = nullptr;
+    }
+    s->group = group;
+    return GMF_OK;
+}
+
+extern "C" int32_t gmf_sweep_group(const gmf_sweep* s) {
+    if (!s) return -1;
+    return s->group > 0 ? s->group : (int32_t)s->models.size();
+}
+
+// The device state a sweep changes, per model: parameters, smoothed derivatives,
+// visit counts and the NB shape.
+static std::vector<std::pair<void*, size_t>> sweep_state(const gmf_sweep* s) {
+    std::vector<std::pair<void*, size_t>> v;
+    for (const gmf_model* h : s->models) {
+        v.push_back({h->L, sizeof(float) * (size_t)h->n * h->KP});
+        v.push_back({h->R, sizeof(float) * (size_t)h->m * h->KP});
+        v.push_back({h->GbR, sizeof(float) * (size_t)h->n * h->fr});
+        v.push_back({h->HbR, sizeof(float) * (size_t)h->n * h->fr});
+        v.push_back({h->GbC, sizeof(float) * (size_t)h->m * h->fc});
+        v.push_back({h->HbC, sizeof(float) * (size_t)h->m * h->fc});
+        v.push_back({h->cntR, sizeof(int) * (size_t)h->n});
+        v.push_back({h->cntC, sizeof(int) * (size_t)h->m});
+        v.push_back({h->alpha, sizeof(float)});
+    }
+    return v;
+}
+
+static cudaError_t copy_state(const std::vector<std::pair<void*, size_t>>& st, char* save, bool to_save,
+                              cudaStream_t stream) {
+    size_t off = 0;
+    for (const auto& b : st) {
+        if (b.second) {
+            const cudaError_t e = to_save ? cudaMemcpyAsync(save + off, b.first, b.second, cudaMemcpyDeviceToDevice, stream)
+                                          : cudaMemcpyAsync(b.first, save + off, b.second, cudaMemcpyDeviceToDevice, stream);
+            if (e != cudaSuccess) return e;
+        }
+        off += (b.second + 255) & ~(size_t)255;
+    }
+    return cudaSuccess;
+}
+
+extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_sweeps, int32_t* group_out,
+                                  float* ms_out, void* stream) {
+    if (!s || !sigma) return gmf_fail(GMF_ERR_ARG, "gmf_sweep_autotune: NULL argument");
+    gmf_model* h0 = s->models[0];
+    const int nm = (int)s->models.size();
+    if (n_sweeps < 1 || n_sweeps > h0->nsw) return gmf_fail(GMF_ERR_ARG, "gmf_sweep_autotune: n_sweeps outside [1, S]");
+    std::vector<char> seen(h0->nsw, 0);
+    for (int w = 0; w < h0->nsw; w++) {
+        if (sigma[w] < 0 || sigma[w] >= h0->nsw || seen[sigma[w]])
+            return gmf_fail(GMF_ERR_ARG, "gmf_sweep_autotune: sigma is not a permutation");
+        seen[sigma[w]] = 1;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (gmf_model* h : s->models) {
+        const int rc = gmf_stage_schedule(h, sigma, 0, h->nsw, st);
+        if (rc) return rc;
+    }
+    const auto state = sweep_state(s);
+    size_t bytes = 0;
+    for (const auto& b : state) bytes += (b.second + 255) & ~(size_t)255;
+    char* save = nullptr;
+    if (cudaMalloc(&save, bytes) != cudaSuccess) return gmf_fail(GMF_ERR_OOM, "gmf_sweep_autotune: no room for the state copy");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = copy_state(state, save, true, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // candidates: all models in one launch, then halved groups down to one model per launch
+    std::vector<int> cand;
+    for (int g = nm;; g = (g + 1) / 2) {
+        cand.push_back(g);
+        if (g == 1) break;
+    }
+    if (ms_out)
+        for (int i = 0; i < nm; i++) ms_out[i] = -1.f;
+    int best = nm;
+    float best_ms = 0.f;
+    for (size_t c = 0; c < cand.size() && e == cudaSuccess; c++) {
+        const int g = cand[c];
+        // one untimed sweep (first use of this launch shape), then the timed sweeps, each from the saved state
+        e = launch(s, 0, st, g);
+        if (e == cudaSuccess) e = copy_state(state, save, false, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int w = 0; w < n_sweeps && e == cudaSuccess; w++) e = launch(s, w, st, g);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = copy_state(state, save, false, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        if (ms_out) ms_out[g - 1] = ms;
+        if (c == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = g;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (e != cudaSuccess)
+        return gmf_fail(GMF_ERR_CUDA, (std::string("gmf_sweep_autotune: ") + cudaGetErrorString(e)).c_str());
+    const int rc = gmf_sweep_set_group(s, best == nm ? 0 : best);
+    if (rc) return rc;
+    if (group_out) *group_out = best;
     return GMF_OK;
 }
 

@@ -63,3 +63,52 @@ def test_sweep_model_matches_oracle(gmf):
         ref.epoch(sig[e])
     assert sw.models[1].deviance() == pytest.approx(ref.deviance(), rel=1e-4)
     assert rel(sw.models[1].get_params()["U"], ref.U) <= 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_sweep_groupings_and_autotune_give_the_same_fits(gmf, precision):
+    """Every launch grouping of the models (all in one launch, groups of 2, one
+    per launch, and a ragged split 3 + 1) gives the same fits bit for bit; the
+    autotuner times the groupings from saved state, restores it (an autotuned
+    sweep then equals one that never ran the trials) and keeps a valid size."""
+    n, m, nbr, nbc = 900, 640, 300, 256
+    d_list = [2, 12, 5, 30]
+    prob = synth.make_problem(n, m, 3, 1, 8, "negbin", seed=11, y_dtype="uint16", zero_frac=0.85, offset=True)
+    starts = [synth.crude_start(prob, d, seed=11 + d) for d in d_list]
+    rp, cp = synth.partitions(n, m, 11)
+    st = synth.fit_settings(alpha_mode=1)
+    sig = synth.sweep_orders(n, m, nbr, nbc, 3, 11)
+    kw = dict(family="negbin", nb_row=nbr, nb_col=nbc, row_perm=rp, col_perm=cp, settings=st, precision=precision)
+
+    def fit(group=None, tune=False):
+        sw = gmf.Sweep(prob.Y, prob.X, prob.Z, prob.offset, starts, d_list, **kw)
+        info = None
+        if tune:
+            info = sw.autotune(sig[0])
+        elif group is not None:
+            sw.group = group
+        for e in range(3):
+            sw.epoch(sig[e])
+        return sw, info
+
+    ref, _ = fit()
+    assert ref.group == len(d_list)
+    for group in (2, 1, 3):
+        sw, _ = fit(group)
+        assert sw.group == group
+        for i in range(len(d_list)):
+            a, b = sw.models[i].get_params(), ref.models[i].get_params()
+            for k in ("U", "V", "B", "Gamma"):
+                np.testing.assert_array_equal(a[k], b[k], err_msg=f"group {group} model {i} {k}")
+            assert a["alpha"] == b["alpha"]
+    sw, (g, times) = fit(tune=True)
+    assert g in (4, 2, 1) and sw.group == g and set(times) == {4, 2, 1} and all(v > 0 for v in times.values())
+    for i in range(len(d_list)):
+        a, b = sw.models[i].get_params(), ref.models[i].get_params()
+        for k in ("U", "V", "B", "Gamma"):
+            np.testing.assert_array_equal(a[k], b[k], err_msg=f"autotuned model {i} {k}")
+        ea, eb = sw.models[i].get_ema(), ref.models[i].get_ema()
+        for k in ("Gb_row", "Hb_row", "Gb_col", "Hb_col", "cnt_row", "cnt_col", "t"):
+            np.testing.assert_array_equal(ea[k], eb[k], err_msg=f"autotuned model {i} {k}")
+    with pytest.raises(gmf.GmfError):
+        sw.group = 5
