@@ -19,7 +19,9 @@
  *   - stream is a cudaStream_t (NULL = legacy default stream). Work is
  *     enqueued on it; functions documented as synchronous wait for it.
  *   - The handle owns all of its device memory. Caller buffers are only read
- *     during the call (or, for outputs, written before a synchronous return).
+ *     during the call (or, for outputs, written before a synchronous return),
+ *     except where a function states otherwise (gmf_update_y_async, and the
+ *     work that asynchronous functions enqueue on their stream).
  *   - A handle must not be used from two host threads at once.
  */
 #ifndef GMF_H
