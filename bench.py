@@ -662,7 +662,9 @@ def run_rank_sweep(args, w):
            "sequential": {"value": work / (ms_s / 1e3), "ms_per_step": ms_s / args.steps},
            "batched_over_sequential": ms_s / ms_b,
            "deviance_batched_equals_sequential": devs_b == devs_s,
-           "autotune": {"models_per_launch": group, "epoch_ms_by_models_per_launch": tune_ms,
+           "autotune": {"models_per_launch": "sequential (each model's own epoch)" if group < 0 else group,
+                        "epoch_ms_by_models_per_launch": {("sequential" if k < 0 else str(k)): v
+                                                          for k, v in tune_ms.items()},
                         "seconds": tune_s}}
     if not args.no_cpu_baseline:
         ent_all, t_all, per_rank = 0, 0.0, {}

@@ -312,23 +312,26 @@ int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n
  * them by default, see gmf_sweep_set_group); one tile launch covers the models
  * of a group and one update launch their strips.
  * Results equal running each model's own gmf_sgd_epoch, whatever the grouping.
- * gmf_sweep_set_group -- models per launch group: 1..n_models, or 0 for all.
- *   Errors: GMF_ERR_ARG (outside [0, n_models]).
- * gmf_sweep_group -- the current group size (n_models when all); -1 for NULL.
+ * gmf_sweep_set_group -- models per launch group: 1..n_models, 0 for all, or
+ *   GMF_SWEEP_SEQUENTIAL: each model's own epoch (gmf_sgd_epoch's launches and
+ *   graph), model after model. Errors: GMF_ERR_ARG (outside [-1, n_models]).
+ * gmf_sweep_group -- the current group size (n_models when all,
+ *   GMF_SWEEP_SEQUENTIAL); -2 for NULL.
  * gmf_sweep_autotune -- times sweeps [0, n_sweeps) of the epoch defined by
  *   sigma (1 <= n_sweeps <= S) for the group sizes n_models, ceil(n_models/2),
- *   ..., 1, each from the same state (the models' parameters, smoothed
- *   derivatives, visit counts and shapes are saved before and restored after,
- *   t is not advanced), and keeps the fastest. group_out (host, may be NULL):
- *   the chosen size; ms_out (host, n_models floats, may be NULL): the time of
- *   each tried size g at ms_out[g - 1], -1 where not tried. Synchronous; needs
- *   device memory for one copy of the models' state. Errors: GMF_ERR_ARG,
- *   GMF_ERR_OOM, GMF_ERR_CUDA.
+ *   ..., 1 and for GMF_SWEEP_SEQUENTIAL, each from the same state (the models'
+ *   parameters, smoothed derivatives, visit counts, shapes and t are saved
+ *   before and restored after), and keeps the fastest. group_out (host, may be
+ *   NULL): the chosen setting; ms_out (host, n_models + 1 floats, may be NULL):
+ *   the time of group size g at ms_out[g - 1] and of the sequential setting at
+ *   ms_out[n_models], -1 where not tried. Synchronous; needs device memory for
+ *   one copy of the models' state. Errors: GMF_ERR_ARG, GMF_ERR_OOM, GMF_ERR_CUDA.
  * gmf_sweep_model -- the i-th model's handle, owned by the sweep and valid until
  * gmf_sweep_free, for gmf_deviance, gmf_get_params, gmf_orthogonalize, ...
  * (NULL if i is out of range). gmf_update_y is not allowed on models i > 0.
  */
 typedef struct gmf_sweep gmf_sweep;
+enum { GMF_SWEEP_SEQUENTIAL = -1 };
 int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int32_t* d_list, int32_t n_models, const void* Y,
                    int32_t y_dtype, int32_t y_on_device, const float* W, const double* X, const double* Z,
                    const double* offset, const int32_t* row_perm, const int32_t* col_perm, const double* const* B0,

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(GMF_THREADS, 3) sweep_kernel(StepArgs a, int w
 }
 
 // Several models sharing the count matrix: blockIdx.z = slot * per + k (see sweep_tc_multi).
-__global__ void __launch_bounds__(GMF_THREADS, 2) sweep_multi(const StepArgs* __restrict__ av,
+__global__ void __launch_bounds__(GMF_THREADS, 3) sweep_multi(const StepArgs* __restrict__ av,
                                                              const int* __restrict__ order, int per, int w) {
     extern __shared__ __align__(16) float smem[];
     __shared__ StepArgs s_a;

@@ -27,13 +27,16 @@ cudaError_t gmf_simt_multi_attr(size_t smem);
 cudaError_t gmf_simt_launch_multi(const gmf_model* h0, const StepArgs* d_args, const int* d_order, int nmodels,
                                   size_t smem, int w, cudaStream_t st);
 
+extern "C" int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begin, int32_t w_end, void* stream);
+
 struct gmf_sweep {
     std::vector<gmf_model*> models;
     std::vector<int> order;        // model of each slot, heaviest first
+    std::vector<size_t> slot_smem; // tile launch shared memory of each slot's model
     StepArgs* d_args = nullptr;    // per slot
     void* d_lays = nullptr;        // per slot (tensor-core layouts)
     int* d_order = nullptr;        // identity: slot -> its own argument entry
-    int group = 0;                 // models per launch (0: all)
+    int group = 0;                 // models per launch (0: all; GMF_SWEEP_SEQUENTIAL: model after model)
     size_t smem = 0;
     size_t upd_smem = 0;   // update launch: the largest model's staging
     int upd_units = 0;     // update launch: CTAs per model
@@ -100,10 +103,11 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
             gmf_tc_grid(h, &args[i].TI, &args[i].TJ);
             const char* l = (const char*)gmf_tc_layout(h);
             lays.insert(lays.end(), l, l + gmf_tc_layout_size());
-            s->smem = std::max<size_t>(s->smem, gmf_tc_smem(h));
+            s->slot_smem.push_back(gmf_tc_smem(h));
         } else {
-            s->smem = std::max(s->smem, gmf_sweep_simt_smem(h));
+            s->slot_smem.push_back(gmf_sweep_simt_smem(h));
         }
+        s->smem = std::max(s->smem, s->slot_smem.back());
         s->upd_smem = std::max(s->upd_smem, gmf_update_smem(args[i]));
     }
     s->upd_units = gmf_update_units(args[0], s->mixed ? 128 : GMF_TILE);
@@ -135,10 +139,13 @@ static cudaError_t launch(gmf_sweep* s, int w, cudaStream_t st, int group) {
     for (int g0 = 0; g0 < nm; g0 += gsz) {
         const int gn = std::min(gsz, nm - g0);
         const StepArgs* args = s->d_args + g0;
+        // the group's own largest tile: small models launched alone keep their occupancy
+        size_t smem = 0;
+        for (int i = g0; i < g0 + gn; i++) smem = std::max(smem, s->slot_smem[i]);
         const cudaError_t e =
             s->mixed ? gmf_tc_launch_multi(s->models[0], args, (const char*)s->d_lays + g0 * lay_bytes, s->d_order, gn,
-                                           (uint32_t)s->smem, w, st)
-                     : gmf_simt_launch_multi(s->models[0], args, s->d_order, gn, s->smem, w, st);
+                                           (uint32_t)smem, w, st)
+                     : gmf_simt_launch_multi(s->models[0], args, s->d_order, gn, smem, w, st);
         if (e != cudaSuccess) return e;
         const cudaError_t e2 =
             gmf_launch_update_multi(args, gn, s->upd_units, s->upd_smem, w, s->mixed ? 128 : GMF_TILE, st);
@@ -156,6 +163,13 @@ extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream)
         if (sigma[w] < 0 || sigma[w] >= h0->nsw || seen[sigma[w]])
             return gmf_fail(GMF_ERR_ARG, "gmf_sweep_epoch: sigma is not a permutation");
         seen[sigma[w]] = 1;
+    }
+    if (s->group == GMF_SWEEP_SEQUENTIAL) {  // each model's own epoch (its single-model launches and graph)
+        for (size_t i = 0; i < s->models.size(); i++) {
+            const int rc = gmf_sgd_sweeps(s->models[s->order[i]], sigma, 0, h0->nsw, stream);
+            if (rc) return rc;
+        }
+        return GMF_OK;
     }
     for (gmf_model* h : s->models) {
         const int rc = gmf_stage_schedule(h, sigma, 0, h->nsw, st);
@@ -183,8 +197,8 @@ extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream)
 }
 
 extern "C" int gmf_sweep_set_group(gmf_sweep* s, int32_t group) {
-    if (!s || group < 0 || group > (int32_t)s->models.size())
-        return gmf_fail(GMF_ERR_ARG, "gmf_sweep_set_group: group outside [0, n_models]");
+    if (!s || group < GMF_SWEEP_SEQUENTIAL || group > (int32_t)s->models.size())
+        return gmf_fail(GMF_ERR_ARG, "gmf_sweep_set_group: group outside [-1, n_models]");
     if (group != s->group && s->graph) {
         cudaGraphExecDestroy(s->graph);  // recaptured by the next epoch
         s->graph = nullptr;
@@ -194,8 +208,8 @@ extern "C" int gmf_sweep_set_group(gmf_sweep* s, int32_t group) {
 }
 
 extern "C" int32_t gmf_sweep_group(const gmf_sweep* s) {
-    if (!s) return -1;
-    return s->group > 0 ? s->group : (int32_t)s->models.size();
+    if (!s) return -2;
+    return s->group != 0 ? s->group : (int32_t)s->models.size();
 }
 
 // The device state a sweep changes, per model: parameters, smoothed derivatives,
@@ -262,24 +276,42 @@ extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_
         cand.push_back(g);
         if (g == 1) break;
     }
+    cand.push_back(GMF_SWEEP_SEQUENTIAL);  // and every model's own launches, model after model
     if (ms_out)
-        for (int i = 0; i < nm; i++) ms_out[i] = -1.f;
+        for (int i = 0; i <= nm; i++) ms_out[i] = -1.f;
+    std::vector<int64_t> t_saved;
+    for (gmf_model* h : s->models) t_saved.push_back(h->t);
+    // one candidate's trial: its launches for sweeps [0, count) of every model
+    auto trial = [&](int g, int count) -> cudaError_t {
+        if (g != GMF_SWEEP_SEQUENTIAL) {
+            cudaError_t r = cudaSuccess;
+            for (int w = 0; w < count && r == cudaSuccess; w++) r = launch(s, w, st, g);
+            return r;
+        }
+        for (int i = 0; i < nm; i++) {
+            gmf_model* h = s->models[s->order[i]];
+            const int rc = gmf_sgd_sweeps(h, sigma, 0, count, st);
+            h->t = t_saved[(size_t)s->order[i]];
+            if (rc) return cudaErrorUnknown;
+        }
+        return cudaSuccess;
+    };
     int best = nm;
     float best_ms = 0.f;
     for (size_t c = 0; c < cand.size() && e == cudaSuccess; c++) {
         const int g = cand[c];
-        // one untimed sweep (first use of this launch shape), then the timed sweeps, each from the saved state
-        e = launch(s, 0, st, g);
+        // one untimed run (first use of this launch shape), then the timed run, each from the saved state
+        e = trial(g, g == GMF_SWEEP_SEQUENTIAL ? n_sweeps : 1);
         if (e == cudaSuccess) e = copy_state(state, save, false, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        for (int w = 0; w < n_sweeps && e == cudaSuccess; w++) e = launch(s, w, st, g);
+        if (e == cudaSuccess) e = trial(g, n_sweeps);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = copy_state(state, save, false, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e != cudaSuccess) break;
-        if (ms_out) ms_out[g - 1] = ms;
+        if (ms_out) ms_out[g == GMF_SWEEP_SEQUENTIAL ? nm : g - 1] = ms;
         if (c == 0 || ms < best_ms) {
             best_ms = ms;
             best = g;
@@ -289,9 +321,10 @@ extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(save);
+    for (int i = 0; i < nm; i++) s->models[i]->t = t_saved[(size_t)i];
     if (e != cudaSuccess)
         return gmf_fail(GMF_ERR_CUDA, (std::string("gmf_sweep_autotune: ") + cudaGetErrorString(e)).c_str());
-    const int rc = gmf_sweep_set_group(s, best == nm ? 0 : best);
+    const int rc = gmf_sweep_set_group(s, best == nm ? 0 : best);  // (GMF_SWEEP_SEQUENTIAL is kept as is)
     if (rc) return rc;
     if (group_out) *group_out = best;
     return GMF_OK;
