@@ -281,6 +281,7 @@ extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_
         for (int i = 0; i <= nm; i++) ms_out[i] = -1.f;
     std::vector<int64_t> t_saved;
     for (gmf_model* h : s->models) t_saved.push_back(h->t);
+    int inner_rc = GMF_OK;  // a failed single-model epoch (its message is kept)
     // one candidate's trial: its launches for sweeps [0, count) of every model
     auto trial = [&](int g, int count) -> cudaError_t {
         if (g != GMF_SWEEP_SEQUENTIAL) {
@@ -292,7 +293,10 @@ extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_
             gmf_model* h = s->models[s->order[i]];
             const int rc = gmf_sgd_sweeps(h, sigma, 0, count, st);
             h->t = t_saved[(size_t)s->order[i]];
-            if (rc) return cudaErrorUnknown;
+            if (rc) {
+                inner_rc = rc;
+                return cudaErrorUnknown;
+            }
         }
         return cudaSuccess;
     };
@@ -322,6 +326,7 @@ extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_
     if (e1) cudaEventDestroy(e1);
     cudaFree(save);
     for (int i = 0; i < nm; i++) s->models[i]->t = t_saved[(size_t)i];
+    if (inner_rc != GMF_OK) return inner_rc;  // gmf_last_error holds the failing call's message
     if (e != cudaSuccess)
         return gmf_fail(GMF_ERR_CUDA, (std::string("gmf_sweep_autotune: ") + cudaGetErrorString(e)).c_str());
     const int rc = gmf_sweep_set_group(s, best == nm ? 0 : best);  // (GMF_SWEEP_SEQUENTIAL is kept as is)
