@@ -50,3 +50,28 @@ def test_clock_sampler_without_a_driver_reports_none():
     c.mark(False)
     out = c.stop()
     assert out["sm_mhz"] is None and out["sm_max_mhz"] is None
+
+
+def test_epoch_algorithmic_matches_the_stated_atlas_figures():
+    """One epoch of nb_atlas (200000 x 5000 uint16, d = 20, p = 3, q = 1, 2048 x
+    1024 blocks: r = 98, s = 5): 1e9 entries, 226 flops per entry, 2 B per count
+    plus 5 visits of every row (4K + 24 fr bytes) and 98 of every column (4K +
+    24 fc bytes) = 2.923 GB."""
+    w = synth.WORKLOADS["nb_atlas"]
+    K, fr, fc = 1 + w.p + w.q + w.d, w.q + w.d, w.p + w.d
+    ent, flops, byts = bench.epoch_algorithmic(w.n, w.m, w.nb_row, w.nb_col, K, fr, fc, 2)
+    assert ent == 10 ** 9 and flops == 226 * 10 ** 9
+    assert byts == 2 * 10 ** 9 + 5 * 200000 * (4 * 25 + 24 * 21) + 98 * 5000 * (4 * 25 + 24 * 23) == 2_923_480_000
+
+
+def test_epoch_algorithmic_equals_the_sum_of_its_sweeps():
+    """The per-epoch bytes equal the sum over an epoch's blocks of the per-block
+    traffic (ragged chunks included), so bytes per sweep = bytes per epoch / sweeps."""
+    n, m, nbr, nbc, K, fr, fc = 4300, 2100, 2048, 1024, 25, 21, 23
+    r, s = -(-n // nbr), -(-m // nbc)
+    tot = 0
+    for a in range(r):
+        for b in range(s):
+            nI, mJ = min(nbr, n - a * nbr), min(nbc, m - b * nbc)
+            tot += nI * mJ * 2 + nI * (4 * K + 24 * fr) + mJ * (4 * K + 24 * fc)
+    assert bench.epoch_algorithmic(n, m, nbr, nbc, K, fr, fc, 2)[2] == tot
