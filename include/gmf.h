@@ -222,6 +222,39 @@ int gmf_sgd_epoch(gmf_model* h, const int32_t* sigma, void* stream);
 int gmf_sgd_sweeps(gmf_model* h, const int32_t* sigma, int32_t w_begin, int32_t w_end, void* stream);
 
 /*
+ * Sharded sweeps (several ranks, each with its own handle and GPU). The s
+ * blocks of one sweep of Algorithm 1 touch disjoint row and column chunks
+ * (Sec. 3.2: their block estimators and local steps commute), so the blocks
+ * of a sweep can run on different ranks. With r >= s a rank that owns column
+ * chunk k runs block k of every sweep: its column chunks' state never moves,
+ * and after each sweep the row chunks the sweep updated are copied to every
+ * other rank (with r < s the roles swap). Done in the sweep order, this gives
+ * every rank the parameters of the single-handle fit bit for bit.
+ *
+ * gmf_sgd_sweep_blocks -- sweep w of the epoch defined by sigma (as
+ *   gmf_sgd_sweeps), restricted to the blocks k listed in `blocks` (host,
+ *   strictly increasing, within [0, per), per = min(r, s); copied before
+ *   return); nblocks = 0 runs nothing. Block k still takes its step factor
+ *   from its place in the sweep, and t advances by per, as if every block had
+ *   run. A pooled NB shape update (alpha_mode 1) needs every block of the sweep
+ *   (GMF_ERR_STATE otherwise). Asynchronous on the stream. Errors: GMF_ERR_ARG,
+ *   GMF_ERR_STATE, GMF_ERR_CUDA.
+ * gmf_chunk_bytes -- bytes of the packed state of row chunk (side 0) or
+ *   column chunk (side 1) `chunk`: rows x (KP + 2 nf + 1) floats, where KP is
+ *   the factor row stride (1+p+q+d rounded up to 4) and nf = q+d (rows) or p+d
+ *   (columns); -1 for a NULL handle or an index out of range.
+ * gmf_chunk_state -- copy that state to (write = 0) or from (write = 1) the
+ *   device buffer buf, row by row in the partition's order: [the augmented
+ *   factor row (L or R, eta = L R') | smoothed gradients | smoothed curvatures
+ *   (eq. 12) | visit count (int32 bits)]. Asynchronous on the stream. Errors:
+ *   GMF_ERR_ARG (NULL pointers, side / chunk out of range), GMF_ERR_CUDA.
+ */
+int gmf_sgd_sweep_blocks(gmf_model* h, const int32_t* sigma, int32_t w, const int32_t* blocks, int32_t nblocks,
+                         void* stream);
+int64_t gmf_chunk_bytes(const gmf_model* h, int32_t side, int32_t chunk);
+int gmf_chunk_state(gmf_model* h, int32_t side, int32_t chunk, void* buf, int32_t write, void* stream);
+
+/*
  * gmf_deviance -- total deviance sum_ij D(y_ij, mu_ij) at the current
  * parameters (Table S1; App. B for NB, with the current shape), each entry in
  * FP32, summed per tile with compensation and combined in FP64.
@@ -409,10 +442,11 @@ int gmf_trace_read(gmf_model* h, double* total_ms, int64_t* launches, void* stre
 
 /*
  * gmf_deviance_noalloc -- the total deviance of gmf_deviance, for callers that
- * cannot allocate device memory: code enqueued while a stream is captured into
- * a CUDA graph (an allocation there breaks or serializes the capture), or a
- * plug-in running inside a framework that owns all device memory through its
- * own pool. The paper has no counterpart; this is a deployment variant of
+ * cannot allocate device memory: a plug-in running inside a framework that
+ * owns all device memory through its own pool (a cudaMalloc of its own would
+ * take memory the framework has already handed out, or is not allowed at
+ * all), or a monitoring call that must not change the memory a long-running
+ * fit sees. The paper has no counterpart; this is a deployment variant of
  * gmf_deviance that needs no handle and allocates nothing.
  *
  *   Y       device, n x m counts (y_dtype GMF_Y_INT32 or GMF_Y_UINT16)
@@ -427,13 +461,30 @@ int gmf_trace_read(gmf_model* h, double* total_ms, int64_t* launches, void* stre
  * library until the process exits), so ceil(n/64) * ceil(m/64) must not exceed
  * 262144; larger sizes return GMF_ERR_ARG. The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture. All calls share the array (each call overwrites
+ * before any stream capture (a failed lookup returns GMF_ERR_CUDA, and
+ * gmf_last_error() gives the CUDA error text). All calls share the array (each call overwrites
  * every slot it reads before reading it): calls that may overlap on the GPU
  * race and must be ordered by the caller (same stream, or events).
  */
 int gmf_deviance_noalloc(const void* Y, int32_t y_dtype, const float* W, int64_t n, int64_t m, const float* L,
                          const float* R, int32_t K, int32_t ld, int32_t family, float alpha, float eta_clamp,
                          double* d_out, void* stream);
+
+/*
+ * gmf_set_wait_limit -- testing hook for the failure detection of the
+ * persistent epoch (GMF_FLAG_PERSIST), whose blocks wait on the global timer
+ * for the earlier visits of their moving strip (gmf_strip_schedule).
+ * limit_ns replaces the 2 s limit of one such wait (0 restores it; at most
+ * 6e10). need_extra (>= 0) is added to every dependency count staged by later
+ * gmf_sgd_epoch / gmf_sgd_sweeps calls: with need_extra > 0 no wait can be
+ * satisfied, so every wait gives up after limit_ns, the launch still runs to
+ * its end (no copy or MMA is left in flight), and the next synchronous call
+ * (gmf_deviance, gmf_get_params) returns GMF_ERR_TIMEOUT. The handle's status
+ * word keeps the flag: make a new handle to go on fitting. Other launch modes
+ * do not wait on strips and ignore both values. The paper has no counterpart.
+ * Errors: GMF_ERR_ARG (NULL handle, values out of range).
+ */
+int gmf_set_wait_limit(gmf_model* h, int64_t limit_ns, int32_t need_extra);
 
 /* Release the handle and all of its device memory (NULL is allowed). */
 void gmf_free(gmf_model* h);

@@ -76,6 +76,8 @@ def lib():
         _lib.gmfo_sgd_epoch.restype = C.c_int
         _lib.gmfo_sgd_sweeps.argtypes = [C.c_void_p] * 4 + [C.c_int64, C.c_int64]
         _lib.gmfo_sgd_sweeps.restype = C.c_int
+        _lib.gmfo_sgd_sweep_blocks.argtypes = [C.c_void_p] * 4 + [C.c_int64, C.c_void_p, C.c_int64]
+        _lib.gmfo_sgd_sweep_blocks.restype = C.c_int
         _lib.gmfo_deviance.argtypes = [C.c_void_p] * 3
         _lib.gmfo_deviance.restype = C.c_double
         _lib.gmfo_eta_entries.argtypes = [C.c_void_p] * 5 + [C.c_int64, C.c_void_p]
@@ -160,6 +162,15 @@ class OracleFit:
                                    sigma.ctypes.data, int(w0), int(w1))
         if rc:
             raise RuntimeError(f"oracle sweeps failed ({rc})")
+
+    def sweep_blocks(self, sigma, w, blocks):
+        """Sweep w restricted to the listed blocks; t advances by the whole sweep."""
+        sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+        b = np.ascontiguousarray(sorted(int(k) for k in blocks), dtype=np.int32)
+        rc = lib().gmfo_sgd_sweep_blocks(C.byref(self.cfg), C.byref(self._data), C.byref(self._state),
+                                         sigma.ctypes.data, int(w), b.ctypes.data, len(b))
+        if rc:
+            raise RuntimeError(f"oracle sweep_blocks failed ({rc})")
 
     def deviance(self):
         return lib().gmfo_deviance(C.byref(self.cfg), C.byref(self._data), C.byref(self._state))

@@ -292,6 +292,38 @@ int gmfo_sgd_sweeps(const gmfo_config* c, const gmfo_data* D, gmfo_state* S, con
     return 0;
 }
 
+/* Sweep w restricted to the listed blocks (strictly increasing indices in
+ * [0, per)), for a fit whose sweeps are split over several ranks: block k
+ * takes global step t_first + k as in the whole sweep, and t ends at
+ * t_first - 1 + per. The pooled NB shape update needs every block of the
+ * sweep (returns -2 for a partial list with alpha_mode 1). */
+int gmfo_sgd_sweep_blocks(const gmfo_config* c, const gmfo_data* D, gmfo_state* S, const int32_t* sigma, int64_t w,
+                          const int32_t* blocks, int64_t nblocks) {
+    const int64_t r = (c->n + c->nb_row - 1) / c->nb_row;
+    const int64_t s = (c->m + c->nb_col - 1) / c->nb_col;
+    const int swap = r < s;
+    const int64_t per = swap ? r : s;
+    if (nblocks == per) return gmfo_sgd_sweeps(c, D, S, sigma, w, w + 1);
+    if (c->family == 1 && c->alpha_mode == 1) return -2;
+    const int64_t t0 = *S->t;
+    double sums[2] = {0.0, 0.0};
+    for (int64_t b = 0; b < nblocks; b++) {
+        const int64_t k = blocks[b];
+        if (k < 0 || k >= per || (b > 0 && k <= blocks[b - 1])) return -1;
+        const int64_t rc = swap ? k : (sigma[w] + k) % r;
+        const int64_t cc = swap ? (sigma[w] + k) % s : k;
+        const int32_t *I, *J;
+        int64_t nI, mJ;
+        chunk(D->row_perm, c->n, c->nb_row, rc, &I, &nI);
+        chunk(D->col_perm, c->m, c->nb_col, cc, &J, &mJ);
+        *S->t = t0 + k;   /* the block step raises it to t0 + k + 1 */
+        int rc2 = gmfo_block_step(c, D, S, I, nI, J, mJ, sums);
+        if (rc2) return rc2;
+    }
+    *S->t = t0 + per;
+    return 0;
+}
+
 /* One epoch of Algorithm 1: all max(r, s) sweeps. */
 int gmfo_sgd_epoch(const gmfo_config* c, const gmfo_data* D, gmfo_state* S, const int32_t* sigma) {
     const int64_t r = (c->n + c->nb_row - 1) / c->nb_row;

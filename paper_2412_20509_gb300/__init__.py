@@ -36,6 +36,7 @@ EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async
            "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
+           "gmf_set_wait_limit", "gmf_sgd_sweep_blocks", "gmf_chunk_bytes", "gmf_chunk_state",
            "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_set_group", "gmf_sweep_group", "gmf_sweep_autotune",
            "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
            "gmf_mlp_set_params", "gmf_mlp_get_params", "gmf_mlp_get_grads", "gmf_mlp_forward", "gmf_mlp_loss_grad",
@@ -92,6 +93,10 @@ def lib():
         "gmf_set_ema": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
         "gmf_orthogonalize": (C.c_int, [VP, C.c_int32, VP]),
         "gmf_project_cells": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, VP, VP, C.c_int32, VP, VP, VP, VP]),
+        "gmf_set_wait_limit": (C.c_int, [VP, C.c_int64, C.c_int32]),
+        "gmf_sgd_sweep_blocks": (C.c_int, [VP, VP, C.c_int32, VP, C.c_int32, VP]),
+        "gmf_chunk_bytes": (C.c_int64, [VP, C.c_int32, C.c_int32]),
+        "gmf_chunk_state": (C.c_int, [VP, C.c_int32, C.c_int32, VP, C.c_int32, VP]),
         "gmf_trace": (C.c_int, [VP, C.c_int32]),
         "gmf_trace_read": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), VP]),
         "gmf_deviance_noalloc": (C.c_int, [VP, C.c_int32, VP, C.c_int64, C.c_int64, VP, VP, C.c_int32, C.c_int32,
@@ -343,6 +348,32 @@ class Model:
     def load_state_dict(self, s):
         self.set_params(s)
         self.set_ema(s)
+
+    def sweep_blocks(self, sigma, w, blocks, stream=None):
+        """Sweep w restricted to the listed blocks (gmf_sgd_sweep_blocks); t advances by the whole sweep."""
+        sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+        b = np.ascontiguousarray(sorted(int(k) for k in blocks), dtype=np.int32)
+        check(lib().gmf_sgd_sweep_blocks(self._h, sigma.ctypes.data, int(w), b.ctypes.data if len(b) else None,
+                                         len(b), _stream(stream)))
+
+    def chunk_floats(self, side, chunk):
+        """Floats of the packed state of row chunk (side 0) or column chunk (side 1)."""
+        nb = lib().gmf_chunk_bytes(self._h, int(side), int(chunk))
+        if nb < 0:
+            raise GmfError(GMF_ERR_ARG, f"chunk {chunk} of side {side} out of range")
+        return nb // 4
+
+    def get_chunk(self, side, chunk, out, stream=None):
+        """Packed state of a chunk into a CUDA float32 tensor of chunk_floats() elements (asynchronous)."""
+        check(lib().gmf_chunk_state(self._h, int(side), int(chunk), out.data_ptr(), 0, _stream(stream)))
+
+    def set_chunk(self, side, chunk, buf, stream=None):
+        """Packed state of a chunk from a CUDA float32 tensor (asynchronous)."""
+        check(lib().gmf_chunk_state(self._h, int(side), int(chunk), buf.data_ptr(), 1, _stream(stream)))
+
+    def set_wait_limit(self, limit_ns=0, need_extra=0):
+        """Testing hook of the persistent epoch's bounded strip waits (gmf_set_wait_limit)."""
+        check(lib().gmf_set_wait_limit(self._h, int(limit_ns), int(need_extra)))
 
     def trace(self, enable=True):
         """Time every block-step launch with CUDA events on its stream."""

@@ -40,8 +40,8 @@ extern "C" const char* gmf_version(void) { return "gmf-gb300 0.1 (sm_103a)"; }
 
 // tensor-core path hooks (gmf_step_tc.cu)
 int gmf_tc_prepare_checked(gmf_model* h, std::string* err);
-cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st);
-cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st);
+cudaError_t gmf_tc_launch(gmf_model* h, const StepArgs& a, int w, cudaStream_t st);
+cudaError_t gmf_tc_launch_update(gmf_model* h, const StepArgs& a, int w, cudaStream_t st);
 int gmf_tc_cluster(const gmf_model* h);
 int gmf_tc_persistent(const gmf_model* h);
 cudaError_t gmf_tc_launch_epoch(gmf_model* h, int w0, int w1, cudaStream_t st);
@@ -55,9 +55,9 @@ static cudaError_t launch_sweep(gmf_model* h, const StepArgs& a, int w, cudaStre
                                 cudaEvent_t t1 = nullptr) {
     const bool mixed = h->cfg.precision == GMF_PREC_MIXED;
     cudaError_t e = t0 ? cudaEventRecord(t0, st) : cudaSuccess;
-    if (e == cudaSuccess) e = mixed ? gmf_tc_launch(h, w, st) : gmf_launch_sweep_simt(h, a, w, st);
+    if (e == cudaSuccess) e = mixed ? gmf_tc_launch(h, a, w, st) : gmf_launch_sweep_simt(h, a, w, st);
     if (e == cudaSuccess && t1) e = cudaEventRecord(t1, st);
-    if (e == cudaSuccess) e = mixed ? gmf_tc_launch_update(h, w, st) : gmf_launch_update(a, w, GMF_TILE, st);
+    if (e == cudaSuccess) e = mixed ? gmf_tc_launch_update(h, a, w, st) : gmf_launch_update(a, w, GMF_TILE, st);
     return e;
 }
 // Algorithm 2 (gmf_orth.cu), per-cell projection (gmf_project.cu)
@@ -147,7 +147,7 @@ static void release(gmf_model* h) {
     }
     void* ptrs[] = {h->Yp, h->Wp, h->ystage2, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
                     h->rperm, h->cperm, h->ystage, h->Rorig, h->kr_buf, h->partR, h->partC, h->nbpart, h->nbctr,
-                    h->sigma, h->rhoc, h->rho1, h->need, h->strip_done, h->err, h->devpart, h->devtot};
+                    h->sigma, h->rhoc, h->rho1, h->need, h->kmap, h->strip_done, h->err, h->devpart, h->devtot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] h->h_rperm;
@@ -324,6 +324,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     INIT_CUDA(dalloc(&h->rhoc, (size_t)h->nsw * h->per));
     INIT_CUDA(dalloc(&h->rho1, (size_t)h->nsw));
     INIT_CUDA(dalloc(&h->need, (size_t)h->nsw * h->per));
+    INIT_CUDA(dalloc(&h->kmap, (size_t)h->per));
     INIT_CUDA(dalloc(&h->strip_done, (size_t)std::max(h->r, h->s)));
     INIT_CUDA(dalloc(&h->err, 1));
     h->devparts = (int)(((c.n + GMF_TILE - 1) / GMF_TILE) * ((c.m + GMF_TILE - 1) / GMF_TILE));
@@ -542,6 +543,8 @@ int gmf_stage_schedule(gmf_model* h, const int32_t* sigma, int w_begin, int w_en
     if (gmf_tc_persistent(h)) {
         std::vector<int32_t> need((size_t)h->nsw * h->per, 0);
         strip_need(h->r, h->s, sigma, w_begin, w_end, need.data() + (size_t)w_begin * h->per);
+        if (h->need_extra > 0)
+            for (size_t i = (size_t)w_begin * h->per; i < (size_t)w_end * h->per; i++) need[i] += h->need_extra;
         CUDA_TRY(cudaMemcpyAsync(h->need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, st));
     }
     return GMF_OK;
@@ -638,6 +641,76 @@ extern "C" int gmf_trace_read(gmf_model* h, double* total_ms, int64_t* launches,
     *launches = h->trace_launches;
     h->trace_ms = 0.0;
     h->trace_launches = 0;
+    return GMF_OK;
+}
+
+extern "C" int gmf_sgd_sweep_blocks(gmf_model* h, const int32_t* sigma, int32_t w, const int32_t* blocks,
+                                    int32_t nblocks, void* stream) {
+    if (!h || !sigma || (nblocks > 0 && !blocks)) return fail(GMF_ERR_ARG, "gmf_sgd_sweep_blocks: NULL argument");
+    if (w < 0 || w >= h->nsw) return fail(GMF_ERR_ARG, "gmf_sgd_sweep_blocks: sweep %d outside [0, %d)", w, h->nsw);
+    if (nblocks < 0 || nblocks > h->per)
+        return fail(GMF_ERR_ARG, "gmf_sgd_sweep_blocks: %d blocks outside [0, %d]", nblocks, h->per);
+    for (int i = 0; i < nblocks; i++)
+        if (blocks[i] < 0 || blocks[i] >= h->per || (i > 0 && blocks[i] <= blocks[i - 1]))
+            return fail(GMF_ERR_ARG, "gmf_sgd_sweep_blocks: blocks must increase within [0, %d)", h->per);
+    if (!is_perm(sigma, h->nsw))
+        return fail(GMF_ERR_ARG, "gmf_sgd_sweep_blocks: sigma is not a permutation of 0..%d", h->nsw - 1);
+    if (h->cfg.family == GMF_NEGBIN && h->cfg.alpha_mode == 1 && nblocks < h->per)
+        return fail(GMF_ERR_STATE, "gmf_sgd_sweep_blocks: the pooled NB shape update needs every block of the sweep");
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        const int rc = gmf_stage_schedule(h, sigma, w, w + 1, st);
+        if (rc) return rc;
+    }
+    if (nblocks > 0) {
+        // a pageable copy of the list: staged before cudaMemcpyAsync returns, whatever memory the caller passed
+        const std::vector<int32_t> kb(blocks, blocks + nblocks);
+        CUDA_TRY(cudaMemcpyAsync(h->kmap, kb.data(), sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice, st));
+        StepArgs a = gmf_make_args(h);
+        a.kmap = h->kmap;
+        a.nk = nblocks;
+        CUDA_TRY(launch_sweep(h, a, w, st));
+    }
+    h->t += h->per;
+    return GMF_OK;
+}
+
+extern "C" int64_t gmf_chunk_bytes(const gmf_model* h, int32_t side, int32_t chunk) {
+    if (!h || (side != 0 && side != 1)) return -1;
+    const int64_t nb = side == 0 ? h->cfg.nb_row : h->cfg.nb_col;
+    const int64_t tot = side == 0 ? h->n : h->m;
+    const int64_t nch = (tot + nb - 1) / nb;
+    if (chunk < 0 || chunk >= nch) return -1;
+    const int64_t rows = std::min(nb, tot - (int64_t)chunk * nb);
+    const int nf = side == 0 ? h->fr : h->fc;
+    return rows * (h->KP + 2 * nf + 1) * (int64_t)sizeof(float);
+}
+
+extern "C" int gmf_chunk_state(gmf_model* h, int32_t side, int32_t chunk, void* buf, int32_t write, void* stream) {
+    if (!h || !buf) return fail(GMF_ERR_ARG, "gmf_chunk_state: NULL argument");
+    if (gmf_chunk_bytes(h, side, chunk) < 0)
+        return fail(GMF_ERR_ARG, "gmf_chunk_state: side %d chunk %d out of range", side, chunk);
+    if (write != 0 && write != 1) return fail(GMF_ERR_ARG, "gmf_chunk_state: write must be 0 or 1");
+    const int64_t nb = side == 0 ? h->cfg.nb_row : h->cfg.nb_col;
+    const int64_t tot = side == 0 ? h->n : h->m;
+    const int64_t first = (int64_t)chunk * nb;
+    const int rows = (int)std::min(nb, tot - first);
+    if (side == 0)
+        CUDA_TRY(gmf_launch_chunk_state(h->L, h->GbR, h->HbR, h->cntR, h->KP, h->fr, first, rows, (float*)buf, write,
+                                        (cudaStream_t)stream));
+    else
+        CUDA_TRY(gmf_launch_chunk_state(h->R, h->GbC, h->HbC, h->cntC, h->KP, h->fc, first, rows, (float*)buf, write,
+                                        (cudaStream_t)stream));
+    return GMF_OK;
+}
+
+extern "C" int gmf_set_wait_limit(gmf_model* h, int64_t limit_ns, int32_t need_extra) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_set_wait_limit: NULL handle");
+    if (limit_ns < 0 || limit_ns > 60000000000ll)
+        return fail(GMF_ERR_ARG, "gmf_set_wait_limit: limit_ns %lld outside [0, 6e10]", (long long)limit_ns);
+    if (need_extra < 0) return fail(GMF_ERR_ARG, "gmf_set_wait_limit: need_extra %d < 0", need_extra);
+    h->wait_ns = limit_ns;
+    h->need_extra = need_extra;
     return GMF_OK;
 }
 

@@ -61,7 +61,13 @@ struct StepArgs {
     const int* need;            // [nsw][per]: earlier visits of each block's moving strip (persistent epochs)
     unsigned* strip_done;       // [max(r, s)]: CTAs done with each moving strip in this launch (persistent epochs)
     unsigned* err;              // device status word
+    unsigned long long wait_ns; // limit of one strip wait of the persistent epoch (global timer)
+    const int* kmap;            // [nk]: the blocks of the sweep that this launch runs (nullptr: all, k = 0..per-1)
+    int nk;                     // blocks this launch runs (grid z of the tile launch)
 };
+
+// Block index of launch slot z (a subset of the sweep's blocks, or all of them).
+__host__ __device__ __forceinline__ int block_of_slot(const StepArgs& a, int z) { return a.kmap ? a.kmap[z] : z; }
 
 struct gmf_model {
     gmf_config cfg;
@@ -111,6 +117,7 @@ struct gmf_model {
     float* rhoc;
     float* rho1;
     int* need;
+    int* kmap;                  // [per]: blocks of a gmf_sgd_sweep_blocks launch
     unsigned* strip_done;
     unsigned* err;
     double* devpart;
@@ -120,6 +127,8 @@ struct gmf_model {
     int32_t* h_rperm;
     int32_t* h_cperm;
     int64_t t;                  // blocks processed so far
+    int64_t wait_ns;            // strip-wait limit of the persistent epoch (gmf_set_wait_limit; 0: 2 s)
+    int32_t need_extra;         // added to every dependency count of a persistent range (gmf_set_wait_limit)
     void* tc;                   // tensor-core path state (gmf_step_tc.cu), or nullptr
     // kernel timing (gmf_trace)
     int trace_on;
@@ -175,6 +184,8 @@ cudaError_t gmf_launch_update(const StepArgs& a, int w, int T, cudaStream_t st);
 cudaError_t gmf_launch_update_multi(const StepArgs* d_args, int nmodels, int units, size_t smem, int w, int T,
                                     cudaStream_t st);
 int gmf_update_units(const StepArgs& a, int T);
+cudaError_t gmf_launch_chunk_state(float* P, float* Gb, float* Hb, int* cnt, int KP, int nf, int64_t first, int rows,
+                                   float* buf, int write, cudaStream_t st);
 size_t gmf_update_smem(const StepArgs& a);
 
 // gmf_api.cu

@@ -1,8 +1,8 @@
 // gmf_deviance_noalloc: the total-deviance kernel in a form that performs no
 // device allocation, for callers that cannot call cudaMalloc -- for example a
 // plug-in hosted by a framework that owns all device memory through its own
-// pool, or code enqueued while a stream is being captured into a CUDA graph,
-// where an allocation would break or serialize the capture.
+// pool, or a monitoring call that must not change the memory a running fit
+// sees.
 //
 // Its per-tile partial sums live in the file-scope array below instead of in a
 // handle's workspace. Every GPU that loads the library holds this array until

@@ -281,7 +281,7 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
 
 __global__ void __launch_bounds__(GMF_THREADS, 3) sweep_kernel(StepArgs a, int w) {
     extern __shared__ __align__(16) float smem[];
-    simt_tile(a, w, blockIdx.z, smem);
+    simt_tile(a, w, block_of_slot(a, blockIdx.z), smem);
 }
 
 // Several models sharing the count matrix: blockIdx.z = slot * per + k (see sweep_tc_multi).
@@ -485,6 +485,9 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.nbpart = h->nbpart;
     a.nbctr = h->nbctr;
     a.sigma = h->sigma;
+    a.wait_ns = h->wait_ns > 0 ? (unsigned long long)h->wait_ns : 2000000000ull;
+    a.kmap = nullptr;
+    a.nk = h->per;
     a.rhoc = h->rhoc;
     a.rho1 = h->rho1;
     a.need = h->need;
@@ -509,7 +512,7 @@ cudaError_t gmf_simt_launch_multi(const gmf_model* h0, const StepArgs* d_args, c
 
 cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaStream_t st) {
     const size_t smem = sweep_smem(h->K, h->fr, h->fc);
-    dim3 grid(h->TJ, h->TI, h->per);
+    dim3 grid(h->TJ, h->TI, a.nk);
     const cudaError_t e = gmf_launch_pdl(sweep_kernel, grid, dim3(GMF_THREADS), smem, st, a, w);
     return e;
 }

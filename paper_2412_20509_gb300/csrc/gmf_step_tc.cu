@@ -5,15 +5,19 @@
 // One CTA per 128 x 128 tile, 16 warps:
 //   1. thread 0 starts the TMA load of the tile's counts (128-byte swizzled
 //      boxes) while all threads build the MMA operands in shared memory:
-//        eta:  A = [L_hi | L_lo | L_hi], B = [R_hi | R_hi | R_lo] (BF16 split of
-//              the FP32 factors, K-concatenated), so one accumulation gives
-//              L_hi R_hi' + L_lo R_hi' + L_hi R_lo' (split-BF16, 3 products);
+//        eta:  A = [L_hi | L_lo], B = [R_hi | R_lo] (BF16 split of the FP32
+//              factors, K-concatenated); one accumulation runs the K chunks of
+//              L_hi R_hi', then L_lo R_hi', then L_hi R_lo' (split-BF16, 3 products);
 //        row side:    B = [Z, V]' and its square, K = tile columns;
 //        column side: B = [X, U]' and its square, K = tile rows;
 //   2. thread 0 issues the eta MMAs (FP32 accumulate in TMEM) and commits;
 //   3. the 16 warps read eta from TMEM (warp w: lanes 32(w%4).., columns
 //      32(w/4)..), compute mu = exp(eta), Ddot, Dddot (Sec. 3) in FP32 and
-//      store them as BF16 into one swizzled tile (over the dead eta operands);
+//      store them as BF16 into swizzled tiles: with 16-bit counts Ddot goes in
+//      place over the count tile (same layout, each thread overwrites the
+//      16 bytes it has just read) and Dddot over the dead eta operands, which
+//      keeps a tile within half of an SM's shared memory (two CTAs per SM);
+//      with 32-bit counts both go over the eta operands;
 //   4. thread 0 issues the contractions: Ddot R_f and Dddot R_f^2 (A = the
 //      tile, K-major) and Ddot' L_f and Dddot' L_f^2 (A = the same tile read
 //      MN-major); warps 0-3 read the row sums, warps 4-7 the column sums, from
@@ -44,11 +48,13 @@ constexpr uint32_t WAIT_POLLS = 1u << 26;
 
 struct TcLayout {
     int KP16;              // K rounded up to 16
-    int KA;                // 128-byte atoms per eta operand row (3*KP16 bf16)
+    int KA;                // 128-byte atoms per eta operand row ([hi | lo]: 2*KP16 bf16)
     int NR, NC;            // contraction widths (q+d, p+d rounded up to 16)
     int JB;                // count columns per TMA box (128 bytes)
     uint32_t y_bytes;      // bytes of the count tile
-    uint32_t off_u;        // union: eta operands, then the Ddot / Dddot tile
+    uint32_t off_u;        // union: eta operands, then the Dddot tile (and Ddot unless it is in the count tile)
+    uint32_t off_dd, off_ddd;  // Ddot and Dddot tiles (2 atoms each)
+    int dd_in_y;           // 1: Ddot overwrites the 16-bit count tile
     uint32_t off_rf, off_rf2, off_lf, off_lf2;
     uint32_t smem;         // dynamic shared memory including alignment slack
     uint32_t tmem_cols, t_row, t_col;
@@ -295,9 +301,9 @@ __device__ __forceinline__ void build_operands(const StepArgs& a, const TcLayout
                         lo[t] = pack_bf16x2(r0, r1);
                     }
 #pragma unroll
-                    for (int seg = 0; seg < 3; seg++) {
-                        // A segments: hi, lo, hi;  B segments: hi, hi, lo
-                        const bool use_lo = isL ? seg == 1 : seg == 2;
+                    for (int seg = 0; seg < 2; seg++) {
+                        // segments of A and of B: hi, lo
+                        const bool use_lo = seg == 1;
                         const int kc = seg * Lo.KP16 + kk0;
                         uint8_t* dst = op + (kc >> 6) * ATOM + sw128_off(r, (kc & 63) * 2);
                         if (use_lo)
@@ -333,16 +339,22 @@ __device__ __forceinline__ void build_operands(const StepArgs& a, const TcLayout
     }
 }
 
-// Thread 0: eta = [L_hi|L_lo|L_hi] [R_hi|R_hi|R_lo]' into TMEM columns [0, 128).
+// Thread 0: eta = L_hi R_hi' + L_lo R_hi' + L_hi R_lo' into TMEM columns [0,
+// 128), from A = [L_hi | L_lo] and B = [R_hi | R_lo] (K chunks of 16 in that order).
+__device__ __forceinline__ uint32_t kchunk_off(int k) {  // element k of a K-major row -> byte offset of its chunk
+    return (uint32_t)(k >> 6) * ATOM + (uint32_t)((k & 63) >> 4) * 32u;
+}
 __device__ __forceinline__ void issue_eta(const TcLayout& Lo, uint8_t* sm, uint32_t tb, uint64_t* bar) {
     const uint8_t* Aop = sm + Lo.off_u;
     const uint8_t* Bop = Aop + Lo.KA * ATOM;
     const uint32_t id = idesc_bf16(TT, TT, 0, 0);
-    const int nks = 3 * Lo.KP16 / 16;
-    for (int ks = 0; ks < nks; ks++) {
-        const uint32_t off = (uint32_t)(ks >> 2) * ATOM + (uint32_t)(ks & 3) * 32u;
-        umma_bf16(tb, sdesc(smem_u32(Aop) + off, 16, 1024, SWIZZLE_128B),
-                  sdesc(smem_u32(Bop) + off, 16, 1024, SWIZZLE_128B), id, ks > 0);
+    const int nkc = Lo.KP16 / 16;
+    for (int pr = 0; pr < 3; pr++) {
+        const int sa = pr == 1 ? Lo.KP16 : 0, sb = pr == 2 ? Lo.KP16 : 0;  // (hi, hi), (lo, hi), (hi, lo)
+        for (int kc = 0; kc < nkc; kc++) {
+            umma_bf16(tb, sdesc(smem_u32(Aop) + kchunk_off(sa + 16 * kc), 16, 1024, SWIZZLE_128B),
+                      sdesc(smem_u32(Bop) + kchunk_off(sb + 16 * kc), 16, 1024, SWIZZLE_128B), id, pr + kc > 0);
+        }
     }
     umma_commit(bar);
 }
@@ -356,8 +368,8 @@ __device__ __forceinline__ void epilogue(const StepArgs& a, const TcLayout& Lo, 
     const bool nb = EPI == EPI_ANY ? a.family == GMF_NEGBIN : EPI == EPI_NB;
     const bool moments = EPI == EPI_ANY && nb && a.alpha_mode == 1;
     const uint8_t* Ys = sm;
-    uint8_t* Dd = sm + Lo.off_u;
-    uint8_t* DDd = Dd + 2 * ATOM;
+    uint8_t* Dd = sm + Lo.off_dd;
+    uint8_t* DDd = sm + Lo.off_ddd;
     const int q = warp & 3, cq = warp >> 2;
     const int i = 32 * q + lane;
     const bool row_ok = i < nr;
@@ -412,8 +424,8 @@ __device__ __forceinline__ void epilogue(const StepArgs& a, const TcLayout& Lo, 
 
 // Thread 0: Ddot R_f, Dddot R_f^2 (row side) and Ddot' L_f, Dddot' L_f^2 (column side).
 __device__ __forceinline__ void issue_contractions(const TcLayout& Lo, uint8_t* sm, uint32_t tb, uint64_t* bar) {
-    const uint8_t* Dd = sm + Lo.off_u;
-    const uint8_t* DDd = Dd + 2 * ATOM;
+    const uint8_t* Dd = sm + Lo.off_dd;
+    const uint8_t* DDd = sm + Lo.off_ddd;
     const uint8_t* RF = sm + Lo.off_rf;
     const uint8_t* RF2 = sm + Lo.off_rf2;
     const uint8_t* LF = sm + Lo.off_lf;
@@ -613,8 +625,6 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
 // written during the launch is read through L2 only. The next block's count
 // tile is loaded while the current block finishes. Results equal the
 // per-sweep launches bit for bit (same phases, same sums in the same order).
-constexpr uint64_t WAIT_NS = 2000000000ull;  // limit of one strip wait
-
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -633,14 +643,15 @@ __device__ __forceinline__ void cluster_arrive_release() {
 }
 
 // One thread: spin until *cnt >= target. Gives up, flagging a time-out, after
-// WAIT_NS or as soon as another CTA has flagged one.
-__device__ __forceinline__ void wait_count(const unsigned* cnt, unsigned target, unsigned* err) {
+// limit_ns of the global timer (2 s unless gmf_set_wait_limit changed it) or as
+// soon as another CTA has flagged one.
+__device__ __forceinline__ void wait_count(const unsigned* cnt, unsigned target, unsigned* err, uint64_t limit_ns) {
     if (ld_acquire_u32(cnt) >= target) return;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (ld_acquire_u32(cnt) >= target) return;
         if (*(volatile unsigned*)err & GMF_DEVERR_TIMEOUT) return;
-        if (global_ns() - t0 > WAIT_NS) {
+        if (global_ns() - t0 > limit_ns) {
             atomicOr(err, GMF_DEVERR_TIMEOUT);
             return;
         }
@@ -711,7 +722,7 @@ __global__ void __launch_bounds__(NTH, 1)
         const ClSlice cls = cl_slice(a, Lo, g, ti, tj, nTI, nTJ);
         const int strip = a.swap ? (int)(g.c0 / a.nb_col) : (int)(g.r0 / a.nb_row);
         cluster_wait();  // the peers finished the previous block: fixed strip written, slots free
-        if (tid == 0 && s_ready != w) wait_count(a.strip_done + strip, need * ncta, a.err);
+        if (tid == 0 && s_ready != w) wait_count(a.strip_done + strip, need * ncta, a.err, a.wait_ns);
         __syncthreads();
         tc_fence_after();
         const int wn = min(w + 1, w1 - 1);  // (the last block loads its own values again)
@@ -789,11 +800,14 @@ __global__ void __launch_bounds__(NTH, 1)
     if (warp == 0) tmem_dealloc(tb, Lo.tmem_cols);
 }
 
+// With 16-bit counts and d up to ~27 a tile takes under half of an SM's shared
+// memory and TMEM, so two CTAs share an SM (one's epilogue runs while the
+// other builds operands or waits for its MMAs): registers are capped to fit.
 template <bool Y16, int EPI>
-__global__ void __launch_bounds__(NTH, 1)
+__global__ void __launch_bounds__(NTH, Y16 ? 2 : 1)
     sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    tc_tile<Y16, false, EPI>(a, Lo, &ymap, w, blockIdx.z, smraw);
+    tc_tile<Y16, false, EPI>(a, Lo, &ymap, w, block_of_slot(a, blockIdx.z), smraw);
 }
 
 // Cluster mode: launched with cluster dimensions (TJ, TI, 1), one cluster per block.
@@ -801,7 +815,7 @@ template <bool Y16, int EPI>
 __global__ void __launch_bounds__(NTH, 1)
     sweep_tc_cluster(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    tc_tile<Y16, true, EPI>(a, Lo, &ymap, w, blockIdx.z, smraw);
+    tc_tile<Y16, true, EPI>(a, Lo, &ymap, w, block_of_slot(a, blockIdx.z), smraw);
 }
 
 // The kernel of a handle: counts type, cluster mode and epilogue variant.
@@ -827,7 +841,7 @@ const void* tc_epoch_fn(int y16, int epi) {
 // settings (so one epilogue variant serves all): blockIdx.z = slot * per + k,
 // slot -> model through `order` (heaviest models first).
 template <bool Y16, int EPI>
-__global__ void __launch_bounds__(NTH, 1) sweep_tc_multi(const StepArgs* __restrict__ av, const TcLayout* __restrict__ lv,
+__global__ void __launch_bounds__(NTH, Y16 ? 2 : 1) sweep_tc_multi(const StepArgs* __restrict__ av, const TcLayout* __restrict__ lv,
                                                          const int* __restrict__ order, int per,
                                                          const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
@@ -900,13 +914,18 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
         delete tc;
         return fail_str(err, "mixed precision supports 1+p+q+d <= 64");
     }
-    L.KA = (3 * L.KP16 + 63) / 64;
+    L.KA = (2 * L.KP16 + 63) / 64;
     L.NR = (std::max(h->fr, 1) + 15) & ~15;
     L.NC = (std::max(h->fc, 1) + 15) & ~15;
     L.JB = 128 / es;
     L.y_bytes = (uint32_t)(TT / L.JB) * ATOM;
     L.off_u = L.y_bytes;
-    const uint32_t size_u = std::max<uint32_t>(2u * L.KA * ATOM, 4u * ATOM);
+    // Ddot in place over 16-bit counts; not in the persistent epoch, which loads
+    // the next block's counts while the contractions still read Ddot
+    L.dd_in_y = (h->y16 && !(h->cfg.flags & GMF_FLAG_PERSIST)) ? 1 : 0;
+    L.off_dd = L.dd_in_y ? 0u : L.off_u;
+    L.off_ddd = L.dd_in_y ? L.off_u : L.off_u + 2u * ATOM;
+    const uint32_t size_u = std::max<uint32_t>(2u * L.KA * ATOM, (L.dd_in_y ? 2u : 4u) * ATOM);
     L.off_rf = L.off_u + size_u;
     L.off_rf2 = L.off_rf + (uint32_t)L.NR * 256u;
     L.off_lf = L.off_rf2 + (uint32_t)L.NR * 256u;
@@ -936,6 +955,10 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
               : h->cfg.family == GMF_NEGBIN ? (h->cfg.alpha_mode == 1 ? EPI_ANY : EPI_NB)
                                             : EPI_PO;
     cudaError_t e = gmf_smem_limit(tc_fn(h->y16, 0, tc->epi), L.smem);
+    // all of the unified L1 / shared array as shared memory: room for two tiles per SM
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_fn(h->y16, 0, tc->epi), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) {
         delete tc;
         if (err) *err = cudaGetErrorString(e);
@@ -1005,17 +1028,18 @@ int tc_cluster_layout(gmf_model* h, TcState* tc) {
 // alpha_mode 1 pools all clusters of a sweep, which this launch never joins.
 int tc_persist_check(gmf_model* h, TcState* tc) {
     if (h->cfg.family == GMF_NEGBIN && h->cfg.alpha_mode == 1) return 0;
+    if (tc->lay.dd_in_y) return 0;  // the next block's count tile would overwrite Ddot
     return cluster_fits(h, tc, tc_epoch_fn(h->y16, tc->epi), tc->lay.smem_cl);
 }
 
 }  // namespace
 
-cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
+cudaError_t gmf_tc_launch(gmf_model* h, const StepArgs& base, int w, cudaStream_t st) {
     TcState* tc = (TcState*)h->tc;
-    StepArgs a = gmf_make_args(h);
+    StepArgs a = base;
     a.TI = tc->TI;
     a.TJ = tc->TJ;
-    dim3 grid(tc->TJ, tc->TI, h->per);
+    dim3 grid(tc->TJ, tc->TI, a.nk);
     if (tc->cluster) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = grid;
@@ -1048,10 +1072,10 @@ cudaError_t gmf_tc_launch(gmf_model* h, int w, cudaStream_t st) {
     return cudaLaunchKernelExC(&cfg, tc_fn(h->y16, 0, tc->epi), args);
 }
 
-cudaError_t gmf_tc_launch_update(gmf_model* h, int w, cudaStream_t st) {
+cudaError_t gmf_tc_launch_update(gmf_model* h, const StepArgs& base, int w, cudaStream_t st) {
     const TcState* tc = (const TcState*)h->tc;
     if (tc->cluster) return cudaSuccess;  // the tile launch did the updates
-    StepArgs a = gmf_make_args(h);
+    StepArgs a = base;
     a.TI = tc->TI;
     a.TJ = tc->TJ;
     return gmf_launch_update(a, w, TT, st);
@@ -1093,7 +1117,11 @@ void gmf_tc_grid(const gmf_model* h, int* TI, int* TJ) {
 }
 
 cudaError_t gmf_tc_multi_attr(const gmf_model* h0, uint32_t smem) {
-    return gmf_smem_limit(tc_multi_fn(h0->y16, ((const TcState*)h0->tc)->epi), smem);
+    const void* fn = tc_multi_fn(h0->y16, ((const TcState*)h0->tc)->epi);
+    cudaError_t e = gmf_smem_limit(fn, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 // One sweep of nmodels models: grid (TJ, TI, nmodels * per), with programmatic

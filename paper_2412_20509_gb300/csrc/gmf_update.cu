@@ -4,6 +4,8 @@
 // complete (griddepcontrol.wait) before it reads the tiles' partials and moment
 // sums; the slice state it loads before that wait is not written by the tile
 // launch.
+#include <algorithm>
+
 #include "gmf_internal.cuh"
 #include "gmf_update.cuh"
 
@@ -29,9 +31,46 @@ __global__ void __launch_bounds__(UPD_NT) update_multi(const StepArgs* __restric
     if (blockIdx.x == 0 && threadIdx.x == 0) nb_shape_update(s_a, w);
 }
 
+// Copy the state of `rows` consecutive rows starting at `first` of one side
+// (row side: L, GbR, HbR, cntR; column side: R, GbC, HbC, cntC) to (write = 0)
+// or from (write = 1) a packed buffer, row by row: [KP factor values | nf
+// smoothed gradients | nf smoothed curvatures | visit count (int32 bits)].
+__global__ void chunk_state_kernel(float* P, float* Gb, float* Hb, int* cnt, int KP, int nf, int64_t first, int rows,
+                                   float* buf, int write) {
+    const int W = KP + 2 * nf + 1;
+    const int64_t total = (int64_t)rows * W;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / W;
+        const int c = (int)(e - i * W);
+        const int64_t g = first + i;
+        float* v;
+        if (c < KP)
+            v = P + g * KP + c;
+        else if (c < KP + nf)
+            v = Gb + g * nf + (c - KP);
+        else if (c < KP + 2 * nf)
+            v = Hb + g * nf + (c - KP - nf);
+        else
+            v = (float*)(cnt + g);
+        if (write)
+            *v = buf[e];
+        else
+            buf[e] = *v;
+    }
+}
+
 }  // namespace
 
-int gmf_update_units(const StepArgs& a, int T) { return update_units(a.per, a.TI, a.TJ, T); }
+cudaError_t gmf_launch_chunk_state(float* P, float* Gb, float* Hb, int* cnt, int KP, int nf, int64_t first, int rows,
+                                   float* buf, int write, cudaStream_t st) {
+    const int64_t total = (int64_t)rows * (KP + 2 * nf + 1);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    if (blocks == 0) return cudaSuccess;
+    chunk_state_kernel<<<blocks, 256, 0, st>>>(P, Gb, Hb, cnt, KP, nf, first, rows, buf, write);
+    return cudaGetLastError();
+}
+
+int gmf_update_units(const StepArgs& a, int T) { return update_units(a.nk, a.TI, a.TJ, T); }
 
 size_t gmf_update_smem(const StepArgs& a) { return sizeof(float) * (size_t)update_stage_floats(a.KP, a.fr, a.fc); }
 

@@ -246,8 +246,9 @@ __host__ __device__ __forceinline__ int update_stage_floats(int KP, int fr, int 
 __device__ __forceinline__ void update_unit(const StepArgs& a, int w, int T, int unit, float* stage) {
     const int nsl = (T + UPD_SR - 1) / UPD_SR;
     const int per_block = (a.TI + a.TJ) * nsl;
-    const int k = unit / per_block;
-    const int rem = unit - k * per_block;
+    const int kz = unit / per_block;
+    const int k = block_of_slot(a, kz);
+    const int rem = unit - kz * per_block;
     const BlockGeo g = block_geo(a, w, k);
     const int nTI = (int)((g.nI + T - 1) / T), nTJ = (int)((g.mJ + T - 1) / T);
     const float rhoc_blk = a.rhoc[w * a.per + k];

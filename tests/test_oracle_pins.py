@@ -332,8 +332,8 @@ def test_orthogonalize_invariants(mode):
     np.testing.assert_allclose(X @ B2.T + G2 @ Z.T + U2 @ V2.T, eta0, atol=1e-10)
     np.testing.assert_allclose(X.T @ G2, 0, atol=1e-10)
     np.testing.assert_allclose(X.T @ U2, 0, atol=1e-10)
-    if mode != "B3":
-        np.testing.assert_allclose(Z.T @ V2, 0, atol=1e-10)
+    # every mode: (B3) whitens and triangularises V by multiplying it on the right, which keeps Z'V = 0
+    np.testing.assert_allclose(Z.T @ V2, 0, atol=1e-10)
     if mode == "B1":
         np.testing.assert_allclose(V2.T @ V2, np.eye(d), atol=1e-10)
         S = U2.T @ U2

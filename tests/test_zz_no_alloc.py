@@ -1,6 +1,6 @@
 """gmf_deviance_noalloc: the deviance for callers that cannot allocate device
-memory (graph-capture regions, plug-ins in frameworks that own the device
-memory). Called through the C ABI twice in a row and checked against the
+memory (plug-ins in frameworks that own all device memory through their own
+pool). Called through the C ABI twice in a row and checked against the
 handle-based gmf_deviance at the deviance tolerance of the other tests (1e-6
 relative: FP32 unit deviances, FP64 total). Collected last on purpose."""
 import ctypes as C
@@ -82,3 +82,68 @@ def test_noalloc_rejects_sizes_beyond_scratch(gmf):
                                         30.0, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert rc == gmf.GMF_ERR_ARG
     assert "262144" in gmf.lib().gmf_last_error().decode()
+
+
+@pytest.mark.parametrize("family,shift,y_mean", [("poisson", 6.0, None), ("negbin", 6.0, None),
+                                                 ("poisson", 29.0, 5.0), ("negbin", 29.0, 5.0)])
+def test_noalloc_large_counts_and_eta_near_the_clamp(gmf, family, shift, y_mean):
+    """Counts far above 256 (beyond the handle kernel's log tables: eta around
+    6, counts around 400) and eta around 29, partly beyond the clamp at 30
+    (small counts, so each term is close to 2 mu): the two deviance kernels and
+    the FP64 oracle agree. Bar 1e-5: exp of an FP32 argument near 30 carries a
+    relative error of about |eta| * 2^-24 ~ 2e-6 in mu, and each term follows it."""
+    import oracle
+    oracle.build()
+    n, m, d = 300, 256, 4
+    prob = synth.make_problem(n, m, 2, 1, d, family, seed=8, offset=True)
+    params = dict(B=prob.B.copy(), Gamma=prob.Gamma.copy(), U=0.5 * prob.U, V=0.5 * prob.V, alpha=2.0)
+    params["B"][:, 0] += shift
+    eta = prob.X @ params["B"].T + params["Gamma"] @ prob.Z.T + params["U"] @ params["V"].T + prob.offset[:, None]
+    rng = np.random.default_rng(8)
+    mean = np.exp(np.clip(eta, -30, 20)) if y_mean is None else np.full(eta.shape, y_mean)
+    prob.Y = rng.poisson(mean).astype(np.int32)
+    if y_mean is None:
+        assert np.median(prob.Y) > 256
+    else:
+        assert eta.max() > 30 > eta.min() > 25
+    rp, cp = synth.partitions(n, m, 8)
+    model = gmf.Model(torch.from_numpy(prob.Y).cuda(), prob.X, prob.Z, prob.offset, params, family=family, nb_row=128,
+                      nb_col=128, row_perm=rp, col_perm=cp, settings=synth.fit_settings())
+    ref = model.deviance()
+    stored = model.get_params()   # the handle's FP32 parameters, as doubles
+    L, R, K = _factors(prob, stored, 8)
+    Yd = torch.from_numpy(prob.Y).cuda()
+    Ld, Rd = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc = gmf.lib().gmf_deviance_noalloc(Yd.data_ptr(), gmf.GMF_Y_INT32, None, n, m, Ld.data_ptr(), Rd.data_ptr(), K, 8,
+                                        gmf.FAMILIES[family], float(stored["alpha"]), 30.0, out.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream)
+    assert rc == gmf.GMF_OK, gmf.lib().gmf_last_error()
+    got = float(out.cpu()[0])
+    orc = oracle.OracleFit(prob.Y, prob.X, prob.Z, prob.offset, stored, family=family, nb_row=128, nb_col=128,
+                           row_perm=rp, col_perm=cp, settings=synth.fit_settings())
+    exact = orc.deviance()
+    assert got == pytest.approx(ref, rel=1e-5)
+    assert got == pytest.approx(exact, rel=1e-5)
+    assert ref == pytest.approx(exact, rel=1e-5)
+
+
+def test_noalloc_takes_no_device_memory(gmf):
+    """Free device memory is the same before and after calls (after the first
+    call on the device, which only looks up the static array's address)."""
+    n, m = 256, 192
+    Y = torch.zeros((n, m), dtype=torch.int32, device="cuda")
+    L = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    R = torch.zeros((m, 4), dtype=torch.float32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    args = (Y.data_ptr(), gmf.GMF_Y_INT32, None, n, m, L.data_ptr(), R.data_ptr(), 1, 4, gmf.GMF_POISSON, 1.0, 30.0,
+            out.data_ptr(), st)
+    assert gmf.lib().gmf_deviance_noalloc(*args) == gmf.GMF_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert gmf.lib().gmf_deviance_noalloc(*args) == gmf.GMF_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert float(out.cpu()[0]) == pytest.approx(2.0 * n * m)   # y = 0, eta = 0: 2 mu per entry
