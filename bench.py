@@ -927,6 +927,56 @@ def run_rank_sweep(args, w):
     return 0
 
 
+def run_select(args, w):
+    """--workload nb_select: rank selection (Sec. 4.2) on the rank-sweep workload's law (50000 x 3000 uint16
+    NB, true d = 10) with 30 % of the entries held out uniformly (Sec. 5.2): the 8 ranks fitted together in
+    the batched sweep (15 epochs, entries marked missing and imputed), then AIC / BIC, the held-out error and
+    relative Poisson deviance of every rank, and the eigenvalue-ratio rank of the d = 50 fit after (B1)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as gmf
+    from paper_2412_20509_gb300 import select
+    prob = synth.workload_problem(w.name, seed=args.seed)
+    obs = synth.holdout_mask(w.n, w.m, 0.3, args.seed)
+    Ym = synth.with_missing(prob.Y, obs)
+    rp, cp = synth.partitions(w.n, w.m, args.seed)
+    starts = [synth.crude_start(prob, d, seed=args.seed) for d in RANKS]
+    sig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, w.epochs, args.seed)
+    kw = dict(family=w.family, nb_row=w.nb_row, nb_col=w.nb_col, row_perm=rp, col_perm=cp,
+              settings=synth.fit_settings(missing=1), precision=args.precision)
+    to_dev = lambda a: torch.from_numpy(a.view(np.int16)).cuda()
+    sw = gmf.Sweep(to_dev(Ym), prob.X, prob.Z, prob.offset, starts, RANKS, **kw)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in sig:
+        sw.epoch(s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fit_ms = e0.elapsed_time(e1)
+    Ytrue = to_dev(prob.Y)
+    t0 = time.perf_counter()
+    sums = [select.fit_summary(mdl, w.family, Ytrue) for mdl in sw.models]
+    sw.models[-1].orthogonalize("B1")
+    spec = select.singular_values(sw.models[-1])
+    pick = select.select_rank(sums, spec)
+    eval_s = time.perf_counter() - t0
+    work = len(RANKS) * w.n * w.m * w.epochs
+    out = {"metric": "rank selection: model x matrix entries/s of the batched fit with 30% held out, and the "
+                     "rank each criterion selects (true d = 10)",
+           "value": work / (fit_ms / 1e3), "unit": "model-entries/s", "n_gpus": 1, "higher_is_better": True,
+           "config": {"workload": f"{w.name}: NB {w.n}x{w.m} uint16 (true d = {w.d}), 30% of the entries held "
+                                  f"out uniformly and marked missing, ranks {RANKS}, {w.epochs} epochs, blocks "
+                                  f"{w.nb_row}x{w.nb_col}", "precision": args.precision,
+                      "data": "synthetic (seeded NB GMF law)"},
+           "fit_ms": fit_ms, "evaluation_s": eval_s, "selected": pick, "per_rank": sums,
+           "spectrum_d50": [float(x) for x in spec]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -954,6 +1004,8 @@ def main():
         return run_rank_sweep(args, w)
     if args.workload == "nb_project":
         return run_projection(args, w)
+    if args.workload == "nb_select":
+        return run_select(args, w)
     if args.warmup < 3:
         raise SystemExit("warm-up must be >= 3 steps")
     ws, rank, local = dist_env()

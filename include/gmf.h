@@ -46,6 +46,7 @@ enum {
 
 enum { GMF_POISSON = 0, GMF_NEGBIN = 1 };          /* log link for both */
 enum { GMF_Y_INT32 = 0, GMF_Y_UINT16 = 1 };        /* count storage type */
+enum { GMF_MISSING_INT32 = -1, GMF_MISSING_UINT16 = 65535 };  /* missing-entry markers (cfg.missing = 1) */
 enum {
     GMF_PREC_FP32 = 0,   /* FP32 on the CUDA cores throughout (reference path) */
     GMF_PREC_MIXED = 1   /* tcgen05 tensor cores: eta as split-BF16 (3 products),
@@ -89,6 +90,10 @@ typedef struct {
                             pooled per sweep */
     int32_t precision;   /* GMF_PREC_FP32 or GMF_PREC_MIXED */
     int32_t flags;       /* GMF_FLAG_* bits; 0 for the defaults */
+    int32_t missing;     /* 1: a count equal to GMF_MISSING_INT32 / GMF_MISSING_UINT16 marks an entry
+                            that is not observed; every block step imputes it with the current mean,
+                            y_ij <- mu_ij (Sec. 3.2), so it adds no score and no deviance but keeps its
+                            Fisher weight. uint16 counts are then at most 65534. [0: all observed] */
     double lambda[4];    /* ridge penalties on (B, Gamma, U, V), eq. 6 [0, 0, 1, 0] */
     double a1, a2;       /* EMA weights of eq. 12 [0.1, 0.01] */
     double k0, k1, tau;  /* rho_t = k0 / (1 + k0 k1 t)^tau (Sec. 3.2) [0.01, 1e-3, 0.75] */
@@ -257,10 +262,41 @@ int gmf_chunk_state(gmf_model* h, int32_t side, int32_t chunk, void* buf, int32_
 /*
  * gmf_deviance -- total deviance sum_ij D(y_ij, mu_ij) at the current
  * parameters (Table S1; App. B for NB, with the current shape), each entry in
- * FP32, summed per tile with compensation and combined in FP64.
+ * FP32, summed per tile with compensation and combined in FP64. Entries marked
+ * missing (cfg.missing = 1) add nothing (D(mu, mu) = 0 after imputation).
  * Synchronous; *out_total is host memory.
  */
 int gmf_deviance(gmf_model* h, double* out_total, void* stream);
+
+/*
+ * gmf_holdout -- out-of-sample reconstruction error of a fit trained with
+ * held-out entries marked missing (cfg.missing = 1), the evaluation of Sec. 5.2.
+ * The held-out set V is the entries marked missing in the fit's counts; Ytrue
+ * (device, n x m counts of the init dtype, the caller's original row and
+ * column order) holds their true values (its other entries are not read).
+ * out (host, 4 doubles): [0] Error = sum_V [log((1+y)/(1+mu))]^2 /
+ * sum_V [log((1+y)/(1+ybar))]^2, [1] Deviance = sum_V D(y, mu) /
+ * sum_V D(y, ybar) with D the Poisson unit deviance (Table S1), ybar the mean of
+ * the observed counts, [2] ybar, [3] |V|; mu = exp(eta) at the current
+ * parameters. FP32 terms, FP64 sums. Synchronous; allocates a few KB of
+ * device workspace on the stream. Errors: GMF_ERR_ARG, GMF_ERR_STATE (no
+ * missing entries, or cfg.missing = 0), GMF_ERR_CUDA, GMF_ERR_OOM.
+ */
+int gmf_holdout(gmf_model* h, const void* Ytrue, double* out, void* stream);
+
+/*
+ * gmf_loglik -- the log-likelihood and the Pearson statistic of the observed
+ * entries at the current parameters, for information criteria (AIC, BIC:
+ * Sec. 4.2) and the Pearson dispersion estimate (App. B, "Unknown dispersion
+ * parameter"). out (host, 3 doubles): [0] sum_ij w_ij log f(y_ij; mu_ij) with
+ * the full densities of Table S1's Poisson and negative binomial laws (log-gamma
+ * terms included; NB with the current shape), [1] sum_ij w_ij (y_ij - mu_ij)^2 /
+ * nu(mu_ij), [2] the number of observed entries. Entries marked missing are
+ * left out. FP32 terms (lgammaf), FP64 sums. Synchronous; allocates a few KB
+ * of device workspace on the stream. Errors: GMF_ERR_ARG, GMF_ERR_CUDA,
+ * GMF_ERR_OOM.
+ */
+int gmf_loglik(gmf_model* h, double* out, void* stream);
 
 /* As gmf_deviance, but writes the FP64 total to device memory d_out and does not synchronize. */
 int gmf_deviance_async(gmf_model* h, double* d_out, void* stream);

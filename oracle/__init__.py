@@ -40,7 +40,8 @@ def build(force=False):
 class _Config(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("p", C.c_int32), ("q", C.c_int32),
                 ("d", C.c_int32), ("family", C.c_int32), ("nb_row", C.c_int32), ("nb_col", C.c_int32),
-                ("bias_corr", C.c_int32), ("alpha_mode", C.c_int32), ("lambda_", C.c_double * 4),
+                ("bias_corr", C.c_int32), ("alpha_mode", C.c_int32), ("missing", C.c_int32),
+                ("lambda_", C.c_double * 4),
                 ("a1", C.c_double), ("a2", C.c_double), ("k0", C.c_double), ("k1", C.c_double),
                 ("tau", C.c_double), ("damping", C.c_double), ("eps", C.c_double),
                 ("eta_clamp", C.c_double)]
@@ -137,7 +138,8 @@ class OracleFit:
         s = settings
         self.cfg = _Config(n=n, m=m, p=p, q=q, d=d, family=FAMILIES[family] if isinstance(family, str) else int(family),
                            nb_row=int(nb_row), nb_col=int(nb_col), bias_corr=int(s["bias_corr"]),
-                           alpha_mode=int(s["alpha_mode"]), lambda_=(C.c_double * 4)(*s["lambda_"]),
+                           alpha_mode=int(s["alpha_mode"]), missing=int(s.get("missing", 0)),
+                           lambda_=(C.c_double * 4)(*s["lambda_"]),
                            a1=s["a1"], a2=s["a2"], k0=s["k0"], k1=s["k1"], tau=s["tau"],
                            damping=s["damping"], eps=s["eps"], eta_clamp=s["eta_clamp"])
         self._data = _Data(Y=self.Y.ctypes.data, y_dtype=0 if self.Y.dtype == np.int32 else 1,

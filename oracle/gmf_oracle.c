@@ -35,6 +35,11 @@
  *     skipped when the denominator is not positive.
  *   - eta is clamped to [-eta_clamp, eta_clamp] before the inverse link.
  *   - phi = 1 (Poisson and NB have no free dispersion in this model).
+ *   - Missing entries (missing = 1): a count equal to the sentinel (-1 for
+ *     int32 counts, 65535 for uint16) is not observed. As Sec. 3.2 prescribes
+ *     for an incomplete matrix, each block step first imputes it with the
+ *     current prediction, y_ij <- mu_ij, so its score term is zero and its
+ *     Fisher weight stays; it adds nothing to the deviance (D(mu, mu) = 0).
  */
 #include <math.h>
 #include <stdint.h>
@@ -48,6 +53,7 @@ typedef struct {
     int32_t nb_row, nb_col;
     int32_t bias_corr;  /* 0 printed formula, 1 per-visit */
     int32_t alpha_mode; /* 0 fixed NB shape, 1 stochastic moment estimator */
+    int32_t missing;    /* 1: the sentinel count marks a missing entry (imputed by mu, Sec. 3.2) */
     double lambda[4];   /* penalties on B, Gamma, U, V */
     double a1, a2;      /* EMA weights of eq. 12 */
     double k0, k1, tau; /* learning-rate schedule */
@@ -85,6 +91,13 @@ typedef struct {
 static double y_at(const gmfo_data* D, int64_t m, int64_t i, int64_t j) {
     if (D->y_dtype == 0) return (double)((const int32_t*)D->Y)[i * m + j];
     return (double)((const uint16_t*)D->Y)[i * m + j];
+}
+
+/* Entry (i, j) is missing: missing values are on and the count is the sentinel. */
+static int missing_at(const gmfo_config* c, const gmfo_data* D, int64_t i, int64_t j) {
+    if (!c->missing) return 0;
+    if (D->y_dtype == 0) return ((const int32_t*)D->Y)[i * c->m + j] == -1;
+    return ((const uint16_t*)D->Y)[i * c->m + j] == 65535;
 }
 
 static double w_at(const gmfo_data* D, int64_t m, int64_t i, int64_t j) {
@@ -156,8 +169,10 @@ int gmfo_block_grad(const gmfo_config* c, const gmfo_data* D, const gmfo_state* 
         for (int64_t b = 0; b < mJ; b++) {
             const int64_t j = J[b];
             double mu, dd, ddd;
-            const double y = y_at(D, m, i, j), w = w_at(D, m, i, j);
-            gmfo_entry(c->family, y, eta_at(c, D, S, i, j), w, alpha, c->eta_clamp, &mu, &dd, &ddd);
+            const double eta = eta_at(c, D, S, i, j), w = w_at(D, m, i, j);
+            double y = y_at(D, m, i, j);
+            if (missing_at(c, D, i, j)) gmfo_entry(c->family, 0.0, eta, w, alpha, c->eta_clamp, &y, NULL, NULL);
+            gmfo_entry(c->family, y, eta, w, alpha, c->eta_clamp, &mu, &dd, &ddd);
             if (nb_sums) {
                 nb_sums[0] += w * mu * mu;
                 nb_sums[1] += w * ((y - mu) * (y - mu) - mu);
@@ -337,6 +352,7 @@ double gmfo_deviance(const gmfo_config* c, const gmfo_data* D, const gmfo_state*
     for (int64_t i = 0; i < c->n; i++) {
         for (int64_t j = 0; j < c->m; j++) {
             double mu;
+            if (missing_at(c, D, i, j)) continue;   /* y <- mu: D(mu, mu) = 0 */
             gmfo_entry(c->family, 0.0, eta_at(c, D, S, i, j), 1.0, *S->alpha, c->eta_clamp, &mu, NULL, NULL);
             total += gmfo_entry_deviance(c->family, y_at(D, c->m, i, j), mu, w_at(D, c->m, i, j), *S->alpha);
         }

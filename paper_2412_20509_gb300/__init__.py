@@ -36,7 +36,8 @@ EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async
            "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
-           "gmf_set_wait_limit", "gmf_sgd_sweep_blocks", "gmf_chunk_bytes", "gmf_chunk_state",
+           "gmf_set_wait_limit", "gmf_sgd_sweep_blocks", "gmf_chunk_bytes", "gmf_chunk_state", "gmf_holdout",
+           "gmf_loglik",
            "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_set_group", "gmf_sweep_group", "gmf_sweep_autotune",
            "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
            "gmf_mlp_set_params", "gmf_mlp_get_params", "gmf_mlp_get_grads", "gmf_mlp_forward", "gmf_mlp_loss_grad",
@@ -53,7 +54,7 @@ class GmfError(RuntimeError):
 class gmf_config(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("p", C.c_int32), ("q", C.c_int32), ("d", C.c_int32),
                 ("family", C.c_int32), ("nb_row", C.c_int32), ("nb_col", C.c_int32), ("bias_corr", C.c_int32),
-                ("alpha_mode", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32),
+                ("alpha_mode", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32), ("missing", C.c_int32),
                 ("lambda_", C.c_double * 4), ("a1", C.c_double), ("a2", C.c_double), ("k0", C.c_double),
                 ("k1", C.c_double), ("tau", C.c_double), ("damping", C.c_double), ("eps", C.c_double),
                 ("eta_clamp", C.c_double)]
@@ -87,6 +88,8 @@ def lib():
         "gmf_sgd_sweeps": (C.c_int, [VP, VP, C.c_int32, C.c_int32, VP]),
         "gmf_deviance": (C.c_int, [VP, C.POINTER(C.c_double), VP]),
         "gmf_deviance_async": (C.c_int, [VP, VP, VP]),
+        "gmf_holdout": (C.c_int, [VP, VP, VP, VP]),
+        "gmf_loglik": (C.c_int, [VP, VP, VP]),
         "gmf_get_params": (C.c_int, [VP, VP, VP, VP, VP, VP, VP]),
         "gmf_set_params": (C.c_int, [VP, VP, VP, VP, VP, VP, VP]),
         "gmf_get_ema": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
@@ -182,6 +185,7 @@ def make_config(n, m, p, q, d, family, nb_row, nb_col, settings, precision="fp32
         setattr(cfg, k, float(s[k]))
     cfg.bias_corr = int(s["bias_corr"])
     cfg.alpha_mode = int(s["alpha_mode"])
+    cfg.missing = int(s.get("missing", 0))
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     cfg.flags = int(flags)
     return cfg
@@ -299,6 +303,19 @@ class Model:
         out = C.c_double()
         check(lib().gmf_deviance(self._h, C.byref(out), _stream(stream)))
         return out.value
+
+    def holdout(self, Ytrue, stream=None):
+        """Out-of-sample error and relative Poisson deviance on the entries marked missing (gmf_holdout);
+        Ytrue: CUDA tensor of the complete counts in the caller's order (int32, or 16-bit counts)."""
+        out = (C.c_double * 4)()
+        check(lib().gmf_holdout(self._h, Ytrue.data_ptr(), out, _stream(stream)))
+        return {"error": out[0], "deviance": out[1], "ybar": out[2], "n_heldout": int(out[3])}
+
+    def loglik(self, stream=None):
+        """Log-likelihood, Pearson statistic and observed-entry count at the current parameters (gmf_loglik)."""
+        out = (C.c_double * 3)()
+        check(lib().gmf_loglik(self._h, out, _stream(stream)))
+        return {"loglik": out[0], "pearson": out[1], "n_obs": int(out[2])}
 
     def deviance_async(self, out, stream=None):
         """Write the FP64 deviance into a 1-element CUDA float64 tensor."""

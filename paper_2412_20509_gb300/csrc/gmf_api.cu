@@ -246,6 +246,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     if (c.precision != GMF_PREC_FP32 && c.precision != GMF_PREC_MIXED)
         return fail(GMF_ERR_ARG, "gmf_init: unknown precision");
     if (c.flags & ~(GMF_FLAG_NO_CLUSTER | GMF_FLAG_PERSIST)) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
+    if (c.missing != 0 && c.missing != 1) return fail(GMF_ERR_ARG, "gmf_init: missing must be 0 or 1");
     if (!(c.a1 > 0 && c.a1 <= 1 && c.a2 > 0 && c.a2 <= 1)) return fail(GMF_ERR_ARG, "gmf_init: a1, a2 in (0, 1]");
     if (!(c.k0 > 0) || c.k1 < 0 || !(c.tau > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad learning-rate schedule");
     if (c.damping < 0 || !(c.eta_clamp > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad damping or eta_clamp");
@@ -733,6 +734,28 @@ extern "C" int gmf_deviance_async(gmf_model* h, double* d_out, void* stream) {
     if (!h || !d_out) return fail(GMF_ERR_ARG, "gmf_deviance_async: NULL argument");
     CUDA_TRY(gmf_launch_deviance(h, d_out, (cudaStream_t)stream));
     return GMF_OK;
+}
+
+int gmf_holdout_run(gmf_model* h, const void* Ytrue, double* out, cudaStream_t st, const char** why);
+int gmf_loglik_run(gmf_model* h, double* out, cudaStream_t st, const char** why);
+
+extern "C" int gmf_loglik(gmf_model* h, double* out, void* stream) {
+    if (!h || !out) return fail(GMF_ERR_ARG, "gmf_loglik: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const char* why = "";
+    const int rc = gmf_loglik_run(h, out, st, &why);
+    if (rc) return fail(rc, "gmf_loglik: %s", why);
+    return check_err_word(h, st);
+}
+
+extern "C" int gmf_holdout(gmf_model* h, const void* Ytrue, double* out, void* stream) {
+    if (!h || !Ytrue || !out) return fail(GMF_ERR_ARG, "gmf_holdout: NULL argument");
+    if (!h->cfg.missing) return fail(GMF_ERR_STATE, "gmf_holdout: the fit has no missing entries (cfg.missing = 0)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const char* why = "";
+    const int rc = gmf_holdout_run(h, Ytrue, out, st, &why);
+    if (rc) return fail(rc, "gmf_holdout: %s", why);
+    return check_err_word(h, st);
 }
 
 extern "C" int gmf_deviance(gmf_model* h, double* out_total, void* stream) {

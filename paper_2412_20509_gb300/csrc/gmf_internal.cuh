@@ -37,6 +37,8 @@ struct StepArgs {
     int nb_row, nb_col, r, s, per, swap;
     int TI, TJ;                 // tiles per block along rows / columns (largest block)
     int family, bias_corr, alpha_mode;
+    int missing;                // 1: a count equal to ymiss is not observed (imputed by mu, Sec. 3.2)
+    float ymiss;                // the missing-count marker as a float: -1 (int32), 65535 (uint16)
     float lam[4];
     float a1, a2, damping, eps, clamp;
     const void* Y;              // Yp (permuted)

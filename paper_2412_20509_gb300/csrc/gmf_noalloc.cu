@@ -23,18 +23,11 @@ constexpr int NT = 256;
 constexpr int T = 64;
 constexpr int LDS = T + 4;
 
-// Unit deviance 2w[...] (Table S1; App. B for the negative binomial) in FP32,
-// arranged so that no difference of two large logarithms appears.
+// Unit deviance / 2w (Table S1; App. B for the negative binomial) in FP32:
+// the shared ratio form for a positive count (no difference of two large
+// logarithms), alpha log1p(mu/alpha) or mu for a zero count.
 __device__ __forceinline__ float unit_dev(bool nb, float y, float e, float mu, float alpha) {
-    if (y > 0.f) {
-        const float r1 = (y - mu) / mu;
-        const float l1 = fabsf(r1) < 0.5f ? log1pf(r1) : logf(y) - e;
-        if (!nb) return y * l1 - (y - mu);
-        const float r2 = (y - mu) / (mu + alpha);
-        const float lma = mu > alpha ? e + log1pf(alpha / mu) : logf(alpha) + log1pf(mu / alpha);
-        const float l2 = fabsf(r2) < 0.5f ? log1pf(r2) : logf(y + alpha) - lma;
-        return y * l1 - (y + alpha) * l2;
-    }
+    if (y > 0.f) return gmfdev::half_dev_ratio(nb, y, e, mu, alpha);
     return nb ? alpha * log1pf(mu / alpha) : mu;
 }
 

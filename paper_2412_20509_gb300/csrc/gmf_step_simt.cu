@@ -252,9 +252,11 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
             for (int v = 0; v < 4; v++) {
                 dd[v] = ddd[v] = 0.f;
                 if (v < valid) {
-                    const float y = yv[u][v], w8 = wv[u][v];
+                    const float w8 = wv[u][v];
                     const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
                     const float mu = expf(e);
+                    // an unobserved entry is imputed by the current mean (Sec. 3.2)
+                    const float y = (a.missing && yv[u][v] == a.ymiss) ? mu : yv[u][v];
                     const float f = nb ? alpha / (alpha + mu) : 1.f;
                     dd[v] = w8 * (y - mu) * f;
                     ddd[v] = w8 * mu * f;
@@ -299,9 +301,17 @@ __global__ void __launch_bounds__(GMF_THREADS, 3) sweep_multi(const StepArgs* __
 //   NB       y (log y - eta) - (y + a)(log(y + a) - log a - log1p(mu / a)),
 // the y log y term zero at y = 0, so a zero count (most entries) is exactly a log1p(mu / a). log y and
 // log(y + a) come from per-CTA tables for y < 256. Near mu = y the logarithms cancel: the rounding is
-// ~6e-8 (y + a) log(y + a) per entry, ~1e-7 of a whole matrix's deviance.
+// ~6e-8 (y + a) log(y + a) per entry, ~1e-7 of a whole matrix's deviance. The form takes log mu = eta
+// but mu itself from exp(eta), so an error in mu enters at first order (as mu times its relative error):
+// mu comes from the accurate expf, whose error is a fraction of an ulp without a common sign. (The fast
+// exponential scales eta by a rounded log2(e) and carries a relative bias of ~1e-8 |eta|, which at
+// counts of a few hundred moved whole-matrix deviances by 4e-5.) Counts of 32 and more take the ratio
+// form instead (half_dev_ratio: log1p of the relative residual), which keeps y log(y/mu) - (y - mu)
+// accurate when y and mu are large and close; they are rare in count data, so the branch seldom
+// splits a warp.
 __device__ __forceinline__ float half_dev_tab(bool nb, float y, float e, float mu, float alpha, float la,
                                               const float* tlog, const float* tloga) {
+    if (y >= 32.f) return half_dev_ratio(nb, y, e, mu, alpha);
     const int yi = (int)y;
     float ly, lya;
     if (yi < 256) {
@@ -363,10 +373,10 @@ __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, doubl
         load_y4(a.Y, a.y16, idx, vec, valid, y);
 #pragma unroll
         for (int v = 0; v < 4; v++) {
-            if (v < valid) {
+            if (v < valid && !(a.missing && y[v] == a.ymiss)) {   // y <- mu: D(mu, mu) = 0
                 const float wv = a.W ? __ldg(a.W + idx + v) : 1.f;
                 const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
-                const float dv = 2.f * wv * half_dev_tab(nb, y[v], e, __expf(e), alpha, la, tlog, tloga);
+                const float dv = 2.f * wv * half_dev_tab(nb, y[v], e, expf(e), alpha, la, tlog, tloga);
                 const float yk = dv - comp;
                 const float tk = sum + yk;
                 comp = (tk - sum) - yk;
@@ -462,6 +472,8 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.family = c.family;
     a.bias_corr = c.bias_corr;
     a.alpha_mode = c.alpha_mode;
+    a.missing = c.missing;
+    a.ymiss = h->y16 ? 65535.f : -1.f;
     for (int i = 0; i < 4; i++) a.lam[i] = (float)c.lambda[i];
     a.a1 = (float)c.a1;
     a.a2 = (float)c.a2;

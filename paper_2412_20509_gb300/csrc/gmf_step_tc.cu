@@ -405,6 +405,7 @@ __device__ __forceinline__ void epilogue(const StepArgs& a, const TcLayout& Lo, 
             const float wv = (Wrow && valid) ? __ldg(Wrow + j) : 1.f;
             const float e = fminf(fmaxf(__uint_as_float(ev[8 * gq + t]), -a.clamp), a.clamp);
             const float mu = __expf(e);
+            if (EPI == EPI_ANY && a.missing && y[t] == a.ymiss) y[t] = mu;  // imputation y <- mu (Sec. 3.2)
             const float f = nb ? __fdividef(alpha, alpha + mu) : 1.f;
             const float wf = valid ? wv * f : 0.f;
             dd[t] = wf * (y[t] - mu);
@@ -951,7 +952,7 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
         if (err) *err = "cuTensorMapEncodeTiled failed for the count matrix";
         return GMF_ERR_CUDA;
     }
-    tc->epi = h->Wp ? EPI_ANY
+    tc->epi = (h->Wp || h->cfg.missing) ? EPI_ANY
               : h->cfg.family == GMF_NEGBIN ? (h->cfg.alpha_mode == 1 ? EPI_ANY : EPI_NB)
                                             : EPI_PO;
     cudaError_t e = gmf_smem_limit(tc_fn(h->y16, 0, tc->epi), L.smem);

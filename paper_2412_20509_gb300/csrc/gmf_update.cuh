@@ -65,6 +65,22 @@ __device__ __forceinline__ float bias_visit(float a1, float a2, int visits) {
     return (1.f - expf(k * log1pf(-a2))) / (1.f - expf(k * log1pf(-a1)));
 }
 
+// Half unit deviance D(y, mu) / 2w (Table S1; App. B for the negative
+// binomial) in FP32 for a positive count, written so that no difference of
+// two large logarithms appears: with r1 = (y - mu)/mu and r2 = (y - mu)/(mu +
+// alpha), log(y/mu) = log1p(r1) and log((y + alpha)/(mu + alpha)) = log1p(r2)
+// while |r| < 1/2, which keeps y log(y/mu) - (y - mu) accurate when y and mu
+// are large and close. e = log mu (the clamped eta).
+__device__ __forceinline__ float half_dev_ratio(bool nb, float y, float e, float mu, float alpha) {
+    const float r1 = (y - mu) / mu;
+    const float l1 = fabsf(r1) < 0.5f ? log1pf(r1) : logf(y) - e;
+    if (!nb) return y * l1 - (y - mu);
+    const float r2 = (y - mu) / (mu + alpha);
+    const float lma = mu > alpha ? e + log1pf(alpha / mu) : logf(alpha) + log1pf(mu / alpha);
+    const float l2 = fabsf(r2) < 0.5f ? log1pf(r2) : logf(y + alpha) - lma;
+    return y * l1 - (y + alpha) * l2;
+}
+
 // Smoothed local step of eq. 12 / eq. 14 for one free parameter.
 __device__ __forceinline__ void smoothed_step(float& theta, float& gbar, float& hbar, float gsum, float hsum,
                                               float scale, float lam, const StepArgs& a, float rho_c) {

@@ -12,6 +12,7 @@ Workloads (rows = cells, columns = genes; Sec. 2, eq. 3 with an offset):
 * ``nb_medium``       20000 x 2000 int32, NB, ~85% zeros, d = 10, p = 3, q = 1.
 * ``nb_atlas``        200000 x 5000 uint16, NB, ~90% zeros, d = 20.
 * ``nb_sweep``        50000 x 3000 uint16, NB (true d = 10) for the rank sweep.
+* ``nb_select``       the same law with 30 % of the entries held out, for rank selection.
 * ``nb_project``      100000 fit + 100000 held-out cells x 3000 genes, NB, d = 20.
 
 Law (all workloads): eta = o + X B^T + Gamma Z^T + U V^T with
@@ -31,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "WORKLOADS", "Problem", "make_problem", "partitions", "sweep_orders",
-    "n_sweeps", "crude_start", "fit_settings",
+    "n_sweeps", "crude_start", "fit_settings", "holdout_mask", "with_missing",
 ]
 
 
@@ -57,6 +58,7 @@ WORKLOADS = {
     "nb_medium": Workload("nb_medium", 20000, 2000, 3, 1, 10, "negbin", "int32", 0.85, True, 500, 500, 20),
     "nb_atlas": Workload("nb_atlas", 200000, 5000, 3, 1, 20, "negbin", "uint16", 0.90, True, 2048, 1024, 10),
     "nb_sweep": Workload("nb_sweep", 50000, 3000, 3, 1, 10, "negbin", "uint16", 0.90, True, 2048, 1024, 15),
+    "nb_select": Workload("nb_select", 50000, 3000, 3, 1, 10, "negbin", "uint16", 0.90, True, 2048, 1024, 15),
     "nb_project": Workload("nb_project", 200000, 3000, 3, 1, 20, "negbin", "uint16", 0.90, True, 2048, 1024, 10),
 }
 
@@ -209,7 +211,7 @@ def fit_settings(**over):
     """Optimiser settings of the paper's sgdGMF runs (Sec. 5.2 / App. C) with the
     unstated constants filled in; keyword arguments override."""
     s = dict(lambda_=(0.0, 0.0, 1.0, 0.0), a1=0.1, a2=0.01, k0=0.01, k1=1e-3, tau=0.75,
-             damping=1e-3, eps=1e-8, eta_clamp=30.0, bias_corr=0, alpha_mode=0)
+             damping=1e-3, eps=1e-8, eta_clamp=30.0, bias_corr=0, alpha_mode=0, missing=0)
     s.update(over)
     return s
 
@@ -267,6 +269,25 @@ def make_problem_device(n, m, p, q, d, family="negbin", *, seed=0, zero_frac=Non
         Y[r0:r1] = torch.where(c > 32767, c - 65536, c).to(torch.int16)
     return Problem(Y=Y, X=X, Z=Z, offset=off, B=B, Gamma=Gamma, U=U, V=V, nb_size=size, family=family,
                    saturated=saturated)
+
+
+MISSING_INT32 = -1        # the count that marks a missing entry in int32 counts
+MISSING_UINT16 = 65535    # ... and in uint16 counts
+
+
+def holdout_mask(n, m, frac, seed):
+    """Observed-entry mask with a uniformly drawn held-out fraction `frac` of
+    the entries (the evaluation protocol of Sec. 5.2: 30 % in the paper)."""
+    rng = np.random.default_rng([seed, 11])
+    return rng.random((n, m)) >= frac
+
+
+def with_missing(Y, observed):
+    """A copy of Y with the held-out entries set to the missing-count marker of
+    its dtype (int32: -1, uint16: 65535)."""
+    Y = np.array(Y, copy=True)
+    Y[~np.asarray(observed, bool)] = MISSING_INT32 if Y.dtype == np.int32 else MISSING_UINT16
+    return Y
 
 
 def mlp_init(n_in, n_h1, n_h2, n_out, seed):

@@ -18,8 +18,11 @@ def bias(cfg, t, visits):
 
 
 class BruteFit:
-    def __init__(self, Y, X, Z, offset, start, family, nb_row, nb_col, row_perm, col_perm, cfg, W=None):
+    def __init__(self, Y, X, Z, offset, start, family, nb_row, nb_col, row_perm, col_perm, cfg, W=None,
+                 observed=None):
         self.Y = np.asarray(Y, dtype=np.float64)
+        # Omega: the observed entries (all by default); the others are imputed by mu each block (Sec. 3.2)
+        self.obs = np.ones(self.Y.shape, bool) if observed is None else np.asarray(observed, bool)
         self.W = np.ones_like(self.Y) if W is None else np.asarray(W, dtype=np.float64)
         self.X, self.Z = np.asarray(X, float), np.asarray(Z, float)
         n, m = self.Y.shape
@@ -59,6 +62,7 @@ class BruteFit:
                 eta = (self.off[I, None] + self.X[I] @ self.B[J].T + self.G[I] @ self.Z[J].T
                        + self.U[I] @ self.V[J].T)
                 mu = np.exp(np.clip(eta, -cfg["eta_clamp"], cfg["eta_clamp"]))
+                Yb = np.where(self.obs[np.ix_(I, J)], Yb, mu)
                 if self.family == "poisson":
                     f = np.ones_like(mu)
                 else:

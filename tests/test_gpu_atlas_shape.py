@@ -1,0 +1,134 @@
+"""Parity at the launch shape of the atlas benchmark (200000 x 5000 uint16 NB,
+d = 20, blocks 2048 x 1024): a block is 16 x 8 tiles of 128 x 128 on the
+tensor cores (32 x 16 tiles of 64 x 64 on the FP32 path), too many for one
+thread-block cluster, so each sweep is a tile launch and an update launch that
+sums 16 column partials and 8 row partials per parameter; the last row and
+column chunks are ragged.
+
+Per-entry bars after one teacher-forced sweep, each parameter against its own
+oracle value: |got - ref| <= rtol * |step| + atol * max|step of its column| +
+1e-7 |ref| (the last term is the FP32 storage of the parameter).
+* FP32 path: rtol 1e-3, atol 1e-5 (FP32 sums of <= 2048 terms);
+* tensor cores: rtol 3e-2, atol 5e-3. The contraction operands are BF16 (unit
+  roundoff 2^-9): a gradient sum of 1024-2048 BF16 terms carries an error of a
+  few 1e-3 of the sum of its terms' magnitudes. Where the terms cancel, that is
+  large against the entry's own step but small against the column's largest
+  step; the column term covers those entries. (Measured at this shape: the
+  column term needed is below 2.1e-3.)
+Over whole epochs the deviance stays within 1e-4 (FP32) and 1e-3 (tensor
+cores) of the oracle's, the stated targets. The full-size test runs the first
+sweep of the benchmark's own fit at 200000 x 5000 in the benchmark's launch
+configuration and checks every updated parameter with the same bar, and that
+every parameter the sweep does not touch is unchanged.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests.test_gpu_parity import Pair
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ATLAS_SHAPE = (4300, 2104, 3, 1, 20, "negbin", 2048, 1024)
+BARS = {"fp32": (1e-3, 1e-5), "mixed": (3e-2, 5e-3)}
+
+
+@pytest.fixture(scope="module")
+def gmf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def oracle_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def check_per_entry(name, got, ref, before, rtol, atol):
+    step = ref - before
+    err = np.abs(got - ref)
+    colmax = np.abs(step).max(axis=0, keepdims=True)
+    bound = rtol * np.abs(step) + atol * colmax + 1e-7 * np.abs(ref)
+    bad = err > bound
+    assert not bad.any(), (name, int(bad.sum()), float((err - bound).max()), float(colmax.max()))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_atlas_shape_one_sweep_per_entry(gmf, oracle_mod, precision):
+    n, m, p, q, d, fam, nbr, nbc = ATLAS_SHAPE
+    P = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, y_dtype="uint16", zero_frac=0.9, precision=precision)
+    assert P.gpu.epoch_mode == "separate"
+    for e in range(2):
+        P.ref.epoch(P.sigmas[e])
+    P.teacher_force()
+    before = P.ref_params()
+    for w in (1, 2):      # every sweep of this shape has the ragged row chunk and the ragged column chunk
+        P.ref.sweeps(P.sigmas[5], w, w + 1)
+        P.gpu.sweeps(P.sigmas[5], w, w + 1)
+        got, ref = P.gpu.get_params(), P.ref_params()
+        rtol, atol = BARS[precision]
+        for k in ("U", "V", "B", "Gamma"):
+            check_per_entry(f"{k} after sweep {w}", got[k], ref[k], before[k], rtol, atol)
+        P.teacher_force()
+        before = P.ref_params()
+    ema, rema = P.gpu.get_ema(), P.ref_ema()
+    np.testing.assert_array_equal(ema["cnt_row"], rema["cnt_row"])
+    np.testing.assert_array_equal(ema["cnt_col"], rema["cnt_col"])
+    assert ema["t"] == rema["t"]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("mixed", 1e-3)])
+def test_atlas_shape_deviance_every_epoch(gmf, oracle_mod, precision, tol):
+    n, m, p, q, d, fam, nbr, nbc = ATLAS_SHAPE
+    P = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, y_dtype="uint16", zero_frac=0.9, precision=precision)
+    d0 = P.ref.deviance()
+    for e in range(4):
+        P.ref.epoch(P.sigmas[e])
+        P.gpu.epoch(P.sigmas[e])
+        dr, dg = P.ref.deviance(), P.gpu.deviance()
+        assert abs(dg - dr) / dr <= tol, (e, dg, dr)
+    assert dr < d0
+
+
+def test_atlas_full_size_first_sweep(gmf, oracle_mod):
+    """The benchmark's workload (200000 x 5000 uint16, drawn on the GPU as the
+    benchmark draws it), its start, partitions and first sweep order, on the
+    tensor cores in the benchmark's launch configuration: one sweep against the
+    oracle's, per entry; untouched rows keep their starting values exactly."""
+    w = synth.WORKLOADS["nb_atlas"]
+    prob = synth.make_problem_device(w.n, w.m, w.p, w.q, w.d, w.family, seed=0, zero_frac=w.zero_frac,
+                                     offset=w.offset)
+    Yh = prob.Y.cpu().numpy().view(np.uint16)
+    hp = synth.Problem(Y=Yh, X=prob.X, Z=prob.Z, offset=prob.offset, B=prob.B, Gamma=prob.Gamma, U=prob.U, V=prob.V,
+                       nb_size=prob.nb_size, family=w.family)
+    start = synth.crude_start(hp, w.d, seed=0)
+    rp, cp = synth.partitions(w.n, w.m, 0)
+    sig = synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, 1, 0)[0]
+    st = synth.fit_settings()
+    model = gmf.Model(prob.Y, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row, nb_col=w.nb_col,
+                      row_perm=rp, col_perm=cp, settings=st, precision="mixed")
+    assert model.epoch_mode == "separate"
+    before = model.get_params()          # the start as stored (FP32)
+    ref = oracle_mod.OracleFit(Yh, prob.X, prob.Z, prob.offset, before, family=w.family, nb_row=w.nb_row,
+                               nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=st)
+    model.sweeps(sig, 0, 1)
+    ref.sweeps(sig, 0, 1)
+    got = model.get_params()
+    r = -(-w.n // w.nb_row)
+    touched = np.zeros(w.n, bool)
+    for k in range(5):
+        c = (int(sig[0]) + k) % r
+        touched[rp[c * w.nb_row:(c + 1) * w.nb_row]] = True
+    rtol, atol = BARS["mixed"]
+    for k, refv in (("U", ref.U), ("Gamma", ref.G)):
+        check_per_entry(k, got[k][touched], refv[touched], before[k][touched], rtol, atol)
+        np.testing.assert_array_equal(got[k][~touched], before[k][~touched])
+    for k, refv in (("V", ref.V), ("B", ref.B)):
+        check_per_entry(k, got[k], refv, before[k], rtol, atol)

@@ -113,3 +113,35 @@ def test_sweep_groupings_and_autotune_give_the_same_fits(gmf, precision):
             np.testing.assert_array_equal(ea[k], eb[k], err_msg=f"autotuned model {i} {k}")
     with pytest.raises(gmf.GmfError):
         sw.group = 5
+
+
+def test_batched_tensor_core_launch_smallest_and_largest_rank_match_oracle(gmf):
+    """The batched tensor-core tile launch (one launch for both models, NB,
+    uint16) with the smallest and the largest rank of the rank sweep, d = 2
+    and d = 50 (K = 7 and 55: one and two 128-byte atoms per split-BF16
+    operand half, contraction widths 16 and 64), against the FP64 oracle
+    after 3 epochs: deviance within 1e-3 (the mixed-precision bar)."""
+    import oracle
+    oracle.build()
+    n, m, nbr, nbc = 900, 640, 300, 256
+    d_list = [2, 50]
+    prob = synth.make_problem(n, m, 3, 1, 10, "negbin", seed=13, y_dtype="uint16", zero_frac=0.85, offset=True)
+    starts = [synth.crude_start(prob, d, seed=13 + d) for d in d_list]
+    rp, cp = synth.partitions(n, m, 13)
+    st = synth.fit_settings()
+    sig = synth.sweep_orders(n, m, nbr, nbc, 3, 13)
+    sw = gmf.Sweep(prob.Y, prob.X, prob.Z, prob.offset, starts, d_list, family="negbin", nb_row=nbr, nb_col=nbc,
+                   row_perm=rp, col_perm=cp, settings=st, precision="mixed")
+    assert sw.group == len(d_list)
+    refs = [oracle.OracleFit(prob.Y, prob.X, prob.Z, prob.offset, s0, family="negbin", nb_row=nbr, nb_col=nbc,
+                             row_perm=rp, col_perm=cp, settings=st) for s0 in starts]
+    d0 = [r.deviance() for r in refs]
+    for e in range(3):
+        sw.epoch(sig[e])
+        for r in refs:
+            r.epoch(sig[e])
+    for i, r in enumerate(refs):
+        dr, dg = r.deviance(), sw.models[i].deviance()
+        assert dr < d0[i]
+        assert abs(dg - dr) / dr <= 1e-3, (d_list[i], dg, dr)
+        assert rel(sw.models[i].get_params()["U"], r.U) <= 2e-2

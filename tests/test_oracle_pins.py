@@ -531,3 +531,128 @@ def test_mlp_adam_first_step_is_signed_learning_rate():
     mlp.adam_step(P, g, {}, lr=0.01, eps=0.0)
     for k in P:
         np.testing.assert_allclose(P[k], P0[k] - 0.01 * np.sign(g[k]), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- missing entries and held-out metrics (Sec. 3.2, 5.2)
+
+@pytest.mark.parametrize("shape,blocks", [((12, 7), (5, 3)), ((7, 12), (3, 5))])
+@pytest.mark.parametrize("family,bias_corr,alpha_mode,y_dtype", [("poisson", 0, 0, np.int32), ("negbin", 1, 1, np.int32),
+                                                                 ("negbin", 0, 1, np.uint16)])
+def test_missing_entries_match_imputation_in_matrix_form(oracle_lib, shape, blocks, family, bias_corr, alpha_mode,
+                                                         y_dtype):
+    """Entries marked missing (the dtype's sentinel count) are imputed by the
+    current mean at every block step, y <- mu on B minus Omega (Sec. 3.2): the
+    scalar C oracle equals the matrix-form restatement that replaces the
+    unobserved entries of each block by mu (three epochs, ragged chunks, both
+    bias readings, the NB shape update from the completed block, r < s)."""
+    n, m = shape
+    obs = synth.holdout_mask(n, m, 0.3, seed=5)
+    assert 0 < (~obs).sum() < n * m
+    f0, D = tiny_fit(oracle_lib, n, m, 2, 1, 2, family, seed=7, nb_row=blocks[0], nb_col=blocks[1],
+                     bias_corr=bias_corr, alpha_mode=alpha_mode, k0=0.3, k1=0.5, lambda_=(0.1, 0.2, 1.0, 0.3),
+                     missing=1)
+    Ym = synth.with_missing(D["Y"].astype(y_dtype), obs)
+    f = oracle_lib.OracleFit(Ym, D["X"], D["Z"], D["off"], D["start"], family=family, nb_row=blocks[0],
+                             nb_col=blocks[1], row_perm=D["rp"], col_perm=D["cp"], settings=D["settings"])
+    bf = BruteFit(D["Y"], D["X"], D["Z"], D["off"], D["start"], family, blocks[0], blocks[1], D["rp"], D["cp"],
+                  D["settings"], observed=obs)
+    nsw = synth.n_sweeps(n, m, blocks[0], blocks[1])
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        sigma = rng.permutation(nsw).astype(np.int32)
+        f.epoch(sigma)
+        bf.epoch(sigma)
+    # FP64 rounding of three epochs in two summation orders (the unobserved entries make some sums cancel more)
+    for a, b in ((f.B, bf.B), (f.G, bf.G), (f.U, bf.U), (f.V, bf.V), (f.Gb_row, bf.GbR), (f.Hb_col, bf.HbC)):
+        np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-12)
+    assert f.alpha[0] == pytest.approx(bf.alpha, rel=1e-12)
+
+
+def test_missing_flag_without_missing_entries_changes_nothing(oracle_lib):
+    a, D = tiny_fit(oracle_lib, 12, 7, 2, 1, 2, "negbin", seed=3, nb_row=5, nb_col=3, alpha_mode=1)
+    b, _ = tiny_fit(oracle_lib, 12, 7, 2, 1, 2, "negbin", seed=3, nb_row=5, nb_col=3, alpha_mode=1, missing=1)
+    for s in synth.sweep_orders(12, 7, 5, 3, 2, 3):
+        a.epoch(s)
+        b.epoch(s)
+    for k in ("B", "G", "U", "V", "Gb_row", "Hb_col", "alpha"):
+        np.testing.assert_array_equal(getattr(a, k), getattr(b, k))
+    assert a.deviance() == b.deviance()
+
+
+def test_deviance_leaves_out_missing_entries(oracle_lib):
+    """With y <- mu a missing entry's unit deviance is D(mu, mu) = 0: the total
+    equals the complete matrix's minus the held-out entries' unit deviances."""
+    n, m = 9, 8
+    obs = synth.holdout_mask(n, m, 0.3, seed=2)
+    full, D = tiny_fit(oracle_lib, n, m, 2, 1, 2, "negbin", seed=4)
+    f = oracle_lib.OracleFit(synth.with_missing(D["Y"], obs), D["X"], D["Z"], D["off"], D["start"], family="negbin",
+                             nb_row=n, nb_col=m, row_perm=D["rp"], col_perm=D["cp"],
+                             settings=synth.fit_settings(missing=1))
+    mu = np.exp(full.eta())
+    held = sum(oracle_lib.entry_deviance(1, D["Y"][i, j], mu[i, j], 1.0, 1.7) for i, j in zip(*np.nonzero(~obs)))
+    assert f.deviance() == pytest.approx(full.deviance() - held, rel=1e-12)
+    assert held > 0
+
+
+def test_holdout_metrics_definitions():
+    """Sec. 5.2: a perfect prediction scores 0 on both, the training mean
+    scores 1 on both, and a 2 x 2 case by hand."""
+    from oracle.holdout import holdout_metrics, poisson_unit_deviance
+    rng = np.random.default_rng(3)
+    Y = rng.poisson(3.0, (20, 15)).astype(float)
+    obs = synth.holdout_mask(20, 15, 0.3, seed=1)
+    e, d, ybar, nv = holdout_metrics(Y, obs, Y)
+    assert e == 0.0 and d == 0.0 and nv == (~obs).sum() and ybar == pytest.approx(Y[obs].mean())
+    e, d, _, _ = holdout_metrics(Y, obs, np.full(Y.shape, Y[obs].mean()))
+    assert e == pytest.approx(1.0) and d == pytest.approx(1.0)
+    # by hand: training entries {2, 4} (mean 3), held-out y = (0, 5) predicted as mu = (1, 4)
+    Y2 = np.array([[2.0, 0.0], [5.0, 4.0]])
+    obs2 = np.array([[True, False], [False, True]])
+    mu2 = np.array([[9.0, 1.0], [4.0, 9.0]])
+    e, d, ybar, nv = holdout_metrics(Y2, obs2, mu2)
+    num = math.log(1 / 2) ** 2 + math.log(6 / 5) ** 2
+    den = math.log(1 / 4) ** 2 + math.log(6 / 4) ** 2
+    assert (ybar, nv) == (3.0, 2) and e == pytest.approx(num / den, rel=1e-14)
+    dnum = 2 * 1.0 + 2 * (5 * math.log(5 / 4) - 1)
+    dden = 2 * 3.0 + 2 * (5 * math.log(5 / 3) - 2)
+    assert d == pytest.approx(dnum / dden, rel=1e-14)
+    assert poisson_unit_deviance(0.0, 2.5) == pytest.approx(5.0)
+
+
+# ---------------------------------------------------------------- rank selection quantities (Sec. 4.2, App. B)
+
+@pytest.mark.parametrize("family", ["poisson", "negbin"])
+def test_loglik_equals_scipy_log_pmf(family):
+    from oracle.select import loglik, pearson
+    rng = np.random.default_rng(4)
+    mu = rng.gamma(2.0, 1.5, (30, 20))
+    Y = rng.poisson(mu).astype(float)
+    W = rng.uniform(0.5, 1.5, Y.shape)
+    obs = synth.holdout_mask(30, 20, 0.3, seed=4)
+    a = 1.7
+    ref = loglik_scipy = (W * (stats.poisson.logpmf(Y, mu) if family == "poisson"
+                               else stats.nbinom.logpmf(Y, a, a / (a + mu))))[obs].sum()
+    assert loglik(Y, mu, family, alpha=a, W=W, observed=obs) == pytest.approx(loglik_scipy, rel=1e-12)
+    nu = mu if family == "poisson" else mu + mu ** 2 / a      # Var(y) of the law
+    assert pearson(Y, mu, family, alpha=a, W=W, observed=obs) == pytest.approx((W * (Y - mu) ** 2 / nu)[obs].sum(),
+                                                                               rel=1e-12)
+    assert ref < 0
+
+
+def test_information_criteria_and_dispersion_by_hand():
+    from oracle.select import aic_bic, free_params, pearson_dispersion
+    assert free_params(100, 40, 2, 1, 3, "negbin") == 40 * 2 + 100 + 140 * 3 + 1
+    aic, bic = aic_bic(-1000.0, 50, 4000)
+    assert aic == 2100.0 and bic == pytest.approx(2000.0 + 50 * math.log(4000))
+    assert pearson_dispersion(371.0, 20, 10, 2, 1, 1) == pytest.approx(371.0 / (200 - 20 - 20 - 30 - 1))
+
+
+def test_eigen_ratio_rank_finds_the_gap():
+    from oracle.select import eigen_ratio_rank
+    assert eigen_ratio_rank([10, 8, 6, 0.6, 0.5, 0.4]) == 3
+    assert eigen_ratio_rank([0.4, 9, 0.5, 10]) == 2          # any order
+    # the sample singular values of a rank-4 signal plus small noise
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((200, 4)) @ np.diag([9, 7, 5, 4]) @ rng.standard_normal((4, 60)) / 8
+    s = np.linalg.svd(A + 0.05 * rng.standard_normal(A.shape), compute_uv=False)
+    assert eigen_ratio_rank(s[:20]) == 4

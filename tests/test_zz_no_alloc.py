@@ -88,10 +88,11 @@ def test_noalloc_rejects_sizes_beyond_scratch(gmf):
                                                  ("poisson", 29.0, 5.0), ("negbin", 29.0, 5.0)])
 def test_noalloc_large_counts_and_eta_near_the_clamp(gmf, family, shift, y_mean):
     """Counts far above 256 (beyond the handle kernel's log tables: eta around
-    6, counts around 400) and eta around 29, partly beyond the clamp at 30
-    (small counts, so each term is close to 2 mu): the two deviance kernels and
-    the FP64 oracle agree. Bar 1e-5: exp of an FP32 argument near 30 carries a
-    relative error of about |eta| * 2^-24 ~ 2e-6 in mu, and each term follows it."""
+    6, counts around 400, where y log(y/mu) - (y - mu) is a small difference of
+    large terms) and eta around 29, partly beyond the clamp at 30 (small
+    counts, so each term is close to 2 mu): the two deviance kernels and the
+    FP64 oracle agree. Bar 1e-5: eta in FP32 carries an error of about
+    |eta| * 2^-24, which exp passes on to mu (~2e-6 relative near the clamp)."""
     import oracle
     oracle.build()
     n, m, d = 300, 256, 4
@@ -105,7 +106,7 @@ def test_noalloc_large_counts_and_eta_near_the_clamp(gmf, family, shift, y_mean)
     if y_mean is None:
         assert np.median(prob.Y) > 256
     else:
-        assert eta.max() > 30 > eta.min() > 25
+        assert eta.max() > 30 > eta.min() > 20
     rp, cp = synth.partitions(n, m, 8)
     model = gmf.Model(torch.from_numpy(prob.Y).cuda(), prob.X, prob.Z, prob.offset, params, family=family, nb_row=128,
                       nb_col=128, row_perm=rp, col_perm=cp, settings=synth.fit_settings())
