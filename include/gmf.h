@@ -87,7 +87,7 @@ typedef struct {
     int32_t bias_corr;   /* 0: c_t = (1-a2^t)/(1-a1^t), global block count t (eq. 11);
                             1: c = (1-(1-a2)^k)/(1-(1-a1)^k), k = visits of the row/column */
     int32_t alpha_mode;  /* NB only. 0: shape fixed; 1: stochastic moment estimator (App. B),
-                            pooled per sweep */
+                            pooled per sweep; 2: one fixed shape per gene (gmf_set_gene_shapes) */
     int32_t precision;   /* GMF_PREC_FP32 or GMF_PREC_MIXED */
     int32_t flags;       /* GMF_FLAG_* bits; 0 for the defaults */
     int32_t missing;     /* 1: a count equal to GMF_MISSING_INT32 / GMF_MISSING_UINT16 marks an entry
@@ -505,6 +505,47 @@ int gmf_trace_read(gmf_model* h, double* total_ms, int64_t* launches, void* stre
 int gmf_deviance_noalloc(const void* Y, int32_t y_dtype, const float* W, int64_t n, int64_t m, const float* L,
                          const float* R, int32_t K, int32_t ld, int32_t family, float alpha, float eta_clamp,
                          double* d_out, void* stream);
+
+/*
+ * Per-gene negative binomial shapes (alpha_mode 2): the model of App. B with
+ * the shape made gene-specific, y_ij ~ NB(mu_ij, alpha_j), as scRNA-seq counts
+ * are usually modelled (and as the synthetic laws draw them). The derivatives,
+ * the deviance and the log-likelihood of entry (i, j) use alpha_j; the shapes
+ * stay fixed during gmf_sgd_epoch. gmf_project_cells does not take them.
+ * gmf_set_gene_shapes / gmf_get_gene_shapes -- the m shapes (host double, the
+ *   caller's gene order; > 0). Synchronous. Errors: GMF_ERR_ARG, GMF_ERR_STATE
+ *   (alpha_mode != 2).
+ * gmf_gene_shape_moments -- App. B's moment estimator applied to each gene's
+ *   column at the current parameters, alpha_j = sum_i w mu^2 /
+ *   sum_i w {(y - mu)^2 - mu} over the observed entries, clipped to [eps, cap];
+ *   a gene whose denominator is not positive gets cap. alpha_out: host, m
+ *   doubles, the caller's gene order. Any alpha_mode (e.g. estimate the shapes
+ *   from a fit with one shape, then continue with them). Synchronous. Errors:
+ *   GMF_ERR_ARG, GMF_ERR_OOM, GMF_ERR_CUDA.
+ */
+int gmf_set_gene_shapes(gmf_model* h, const double* alpha, void* stream);
+int gmf_get_gene_shapes(gmf_model* h, double* alpha, void* stream);
+int gmf_gene_shape_moments(gmf_model* h, double eps, double cap, double* alpha_out, void* stream);
+
+/*
+ * gmf_initialize -- the starting values of Sec. 4.1 in the least-squares form
+ * the paper gives for high-dimensional data, written over the handle's B,
+ * Gamma, U and V (X, Z, the offset, the counts and the NB shape are kept):
+ *   E = log(Y + 1/2) - o 1';  B = E' X (X'X)^-1;  Gamma = (E - X B') Z (Z'Z)^-1;
+ *   U = P diag(s)^(1/2), V = Q diag(s)^(1/2) from the rank-d truncated SVD
+ *   P diag(s) Q' of E - X B' - Gamma Z'.
+ * The n x m residual is formed in FP32 in device memory (4 n m bytes, allocated
+ * and released on the stream); its products run as FP32 cuBLAS GEMMs; the
+ * truncated SVD is a randomized subspace iteration (d + 10 Gaussian test
+ * vectors drawn from `seed`, power_iters power steps in [0, 20], each basis
+ * orthonormalised in FP64); small systems are solved in FP64 on the host. The
+ * smoothed derivatives, visit counts and t restart from zero. sv_out (host, d
+ * doubles, may be NULL) receives s, the residual's leading singular values (a
+ * scree for rank selection, Sec. 4.2). Synchronous. Errors: GMF_ERR_ARG,
+ * GMF_ERR_STATE (missing entries, X'X or Z'Z singular, a residual of rank < d),
+ * GMF_ERR_OOM, GMF_ERR_CUDA.
+ */
+int gmf_initialize(gmf_model* h, int32_t power_iters, uint64_t seed, double* sv_out, void* stream);
 
 /*
  * gmf_set_wait_limit -- testing hook for the failure detection of the

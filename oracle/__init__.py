@@ -50,7 +50,7 @@ class _Config(C.Structure):
 class _Data(C.Structure):
     _fields_ = [("Y", C.c_void_p), ("y_dtype", C.c_int32), ("W", C.c_void_p), ("X", C.c_void_p),
                 ("Z", C.c_void_p), ("offset", C.c_void_p), ("row_perm", C.c_void_p),
-                ("col_perm", C.c_void_p)]
+                ("col_perm", C.c_void_p), ("alpha_col", C.c_void_p)]
 
 
 class _State(C.Structure):
@@ -110,7 +110,7 @@ class OracleFit:
     smoothed derivatives of eq. 12, visit counters, the NB shape and t."""
 
     def __init__(self, Y, X, Z, offset, start, *, family, nb_row, nb_col, row_perm, col_perm,
-                 settings, W=None):
+                 settings, W=None, alpha_col=None):
         self.Y = np.ascontiguousarray(Y)
         if self.Y.dtype not in (np.int32, np.uint16):
             raise TypeError("Y must be int32 or uint16")
@@ -121,6 +121,8 @@ class OracleFit:
         d = np.asarray(start["U"]).shape[1]
         self.offset = None if offset is None else np.ascontiguousarray(offset, dtype=np.float64)
         self.W = None if W is None else np.ascontiguousarray(W, dtype=np.float64)
+        # per-gene NB shapes (alpha_mode 2), in the original gene order
+        self.alpha_col = None if alpha_col is None else np.ascontiguousarray(alpha_col, dtype=np.float64)
         self.row_perm = np.ascontiguousarray(row_perm, dtype=np.int32)
         self.col_perm = np.ascontiguousarray(col_perm, dtype=np.int32)
         self.B = np.array(start["B"], dtype=np.float64, order="C").reshape(m, p)
@@ -144,7 +146,7 @@ class OracleFit:
                            damping=s["damping"], eps=s["eps"], eta_clamp=s["eta_clamp"])
         self._data = _Data(Y=self.Y.ctypes.data, y_dtype=0 if self.Y.dtype == np.int32 else 1,
                            W=_p(self.W), X=_p(self.X), Z=_p(self.Z), offset=_p(self.offset),
-                           row_perm=_p(self.row_perm), col_perm=_p(self.col_perm))
+                           row_perm=_p(self.row_perm), col_perm=_p(self.col_perm), alpha_col=_p(self.alpha_col))
         self._state = _State(**{k: getattr(self, k).ctypes.data for k, _ in _State._fields_})
 
     @property

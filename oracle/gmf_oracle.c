@@ -35,6 +35,9 @@
  *     skipped when the denominator is not positive.
  *   - eta is clamped to [-eta_clamp, eta_clamp] before the inverse link.
  *   - phi = 1 (Poisson and NB have no free dispersion in this model).
+ *   - Per-gene NB shapes (alpha_mode 2): gene j has its own fixed shape alpha_j
+ *     (the model of App. B with the shape made column-specific, as the data
+ *     laws draw it); the derivatives and deviance of entry (i, j) use alpha_j.
  *   - Missing entries (missing = 1): a count equal to the sentinel (-1 for
  *     int32 counts, 65535 for uint16) is not observed. As Sec. 3.2 prescribes
  *     for an incomplete matrix, each block step first imputes it with the
@@ -52,7 +55,7 @@ typedef struct {
     int32_t family;     /* 0 Poisson, 1 negative binomial; log link */
     int32_t nb_row, nb_col;
     int32_t bias_corr;  /* 0 printed formula, 1 per-visit */
-    int32_t alpha_mode; /* 0 fixed NB shape, 1 stochastic moment estimator */
+    int32_t alpha_mode; /* 0 fixed NB shape, 1 stochastic moment estimator, 2 fixed per-gene shapes */
     int32_t missing;    /* 1: the sentinel count marks a missing entry (imputed by mu, Sec. 3.2) */
     double lambda[4];   /* penalties on B, Gamma, U, V */
     double a1, a2;      /* EMA weights of eq. 12 */
@@ -71,6 +74,7 @@ typedef struct {
     const double* offset;  /* n or NULL */
     const int32_t* row_perm; /* n: chunk c of rows is row_perm[c*nb_row ...] */
     const int32_t* col_perm; /* m */
+    const double* alpha_col; /* m per-gene NB shapes (alpha_mode 2), original order, or NULL */
 } gmfo_data;
 
 typedef struct {
@@ -170,9 +174,10 @@ int gmfo_block_grad(const gmfo_config* c, const gmfo_data* D, const gmfo_state* 
             const int64_t j = J[b];
             double mu, dd, ddd;
             const double eta = eta_at(c, D, S, i, j), w = w_at(D, m, i, j);
+            const double aj = D->alpha_col ? D->alpha_col[j] : alpha;
             double y = y_at(D, m, i, j);
-            if (missing_at(c, D, i, j)) gmfo_entry(c->family, 0.0, eta, w, alpha, c->eta_clamp, &y, NULL, NULL);
-            gmfo_entry(c->family, y, eta, w, alpha, c->eta_clamp, &mu, &dd, &ddd);
+            if (missing_at(c, D, i, j)) gmfo_entry(c->family, 0.0, eta, w, aj, c->eta_clamp, &y, NULL, NULL);
+            gmfo_entry(c->family, y, eta, w, aj, c->eta_clamp, &mu, &dd, &ddd);
             if (nb_sums) {
                 nb_sums[0] += w * mu * mu;
                 nb_sums[1] += w * ((y - mu) * (y - mu) - mu);
@@ -353,8 +358,9 @@ double gmfo_deviance(const gmfo_config* c, const gmfo_data* D, const gmfo_state*
         for (int64_t j = 0; j < c->m; j++) {
             double mu;
             if (missing_at(c, D, i, j)) continue;   /* y <- mu: D(mu, mu) = 0 */
-            gmfo_entry(c->family, 0.0, eta_at(c, D, S, i, j), 1.0, *S->alpha, c->eta_clamp, &mu, NULL, NULL);
-            total += gmfo_entry_deviance(c->family, y_at(D, c->m, i, j), mu, w_at(D, c->m, i, j), *S->alpha);
+            const double aj = D->alpha_col ? D->alpha_col[j] : *S->alpha;
+            gmfo_entry(c->family, 0.0, eta_at(c, D, S, i, j), 1.0, aj, c->eta_clamp, &mu, NULL, NULL);
+            total += gmfo_entry_deviance(c->family, y_at(D, c->m, i, j), mu, w_at(D, c->m, i, j), aj);
         }
     }
     return total;

@@ -37,7 +37,7 @@ EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
            "gmf_set_wait_limit", "gmf_sgd_sweep_blocks", "gmf_chunk_bytes", "gmf_chunk_state", "gmf_holdout",
-           "gmf_loglik",
+           "gmf_loglik", "gmf_initialize", "gmf_set_gene_shapes", "gmf_get_gene_shapes", "gmf_gene_shape_moments",
            "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_set_group", "gmf_sweep_group", "gmf_sweep_autotune",
            "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
            "gmf_mlp_set_params", "gmf_mlp_get_params", "gmf_mlp_get_grads", "gmf_mlp_forward", "gmf_mlp_loss_grad",
@@ -90,6 +90,10 @@ def lib():
         "gmf_deviance_async": (C.c_int, [VP, VP, VP]),
         "gmf_holdout": (C.c_int, [VP, VP, VP, VP]),
         "gmf_loglik": (C.c_int, [VP, VP, VP]),
+        "gmf_initialize": (C.c_int, [VP, C.c_int32, C.c_uint64, VP, VP]),
+        "gmf_set_gene_shapes": (C.c_int, [VP, VP, VP]),
+        "gmf_get_gene_shapes": (C.c_int, [VP, VP, VP]),
+        "gmf_gene_shape_moments": (C.c_int, [VP, C.c_double, C.c_double, VP, VP]),
         "gmf_get_params": (C.c_int, [VP, VP, VP, VP, VP, VP, VP]),
         "gmf_set_params": (C.c_int, [VP, VP, VP, VP, VP, VP, VP]),
         "gmf_get_ema": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
@@ -310,6 +314,29 @@ class Model:
         out = (C.c_double * 4)()
         check(lib().gmf_holdout(self._h, Ytrue.data_ptr(), out, _stream(stream)))
         return {"error": out[0], "deviance": out[1], "ybar": out[2], "n_heldout": int(out[3])}
+
+    def set_gene_shapes(self, alpha, stream=None):
+        """Per-gene NB shapes (alpha_mode 2), the caller's gene order."""
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        check(lib().gmf_set_gene_shapes(self._h, a.ctypes.data, _stream(stream)))
+
+    def get_gene_shapes(self, stream=None):
+        out = np.empty(self.dims[1])
+        check(lib().gmf_get_gene_shapes(self._h, out.ctypes.data, _stream(stream)))
+        return out
+
+    def gene_shape_moments(self, eps=1e-8, cap=1e6, stream=None):
+        """App. B's moment estimator per gene at the current parameters (gmf_gene_shape_moments)."""
+        out = np.empty(self.dims[1])
+        check(lib().gmf_gene_shape_moments(self._h, float(eps), float(cap), out.ctypes.data, _stream(stream)))
+        return out
+
+    def initialize(self, power_iters=2, seed=0, stream=None):
+        """The least-squares start of Sec. 4.1 (gmf_initialize); returns the residual's d leading singular values."""
+        d = self.dims[4]
+        sv = np.zeros(max(d, 1))
+        check(lib().gmf_initialize(self._h, int(power_iters), int(seed), sv.ctypes.data, _stream(stream)))
+        return sv[:d]
 
     def loglik(self, stream=None):
         """Log-likelihood, Pearson statistic and observed-entry count at the current parameters (gmf_loglik)."""

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -147,7 +148,8 @@ static void release(gmf_model* h) {
     }
     void* ptrs[] = {h->Yp, h->Wp, h->ystage2, h->L, h->R, h->GbR, h->HbR, h->GbC, h->HbC, h->cntR, h->cntC, h->alpha,
                     h->rperm, h->cperm, h->ystage, h->Rorig, h->kr_buf, h->partR, h->partC, h->nbpart, h->nbctr,
-                    h->sigma, h->rhoc, h->rho1, h->need, h->kmap, h->strip_done, h->err, h->devpart, h->devtot};
+                    h->sigma, h->rhoc, h->rho1, h->need, h->kmap, h->strip_done, h->err, h->devpart, h->devtot,
+                    h->alpha_col};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] h->h_rperm;
@@ -242,7 +244,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     if (c.family != GMF_POISSON && c.family != GMF_NEGBIN) return fail(GMF_ERR_ARG, "gmf_init: unknown family");
     if (c.nb_row <= 0 || c.nb_col <= 0) return fail(GMF_ERR_ARG, "gmf_init: minibatch sizes must be positive");
     if (c.bias_corr != 0 && c.bias_corr != 1) return fail(GMF_ERR_ARG, "gmf_init: bias_corr must be 0 or 1");
-    if (c.alpha_mode != 0 && c.alpha_mode != 1) return fail(GMF_ERR_ARG, "gmf_init: alpha_mode must be 0 or 1");
+    if (c.alpha_mode < 0 || c.alpha_mode > 2) return fail(GMF_ERR_ARG, "gmf_init: alpha_mode must be 0, 1 or 2");
     if (c.precision != GMF_PREC_FP32 && c.precision != GMF_PREC_MIXED)
         return fail(GMF_ERR_ARG, "gmf_init: unknown precision");
     if (c.flags & ~(GMF_FLAG_NO_CLUSTER | GMF_FLAG_PERSIST)) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
@@ -315,10 +317,17 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     INIT_CUDA(dalloc(&h->cntR, (size_t)c.n));
     INIT_CUDA(dalloc(&h->cntC, (size_t)c.m));
     INIT_CUDA(dalloc(&h->alpha, 1));
+    if (c.alpha_mode == 2) INIT_CUDA(dalloc(&h->alpha_col, (size_t)c.m));
     INIT_CUDA(dalloc(&h->rperm, (size_t)c.n));
     INIT_CUDA(dalloc(&h->cperm, (size_t)c.m));
-    INIT_CUDA(dalloc(&h->partR, (size_t)h->per * h->TI * h->TJ * GMF_TILE * 2 * std::max(h->fr, 1)));
-    INIT_CUDA(dalloc(&h->partC, (size_t)h->per * h->TI * h->TJ * GMF_TILE * 2 * std::max(h->fc, 1)));
+    {
+        // partial slots of the FP32 path's 64 x 64 tiles or the tensor-core path's 128 x 128 tiles
+        const size_t TI2 = (size_t)((std::min<int64_t>(c.nb_row, c.n) + 127) / 128);
+        const size_t TJ2 = (size_t)((std::min<int64_t>(c.nb_col, c.m) + 127) / 128);
+        const size_t tiles = std::max((size_t)h->TI * h->TJ * GMF_TILE, TI2 * TJ2 * 128);
+        INIT_CUDA(dalloc(&h->partR, (size_t)h->per * tiles * 2 * std::max(h->fr, 1)));
+        INIT_CUDA(dalloc(&h->partC, (size_t)h->per * tiles * 2 * std::max(h->fc, 1)));
+    }
     INIT_CUDA(dalloc(&h->nbpart, (size_t)2 * h->per * h->TI * h->TJ));
     INIT_CUDA(dalloc(&h->nbctr, 1));
     INIT_CUDA(dalloc(&h->sigma, (size_t)h->nsw));
@@ -344,6 +353,10 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     INIT_CUDA(cudaMemsetAsync(h->nbctr, 0, sizeof(unsigned), st));
     float a0 = (float)alpha0;
     INIT_CUDA(cudaMemcpyAsync(h->alpha, &a0, sizeof(float), cudaMemcpyHostToDevice, st));
+    if (h->alpha_col) {   // every gene starts from alpha0
+        const std::vector<float> ac((size_t)c.m, a0);
+        INIT_CUDA(cudaMemcpyAsync(h->alpha_col, ac.data(), sizeof(float) * c.m, cudaMemcpyHostToDevice, st));
+    }
     {
         std::vector<float> L, R;
         build_factors(h, X, Z, offset, B0, G0, U0, V0, L, R);
@@ -705,6 +718,72 @@ extern "C" int gmf_chunk_state(gmf_model* h, int32_t side, int32_t chunk, void* 
     return GMF_OK;
 }
 
+int gmf_gene_moments_run(gmf_model* h, double* sums, cudaStream_t st, const char** why);
+static int check_err_word(gmf_model* h, cudaStream_t st);
+
+extern "C" int gmf_set_gene_shapes(gmf_model* h, const double* alpha, void* stream) {
+    if (!h || !alpha) return fail(GMF_ERR_ARG, "gmf_set_gene_shapes: NULL argument");
+    if (h->cfg.alpha_mode != 2) return fail(GMF_ERR_STATE, "gmf_set_gene_shapes: the fit has one shape (alpha_mode != 2)");
+    std::vector<float> ac((size_t)h->m);
+    for (int64_t jp = 0; jp < h->m; jp++) {
+        const double v = alpha[h->h_cperm[jp]];
+        if (!(v > 0) || !std::isfinite(v)) return fail(GMF_ERR_ARG, "gmf_set_gene_shapes: shapes must be positive");
+        ac[jp] = (float)v;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(h->alpha_col, ac.data(), sizeof(float) * ac.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return GMF_OK;
+}
+
+extern "C" int gmf_get_gene_shapes(gmf_model* h, double* alpha, void* stream) {
+    if (!h || !alpha) return fail(GMF_ERR_ARG, "gmf_get_gene_shapes: NULL argument");
+    if (h->cfg.alpha_mode != 2) return fail(GMF_ERR_STATE, "gmf_get_gene_shapes: the fit has one shape (alpha_mode != 2)");
+    std::vector<float> ac((size_t)h->m);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(ac.data(), h->alpha_col, sizeof(float) * ac.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t jp = 0; jp < h->m; jp++) alpha[h->h_cperm[jp]] = ac[jp];
+    return GMF_OK;
+}
+
+extern "C" int gmf_gene_shape_moments(gmf_model* h, double eps, double cap, double* alpha_out, void* stream) {
+    if (!h || !alpha_out) return fail(GMF_ERR_ARG, "gmf_gene_shape_moments: NULL argument");
+    if (!(eps > 0) || !(cap >= eps)) return fail(GMF_ERR_ARG, "gmf_gene_shape_moments: need 0 < eps <= cap");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> sums((size_t)2 * h->m);
+    const char* why = "";
+    const int rc = gmf_gene_moments_run(h, sums.data(), st, &why);
+    if (rc) return fail(rc, "gmf_gene_shape_moments: %s", why);
+    for (int64_t jp = 0; jp < h->m; jp++) {
+        const double num = sums[2 * jp], den = sums[2 * jp + 1];
+        alpha_out[h->h_cperm[jp]] = den > 0 ? std::min(std::max(num / den, eps), cap) : cap;
+    }
+    return check_err_word(h, st);
+}
+
+int gmf_init_run(gmf_model* h, int power_iters, uint64_t seed, double* sv_out, cudaStream_t st, std::string* err);
+
+extern "C" int gmf_initialize(gmf_model* h, int32_t power_iters, uint64_t seed, double* sv_out, void* stream) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_initialize: NULL handle");
+    if (power_iters < 0 || power_iters > 20)
+        return fail(GMF_ERR_ARG, "gmf_initialize: power_iters %d outside [0, 20]", power_iters);
+    if (h->cfg.missing) return fail(GMF_ERR_STATE, "gmf_initialize: the least-squares start needs every count observed");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::string err;
+    const int rc = gmf_init_run(h, power_iters, seed, sv_out, st, &err);
+    if (rc) return fail(rc, "gmf_initialize: %s", err.c_str());
+    // a new start: the smoothed derivatives, visit counts and t begin again
+    CUDA_TRY(cudaMemsetAsync(h->GbR, 0, sizeof(float) * h->n * h->fr, st));
+    CUDA_TRY(cudaMemsetAsync(h->HbR, 0, sizeof(float) * h->n * h->fr, st));
+    CUDA_TRY(cudaMemsetAsync(h->GbC, 0, sizeof(float) * h->m * h->fc, st));
+    CUDA_TRY(cudaMemsetAsync(h->HbC, 0, sizeof(float) * h->m * h->fc, st));
+    CUDA_TRY(cudaMemsetAsync(h->cntR, 0, sizeof(int) * h->n, st));
+    CUDA_TRY(cudaMemsetAsync(h->cntC, 0, sizeof(int) * h->m, st));
+    h->t = 0;
+    return check_err_word(h, st);
+}
+
 extern "C" int gmf_set_wait_limit(gmf_model* h, int64_t limit_ns, int32_t need_extra) {
     if (!h) return fail(GMF_ERR_ARG, "gmf_set_wait_limit: NULL handle");
     if (limit_ns < 0 || limit_ns > 60000000000ll)
@@ -929,6 +1008,8 @@ extern "C" int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype
     if (n_steps < 0 || n_steps > 1000) return fail(GMF_ERR_ARG, "gmf_project_cells: n_steps in [0, 1000]");
     if (n_new == 0) return GMF_OK;  // an empty batch (its pointers may be NULL)
     if (!Ynew || !U_out || !G_out) return fail(GMF_ERR_ARG, "gmf_project_cells: NULL argument");
+    if (h->cfg.alpha_mode == 2)
+        return fail(GMF_ERR_STATE, "gmf_project_cells: per-gene NB shapes are not supported by the projection");
     if (h->p > 0 && !Xnew) return fail(GMF_ERR_ARG, "gmf_project_cells: Xnew is NULL");
     std::string err;
     int rc = gmf_project_run(h, Ynew, y_dtype == GMF_Y_UINT16, n_new, Xnew, offset_new, U_start, n_steps, U_out,

@@ -141,9 +141,12 @@ __global__ void __launch_bounds__(NT) loglik_kernel(StepArgs a, double* part) {
             const float mu = expf(ec);
             float lf, nu;
             if (nb) {
-                const float lam = la + log1pf(mu / alpha);   // log(alpha + mu)
-                lf = lgammaf(y + alpha) - lga - lgammaf(y + 1.f) + alpha * (la - lam) + y * (ec - lam);
-                nu = mu * (1.f + mu / alpha);
+                const bool pg = a.alpha_col != nullptr;   // per-gene shapes
+                const float aj = pg ? __ldg(a.alpha_col + col0 + j) : alpha;
+                const float laj = pg ? logf(aj) : la, lgaj = pg ? lgammaf(aj) : lga;
+                const float lam = laj + log1pf(mu / aj);   // log(alpha + mu)
+                lf = lgammaf(y + aj) - lgaj - lgammaf(y + 1.f) + aj * (laj - lam) + y * (ec - lam);
+                nu = mu * (1.f + mu / aj);
             } else {
                 lf = y * ec - mu - lgammaf(y + 1.f);
                 nu = mu;
@@ -159,7 +162,92 @@ __global__ void __launch_bounds__(NT) loglik_kernel(StepArgs a, double* part) {
     }
 }
 
+// Per-gene moment sums of App. B's shape estimator at the current parameters:
+// part[ry][j] = {sum_i w mu^2, sum_i w ((y - mu)^2 - mu)} over the observed
+// entries of the row tiles ry, ry + gridDim.y, ... of column tile blockIdx.x.
+// Thread t always owns column t % 64 of the tile, so its sums need no atomics.
+__global__ void __launch_bounds__(NT) gene_moments_kernel(StepArgs a, double* part) {
+    __shared__ __align__(16) float Ls[GMF_KMAX * LDT];
+    __shared__ __align__(16) float Rs[GMF_KMAX * LDT];
+    __shared__ double red[NT][2];
+    const int tid = threadIdx.x;
+    const int64_t col0 = (int64_t)blockIdx.x * T;
+    const int nc = (int)min((int64_t)T, a.m - col0);
+    const int64_t tiles_r = (a.n + T - 1) / T;
+    const int j = tid % T;
+    double s1 = 0.0, s2 = 0.0;
+    for (int e = tid; e < T * a.K; e += NT) {
+        const int i = e / a.K, c = e - i * a.K;
+        Rs[c * LDT + i] = i < nc ? a.R[(col0 + i) * a.KP + c] : 0.f;
+    }
+    for (int64_t rt = blockIdx.y; rt < tiles_r; rt += gridDim.y) {
+        const int64_t row0 = rt * T;
+        const int nr = (int)min((int64_t)T, a.n - row0);
+        __syncthreads();
+        for (int e = tid; e < T * a.K; e += NT) {
+            const int i = e / a.K, c = e - i * a.K;
+            Ls[c * LDT + i] = i < nr ? a.L[(row0 + i) * a.KP + c] : 0.f;
+        }
+        __syncthreads();
+        if (j < nc) {
+            for (int i = tid / T; i < nr; i += NT / T) {
+                const int64_t idx = (row0 + i) * a.m + col0 + j;
+                const float y = yval(a.Y, a.y16, idx);
+                if (a.missing && y == a.ymiss) continue;
+                const float w = a.W ? __ldg(a.W + idx) : 1.f;
+                float eta = 0.f;
+                for (int c = 0; c < a.K; c++) eta = fmaf(Ls[c * LDT + i], Rs[c * LDT + j], eta);
+                const float mu = expf(fminf(fmaxf(eta, -a.clamp), a.clamp));
+                s1 += (double)(w * mu * mu);
+                s2 += (double)(w * ((y - mu) * (y - mu) - mu));
+            }
+        }
+    }
+    red[tid][0] = s1;
+    red[tid][1] = s2;
+    __syncthreads();
+    if (tid < T && tid < nc) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int u = tid; u < NT; u += T) {
+            t1 += red[u][0];
+            t2 += red[u][1];
+        }
+        part[((int64_t)blockIdx.y * a.m + col0 + tid) * 2] = t1;
+        part[((int64_t)blockIdx.y * a.m + col0 + tid) * 2 + 1] = t2;
+    }
+}
+
 }  // namespace
+
+int gmf_gene_moments_run(gmf_model* h, double* sums, cudaStream_t st, const char** why) {
+    StepArgs a = gmf_make_args(h);
+    const int RY = 16;
+    double* part = nullptr;
+    if (cudaMallocAsync((void**)&part, sizeof(double) * 2 * RY * (size_t)h->m, st) != cudaSuccess) {
+        *why = "device allocation of the partial sums failed";
+        return GMF_ERR_OOM;
+    }
+    std::vector<double> hp((size_t)2 * RY * h->m);
+    gene_moments_kernel<<<dim3((unsigned)((h->m + T - 1) / T), RY), NT, 0, st>>>(a, part);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(part, st);
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return GMF_ERR_CUDA;
+    }
+    for (int64_t j = 0; j < h->m; j++) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int r = 0; r < RY; r++) {
+            t1 += hp[((size_t)r * h->m + j) * 2];
+            t2 += hp[((size_t)r * h->m + j) * 2 + 1];
+        }
+        sums[2 * j] = t1;
+        sums[2 * j + 1] = t2;
+    }
+    return GMF_OK;
+}
 
 int gmf_loglik_run(gmf_model* h, double* out, cudaStream_t st, const char** why) {
     StepArgs a = gmf_make_args(h);

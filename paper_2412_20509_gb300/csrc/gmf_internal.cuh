@@ -53,6 +53,7 @@ struct StepArgs {
     int* cntR;
     int* cntC;
     float* alpha;               // device scalar (NB shape)
+    const float* alpha_col;     // [m] per-gene NB shapes, permuted (alpha_mode 2), else nullptr
     float* partR;               // [per][TI][TJ][TILE][2*fr]: row partials of tile (ti, tj)
     float* partC;               // [per][TJ][TI][TILE][2*fc]: column partials of tile (ti, tj)
     double* nbpart;             // [per*TI*TJ][2]: NB moment sums of each tile
@@ -92,6 +93,7 @@ struct gmf_model {
     int* cntR;
     int* cntC;
     float* alpha;
+    float* alpha_col;           // [m] per-gene NB shapes, permuted order (alpha_mode 2)
     int* rperm;
     int* cperm;
     void* ystage;               // staging for counts uploaded from the host
@@ -186,6 +188,12 @@ cudaError_t gmf_launch_update(const StepArgs& a, int w, int T, cudaStream_t st);
 cudaError_t gmf_launch_update_multi(const StepArgs* d_args, int nmodels, int units, size_t smem, int w, int T,
                                     cudaStream_t st);
 int gmf_update_units(const StepArgs& a, int T);
+// the tensor-core path's update launch (row-major partial slots, see gmf_update.cuh)
+cudaError_t gmf_launch_update_tc(const StepArgs& a, int w, int T, cudaStream_t st);
+cudaError_t gmf_launch_update_tc_multi(const StepArgs* d_args, int nmodels, int units, int threads, int w, int T,
+                                       cudaStream_t st);
+int gmf_update_tc_threads(const StepArgs& a);
+int gmf_update_tc_units(const StepArgs& a, int T);
 cudaError_t gmf_launch_chunk_state(float* P, float* Gb, float* Hb, int* cnt, int KP, int nf, int64_t first, int rows,
                                    float* buf, int write, cudaStream_t st);
 size_t gmf_update_smem(const StepArgs& a);

@@ -257,7 +257,8 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
                     const float mu = expf(e);
                     // an unobserved entry is imputed by the current mean (Sec. 3.2)
                     const float y = (a.missing && yv[u][v] == a.ymiss) ? mu : yv[u][v];
-                    const float f = nb ? alpha / (alpha + mu) : 1.f;
+                    const float aj = a.alpha_col ? __ldg(a.alpha_col + col0 + jl0 + v) : alpha;
+                    const float f = nb ? aj / (aj + mu) : 1.f;
                     dd[v] = w8 * (y - mu) * f;
                     ddd[v] = w8 * mu * f;
                     if (moments) {
@@ -376,7 +377,14 @@ __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, doubl
             if (v < valid && !(a.missing && y[v] == a.ymiss)) {   // y <- mu: D(mu, mu) = 0
                 const float wv = a.W ? __ldg(a.W + idx + v) : 1.f;
                 const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
-                const float dv = 2.f * wv * half_dev_tab(nb, y[v], e, expf(e), alpha, la, tlog, tloga);
+                float hd;
+                if (a.alpha_col) {   // per-gene shapes: no tables of log(y + alpha)
+                    const float aj = __ldg(a.alpha_col + col0 + jl0 + v), mu = expf(e);
+                    hd = y[v] > 0.f ? half_dev_ratio(nb, y[v], e, mu, aj) : (nb ? aj * log1pf(mu / aj) : mu);
+                } else {
+                    hd = half_dev_tab(nb, y[v], e, expf(e), alpha, la, tlog, tloga);
+                }
+                const float dv = 2.f * wv * hd;
                 const float yk = dv - comp;
                 const float tk = sum + yk;
                 comp = (tk - sum) - yk;
@@ -472,6 +480,7 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.family = c.family;
     a.bias_corr = c.bias_corr;
     a.alpha_mode = c.alpha_mode;
+    a.alpha_col = c.alpha_mode == 2 ? h->alpha_col : nullptr;
     a.missing = c.missing;
     a.ymiss = h->y16 ? 65535.f : -1.f;
     for (int i = 0; i < 4; i++) a.lam[i] = (float)c.lambda[i];

@@ -83,12 +83,21 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
     return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
-// Bounded wait shared by the CTA: returns true when every thread saw the phase.
+// Bounded wait shared by the CTA: thread 0 polls the mbarrier while the other
+// threads wait at the CTA barrier, which takes no issue slots (with two tiles on
+// an SM, 16 polling warps would steal them from the other tile's epilogue). The
+// phase's completion, observed by thread 0, reaches the other threads through
+// the barrier (its writes by TMA or by the tensor cores are visible to them
+// after it; tcgen05 reads still follow a tcgen05 fence). True when the phase
+// completed.
 __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
-    bool ok = mbar_wait(bar, parity, WAIT_POLLS);
-    if (!ok) {
-        atomicOr(err, GMF_DEVERR_TIMEOUT);
-        ok = mbar_wait(bar, parity, WAIT_POLLS);  // drain this CTA's own copies / MMAs
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        ok = mbar_wait(bar, parity, WAIT_POLLS);
+        if (!ok) {
+            atomicOr(err, GMF_DEVERR_TIMEOUT);
+            ok = mbar_wait(bar, parity, WAIT_POLLS);  // drain this CTA's own copies / MMAs
+        }
     }
     return __syncthreads_and(ok) != 0;
 }
@@ -315,25 +324,35 @@ __device__ __forceinline__ void build_operands(const StepArgs& a, const TcLayout
             }
         }
     } else {
-        // value and square of each multiplier column; K index of the contraction = r
+        // value and square of each multiplier column; K index of the contraction = the tile's row
+        // (L side) or column (R side). Warp-wide: lane c reads column c of 8 consecutive rows (one
+        // coalesced load per row) and writes those rows' BF16 values, 16 bytes, with one store.
         const int NF = isL ? Lo.NC : Lo.NR;
         const int nf = isL ? a.fc : a.fr;
+        const int nvalid = isL ? nr : nc;
+        const float* base = isL ? a.L + row0 * a.KP : a.R + col0 * a.KP;
         uint8_t* o1 = sm + (isL ? Lo.off_lf : Lo.off_rf);
         uint8_t* o2 = sm + (isL ? Lo.off_lf2 : Lo.off_rf2);
         const uint32_t atom = (uint32_t)NF * 128u;
-        for (int c0 = 0; c0 < NF; c0 += 16) {
-            float v[16];
+        const int wq = (tid >> 5) & 3, lane = tid & 31;
+        for (int c0 = 0; c0 < NF; c0 += 32) {
+            const int c = c0 + lane;
+            const bool cok = c < nf;
+            const int col = cok ? (isL ? (c < a.p ? 1 + c : 1 + a.q + c) : 1 + a.p + c) : 0;
+            for (int rg = wq; rg < TT / 8; rg += 4) {
+                float v[8];
 #pragma unroll
-            for (int u = 0; u < 16; u++) {
-                const int c = c0 + u;
-                const int col = isL ? (c < a.p ? 1 + c : 1 + a.q + c) : 1 + a.p + c;
-                v[u] = (ok && c < nf) ? ld_state<COH>(src + col) : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 16; u++) {
-                const uint32_t off = (r >> 6) * atom + sw128_off(c0 + u, (r & 63) * 2);
-                *(__nv_bfloat16*)(o1 + off) = __float2bfloat16_rn(v[u]);
-                *(__nv_bfloat16*)(o2 + off) = __float2bfloat16_rn(v[u] * v[u]);
+                for (int u = 0; u < 8; u++) {
+                    const int rr = 8 * rg + u;
+                    v[u] = (cok && rr < nvalid) ? ld_state<COH>(base + (int64_t)rr * a.KP + col) : 0.f;
+                }
+                if (c < NF) {
+                    const uint32_t off = (uint32_t)(rg >> 3) * atom + sw128_off(c, (8 * rg & 63) * 2);
+                    st_shared_v4(o1 + off, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                                 pack_bf16x2(v[6], v[7]));
+                    st_shared_v4(o2 + off, pack_bf16x2(v[0] * v[0], v[1] * v[1]), pack_bf16x2(v[2] * v[2], v[3] * v[3]),
+                                 pack_bf16x2(v[4] * v[4], v[5] * v[5]), pack_bf16x2(v[6] * v[6], v[7] * v[7]));
+                }
             }
         }
     }
@@ -406,7 +425,8 @@ __device__ __forceinline__ void epilogue(const StepArgs& a, const TcLayout& Lo, 
             const float e = fminf(fmaxf(__uint_as_float(ev[8 * gq + t]), -a.clamp), a.clamp);
             const float mu = __expf(e);
             if (EPI == EPI_ANY && a.missing && y[t] == a.ymiss) y[t] = mu;  // imputation y <- mu (Sec. 3.2)
-            const float f = nb ? __fdividef(alpha, alpha + mu) : 1.f;
+            const float aj = (EPI == EPI_ANY && a.alpha_col && valid) ? __ldg(a.alpha_col + col0 + j) : alpha;
+            const float f = nb ? __fdividef(aj, aj + mu) : 1.f;
             const float wf = valid ? wv * f : 0.f;
             dd[t] = wf * (y[t] - mu);
             ddd[t] = wf * mu;
@@ -952,7 +972,7 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
         if (err) *err = "cuTensorMapEncodeTiled failed for the count matrix";
         return GMF_ERR_CUDA;
     }
-    tc->epi = (h->Wp || h->cfg.missing) ? EPI_ANY
+    tc->epi = (h->Wp || h->cfg.missing || h->cfg.alpha_mode == 2) ? EPI_ANY
               : h->cfg.family == GMF_NEGBIN ? (h->cfg.alpha_mode == 1 ? EPI_ANY : EPI_NB)
                                             : EPI_PO;
     cudaError_t e = gmf_smem_limit(tc_fn(h->y16, 0, tc->epi), L.smem);
@@ -1079,7 +1099,7 @@ cudaError_t gmf_tc_launch_update(gmf_model* h, const StepArgs& base, int w, cuda
     StepArgs a = base;
     a.TI = tc->TI;
     a.TJ = tc->TJ;
-    return gmf_launch_update(a, w, TT, st);
+    return gmf_launch_update_tc(a, w, TT, st);
 }
 
 // The sweeps [w0, w1) as one persistent launch (sweep_tc_epoch): the strip

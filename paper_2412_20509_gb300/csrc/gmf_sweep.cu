@@ -40,6 +40,7 @@ struct gmf_sweep {
     size_t smem = 0;
     size_t upd_smem = 0;   // update launch: the largest model's staging
     int upd_units = 0;     // update launch: CTAs per model
+    int upd_threads = 0;   // tensor-core update launch: threads per CTA (the widest model's)
     int mixed = 0;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t cap = nullptr;
@@ -111,6 +112,7 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
         s->upd_smem = std::max(s->upd_smem, gmf_update_smem(args[i]));
     }
     s->upd_units = gmf_update_units(args[0], s->mixed ? 128 : GMF_TILE);
+    for (int i = 0; i < n_models; i++) s->upd_threads = std::max(s->upd_threads, gmf_update_tc_threads(args[i]));
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMalloc(&s->d_args, sizeof(StepArgs) * n_models) != cudaSuccess ||
         cudaMalloc(&s->d_order, sizeof(int) * n_models) != cudaSuccess ||
@@ -148,7 +150,8 @@ static cudaError_t launch(gmf_sweep* s, int w, cudaStream_t st, int group) {
                      : gmf_simt_launch_multi(s->models[0], args, s->d_order, gn, smem, w, st);
         if (e != cudaSuccess) return e;
         const cudaError_t e2 =
-            gmf_launch_update_multi(args, gn, s->upd_units, s->upd_smem, w, s->mixed ? 128 : GMF_TILE, st);
+            (s->mixed ? gmf_launch_update_tc_multi(args, gn, s->upd_units, s->upd_threads, w, 128, st)
+                     : gmf_launch_update_multi(args, gn, s->upd_units, s->upd_smem, w, GMF_TILE, st));
         if (e2 != cudaSuccess) return e2;
     }
     return cudaSuccess;

@@ -31,6 +31,26 @@ __global__ void __launch_bounds__(UPD_NT) update_multi(const StepArgs* __restric
     if (blockIdx.x == 0 && threadIdx.x == 0) nb_shape_update(s_a, w);
 }
 
+// The update launch of the tensor-core path (row-major partial slots).
+__global__ void __launch_bounds__(512, 2) update_tc_kernel(StepArgs a, int w, int T) {
+    __shared__ int s_cnt[UTC_SR];
+    grid_launch_dependents();
+    update_unit_tc(a, w, T, blockIdx.x, s_cnt);  // waits for the tile launch inside
+    if (blockIdx.x == 0 && threadIdx.x == 0) nb_shape_update(a, w);
+}
+
+// Several models sharing the partitions (rank sweep): blockIdx.y = model.
+__global__ void __launch_bounds__(512, 2) update_tc_multi(const StepArgs* __restrict__ av, int w, int T) {
+    __shared__ StepArgs s_a;
+    __shared__ int s_cnt[UTC_SR];
+    grid_launch_dependents();
+    if (threadIdx.x == 0) s_a = av[blockIdx.y];
+    __syncthreads();
+    // every thread takes part (the block may be wider than this model needs: the extra threads own no row)
+    update_unit_tc(s_a, w, T, blockIdx.x, s_cnt);
+    if (blockIdx.x == 0 && threadIdx.x == 0) nb_shape_update(s_a, w);
+}
+
 // Copy the state of `rows` consecutive rows starting at `first` of one side
 // (row side: L, GbR, HbR, cntR; column side: R, GbC, HbC, cntC) to (write = 0)
 // or from (write = 1) a packed buffer, row by row: [KP factor values | nf
@@ -69,6 +89,20 @@ cudaError_t gmf_launch_chunk_state(float* P, float* Gb, float* Hb, int* cnt, int
     chunk_state_kernel<<<blocks, 256, 0, st>>>(P, Gb, Hb, cnt, KP, nf, first, rows, buf, write);
     return cudaGetLastError();
 }
+
+cudaError_t gmf_launch_update_tc(const StepArgs& a, int w, int T, cudaStream_t st) {
+    return gmf_launch_pdl(update_tc_kernel, dim3((unsigned)utc_units(a.nk, a.TI, a.TJ, T)),
+                          dim3((unsigned)(UTC_SR * utc_groups(a.fr, a.fc))), 0, st, a, w, T);
+}
+
+cudaError_t gmf_launch_update_tc_multi(const StepArgs* d_args, int nmodels, int units, int threads, int w, int T,
+                                       cudaStream_t st) {
+    return gmf_launch_pdl(update_tc_multi, dim3((unsigned)units, (unsigned)nmodels), dim3((unsigned)threads), 0, st,
+                          d_args, w, T);
+}
+
+int gmf_update_tc_threads(const StepArgs& a) { return UTC_SR * utc_groups(a.fr, a.fc); }
+int gmf_update_tc_units(const StepArgs& a, int T) { return utc_units(a.nk, a.TI, a.TJ, T); }
 
 int gmf_update_units(const StepArgs& a, int T) { return update_units(a.nk, a.TI, a.TJ, T); }
 

@@ -295,6 +295,132 @@ __device__ __forceinline__ void update_unit(const StepArgs& a, int w, int T, int
     }
 }
 
+// ---- the update launch of the tensor-core path. Its tile kernel writes each
+// tile's partials column-major, slot[c * T + o] (G) and slot[(nf + c) * T + o]
+// (H), as the FP32 path does. One CTA per 32-row slice of a strip: lane r of
+// warp g owns row r of the slice and the free columns 4g..4g+3, so every load
+// of a slot is one coalesced row of 32 floats. Each thread loads its
+// parameters and smoothed derivatives before griddepcontrol.wait, then adds
+// the strip's slots in tile order (the same FP32 additions as slice_update, so
+// both give the same bits) with the loads of two slots in flight; few
+// registers a thread, so that every CTA of a sweep's update is resident at
+// once.
+constexpr int UTC_SR = 32;   // rows (columns) per slice
+
+constexpr int UTC_CG = 4;    // free columns per thread
+constexpr int UTC_SIF = 2;   // slots whose loads are in flight together
+__host__ __device__ __forceinline__ int utc_groups(int fr, int fc) {
+    return (fr > fc ? fr + UTC_CG - 1 : fc + UTC_CG - 1) / UTC_CG;
+}
+__host__ __device__ __forceinline__ int utc_units(int nk, int TI, int TJ, int T) {
+    return nk * (TI + TJ) * ((T + UTC_SR - 1) / UTC_SR);
+}
+
+__device__ __forceinline__ void slice_update_tc(const StepArgs& a, const float* __restrict__ part, size_t slot_stride,
+                                                int nslots, int T, int o_begin, int nr, int nf, int64_t first,
+                                                bool rowside, float scale, float rhoc_blk, int* s_cnt) {
+    const int r = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int c0 = UTC_CG * g;
+    const bool act = r < nr && c0 < nf;
+    const int nc = act ? min(UTC_CG, nf - c0) : 0;
+    float* P = rowside ? a.L : a.R;
+    float* Gb = rowside ? a.GbR : a.GbC;
+    float* Hb = rowside ? a.HbR : a.HbC;
+    int* cnt = rowside ? a.cntR : a.cntC;
+    const int64_t row = first + r;
+    int col[UTC_CG];
+    float th[UTC_CG], gb[UTC_CG], hb[UTC_CG];
+#pragma unroll
+    for (int u = 0; u < UTC_CG; u++) {
+        const int c = c0 + u;
+        col[u] = rowside ? 1 + a.p + c : (c < a.p ? 1 + c : 1 + a.q + c);
+        th[u] = gb[u] = hb[u] = 0.f;
+        if (u < nc) {
+            th[u] = __ldcg(P + row * a.KP + col[u]);
+            gb[u] = __ldcg(Gb + row * nf + c);
+            hb[u] = __ldcg(Hb + row * nf + c);
+        }
+    }
+    if (g == 0 && r < nr) s_cnt[r] = __ldcg(cnt + row);
+
+    grid_dependency_wait();
+
+    float gs[UTC_CG] = {}, hs[UTC_CG] = {};
+    if (act) {
+        const float* base = part + o_begin + r;
+        for (int t0 = 0; t0 < nslots; t0 += UTC_SIF) {
+            float gv[UTC_SIF][UTC_CG], hv[UTC_SIF][UTC_CG];
+#pragma unroll
+            for (int v = 0; v < UTC_SIF; v++)
+#pragma unroll
+                for (int u = 0; u < UTC_CG; u++) {
+                    const bool l = t0 + v < nslots && u < nc;
+                    const float* sp = base + (size_t)(t0 + v) * slot_stride + (size_t)(c0 + u) * T;
+                    gv[v][u] = l ? __ldcg(sp) : 0.f;
+                    hv[v][u] = l ? __ldcg(sp + (size_t)nf * T) : 0.f;
+                }
+#pragma unroll
+            for (int v = 0; v < UTC_SIF; v++)
+                if (t0 + v < nslots)
+#pragma unroll
+                    for (int u = 0; u < UTC_CG; u++) {
+                        gs[u] += gv[v][u];
+                        hs[u] += hv[v][u];
+                    }
+        }
+    }
+    __syncthreads();  // the slice's visit counts are in shared memory
+#pragma unroll
+    for (int u = 0; u < UTC_CG; u++) {
+        if (u < nc) {
+            const int c = c0 + u;
+            const float lam = rowside ? (c < a.q ? a.lam[1] : a.lam[2]) : (c < a.p ? a.lam[0] : a.lam[3]);
+            const float rc = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, s_cnt[r] + 1) : rhoc_blk;
+            smoothed_step(th[u], gb[u], hb[u], gs[u], hs[u], scale, lam, a, rc);
+            P[row * a.KP + col[u]] = th[u];
+            Gb[row * nf + c] = gb[u];
+            Hb[row * nf + c] = hb[u];
+        }
+    }
+    if (g == 0 && r < nr) cnt[row] = s_cnt[r] + 1;
+}
+
+// One unit of the tensor-core update launch (tile edge T = 128).
+__device__ __forceinline__ void update_unit_tc(const StepArgs& a, int w, int T, int unit, int* s_cnt) {
+    const int nsl = (T + UTC_SR - 1) / UTC_SR;
+    const int per_block = (a.TI + a.TJ) * nsl;
+    const int kz = unit / per_block;
+    const int k = block_of_slot(a, kz);
+    const int rem = unit - kz * per_block;
+    const BlockGeo g = block_geo(a, w, k);
+    const int nTI = (int)((g.nI + T - 1) / T), nTJ = (int)((g.mJ + T - 1) / T);
+    const float rhoc_blk = a.rhoc[w * a.per + k];
+    if (rem < a.TI * nsl) {  // row strip ti of block k
+        const int ti = rem / nsl, o_begin = (rem - ti * nsl) * UTC_SR;
+        const int nstrip = ti < nTI ? (int)min((int64_t)T, g.nI - (int64_t)ti * T) : 0;
+        if (o_begin >= nstrip) {
+            grid_dependency_wait();
+            return;
+        }
+        const size_t ss = (size_t)T * 2 * a.fr;
+        slice_update_tc(a, a.partR + (size_t)((k * a.TI + ti) * a.TJ) * ss, ss, nTJ, T, o_begin,
+                        min(UTC_SR, nstrip - o_begin), a.fr, g.r0 + (int64_t)ti * T + o_begin, true,
+                        (float)a.m / (float)g.mJ, rhoc_blk, s_cnt);
+    } else {  // column strip tj of block k
+        const int r2 = rem - a.TI * nsl;
+        const int tj = r2 / nsl, o_begin = (r2 - tj * nsl) * UTC_SR;
+        const int nstrip = tj < nTJ ? (int)min((int64_t)T, g.mJ - (int64_t)tj * T) : 0;
+        if (o_begin >= nstrip) {
+            grid_dependency_wait();
+            return;
+        }
+        const size_t ss = (size_t)T * 2 * a.fc;
+        slice_update_tc(a, a.partC + (size_t)((k * a.TJ + tj) * a.TI) * ss, ss, nTI, T, o_begin,
+                        min(UTC_SR, nstrip - o_begin), a.fc, g.c0 + (int64_t)tj * T + o_begin, false,
+                        (float)a.n / (float)g.nI, rhoc_blk, s_cnt);
+    }
+}
+
 // NB shape: moment sums of all tiles of the sweep, in tile order, then one
 // smoothed update per sweep (App. B). One thread.
 __device__ __forceinline__ void nb_shape_update(const StepArgs& a, int w) {

@@ -19,8 +19,9 @@ def bias(cfg, t, visits):
 
 class BruteFit:
     def __init__(self, Y, X, Z, offset, start, family, nb_row, nb_col, row_perm, col_perm, cfg, W=None,
-                 observed=None):
+                 observed=None, alpha_col=None):
         self.Y = np.asarray(Y, dtype=np.float64)
+        self.alpha_col = None if alpha_col is None else np.asarray(alpha_col, float)   # per-gene NB shapes
         # Omega: the observed entries (all by default); the others are imputed by mu each block (Sec. 3.2)
         self.obs = np.ones(self.Y.shape, bool) if observed is None else np.asarray(observed, bool)
         self.W = np.ones_like(self.Y) if W is None else np.asarray(W, dtype=np.float64)
@@ -66,7 +67,8 @@ class BruteFit:
                 if self.family == "poisson":
                     f = np.ones_like(mu)
                 else:
-                    f = self.alpha / (self.alpha + mu)
+                    a = self.alpha if self.alpha_col is None else self.alpha_col[J][None, :]
+                    f = a / (a + mu)
                 Dd = Wb * (Yb - mu) * f
                 Ddd = Wb * mu * f
                 s1 += float((Wb * mu * mu).sum())

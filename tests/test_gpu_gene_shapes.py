@@ -1,0 +1,106 @@
+"""Per-gene negative binomial shapes (alpha_mode 2) on the GPU against the FP64
+oracle with the same shapes: one teacher-forced sweep within 1e-5 (FP32) /
+5e-4 (tensor cores), the deviance at identical parameters within 1e-6 and
+after several epochs within 1e-4 / 1e-3, the log-likelihood within 2e-6; the
+per-gene moment estimator (App. B applied per column) within 1e-5 of its FP64
+definition; and on data drawn with per-gene sizes, shapes estimated from a
+one-shape fit raise the log-likelihood of the continued fit."""
+import numpy as np
+import pytest
+
+import synth
+from tests.test_gpu_parity import Pair, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gmf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_20509_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def oracle_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _pair(gmf, oracle_mod, precision, n=1100, m=704, d=6, nbr=500, nbc=384, y_dtype="int32"):
+    P = Pair(gmf, oracle_mod, n, m, 3, 1, d, "negbin", nbr, nbc, zero_frac=0.8, precision=precision,
+             y_dtype=y_dtype, alpha_mode=2)
+    ac = P.prob.nb_size + 0.05
+    P.ref.alpha_col = np.ascontiguousarray(ac, dtype=np.float64)
+    P.ref._data.alpha_col = P.ref.alpha_col.ctypes.data
+    P.gpu.set_gene_shapes(ac)
+    return P, ac
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_gene_shapes_one_sweep_and_deviance(gmf, oracle_mod, precision):
+    P, ac = _pair(gmf, oracle_mod, precision)
+    np.testing.assert_allclose(P.gpu.get_gene_shapes(), ac.astype(np.float32), rtol=0)
+    assert P.gpu.deviance() == pytest.approx(P.ref.deviance(), rel=1e-6)
+    for e in range(2):
+        P.ref.epoch(P.sigmas[e])
+    P.teacher_force()
+    P.ref.sweeps(P.sigmas[5], 1, 2)
+    P.gpu.sweeps(P.sigmas[5], 1, 2)
+    got, ref = P.gpu.get_params(), P.ref_params()
+    bar = 1e-5 if precision == "fp32" else 5e-4
+    for k in ("U", "V", "B", "Gamma"):
+        assert rel(got[k], ref[k]) <= bar, (k, rel(got[k], ref[k]))
+    for e in range(2, 5):
+        P.ref.epoch(P.sigmas[e])
+        P.gpu.epoch(P.sigmas[e])
+    assert abs(P.gpu.deviance() / P.ref.deviance() - 1) <= (1e-4 if precision == "fp32" else 1e-3)
+
+
+def test_gene_shape_moments_and_loglik_match_definitions(gmf, oracle_mod):
+    from oracle.select import loglik
+    from oracle.shapes import gene_shape_moments
+    P, ac = _pair(gmf, oracle_mod, "fp32")
+    for e in range(2):
+        P.gpu.epoch(P.sigmas[e])
+    par = P.gpu.get_params()
+    pr = P.prob
+    mu = np.exp(np.clip(pr.offset[:, None] + pr.X @ par["B"].T + par["Gamma"] @ pr.Z.T + par["U"] @ par["V"].T,
+                        -30, 30))
+    np.testing.assert_allclose(P.gpu.gene_shape_moments(eps=1e-8, cap=1e6), gene_shape_moments(pr.Y, mu), rtol=1e-5)
+    ll = P.gpu.loglik()["loglik"]
+    assert ll == pytest.approx(loglik(pr.Y, mu, "negbin", ac.astype(np.float32).astype(np.float64)), rel=2e-6)
+
+
+def test_estimated_gene_shapes_raise_the_likelihood(gmf):
+    """Counts drawn with per-gene sizes Gamma(2, scale 0.5): a fit with one
+    shape (estimated per sweep, App. B), then the per-gene moment estimates
+    from it; continuing from the same parameters with the gene shapes gives a
+    higher log-likelihood than continuing with the one shape."""
+    n, m, d, nbr, nbc = 3000, 1024, 5, 500, 256
+    prob = synth.make_problem(n, m, 3, 1, d, "negbin", seed=14, zero_frac=0.8, offset=True)
+    start = synth.crude_start(prob, d, seed=14)
+    rp, cp = synth.partitions(n, m, 14)
+    sig = synth.sweep_orders(n, m, nbr, nbc, 16, 14)
+    Y = torch.from_numpy(prob.Y).cuda()
+    kw = dict(family="negbin", nb_row=nbr, nb_col=nbc, row_perm=rp, col_perm=cp, precision="mixed")
+    one = gmf.Model(Y, prob.X, prob.Z, prob.offset, start, settings=synth.fit_settings(alpha_mode=1), **kw)
+    for s in sig[:8]:
+        one.epoch(s)
+    shapes = one.gene_shape_moments(eps=1e-3, cap=1e3)
+    par = one.get_params()
+    genes = gmf.Model(Y, prob.X, prob.Z, prob.offset, par, settings=synth.fit_settings(alpha_mode=2), **kw)
+    genes.set_gene_shapes(shapes)
+    cont = gmf.Model(Y, prob.X, prob.Z, prob.offset, par, settings=synth.fit_settings(), **kw)
+    for s in sig[8:]:
+        genes.epoch(s)
+        cont.epoch(s)
+    assert genes.loglik()["loglik"] > cont.loglik()["loglik"]
+    # the estimates follow the drawn sizes (rank correlation)
+    r = np.corrcoef(np.argsort(np.argsort(shapes)), np.argsort(np.argsort(prob.nb_size)))[0, 1]
+    assert r > 0.5

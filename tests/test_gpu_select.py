@@ -65,11 +65,11 @@ def test_rank_sweep_with_held_out_entries(gmf):
     starts = [synth.crude_start(prob, d, seed=21 + d) for d in ranks]
     rp, cp = synth.partitions(n, m, 21)
     kw = dict(family="poisson", nb_row=256, nb_col=128, row_perm=rp, col_perm=cp,
-              settings=synth.fit_settings(missing=1, k0=0.05), precision="mixed")
+              settings=synth.fit_settings(missing=1, bias_corr=1), precision="mixed")
     Yd = torch.from_numpy(Ym).cuda()
     sw = gmf.Sweep(Yd, prob.X, prob.Z, prob.offset, starts, ranks, **kw)
     solo = gmf.Model(Yd, prob.X, prob.Z, prob.offset, starts[2], **kw)
-    for s in synth.sweep_orders(n, m, 256, 128, 12, 21):
+    for s in synth.sweep_orders(n, m, 256, 128, 20, 21):
         sw.epoch(s)
         solo.epoch(s)
     a, b = sw.models[2].get_params(), solo.get_params()

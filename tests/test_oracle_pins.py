@@ -656,3 +656,90 @@ def test_eigen_ratio_rank_finds_the_gap():
     A = rng.standard_normal((200, 4)) @ np.diag([9, 7, 5, 4]) @ rng.standard_normal((4, 60)) / 8
     s = np.linalg.svd(A + 0.05 * rng.standard_normal(A.shape), compute_uv=False)
     assert eigen_ratio_rank(s[:20]) == 4
+
+
+# ---------------------------------------------------------------- initialisation (Sec. 4.1, least-squares form)
+
+def test_init_ols_satisfies_its_normal_equations_and_eckart_young():
+    """B and Gamma solve their least-squares problems (residuals orthogonal to X and
+    to Z), U V' is the best rank-d approximation of the remaining residual (it is
+    orthogonal to both factors, and its squared norm is what the trailing singular
+    values leave), and U'U = V'V = diag(s)."""
+    from oracle.init import init_ols
+    prob = synth.make_problem(300, 120, 3, 2, 4, "negbin", seed=6, zero_frac=0.7, offset=True)
+    B, G, U, V, s = init_ols(prob.Y, prob.X, prob.Z, prob.offset, 4)
+    zt = np.log(prob.Y + 0.5) - prob.offset[:, None]
+    E1 = zt - prob.X @ B.T
+    np.testing.assert_allclose(prob.X.T @ E1, 0, atol=1e-8)
+    E2 = E1 - G @ prob.Z.T
+    np.testing.assert_allclose(E2 @ prob.Z, 0, atol=1e-8)
+    R = E2 - U @ V.T
+    np.testing.assert_allclose(R @ V, 0, atol=1e-8)
+    np.testing.assert_allclose(U.T @ R, 0, atol=1e-8)
+    np.testing.assert_allclose(U.T @ U, np.diag(s), atol=1e-8)
+    np.testing.assert_allclose(V.T @ V, np.diag(s), atol=1e-8)
+    sv = np.linalg.svd(E2, compute_uv=False)
+    assert np.sum(R ** 2) == pytest.approx(np.sum(sv[4:] ** 2), rel=1e-10)
+    assert np.all(np.diff(s) <= 0)
+
+
+def test_init_ols_starts_closer_than_the_crude_start(oracle_lib):
+    """On the synthetic NB law the Sec. 4.1 start has a lower deviance than the crude
+    start, and a short fit from it stays lower."""
+    from oracle.init import init_ols
+    n, m, d = 400, 160, 4
+    prob = synth.make_problem(n, m, 2, 1, d, "negbin", seed=8, zero_frac=0.7, offset=True)
+    B, G, U, V, _ = init_ols(prob.Y, prob.X, prob.Z, prob.offset, d)
+    rp, cp = synth.partitions(n, m, 8)
+    kw = dict(family="negbin", nb_row=100, nb_col=80, row_perm=rp, col_perm=cp, settings=synth.fit_settings())
+    fi = oracle_lib.OracleFit(prob.Y, prob.X, prob.Z, prob.offset, dict(B=B, Gamma=G, U=U, V=V, alpha=1.0), **kw)
+    fc = oracle_lib.OracleFit(prob.Y, prob.X, prob.Z, prob.offset, synth.crude_start(prob, d, seed=8), **kw)
+    assert fi.deviance() < fc.deviance()
+    for s_ in synth.sweep_orders(n, m, 100, 80, 3, 8):
+        fi.epoch(s_)
+        fc.epoch(s_)
+    assert fi.deviance() < fc.deviance()
+
+
+# ---------------------------------------------------------------- per-gene NB shapes (App. B per column)
+
+@pytest.mark.parametrize("shape,blocks", [((12, 7), (5, 3)), ((7, 12), (3, 5))])
+def test_per_gene_shapes_match_matrix_form(oracle_lib, shape, blocks):
+    """alpha_mode 2: every gene uses its own fixed shape in the derivatives; the
+    scalar C oracle equals the matrix-form restatement with a column of shapes."""
+    n, m = shape
+    ac = np.random.default_rng(3).gamma(2.0, 0.5, m) + 0.2
+    f0, D = tiny_fit(oracle_lib, n, m, 2, 1, 2, "negbin", seed=7, nb_row=blocks[0], nb_col=blocks[1],
+                     bias_corr=1, alpha_mode=2, k0=0.3, k1=0.5, lambda_=(0.1, 0.2, 1.0, 0.3))
+    f = oracle_lib.OracleFit(D["Y"], D["X"], D["Z"], D["off"], D["start"], family="negbin", nb_row=blocks[0],
+                             nb_col=blocks[1], row_perm=D["rp"], col_perm=D["cp"], settings=D["settings"],
+                             alpha_col=ac)
+    bf = BruteFit(D["Y"], D["X"], D["Z"], D["off"], D["start"], "negbin", blocks[0], blocks[1], D["rp"], D["cp"],
+                  D["settings"], alpha_col=ac)
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        sigma = rng.permutation(synth.n_sweeps(n, m, blocks[0], blocks[1])).astype(np.int32)
+        f.epoch(sigma)
+        bf.epoch(sigma)
+    for a, b in ((f.B, bf.B), (f.G, bf.G), (f.U, bf.U), (f.V, bf.V), (f.Gb_row, bf.GbR), (f.Hb_col, bf.HbC)):
+        np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-13)
+    # the deviance of entry (i, j) uses alpha_j (Table S1 / App. B)
+    mu = np.exp(f.eta())
+    ref = sum(oracle_lib.entry_deviance(1, D["Y"][i, j], mu[i, j], 1.0, ac[j]) for i in range(n) for j in range(m))
+    assert f.deviance() == pytest.approx(ref, rel=1e-12)
+
+
+def test_gene_shape_moments_recover_known_shapes():
+    """Counts drawn from NB(mu, alpha_j) with the true means plugged in: every
+    gene's moment estimate is within 25 % of its shape (20000 cells per gene)."""
+    from oracle.shapes import gene_shape_moments
+    rng = np.random.default_rng(5)
+    n, m = 20000, 12
+    a = np.linspace(0.5, 4.0, m)
+    mu = rng.gamma(4.0, 1.0, (n, 1)) * rng.uniform(0.5, 2.0, (1, m))
+    Y = rng.poisson(rng.gamma(a[None, :], mu / a[None, :]))
+    est = gene_shape_moments(Y, mu)
+    np.testing.assert_allclose(est, a, rtol=0.25)
+    # a Poisson gene has no overdispersion: capped
+    Yp = rng.poisson(np.full((5000, 3), 3.0))
+    assert np.all(gene_shape_moments(Yp, np.full((5000, 3), 3.0), cap=1e6) >= 20)
