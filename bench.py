@@ -381,6 +381,8 @@ KERNEL_SOURCES = {
     "sweep_tc_epoch": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
     "sweep_kernel": ["gmf_step_simt.cu", "gmf_update.cuh", "gmf_internal.cuh"],
     "update_kernel": ["gmf_update.cu", "gmf_update.cuh", "gmf_internal.cuh"],
+    "update_tc_kernel": ["gmf_update.cu", "gmf_update.cuh", "gmf_internal.cuh"],
+    "deviance_kernel": ["gmf_step_simt.cu", "gmf_update.cuh", "gmf_internal.cuh"],
 }
 
 
@@ -687,7 +689,7 @@ def run_headline(args, w):
     tflops_exec = per_sweep["entries"] * (6 * K + 4 * fr + 4 * fc) / sweep_s / 1e12
     sfu = per_sweep["entries"] * 2 / sweep_s
     tile_k = {"cluster": "sweep_tc_cluster", "persistent": "sweep_tc_epoch"}.get(epoch_mode, "sweep_tc_kernel")
-    sweep_kernels = [tile_k] if epoch_mode != "separate" else [tile_k, "update_kernel"]
+    sweep_kernels = [tile_k] if epoch_mode != "separate" else [tile_k, "update_tc_kernel"]
     roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s", "frac": hbm_gbs / peak,
             "traffic": committed_sweep_traffic(w.name, sweep_kernels),
             "kernel": " + ".join(sweep_kernels) + f" (one sweep: {launches_per_sweep} launch(es), graph-replayed)",

@@ -25,7 +25,7 @@ def loglik(Y, mu, family, alpha=None, W=None, observed=None):
     if family == "poisson":
         lf = Y * np.log(mu) - mu - gammaln(Y + 1)
     else:
-        a = float(alpha)
+        a = np.asarray(alpha, float)      # one shape, or one per gene (broadcast along the columns)
         lf = (gammaln(Y + a) - gammaln(a) - gammaln(Y + 1) + a * np.log(a / (a + mu)) + Y * np.log(mu / (a + mu)))
     if W is not None:
         lf = lf * W
@@ -37,7 +37,7 @@ def loglik(Y, mu, family, alpha=None, W=None, observed=None):
 def pearson(Y, mu, family, alpha=None, W=None, observed=None):
     Y = np.asarray(Y, float)
     mu = np.asarray(mu, float)
-    nu = mu if family == "poisson" else mu * (1 + mu / float(alpha))
+    nu = mu if family == "poisson" else mu * (1 + mu / np.asarray(alpha, float))
     t = (Y - mu) ** 2 / nu
     if W is not None:
         t = t * W

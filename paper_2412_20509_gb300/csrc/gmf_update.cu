@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(UPD_NT) update_multi(const StepArgs* __restric
 }
 
 // The update launch of the tensor-core path (row-major partial slots).
-__global__ void __launch_bounds__(512, 2) update_tc_kernel(StepArgs a, int w, int T) {
+__global__ void __launch_bounds__(1024) update_tc_kernel(StepArgs a, int w, int T) {
     __shared__ int s_cnt[UTC_SR];
     grid_launch_dependents();
     update_unit_tc(a, w, T, blockIdx.x, s_cnt);  // waits for the tile launch inside
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(512, 2) update_tc_kernel(StepArgs a, int w, in
 }
 
 // Several models sharing the partitions (rank sweep): blockIdx.y = model.
-__global__ void __launch_bounds__(512, 2) update_tc_multi(const StepArgs* __restrict__ av, int w, int T) {
+__global__ void __launch_bounds__(1024) update_tc_multi(const StepArgs* __restrict__ av, int w, int T) {
     __shared__ StepArgs s_a;
     __shared__ int s_cnt[UTC_SR];
     grid_launch_dependents();

@@ -298,17 +298,15 @@ __device__ __forceinline__ void update_unit(const StepArgs& a, int w, int T, int
 // ---- the update launch of the tensor-core path. Its tile kernel writes each
 // tile's partials column-major, slot[c * T + o] (G) and slot[(nf + c) * T + o]
 // (H), as the FP32 path does. One CTA per 32-row slice of a strip: lane r of
-// warp g owns row r of the slice and the free columns 4g..4g+3, so every load
+// warp g owns row r of the slice and the free columns 2g, 2g+1, so every load
 // of a slot is one coalesced row of 32 floats. Each thread loads its
 // parameters and smoothed derivatives before griddepcontrol.wait, then adds
 // the strip's slots in tile order (the same FP32 additions as slice_update, so
-// both give the same bits) with the loads of two slots in flight; few
-// registers a thread, so that every CTA of a sweep's update is resident at
-// once.
+// both give the same bits) with the loads of four slots in flight.
 constexpr int UTC_SR = 32;   // rows (columns) per slice
 
-constexpr int UTC_CG = 4;    // free columns per thread
-constexpr int UTC_SIF = 2;   // slots whose loads are in flight together
+constexpr int UTC_CG = 2;    // free columns per thread
+constexpr int UTC_SIF = 4;   // slots whose loads are in flight together
 __host__ __device__ __forceinline__ int utc_groups(int fr, int fc) {
     return (fr > fc ? fr + UTC_CG - 1 : fc + UTC_CG - 1) / UTC_CG;
 }
