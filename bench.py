@@ -860,6 +860,15 @@ def run_case(args):
     return 0
 
 
+def setting_name(group):
+    """The rank sweep's launch setting in words."""
+    if group == -1:
+        return "sequential (each model's own epoch)"
+    if group == -3:
+        return "one persistent launch per sweep (all models)"
+    return str(group)
+
+
 def run_rank_sweep(args, w):
     """--workload nb_sweep: 8 ranks on one 50000 x 3000 NB matrix, batched (one
     launch per sweep for all models) vs the same 8 fits one after another."""
@@ -909,9 +918,8 @@ def run_rank_sweep(args, w):
            "sequential": {"value": work / (ms_s / 1e3), "ms_per_step": ms_s / args.steps},
            "batched_over_sequential": ms_s / ms_b,
            "deviance_batched_equals_sequential": devs_b == devs_s,
-           "autotune": {"models_per_launch": "sequential (each model's own epoch)" if group < 0 else group,
-                        "epoch_ms_by_models_per_launch": {("sequential" if k < 0 else str(k)): v
-                                                          for k, v in tune_ms.items()},
+           "autotune": {"models_per_launch": setting_name(group),
+                        "epoch_ms_by_models_per_launch": {setting_name(k): v for k, v in tune_ms.items()},
                         "seconds": tune_s}}
     if not args.no_cpu_baseline:
         ent_all, t_all, per_rank = 0, 0.0, {}

@@ -381,26 +381,32 @@ int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype, int64_t n
  * them by default, see gmf_sweep_set_group); one tile launch covers the models
  * of a group and one update launch their strips.
  * Results equal running each model's own gmf_sgd_epoch, whatever the grouping.
- * gmf_sweep_set_group -- models per launch group: 1..n_models, 0 for all, or
+ * gmf_sweep_set_group -- models per launch group: 1..n_models, 0 for all,
  *   GMF_SWEEP_SEQUENTIAL: each model's own epoch (gmf_sgd_epoch's launches and
- *   graph), model after model. Errors: GMF_ERR_ARG (outside [-1, n_models]).
+ *   graph), model after model, or GMF_SWEEP_PERSISTENT (mixed precision): per
+ *   sweep, one cooperative persistent launch for all models, whose CTAs (as many
+ *   as fit on the device) take the tiles of every model, heaviest model first,
+ *   pass a grid barrier (bounded by the global timer, GMF_ERR_TIMEOUT past 2 s)
+ *   and take the strip updates. Errors: GMF_ERR_ARG (outside [-1, n_models]
+ *   and not GMF_SWEEP_PERSISTENT, or GMF_SWEEP_PERSISTENT on the FP32 path).
  * gmf_sweep_group -- the current group size (n_models when all,
- *   GMF_SWEEP_SEQUENTIAL); -2 for NULL.
+ *   GMF_SWEEP_SEQUENTIAL, GMF_SWEEP_PERSISTENT); -2 for NULL.
  * gmf_sweep_autotune -- times sweeps [0, n_sweeps) of the epoch defined by
  *   sigma (1 <= n_sweeps <= S) for the group sizes n_models, ceil(n_models/2),
- *   ..., 1 and for GMF_SWEEP_SEQUENTIAL, each from the same state (the models'
- *   parameters, smoothed derivatives, visit counts, shapes and t are saved
- *   before and restored after), and keeps the fastest. group_out (host, may be
- *   NULL): the chosen setting; ms_out (host, n_models + 1 floats, may be NULL):
- *   the time of group size g at ms_out[g - 1] and of the sequential setting at
- *   ms_out[n_models], -1 where not tried. Synchronous; needs device memory for
+ *   ..., 1, for GMF_SWEEP_SEQUENTIAL and (mixed precision) GMF_SWEEP_PERSISTENT,
+ *   each from the same state (the models' parameters, smoothed derivatives,
+ *   visit counts, shapes and t are saved before and restored after), and keeps
+ *   the fastest. group_out (host, may be NULL): the chosen setting; ms_out
+ *   (host, n_models + 2 floats, may be NULL): the time of group size g at
+ *   ms_out[g - 1], of the sequential setting at ms_out[n_models] and of the
+ *   persistent launch at ms_out[n_models + 1], -1 where not tried. Synchronous; needs device memory for
  *   one copy of the models' state. Errors: GMF_ERR_ARG, GMF_ERR_OOM, GMF_ERR_CUDA.
  * gmf_sweep_model -- the i-th model's handle, owned by the sweep and valid until
  * gmf_sweep_free, for gmf_deviance, gmf_get_params, gmf_orthogonalize, ...
  * (NULL if i is out of range). gmf_update_y is not allowed on models i > 0.
  */
 typedef struct gmf_sweep gmf_sweep;
-enum { GMF_SWEEP_SEQUENTIAL = -1 };
+enum { GMF_SWEEP_SEQUENTIAL = -1, GMF_SWEEP_PERSISTENT = -3 };
 int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int32_t* d_list, int32_t n_models, const void* Y,
                    int32_t y_dtype, int32_t y_on_device, const float* W, const double* X, const double* Z,
                    const double* offset, const int32_t* row_perm, const int32_t* col_perm, const double* const* B0,

@@ -22,7 +22,7 @@ GMF_Y_INT32, GMF_Y_UINT16 = 0, 1
 GMF_PREC_FP32, GMF_PREC_MIXED = 0, 1
 GMF_ORTH_B1, GMF_ORTH_B2, GMF_ORTH_B3 = 1, 2, 3
 GMF_FLAG_NO_CLUSTER, GMF_FLAG_PERSIST = 1, 2
-GMF_SWEEP_SEQUENTIAL = -1
+GMF_SWEEP_SEQUENTIAL, GMF_SWEEP_PERSISTENT = -1, -3
 GMF_EPOCH_SEPARATE, GMF_EPOCH_CLUSTER, GMF_EPOCH_PERSISTENT = 0, 1, 2
 EPOCH_MODES = {GMF_EPOCH_SEPARATE: "separate", GMF_EPOCH_CLUSTER: "cluster", GMF_EPOCH_PERSISTENT: "persistent"}
 
@@ -507,19 +507,22 @@ class Sweep:
         check(lib().gmf_sweep_set_group(self._h, int(g)))
 
     def autotune(self, sigma, n_sweeps=None, stream=None):
-        """Time the launch groupings and the sequential setting on sweeps of the epoch sigma from the
-        models' current state (restored afterwards) and keep the fastest; returns (group, {group: ms}),
-        group GMF_SWEEP_SEQUENTIAL (-1) for the sequential setting."""
+        """Time the launch groupings, the sequential setting and (mixed precision) the persistent launch on
+        sweeps of the epoch sigma from the models' current state (restored afterwards) and keep the fastest;
+        returns (group, {group: ms}), group GMF_SWEEP_SEQUENTIAL (-1) for the sequential setting and
+        GMF_SWEEP_PERSISTENT (-3) for the persistent launch."""
         sigma = np.ascontiguousarray(sigma, dtype=np.int32)
         n_sweeps = len(sigma) if n_sweeps is None else int(n_sweeps)
         nm = len(self.models)
         g = C.c_int32()
-        ms = np.empty(nm + 1, dtype=np.float32)
+        ms = np.empty(nm + 2, dtype=np.float32)
         check(lib().gmf_sweep_autotune(self._h, sigma.ctypes.data, n_sweeps, C.addressof(g), ms.ctypes.data,
                                        _stream(stream)))
         times = {i + 1: float(v) for i, v in enumerate(ms[:nm]) if v >= 0}
         if ms[nm] >= 0:
             times[GMF_SWEEP_SEQUENTIAL] = float(ms[nm])
+        if ms[nm + 1] >= 0:
+            times[GMF_SWEEP_PERSISTENT] = float(ms[nm + 1])
         return g.value, times
 
     def __del__(self):

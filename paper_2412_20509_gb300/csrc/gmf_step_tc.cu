@@ -523,16 +523,27 @@ __device__ __forceinline__ void store_partials(const StepArgs& a, const TcLayout
     }
 }
 
-// One tile (blockIdx.x, blockIdx.y) of block k of sweep w for the model whose
-// arguments are a / Lo. CL: cluster mode (the strip updates run here).
-template <bool Y16, bool CL, int EPI>
-__device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, const CUtensorMap* ymap_p, int w,
-                                        int k, uint8_t* smraw) {
-    __shared__ uint64_t bars[3];
-    __shared__ uint32_t tmem_base;
+// The CTA's three mbarriers (count tile, eta MMA, contraction MMAs) and its TMEM base.
+struct TileSync {
+    uint64_t bars[3];
+    uint32_t tmem_base;
+};
 
+// One tile (ti, tj) of block k of sweep w for the model whose arguments are a
+// / Lo. CL: cluster mode (the strip updates run here). The mbarriers are
+// initialised here when init_bars, else they were initialised before and par
+// is the parity of their next phase (a CTA that runs several tiles). With
+// tmem_held the caller owns a TMEM allocation of at least Lo.tmem_cols columns
+// at ts.tmem_base (a CTA may allocate only until it gives up its permit, so a
+// CTA running several tiles allocates once); else the tile allocates and frees
+// its own. Returns true when the tile was active (its mbarriers completed one
+// phase).
+template <bool Y16, bool CL, int EPI>
+__device__ __forceinline__ bool tc_tile(const StepArgs& a, const TcLayout& Lo, const CUtensorMap* ymap_p, int w,
+                                        int k, int ti, int tj, uint8_t* smraw, TileSync& ts, uint32_t par,
+                                        bool init_bars, bool tmem_held) {
+    uint64_t* bars = ts.bars;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int tj = blockIdx.x, ti = blockIdx.y;
     const BlockGeo g = block_geo(a, w, k);
     const int nTI = (int)((g.nI + TT - 1) / TT), nTJ = (int)((g.mJ + TT - 1) / TT);
     const bool active = ti < nTI && tj < nTJ;
@@ -551,17 +562,17 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
         const int nr = (int)min((int64_t)TT, g.nI - (int64_t)ti * TT);
         const int nc = (int)min((int64_t)TT, g.mJ - (int64_t)tj * TT);
 
-        if (tid == 0) {
+        if (tid == 0 && init_bars) {
             mbar_init(&bars[0], 1);
             mbar_init(&bars[1], 1);
             mbar_init(&bars[2], 1);
             fence_mbar_init();
         }
-        if (warp == 0) tmem_alloc(&tmem_base, Lo.tmem_cols);
+        if (warp == 0 && !tmem_held) tmem_alloc(&ts.tmem_base, Lo.tmem_cols);
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        const uint32_t tb = tmem_base;
+        const uint32_t tb = ts.tmem_base;
 
         if (tid == 0) issue_counts(Lo, ymap_p, sm, row0, col0, &bars[0]);
         // the counts are read-only; everything below reads or writes model state
@@ -579,8 +590,8 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
         tc_fence_after();
 
         if (tid == 0) issue_eta(Lo, sm, tb, &bars[1]);
-        bool ok = cta_wait(&bars[0], 0, a.err);
-        ok = cta_wait(&bars[1], 0, a.err) && ok;
+        bool ok = cta_wait(&bars[0], par, a.err);
+        ok = cta_wait(&bars[1], par, a.err) && ok;
         tc_fence_after();
 
         if (ok) epilogue<Y16, EPI>(a, Lo, sm, tb, row0, col0, nr, nc, alpha, s1, s2);
@@ -592,15 +603,16 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
         if (ok && tid == 0) issue_contractions(Lo, sm, tb, &bars[2]);
         // warps 8-15 have no partials to read: they start the update slices' copies
         if (CL) cl_stage_issue(a, Lo, sm, cls, NTH / 2, NTH / 2);
-        if (ok) ok = cta_wait(&bars[2], 0, a.err);
+        if (ok) ok = cta_wait(&bars[2], par, a.err);
         tc_fence_after();
         if (CL) cluster_wait();
 
         if (ok) store_partials<CL>(a, Lo, sm, tb, k, ti, tj, nr, nc);
         if (!ok && tid == 0) atomicOr(a.err, GMF_DEVERR_TIMEOUT);
+        fence_proxy_async_smem();  // a next tile of this CTA loads its counts over this one's operands
         tc_fence_before();
         __syncthreads();
-        if (warp == 0) tmem_dealloc(tb, Lo.tmem_cols);
+        if (warp == 0 && !tmem_held) tmem_dealloc(tb, Lo.tmem_cols);
     } else {
         grid_dependency_wait();  // before writing this sweep's moment slot
         grid_launch_dependents();
@@ -626,6 +638,7 @@ __device__ __forceinline__ void tc_tile(const StepArgs& a, const TcLayout& Lo, c
             }
         }
     }
+    return active;
 }
 
 // ---- persistent epoch (cluster mode). One launch runs the sweeps [w0, w1);
@@ -828,7 +841,9 @@ template <bool Y16, int EPI>
 __global__ void __launch_bounds__(NTH, Y16 ? 2 : 1)
     sweep_tc_kernel(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    tc_tile<Y16, false, EPI>(a, Lo, &ymap, w, block_of_slot(a, blockIdx.z), smraw);
+    __shared__ TileSync ts;
+    tc_tile<Y16, false, EPI>(a, Lo, &ymap, w, block_of_slot(a, blockIdx.z), blockIdx.y, blockIdx.x, smraw, ts, 0u,
+                             true, false);
 }
 
 // Cluster mode: launched with cluster dimensions (TJ, TI, 1), one cluster per block.
@@ -836,7 +851,9 @@ template <bool Y16, int EPI>
 __global__ void __launch_bounds__(NTH, 1)
     sweep_tc_cluster(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w) {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    tc_tile<Y16, true, EPI>(a, Lo, &ymap, w, block_of_slot(a, blockIdx.z), smraw);
+    __shared__ TileSync ts;
+    tc_tile<Y16, true, EPI>(a, Lo, &ymap, w, block_of_slot(a, blockIdx.z), blockIdx.y, blockIdx.x, smraw, ts, 0u,
+                            true, false);
 }
 
 // The kernel of a handle: counts type, cluster mode and epilogue variant.
@@ -874,7 +891,99 @@ __global__ void __launch_bounds__(NTH, Y16 ? 2 : 1) sweep_tc_multi(const StepArg
         s_l = lv[model];
     }
     __syncthreads();
-    tc_tile<Y16, false, EPI>(s_a, s_l, &ymap, w, blockIdx.z % per, smraw);
+    __shared__ TileSync ts;
+    tc_tile<Y16, false, EPI>(s_a, s_l, &ymap, w, blockIdx.z % per, blockIdx.y, blockIdx.x, smraw, ts, 0u, true, false);
+}
+
+// One sweep of several models as one persistent launch (cooperative, so every
+// CTA is resident): the CTAs first take the tiles of every model's blocks,
+// heaviest model first (slot order), one after another; then, past a grid
+// barrier, the strip updates of every model (the update launch's units); then
+// each model's NB shape. The same tile and update functions as the tile and
+// update launches, in the same order of additions, so the results are equal
+// bit for bit. The grid barrier is a counter raised by every CTA; each CTA
+// waits (thread 0, bounded by the global timer: past wait_ns it flags
+// GMF_DEVERR_TIMEOUT and goes on, so the launch ends) until the counter reaches
+// the next multiple of the grid size. The counter is cleared before each epoch.
+__device__ __forceinline__ void grid_barrier(unsigned* ctr, uint64_t wait_ns, unsigned* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // this CTA's partial sums and moment sums, before its arrival
+        const unsigned old = atomicAdd(ctr, 1u);
+        const unsigned target = (old / gridDim.x + 1u) * gridDim.x;
+        if (ld_acquire_u32(ctr) < target) {
+            const uint64_t t0 = global_ns();
+            while (ld_acquire_u32(ctr) < target) {
+                if (*(volatile unsigned*)err & GMF_DEVERR_TIMEOUT) break;
+                if (global_ns() - t0 > wait_ns) {
+                    atomicOr(err, GMF_DEVERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// The CTA holds one TMEM allocation of tmem_cols columns (the widest model's)
+// for all its tiles; the host keeps (CTAs per SM) x tmem_cols within the SM's
+// 512 columns, so no allocation waits for a CTA that is itself waiting at the
+// grid barrier.
+template <bool Y16, int EPI>
+__global__ void __launch_bounds__(NTH, Y16 ? 2 : 1)
+    sweep_tc_multi_persist(const StepArgs* __restrict__ av, const TcLayout* __restrict__ lv,
+                           const int* __restrict__ order, int nmod, int per, const __grid_constant__ CUtensorMap ymap,
+                           int w, unsigned* gctr, unsigned long long wait_ns, unsigned* err, uint32_t tmem_cols) {
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    __shared__ StepArgs s_a;
+    __shared__ TcLayout s_l;
+    __shared__ TileSync ts;
+    __shared__ int s_cnt[UTC_SR];
+    const int TI = av[0].TI, TJ = av[0].TJ;  // the same partitions for every model
+    const int tiles = per * TI * TJ;
+    uint32_t par = 0;
+    bool init = true;
+    if ((int)blockIdx.x < nmod * tiles && (threadIdx.x >> 5) == 0) tmem_alloc(&ts.tmem_base, tmem_cols);
+    for (int it = blockIdx.x; it < nmod * tiles; it += gridDim.x) {
+        const int slot = it / tiles, rem = it - slot * tiles;
+        const int k = rem / (TI * TJ), r2 = rem - k * (TI * TJ);
+        const int ti = r2 / TJ, tj = r2 - ti * TJ;
+        __syncthreads();  // the previous tile no longer reads the shared arguments
+        if (threadIdx.x == 0) {
+            s_a = av[order[slot]];
+            s_l = lv[order[slot]];
+        }
+        __syncthreads();
+        if (tc_tile<Y16, false, EPI>(s_a, s_l, &ymap, w, k, ti, tj, smraw, ts, par, init, true)) {
+            par ^= 1u;
+            init = false;
+        }
+    }
+    if ((int)blockIdx.x < nmod * tiles) {
+        tc_fence_before();
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0) tmem_dealloc(ts.tmem_base, tmem_cols);
+    }
+    grid_barrier(gctr, wait_ns, err);
+    const int units = utc_units(per, TI, TJ, TT);
+    for (int it = blockIdx.x; it < nmod * units; it += gridDim.x) {
+        const int slot = it / units;
+        __syncthreads();
+        if (threadIdx.x == 0) s_a = av[order[slot]];
+        __syncthreads();
+        update_unit_tc(s_a, w, TT, it - slot * units, s_cnt);
+    }
+    if (threadIdx.x == 0)
+        for (int mm = blockIdx.x; mm < nmod; mm += gridDim.x) nb_shape_update(av[mm], w);
+}
+
+template <int EPI>
+const void* tc_persist_fn_epi(int y16) {
+    return y16 ? (const void*)sweep_tc_multi_persist<true, EPI> : (const void*)sweep_tc_multi_persist<false, EPI>;
+}
+const void* tc_persist_fn(int y16, int epi) {
+    return epi == EPI_NB ? tc_persist_fn_epi<EPI_NB>(y16) : epi == EPI_PO ? tc_persist_fn_epi<EPI_PO>(y16)
+                                                                          : tc_persist_fn_epi<EPI_ANY>(y16);
 }
 
 template <int EPI>
@@ -1132,6 +1241,7 @@ int gmf_tc_persistent(const gmf_model* h) { return h->tc && ((const TcState*)h->
 size_t gmf_tc_layout_size() { return sizeof(TcLayout); }
 const void* gmf_tc_layout(const gmf_model* h) { return &((const TcState*)h->tc)->lay; }
 uint32_t gmf_tc_smem(const gmf_model* h) { return ((const TcState*)h->tc)->lay.smem; }
+uint32_t gmf_tc_tmem_cols(const gmf_model* h) { return ((const TcState*)h->tc)->lay.tmem_cols; }
 void gmf_tc_grid(const gmf_model* h, int* TI, int* TJ) {
     *TI = ((const TcState*)h->tc)->TI;
     *TJ = ((const TcState*)h->tc)->TJ;
@@ -1164,6 +1274,43 @@ cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, con
     int per = h0->per;
     void* args[] = {(void*)&d_args, (void*)&lays, (void*)&d_order, &per, (void*)&tc->ymap[h0->ycur], &w};
     return cudaLaunchKernelExC(&cfg, tc_multi_fn(h0->y16, tc->epi), args);
+}
+
+// One sweep of nmodels models as one cooperative persistent launch: as many CTAs
+// as can be resident at once (at most one per tile); returns the grid size in *grid.
+cudaError_t gmf_tc_launch_multi_persist(const gmf_model* h0, const StepArgs* d_args, const void* d_lays,
+                                        const int* d_order, int nmodels, uint32_t smem, uint32_t tmem_cols, int w,
+                                        unsigned* gctr, unsigned* err, cudaStream_t st) {
+    const TcState* tc = (const TcState*)h0->tc;
+    const void* fn = tc_persist_fn(h0->y16, tc->epi);
+    cudaError_t e = gmf_smem_limit(fn, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NTH, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    if (tmem_cols < 32 || tmem_cols > 512) return cudaErrorInvalidValue;
+    per_sm = std::min(per_sm, (int)(512u / tmem_cols));  // every resident CTA holds its TMEM for the tile phase
+    const int tiles = h0->per * tc->TI * tc->TJ * nmodels;
+    const int grid = std::max(1, std::min(per_sm * sms, tiles));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const TcLayout* lays = (const TcLayout*)d_lays;
+    int per = h0->per;
+    unsigned long long wait_ns = h0->wait_ns > 0 ? (unsigned long long)h0->wait_ns : 2000000000ull;
+    void* args[] = {(void*)&d_args, (void*)&lays, (void*)&d_order, &nmodels, &per, (void*)&tc->ymap[h0->ycur], &w,
+                    &gctr, &wait_ns, &err, &tmem_cols};
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 int gmf_tc_cluster(const gmf_model* h) { return h->tc && ((const TcState*)h->tc)->cluster; }

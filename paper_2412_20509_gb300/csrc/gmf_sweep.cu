@@ -18,10 +18,14 @@
 size_t gmf_tc_layout_size();
 const void* gmf_tc_layout(const gmf_model* h);
 uint32_t gmf_tc_smem(const gmf_model* h);
+uint32_t gmf_tc_tmem_cols(const gmf_model* h);
 void gmf_tc_grid(const gmf_model* h, int* TI, int* TJ);
 cudaError_t gmf_tc_multi_attr(const gmf_model* h0, uint32_t smem);
 cudaError_t gmf_tc_launch_multi(const gmf_model* h0, const StepArgs* d_args, const void* d_lays, const int* d_order,
                                 int nmodels, uint32_t smem, int w, cudaStream_t st);
+cudaError_t gmf_tc_launch_multi_persist(const gmf_model* h0, const StepArgs* d_args, const void* d_lays,
+                                        const int* d_order, int nmodels, uint32_t smem, uint32_t tmem_cols, int w,
+                                        unsigned* gctr, unsigned* err, cudaStream_t st);
 size_t gmf_sweep_simt_smem(const gmf_model* h);
 cudaError_t gmf_simt_multi_attr(size_t smem);
 cudaError_t gmf_simt_launch_multi(const gmf_model* h0, const StepArgs* d_args, const int* d_order, int nmodels,
@@ -38,10 +42,12 @@ struct gmf_sweep {
     int* d_order = nullptr;        // identity: slot -> its own argument entry
     int group = 0;                 // models per launch (0: all; GMF_SWEEP_SEQUENTIAL: model after model)
     size_t smem = 0;
+    uint32_t tmem_cols = 0;        // TMEM columns of the widest model's tile (persistent launch)
     size_t upd_smem = 0;   // update launch: the largest model's staging
     int upd_units = 0;     // update launch: CTAs per model
     int upd_threads = 0;   // tensor-core update launch: threads per CTA (the widest model's)
     int mixed = 0;
+    unsigned* gctr = nullptr;      // grid-barrier counter of the persistent launch
     cudaGraphExec_t graph = nullptr;
     cudaStream_t cap = nullptr;
 };
@@ -53,6 +59,7 @@ static void sweep_release(gmf_sweep* s) {
     if (s->d_args) cudaFree(s->d_args);
     if (s->d_lays) cudaFree(s->d_lays);
     if (s->d_order) cudaFree(s->d_order);
+    if (s->gctr) cudaFree(s->gctr);
     for (size_t i = s->models.size(); i-- > 0;) gmf_free(s->models[i]);  // the owner of the counts last
     delete s;
 }
@@ -105,19 +112,22 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
             const char* l = (const char*)gmf_tc_layout(h);
             lays.insert(lays.end(), l, l + gmf_tc_layout_size());
             s->slot_smem.push_back(gmf_tc_smem(h));
+            s->tmem_cols = std::max(s->tmem_cols, gmf_tc_tmem_cols(h));
         } else {
             s->slot_smem.push_back(gmf_sweep_simt_smem(h));
         }
         s->smem = std::max(s->smem, s->slot_smem.back());
         s->upd_smem = std::max(s->upd_smem, gmf_update_smem(args[i]));
     }
-    s->upd_units = gmf_update_units(args[0], s->mixed ? 128 : GMF_TILE);
+    s->upd_units = s->mixed ? gmf_update_tc_units(args[0], 128) : gmf_update_units(args[0], GMF_TILE);
     for (int i = 0; i < n_models; i++) s->upd_threads = std::max(s->upd_threads, gmf_update_tc_threads(args[i]));
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMalloc(&s->d_args, sizeof(StepArgs) * n_models) != cudaSuccess ||
         cudaMalloc(&s->d_order, sizeof(int) * n_models) != cudaSuccess ||
-        (s->mixed && cudaMalloc(&s->d_lays, lays.size()) != cudaSuccess))
+        (s->mixed && cudaMalloc(&s->d_lays, lays.size()) != cudaSuccess) ||
+        (s->mixed && cudaMalloc(&s->gctr, sizeof(unsigned)) != cudaSuccess))
         return sweep_fail(s, GMF_ERR_OOM, "gmf_sweep_init: device allocation failed");
+    if (s->gctr) cudaMemsetAsync(s->gctr, 0, sizeof(unsigned), st);
     cudaMemcpyAsync(s->d_args, args.data(), sizeof(StepArgs) * n_models, cudaMemcpyHostToDevice, st);
     std::vector<int> ident(n_models);
     for (int i = 0; i < n_models; i++) ident[i] = i;
@@ -133,9 +143,13 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
     return GMF_OK;
 }
 
-// One sweep of every model: per group of slots [g0, g0 + gn), a tile launch and an update launch.
+// One sweep of every model: per group of slots [g0, g0 + gn), a tile launch and an update launch, or one
+// persistent launch for all models.
 static cudaError_t launch(gmf_sweep* s, int w, cudaStream_t st, int group) {
     const int nm = (int)s->models.size();
+    if (group == GMF_SWEEP_PERSISTENT)
+        return gmf_tc_launch_multi_persist(s->models[0], s->d_args, s->d_lays, s->d_order, nm, (uint32_t)s->smem,
+                                           s->tmem_cols, w, s->gctr, s->models[0]->err, st);
     const int gsz = group > 0 ? std::min(group, nm) : nm;
     const size_t lay_bytes = s->mixed ? gmf_tc_layout_size() : 0;
     for (int g0 = 0; g0 < nm; g0 += gsz) {
@@ -185,6 +199,7 @@ extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream)
         if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return gmf_fail(GMF_ERR_CUDA, "gmf_sweep_epoch: capture failed");
         cudaError_t e = cudaSuccess;
+        if (s->group == GMF_SWEEP_PERSISTENT) e = cudaMemsetAsync(s->gctr, 0, sizeof(unsigned), s->cap);
         for (int w = 0; w < h0->nsw && e == cudaSuccess; w++) e = launch(s, w, s->cap, s->group);
         const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
         if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&s->graph, g, 0);
@@ -200,8 +215,10 @@ extern "C" int gmf_sweep_epoch(gmf_sweep* s, const int32_t* sigma, void* stream)
 }
 
 extern "C" int gmf_sweep_set_group(gmf_sweep* s, int32_t group) {
-    if (!s || group < GMF_SWEEP_SEQUENTIAL || group > (int32_t)s->models.size())
-        return gmf_fail(GMF_ERR_ARG, "gmf_sweep_set_group: group outside [-1, n_models]");
+    if (!s || ((group < GMF_SWEEP_SEQUENTIAL || group > (int32_t)s->models.size()) &&
+               !(group == GMF_SWEEP_PERSISTENT && s->mixed)))
+        return gmf_fail(GMF_ERR_ARG, "gmf_sweep_set_group: group outside [-1, n_models] (or a persistent launch on "
+                                     "the FP32 path)");
     if (group != s->group && s->graph) {
         cudaGraphExecDestroy(s->graph);  // recaptured by the next epoch
         s->graph = nullptr;
@@ -280,15 +297,16 @@ extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_
         if (g == 1) break;
     }
     cand.push_back(GMF_SWEEP_SEQUENTIAL);  // and every model's own launches, model after model
+    if (s->mixed) cand.push_back(GMF_SWEEP_PERSISTENT);  // and one persistent launch per sweep
     if (ms_out)
-        for (int i = 0; i <= nm; i++) ms_out[i] = -1.f;
+        for (int i = 0; i <= nm + 1; i++) ms_out[i] = -1.f;
     std::vector<int64_t> t_saved;
     for (gmf_model* h : s->models) t_saved.push_back(h->t);
     int inner_rc = GMF_OK;  // a failed single-model epoch (its message is kept)
     // one candidate's trial: its launches for sweeps [0, count) of every model
     auto trial = [&](int g, int count) -> cudaError_t {
         if (g != GMF_SWEEP_SEQUENTIAL) {
-            cudaError_t r = cudaSuccess;
+            cudaError_t r = g == GMF_SWEEP_PERSISTENT ? cudaMemsetAsync(s->gctr, 0, sizeof(unsigned), st) : cudaSuccess;
             for (int w = 0; w < count && r == cudaSuccess; w++) r = launch(s, w, st, g);
             return r;
         }
@@ -318,7 +336,7 @@ extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e != cudaSuccess) break;
-        if (ms_out) ms_out[g == GMF_SWEEP_SEQUENTIAL ? nm : g - 1] = ms;
+        if (ms_out) ms_out[g == GMF_SWEEP_SEQUENTIAL ? nm : g == GMF_SWEEP_PERSISTENT ? nm + 1 : g - 1] = ms;
         if (c == 0 || ms < best_ms) {
             best_ms = ms;
             best = g;
@@ -332,7 +350,7 @@ extern "C" int gmf_sweep_autotune(gmf_sweep* s, const int32_t* sigma, int32_t n_
     if (inner_rc != GMF_OK) return inner_rc;  // gmf_last_error holds the failing call's message
     if (e != cudaSuccess)
         return gmf_fail(GMF_ERR_CUDA, (std::string("gmf_sweep_autotune: ") + cudaGetErrorString(e)).c_str());
-    const int rc = gmf_sweep_set_group(s, best == nm ? 0 : best);  // (GMF_SWEEP_SEQUENTIAL is kept as is)
+    const int rc = gmf_sweep_set_group(s, best == nm ? 0 : best);  // (the negative settings are kept as they are)
     if (rc) return rc;
     if (group_out) *group_out = best;
     return GMF_OK;

@@ -298,8 +298,9 @@ __device__ __forceinline__ void update_unit(const StepArgs& a, int w, int T, int
 // ---- the update launch of the tensor-core path. Its tile kernel writes each
 // tile's partials column-major, slot[c * T + o] (G) and slot[(nf + c) * T + o]
 // (H), as the FP32 path does. One CTA per 32-row slice of a strip: lane r of
-// warp g owns row r of the slice and the free columns 2g, 2g+1, so every load
-// of a slot is one coalesced row of 32 floats. Each thread loads its
+// warp g owns row r of the slice and the free columns 2g, 2g+1 (a narrower
+// block takes the column groups in passes), so every load of a slot is one
+// coalesced row of 32 floats. Each thread loads its
 // parameters and smoothed derivatives before griddepcontrol.wait, then adds
 // the strip's slots in tile order (the same FP32 additions as slice_update, so
 // both give the same bits) with the loads of four slots in flight.
@@ -317,70 +318,73 @@ __host__ __device__ __forceinline__ int utc_units(int nk, int TI, int TJ, int T)
 __device__ __forceinline__ void slice_update_tc(const StepArgs& a, const float* __restrict__ part, size_t slot_stride,
                                                 int nslots, int T, int o_begin, int nr, int nf, int64_t first,
                                                 bool rowside, float scale, float rhoc_blk, int* s_cnt) {
-    const int r = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int c0 = UTC_CG * g;
-    const bool act = r < nr && c0 < nf;
-    const int nc = act ? min(UTC_CG, nf - c0) : 0;
+    const int r = threadIdx.x & 31, wq = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int G = (nf + UTC_CG - 1) / UTC_CG;  // column groups of this side
+    const int npass = (G + nw - 1) / nw;       // 1 when the block has a warp per group (the update launch)
     float* P = rowside ? a.L : a.R;
     float* Gb = rowside ? a.GbR : a.GbC;
     float* Hb = rowside ? a.HbR : a.HbC;
     int* cnt = rowside ? a.cntR : a.cntC;
     const int64_t row = first + r;
-    int col[UTC_CG];
-    float th[UTC_CG], gb[UTC_CG], hb[UTC_CG];
+    if (wq == 0 && r < nr) s_cnt[r] = __ldcg(cnt + row);
+    for (int pass = 0; pass < npass; pass++) {
+        const int c0 = UTC_CG * (wq + pass * nw);
+        const bool act = r < nr && c0 < nf;
+        const int nc = act ? min(UTC_CG, nf - c0) : 0;
+        int col[UTC_CG];
+        float th[UTC_CG], gb[UTC_CG], hb[UTC_CG];
 #pragma unroll
-    for (int u = 0; u < UTC_CG; u++) {
-        const int c = c0 + u;
-        col[u] = rowside ? 1 + a.p + c : (c < a.p ? 1 + c : 1 + a.q + c);
-        th[u] = gb[u] = hb[u] = 0.f;
-        if (u < nc) {
-            th[u] = __ldcg(P + row * a.KP + col[u]);
-            gb[u] = __ldcg(Gb + row * nf + c);
-            hb[u] = __ldcg(Hb + row * nf + c);
+        for (int u = 0; u < UTC_CG; u++) {
+            const int c = c0 + u;
+            col[u] = rowside ? 1 + a.p + c : (c < a.p ? 1 + c : 1 + a.q + c);
+            th[u] = gb[u] = hb[u] = 0.f;
+            if (u < nc) {
+                th[u] = __ldcg(P + row * a.KP + col[u]);
+                gb[u] = __ldcg(Gb + row * nf + c);
+                hb[u] = __ldcg(Hb + row * nf + c);
+            }
         }
-    }
-    if (g == 0 && r < nr) s_cnt[r] = __ldcg(cnt + row);
+        if (pass == 0) grid_dependency_wait();
 
-    grid_dependency_wait();
-
-    float gs[UTC_CG] = {}, hs[UTC_CG] = {};
-    if (act) {
-        const float* base = part + o_begin + r;
-        for (int t0 = 0; t0 < nslots; t0 += UTC_SIF) {
-            float gv[UTC_SIF][UTC_CG], hv[UTC_SIF][UTC_CG];
+        float gs[UTC_CG] = {}, hs[UTC_CG] = {};
+        if (act) {
+            const float* base = part + o_begin + r;
+            for (int t0 = 0; t0 < nslots; t0 += UTC_SIF) {
+                float gv[UTC_SIF][UTC_CG], hv[UTC_SIF][UTC_CG];
 #pragma unroll
-            for (int v = 0; v < UTC_SIF; v++)
-#pragma unroll
-                for (int u = 0; u < UTC_CG; u++) {
-                    const bool l = t0 + v < nslots && u < nc;
-                    const float* sp = base + (size_t)(t0 + v) * slot_stride + (size_t)(c0 + u) * T;
-                    gv[v][u] = l ? __ldcg(sp) : 0.f;
-                    hv[v][u] = l ? __ldcg(sp + (size_t)nf * T) : 0.f;
-                }
-#pragma unroll
-            for (int v = 0; v < UTC_SIF; v++)
-                if (t0 + v < nslots)
+                for (int v = 0; v < UTC_SIF; v++)
 #pragma unroll
                     for (int u = 0; u < UTC_CG; u++) {
-                        gs[u] += gv[v][u];
-                        hs[u] += hv[v][u];
+                        const bool l = t0 + v < nslots && u < nc;
+                        const float* sp = base + (size_t)(t0 + v) * slot_stride + (size_t)(c0 + u) * T;
+                        gv[v][u] = l ? __ldcg(sp) : 0.f;
+                        hv[v][u] = l ? __ldcg(sp + (size_t)nf * T) : 0.f;
                     }
-        }
-    }
-    __syncthreads();  // the slice's visit counts are in shared memory
 #pragma unroll
-    for (int u = 0; u < UTC_CG; u++) {
-        if (u < nc) {
-            const int c = c0 + u;
-            const float lam = rowside ? (c < a.q ? a.lam[1] : a.lam[2]) : (c < a.p ? a.lam[0] : a.lam[3]);
-            const float rc = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, s_cnt[r] + 1) : rhoc_blk;
-            smoothed_step(th[u], gb[u], hb[u], gs[u], hs[u], scale, lam, a, rc);
-            P[row * a.KP + col[u]] = th[u];
-            Gb[row * nf + c] = gb[u];
-            Hb[row * nf + c] = hb[u];
+                for (int v = 0; v < UTC_SIF; v++)
+                    if (t0 + v < nslots)
+#pragma unroll
+                        for (int u = 0; u < UTC_CG; u++) {
+                            gs[u] += gv[v][u];
+                            hs[u] += hv[v][u];
+                        }
+            }
+        }
+        if (pass == 0) __syncthreads();  // the slice's visit counts are in shared memory
+#pragma unroll
+        for (int u = 0; u < UTC_CG; u++) {
+            if (u < nc) {
+                const int c = c0 + u;
+                const float lam = rowside ? (c < a.q ? a.lam[1] : a.lam[2]) : (c < a.p ? a.lam[0] : a.lam[3]);
+                const float rc = a.bias_corr ? rhoc_blk * bias_visit(a.a1, a.a2, s_cnt[r] + 1) : rhoc_blk;
+                smoothed_step(th[u], gb[u], hb[u], gs[u], hs[u], scale, lam, a, rc);
+                P[row * a.KP + col[u]] = th[u];
+                Gb[row * nf + c] = gb[u];
+                Hb[row * nf + c] = hb[u];
+            }
         }
     }
-    if (g == 0 && r < nr) cnt[row] = s_cnt[r] + 1;
+    if (wq == 0 && r < nr) cnt[row] = s_cnt[r] + 1;
 }
 
 // One unit of the tensor-core update launch (tile edge T = 128).

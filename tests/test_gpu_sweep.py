@@ -94,7 +94,8 @@ def test_sweep_groupings_and_autotune_give_the_same_fits(gmf, precision):
 
     ref, _ = fit()
     assert ref.group == len(d_list)
-    for group in (2, 1, 3, gmf.GMF_SWEEP_SEQUENTIAL):
+    settings = (2, 1, 3, gmf.GMF_SWEEP_SEQUENTIAL) + ((gmf.GMF_SWEEP_PERSISTENT,) if precision == "mixed" else ())
+    for group in settings:
         sw, _ = fit(group)
         assert sw.group == group
         for i in range(len(d_list)):
@@ -103,7 +104,8 @@ def test_sweep_groupings_and_autotune_give_the_same_fits(gmf, precision):
                 np.testing.assert_array_equal(a[k], b[k], err_msg=f"group {group} model {i} {k}")
             assert a["alpha"] == b["alpha"]
     sw, (g, times) = fit(tune=True)
-    assert g in (4, 2, 1, -1) and sw.group == g and set(times) == {4, 2, 1, -1} and all(v > 0 for v in times.values())
+    tried = {4, 2, 1, -1} | ({gmf.GMF_SWEEP_PERSISTENT} if precision == "mixed" else set())
+    assert g in tried and sw.group == g and set(times) == tried and all(v > 0 for v in times.values())
     for i in range(len(d_list)):
         a, b = sw.models[i].get_params(), ref.models[i].get_params()
         for k in ("U", "V", "B", "Gamma"):
@@ -113,6 +115,9 @@ def test_sweep_groupings_and_autotune_give_the_same_fits(gmf, precision):
             np.testing.assert_array_equal(ea[k], eb[k], err_msg=f"autotuned model {i} {k}")
     with pytest.raises(gmf.GmfError):
         sw.group = 5
+    if precision == "fp32":
+        with pytest.raises(gmf.GmfError):
+            sw.group = gmf.GMF_SWEEP_PERSISTENT
 
 
 def test_batched_tensor_core_launch_smallest_and_largest_rank_match_oracle(gmf):
@@ -145,3 +150,33 @@ def test_batched_tensor_core_launch_smallest_and_largest_rank_match_oracle(gmf):
         assert dr < d0[i]
         assert abs(dg - dr) / dr <= 1e-3, (d_list[i], dg, dr)
         assert rel(sw.models[i].get_params()["U"], r.U) <= 2e-2
+
+
+@pytest.mark.parametrize("d_list", [[30, 2, 12, 20], [2, 5, 12, 20, 2, 5]])
+def test_persistent_launch_with_several_tiles_per_cta(gmf, d_list):
+    """The persistent rank-sweep launch with more tiles than resident CTAs, so
+    that most CTAs run two or more tiles of different models in turn: one
+    TMEM allocation per CTA (512 columns with d = 30 at one CTA per SM; 256
+    columns at two CTAs per SM when every d <= 27), mbarrier phases carried
+    across tiles. The fits equal those of the grouped launches bit for bit and
+    no wait timed out. 3000 x 1024 uint16 counts in 1000 x 512 blocks: 2
+    blocks of 8 x 4 tiles per sweep, 64 tiles per model and sweep."""
+    n, m, nbr, nbc = 3000, 1024, 1000, 512
+    prob = synth.make_problem(n, m, 3, 1, 8, "negbin", seed=21, y_dtype="uint16", zero_frac=0.85, offset=True)
+    starts = [synth.crude_start(prob, d, seed=21 + i) for i, d in enumerate(d_list)]
+    rp, cp = synth.partitions(n, m, 21)
+    st = synth.fit_settings(alpha_mode=1)
+    sig = synth.sweep_orders(n, m, nbr, nbc, 2, 21)
+    kw = dict(family="negbin", nb_row=nbr, nb_col=nbc, row_perm=rp, col_perm=cp, settings=st, precision="mixed")
+    fits = {}
+    for group in (len(d_list), gmf.GMF_SWEEP_PERSISTENT):
+        sw = gmf.Sweep(prob.Y, prob.X, prob.Z, prob.offset, starts, d_list, **kw)
+        sw.group = group
+        for e in range(2):
+            sw.epoch(sig[e])
+        fits[group] = [dict(mdl.get_params(), dev=mdl.deviance()) for mdl in sw.models]  # raises on a flagged wait
+    for i in range(len(d_list)):
+        a, b = fits[gmf.GMF_SWEEP_PERSISTENT][i], fits[len(d_list)][i]
+        for k in ("U", "V", "B", "Gamma"):
+            np.testing.assert_array_equal(a[k], b[k], err_msg=f"model {i} {k}")
+        assert a["alpha"] == b["alpha"] and a["dev"] == b["dev"]
