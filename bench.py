@@ -593,9 +593,13 @@ def run_headline(args, w):
     eps = w.epochs                      # epochs per step: one full fit pass
 
     def make(precision, Y=None):
-        return gmf.Model(prob.Y if Y is None else Y, prob.X, prob.Z, prob.offset, start, family=w.family,
-                         nb_row=w.nb_row, nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=settings,
-                         precision=precision)
+        flags = gmf.GMF_FLAG_PERSIST if (precision == "mixed" and args.epoch_launch == "persistent") else 0
+        mdl = gmf.Model(prob.Y if Y is None else Y, prob.X, prob.Z, prob.offset, start, family=w.family,
+                        nb_row=w.nb_row, nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=settings,
+                        precision=precision, flags=flags)
+        if args.flow_lag is not None:
+            mdl.set_flow_lag(args.flow_lag)
+        return mdl
 
     def step(mdl):
         for e in range(eps):
@@ -688,7 +692,9 @@ def run_headline(args, w):
     tflops = per_sweep["flops"] / sweep_s / 1e12
     tflops_exec = per_sweep["entries"] * (6 * K + 4 * fr + 4 * fc) / sweep_s / 1e12
     sfu = per_sweep["entries"] * 2 / sweep_s
-    tile_k = {"cluster": "sweep_tc_cluster", "persistent": "sweep_tc_epoch"}.get(epoch_mode, "sweep_tc_kernel")
+    flow = epoch_mode == "persistent" and -(-w.nb_row // 128) * -(-w.nb_col // 128) > 16
+    tile_k = {"cluster": "sweep_tc_cluster", "persistent": "sweep_tc_flow" if flow else "sweep_tc_epoch"}.get(
+        epoch_mode, "sweep_tc_kernel")
     sweep_kernels = [tile_k] if epoch_mode != "separate" else [tile_k, "update_tc_kernel"]
     roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s", "frac": hbm_gbs / peak,
             "traffic": committed_sweep_traffic(w.name, sweep_kernels),
@@ -998,6 +1004,10 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttd", action="store_true", help="skip the time-to-deviance comparison")
+    ap.add_argument("--epoch-launch", default="per-sweep", choices=["per-sweep", "persistent"],
+                    help="mixed precision on nb_atlas: per-sweep tile and update launches, or one persistent "
+                         "launch per epoch (GMF_FLAG_PERSIST)")
+    ap.add_argument("--flow-lag", type=int, default=None, help="item order of the persistent epoch (gmf_set_flow_lag)")
     ap.add_argument("--encoder-precision", default="mixed", choices=["fp32", "mixed"],
                     help="nb_project: the encoder's first layer on the tensor cores (mixed) or FP32")
     ap.add_argument("--case", default=None, choices=["atlas_sweep", "project_20000", "encoder_16384"],

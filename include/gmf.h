@@ -60,15 +60,21 @@ enum {
        exchange their partial sums through distributed shared memory. This flag
        keeps them in their own launch instead. Both give bitwise equal results. */
     GMF_FLAG_NO_CLUSTER = 1,
-    /* Mixed precision in cluster mode with a fixed NB shape (or Poisson): run
-       a whole epoch (or sweep range) as one persistent launch in which each
-       cluster runs its block of every sweep in turn and waits only for the
-       blocks that updated its moving strip earlier in the epoch (see
-       gmf_strip_schedule), instead of one launch per sweep. Bitwise equal
-       results. Off by default: on the 20000 x 2000 benchmark it is about 6%
-       slower, since the blocks of a cluster form a serial chain through the
-       fixed strip and each exchange of the moving strip between clusters
-       costs a device-scope release and acquire. */
+    /* Mixed precision: run a whole epoch (or sweep range) as one persistent
+       launch instead of one or two launches per sweep. Bitwise equal results.
+       In cluster mode (fixed NB shape or Poisson) each cluster runs its block
+       of every sweep in turn and waits only for the blocks that updated its
+       moving strip earlier in the epoch (see gmf_strip_schedule); on the
+       20000 x 2000 benchmark this is about 6% slower than the per-sweep
+       cluster launches, since the blocks of a cluster form a serial chain
+       through the fixed strip. Otherwise (blocks of more than 16 tiles, or
+       GMF_FLAG_NO_CLUSTER; any NB shape mode) the launch is a dataflow of
+       tile and update items taken in a fixed order by all resident CTAs, each
+       item waiting only for the updates of the strips it reads (see
+       gmf_set_flow_lag), so tiles of the next sweep run while the last tiles
+       and the updates of the current one finish. Without a device that can
+       keep every CTA resident the per-sweep launches stay (gmf_epoch_mode
+       tells which mode runs). */
     GMF_FLAG_PERSIST = 2
 };
 
@@ -568,6 +574,18 @@ int gmf_initialize(gmf_model* h, int32_t power_iters, uint64_t seed, double* sv_
  * Errors: GMF_ERR_ARG (NULL handle, values out of range).
  */
 int gmf_set_wait_limit(gmf_model* h, int64_t limit_ns, int32_t need_extra);
+
+/*
+ * gmf_set_flow_lag -- item order of the dataflow epoch (GMF_FLAG_PERSIST
+ * outside cluster mode): a block's update units are queued once `lag` further
+ * tile groups (blocks) have been queued after its tiles, or earlier where a
+ * later tile reads what they write (0 <= lag <= 64, default 2). A larger lag
+ * leaves the updates less waiting for their tiles, a smaller one frees the
+ * next sweep's tiles sooner. Takes effect from the next gmf_sgd_epoch /
+ * gmf_sgd_sweeps; results are bitwise the same for every lag. The paper has
+ * no counterpart. Errors: GMF_ERR_ARG (NULL handle, lag out of range).
+ */
+int gmf_set_flow_lag(gmf_model* h, int32_t lag);
 
 /* Release the handle and all of its device memory (NULL is allowed). */
 void gmf_free(gmf_model* h);

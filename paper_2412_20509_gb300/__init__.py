@@ -36,7 +36,7 @@ EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async
            "gmf_sgd_epoch", "gmf_sgd_sweeps",
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
-           "gmf_set_wait_limit", "gmf_sgd_sweep_blocks", "gmf_chunk_bytes", "gmf_chunk_state", "gmf_holdout",
+           "gmf_set_wait_limit", "gmf_set_flow_lag", "gmf_sgd_sweep_blocks", "gmf_chunk_bytes", "gmf_chunk_state", "gmf_holdout",
            "gmf_loglik", "gmf_initialize", "gmf_set_gene_shapes", "gmf_get_gene_shapes", "gmf_gene_shape_moments",
            "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_set_group", "gmf_sweep_group", "gmf_sweep_autotune",
            "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
@@ -101,6 +101,7 @@ def lib():
         "gmf_orthogonalize": (C.c_int, [VP, C.c_int32, VP]),
         "gmf_project_cells": (C.c_int, [VP, VP, C.c_int32, C.c_int64, VP, VP, VP, C.c_int32, VP, VP, VP, VP]),
         "gmf_set_wait_limit": (C.c_int, [VP, C.c_int64, C.c_int32]),
+        "gmf_set_flow_lag": (C.c_int, [VP, C.c_int32]),
         "gmf_sgd_sweep_blocks": (C.c_int, [VP, VP, C.c_int32, VP, C.c_int32, VP]),
         "gmf_chunk_bytes": (C.c_int64, [VP, C.c_int32, C.c_int32]),
         "gmf_chunk_state": (C.c_int, [VP, C.c_int32, C.c_int32, VP, C.c_int32, VP]),
@@ -418,6 +419,11 @@ class Model:
     def set_wait_limit(self, limit_ns=0, need_extra=0):
         """Testing hook of the persistent epoch's bounded strip waits (gmf_set_wait_limit)."""
         check(lib().gmf_set_wait_limit(self._h, int(limit_ns), int(need_extra)))
+
+    def set_flow_lag(self, lag):
+        """Item order of the dataflow epoch: a block's updates trail its tiles by
+        `lag` tile groups (gmf_set_flow_lag; bitwise the same results)."""
+        check(lib().gmf_set_flow_lag(self._h, int(lag)))
 
     def trace(self, enable=True):
         """Time every block-step launch with CUDA events on its stream."""

@@ -45,6 +45,8 @@ cudaError_t gmf_tc_launch(gmf_model* h, const StepArgs& a, int w, cudaStream_t s
 cudaError_t gmf_tc_launch_update(gmf_model* h, const StepArgs& a, int w, cudaStream_t st);
 int gmf_tc_cluster(const gmf_model* h);
 int gmf_tc_persistent(const gmf_model* h);
+int gmf_tc_flow(const gmf_model* h);
+int gmf_tc_stage_flow(gmf_model* h, const int32_t* sigma, int w0, int w1, cudaStream_t st);
 cudaError_t gmf_tc_launch_epoch(gmf_model* h, int w0, int w1, cudaStream_t st);
 int gmf_tc_set_ybuf(gmf_model* h, int idx, const void* Y);
 void gmf_tc_free(gmf_model* h);
@@ -262,6 +264,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     gmf_model* h = new gmf_model();
     memset(h, 0, sizeof *h);
     h->cfg = c;
+    h->flow_lag = 2;
     cudaGetDevice(&h->device);
     h->n = c.n;
     h->m = c.m;
@@ -488,8 +491,9 @@ extern "C" int32_t gmf_count_buffers(const gmf_model* h) {
 
 extern "C" int32_t gmf_epoch_mode(const gmf_model* h) {
     if (!h) return -1;
-    if (h->cfg.precision != GMF_PREC_MIXED || !gmf_tc_cluster(h)) return GMF_EPOCH_SEPARATE;
-    return gmf_tc_persistent(h) ? GMF_EPOCH_PERSISTENT : GMF_EPOCH_CLUSTER;
+    if (h->cfg.precision != GMF_PREC_MIXED) return GMF_EPOCH_SEPARATE;
+    if (gmf_tc_persistent(h)) return GMF_EPOCH_PERSISTENT;
+    return gmf_tc_cluster(h) ? GMF_EPOCH_CLUSTER : GMF_EPOCH_SEPARATE;
 }
 
 extern "C" int32_t gmf_launches_per_sweep(const gmf_model* h) {
@@ -560,6 +564,10 @@ int gmf_stage_schedule(gmf_model* h, const int32_t* sigma, int w_begin, int w_en
         if (h->need_extra > 0)
             for (size_t i = (size_t)w_begin * h->per; i < (size_t)w_end * h->per; i++) need[i] += h->need_extra;
         CUDA_TRY(cudaMemcpyAsync(h->need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, st));
+        if (gmf_tc_flow(h)) {
+            const int rc = gmf_tc_stage_flow(h, sigma, w_begin, w_end, st);
+            if (rc) return fail(rc, "staging the dataflow epoch's item order failed");
+        }
     }
     return GMF_OK;
 }
@@ -782,6 +790,13 @@ extern "C" int gmf_initialize(gmf_model* h, int32_t power_iters, uint64_t seed, 
     CUDA_TRY(cudaMemsetAsync(h->cntC, 0, sizeof(int) * h->m, st));
     h->t = 0;
     return check_err_word(h, st);
+}
+
+extern "C" int gmf_set_flow_lag(gmf_model* h, int32_t lag) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_set_flow_lag: NULL handle");
+    if (lag < 0 || lag > 64) return fail(GMF_ERR_ARG, "gmf_set_flow_lag: lag %d outside [0, 64]", lag);
+    h->flow_lag = lag;
+    return GMF_OK;
 }
 
 extern "C" int gmf_set_wait_limit(gmf_model* h, int64_t limit_ns, int32_t need_extra) {

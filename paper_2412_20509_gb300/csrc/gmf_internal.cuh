@@ -133,6 +133,7 @@ struct gmf_model {
     int64_t t;                  // blocks processed so far
     int64_t wait_ns;            // strip-wait limit of the persistent epoch (gmf_set_wait_limit; 0: 2 s)
     int32_t need_extra;         // added to every dependency count of a persistent range (gmf_set_wait_limit)
+    int32_t flow_lag;           // dataflow epoch: tile groups between a block's tiles and its updates (gmf_set_flow_lag)
     void* tc;                   // tensor-core path state (gmf_step_tc.cu), or nullptr
     // kernel timing (gmf_trace)
     int trace_on;

@@ -30,6 +30,10 @@
 #include <cudaTypedefs.h>
 #include <string.h>
 
+#include <algorithm>
+#include <deque>
+#include <vector>
+
 #include <string>
 
 #include "gmf_internal.cuh"
@@ -72,6 +76,12 @@ struct TcState {
     int cluster;           // 1: the strip updates run inside the tile launch (cluster mode)
     int persist;           // 1: a sweep range runs as one persistent launch (sweep_tc_epoch)
     int epi;               // epilogue variant (EPI_*)
+    int flow;              // 1: a sweep range runs as one dataflow launch (sweep_tc_flow)
+    int flow_grid;         // its CTAs
+    int flow_groups;       // item groups staged for the next launch
+    int4* fent;            // [2 nsw per]: group entries in launch order (see sweep_tc_flow)
+    int* fstart;           // [2 nsw per + 1]: first ticket of each group
+    unsigned* fctr;        // [3 + 2 per + max(r, s)]: the launch's counters
 };
 
 __device__ __forceinline__ void st_shared_v4(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -523,6 +533,122 @@ __device__ __forceinline__ void store_partials(const StepArgs& a, const TcLayout
     }
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+
+// One thread: spin until *cnt >= target. Gives up, flagging a time-out, after
+// limit_ns of the global timer (2 s unless gmf_set_wait_limit changed it) or as
+// soon as another CTA has flagged one.
+__device__ __forceinline__ void wait_count(const unsigned* cnt, unsigned target, unsigned* err, uint64_t limit_ns) {
+    if (ld_acquire_u32(cnt) >= target) return;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (ld_acquire_u32(cnt) >= target) return;
+        if (*(volatile unsigned*)err & GMF_DEVERR_TIMEOUT) return;
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(err, GMF_DEVERR_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// ---- the item queue of the dataflow epoch (sweep_tc_flow). One per CTA, in
+// shared memory. A CTA holds the item it works on (buffer cur), the next one,
+// decoded into buffer cur ^ 1 while the current one runs, and the ticket
+// after that (next).
+struct FlowQueue {
+    unsigned* ctr;       // the launch's counters
+    const int* gstart;   // [groups + 1]: first ticket of each group
+    const int4* gent;    // [groups]: group entries
+    int total;           // tickets of the launch
+    int next;            // the ticket taken ahead
+    int g;               // group of the last decoded ticket
+    int4 item[2];        // {ticket, index in its group}
+    int4 ent[2];         // the group entry
+    int ready[2];        // 1: the item's prerequisites were already met when looked at ahead
+};
+
+// Prerequisite i (0-2) of an item with group entry e: the counter (nullptr:
+// none) and the count it must reach (see sweep_tc_flow).
+__device__ __forceinline__ const unsigned* flow_dep(const StepArgs& a, unsigned* ctr, int4 e, int i,
+                                                    unsigned& target) {
+    const int pi = e.x >> 1, wr = pi / a.per, k = pi - wr * a.per;
+    if (e.x & 1) {  // update units: the block's tiles
+        target = (unsigned)e.y;
+        return i == 0 ? ctr + 3 + a.per + k : nullptr;
+    }
+    if (i == 0) {  // tiles: the previous update of the fixed strip (and of the block slot's partial slots)
+        target = (unsigned)e.y;
+        return e.y > 0 ? ctr + 3 + k : nullptr;
+    }
+    if (i == 1) {  // the last update of the moving strip
+        target = (unsigned)e.w;
+        return e.w > 0 ? ctr + 3 + 2 * a.per + e.z : nullptr;
+    }
+    target = (unsigned)wr;  // the NB shape after the previous sweep
+    return (a.family == GMF_NEGBIN && a.alpha_mode == 1 && wr > 0) ? ctr + 1 : nullptr;
+}
+
+// One thread: decode the ticket taken ahead into buffer nb and take another.
+__device__ __forceinline__ void flow_take(FlowQueue& q, int nb) {
+    const int t = q.next;
+    q.ready[nb] = 0;
+    if (t < q.total) {
+        int g = q.g;
+        while (__ldg(q.gstart + g + 1) <= t) g++;
+        q.g = g;
+        q.ent[nb] = __ldg(q.gent + g);
+        q.item[nb] = make_int4(t, t - __ldg(q.gstart + g), 0, 0);
+        q.next = (int)atomicAdd(q.ctr, 1u);
+    } else {
+        q.item[nb] = make_int4(t, 0, 0, 0);
+    }
+}
+
+// One warp, after its lane 0 decoded buffer nb: look once (lanes 0-2, acquire)
+// at the item's prerequisites; if all are met its wait is skipped.
+__device__ __forceinline__ void flow_look(FlowQueue& q, const StepArgs& a, int nb) {
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < 3 && q.item[nb].x < q.total) {
+        unsigned target;
+        const unsigned* c = flow_dep(a, q.ctr, q.ent[nb], lane, target);
+        if (c) ok = ld_acquire_u32(c) >= target;
+    }
+    const unsigned all = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) q.ready[nb] = all == 0xffffffffu;
+}
+
+// All threads: threads 0-2 wait for the prerequisites of the item in buffer
+// cur unless they were met at the look ahead; with take_next thread 3 decodes
+// the next item meanwhile.
+__device__ __forceinline__ void flow_wait(FlowQueue& q, const StepArgs& a, int cur, bool take_next) {
+    const int t = threadIdx.x;
+    if (t < 3 && !q.ready[cur]) {
+        unsigned target;
+        const unsigned* c = flow_dep(a, q.ctr, q.ent[cur], t, target);
+        if (c) wait_count(c, target, a.err, a.wait_ns);
+    } else if (t == 3 && take_next) {
+        flow_take(q, cur ^ 1);
+    }
+    __syncthreads();
+}
+
 // The CTA's three mbarriers (count tile, eta MMA, contraction MMAs) and its TMEM base.
 struct TileSync {
     uint64_t bars[3];
@@ -536,15 +662,19 @@ struct TileSync {
 // tmem_held the caller owns a TMEM allocation of at least Lo.tmem_cols columns
 // at ts.tmem_base (a CTA may allocate only until it gives up its permit, so a
 // CTA running several tiles allocates once); else the tile allocates and frees
-// its own. Returns true when the tile was active (its mbarriers completed one
-// phase).
-template <bool Y16, bool CL, int EPI>
+// its own. COH: model state is read through L2 only (other CTAs of the same
+// launch wrote it). fq: the dataflow queue whose item (buffer cur) this tile
+// is -- it waits for the item's prerequisites where a per-sweep launch waits
+// for the previous launch, and decodes and looks at the CTA's next item while
+// warps 0-7 store the partial sums; nullptr elsewhere. Returns true when the
+// tile was active (its mbarriers completed one phase).
+template <bool Y16, bool CL, int EPI, bool COH = false>
 __device__ __forceinline__ bool tc_tile(const StepArgs& a, const TcLayout& Lo, const CUtensorMap* ymap_p, int w,
                                         int k, int ti, int tj, uint8_t* smraw, TileSync& ts, uint32_t par,
-                                        bool init_bars, bool tmem_held) {
+                                        bool init_bars, bool tmem_held, FlowQueue* fq = nullptr, int cur = 0) {
     uint64_t* bars = ts.bars;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const BlockGeo g = block_geo(a, w, k);
+    const BlockGeo g = fq ? block_geo_strip(a, fq->ent[cur].z, k) : block_geo(a, w, k);
     const int nTI = (int)((g.nI + TT - 1) / TT), nTJ = (int)((g.mJ + TT - 1) / TT);
     const bool active = ti < nTI && tj < nTJ;
     float s1 = 0.f, s2 = 0.f;
@@ -579,11 +709,14 @@ __device__ __forceinline__ bool tc_tile(const StepArgs& a, const TcLayout& Lo, c
         // that the previous sweep's update launch may still be writing. The
         // next launch (this sweep's update) may start once every CTA is here,
         // i.e. once the previous update has completed.
-        grid_dependency_wait();
+        if (fq)
+            flow_wait(*fq, a, cur, false);
+        else
+            grid_dependency_wait();
         grid_launch_dependents();
-        const float alpha = *a.alpha;
+        const float alpha = COH ? __ldcg(a.alpha) : *a.alpha;
 
-        build_operands<false>(a, Lo, sm, row0, col0, nr, nc);
+        build_operands<COH>(a, Lo, sm, row0, col0, nr, nc);
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -603,10 +736,12 @@ __device__ __forceinline__ bool tc_tile(const StepArgs& a, const TcLayout& Lo, c
         if (ok && tid == 0) issue_contractions(Lo, sm, tb, &bars[2]);
         // warps 8-15 have no partials to read: they start the update slices' copies
         if (CL) cl_stage_issue(a, Lo, sm, cls, NTH / 2, NTH / 2);
+        if (fq && tid == 256) flow_take(*fq, cur ^ 1);  // its ticket's round trip overlaps the MMAs
         if (ok) ok = cta_wait(&bars[2], par, a.err);
         tc_fence_after();
         if (CL) cluster_wait();
 
+        if (fq && warp == 8) flow_look(*fq, a, cur ^ 1);  // beside the partial stores of warps 0-7
         if (ok) store_partials<CL>(a, Lo, sm, tb, k, ti, tj, nr, nc);
         if (!ok && tid == 0) atomicOr(a.err, GMF_DEVERR_TIMEOUT);
         fence_proxy_async_smem();  // a next tile of this CTA loads its counts over this one's operands
@@ -614,7 +749,10 @@ __device__ __forceinline__ bool tc_tile(const StepArgs& a, const TcLayout& Lo, c
         __syncthreads();
         if (warp == 0 && !tmem_held) tmem_dealloc(tb, Lo.tmem_cols);
     } else {
-        grid_dependency_wait();  // before writing this sweep's moment slot
+        if (fq)  // before writing this sweep's moment slot
+            flow_wait(*fq, a, cur, true);
+        else
+            grid_dependency_wait();
         grid_launch_dependents();
         if (CL) {
             cl_stage_issue(a, Lo, sm, cls, 0, NTH);
@@ -659,39 +797,6 @@ __device__ __forceinline__ bool tc_tile(const StepArgs& a, const TcLayout& Lo, c
 // written during the launch is read through L2 only. The next block's count
 // tile is loaded while the current block finishes. Results equal the
 // per-sweep launches bit for bit (same phases, same sums in the same order).
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void cluster_arrive_release() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-}
-
-// One thread: spin until *cnt >= target. Gives up, flagging a time-out, after
-// limit_ns of the global timer (2 s unless gmf_set_wait_limit changed it) or as
-// soon as another CTA has flagged one.
-__device__ __forceinline__ void wait_count(const unsigned* cnt, unsigned target, unsigned* err, uint64_t limit_ns) {
-    if (ld_acquire_u32(cnt) >= target) return;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        if (ld_acquire_u32(cnt) >= target) return;
-        if (*(volatile unsigned*)err & GMF_DEVERR_TIMEOUT) return;
-        if (global_ns() - t0 > limit_ns) {
-            atomicOr(err, GMF_DEVERR_TIMEOUT);
-            return;
-        }
-    }
-}
-
 // Block k of a sweep whose offset sigma[w] is sg (block_geo without the load).
 __device__ __forceinline__ BlockGeo block_geo_sg(const StepArgs& a, int sg, int k) {
     int rc, cc;
@@ -977,6 +1082,113 @@ __global__ void __launch_bounds__(NTH, Y16 ? 2 : 1)
         for (int mm = blockIdx.x; mm < nmod; mm += gridDim.x) nb_shape_update(av[mm], w);
 }
 
+// ---- dataflow epoch (tiles and updates of a sweep range in one persistent
+// launch, for blocks too large for cluster mode). The work items are the
+// tiles of block (w, k) -- group T(p), p = (w - w0) * per + k -- and that
+// block's update units -- group U(p). Every CTA takes items in ticket order
+// from a global counter. The host lays the groups out so that each item's
+// prerequisites come earlier: T(p) before U(p), and before T(p) the update of
+// the previous visit of each strip it reads (U(p - per) for the fixed strip,
+// the last earlier visit of the moving strip). A CTA takes a ticket only when
+// it runs, and holds at most the item it works on, the next one (decoded)
+// and the ticket after it; so the smallest unfinished item is always held by
+// a running CTA whose prerequisites are done, and the launch ends without any
+// CTA having to be resident at the same time as another (no cooperative
+// launch). The waits are bounded by the global timer all the same. A block's
+// updates trail its tiles by a few groups, so the tiles of the next sweep fill
+// the SMs that the last wave of a sweep leaves idle.
+// Counters, cumulative over the launch and zeroed before it:
+//   ctr[0]              tickets handed out
+//   ctr[1]              NB shape updates done (alpha_mode 1)
+//   ctr[2]              tiles done, all blocks (alpha_mode 1: the CTA finishing a sweep's last tile updates the shape)
+//   ctr[3 + k]          update units done of block slot k (its fixed strip and its partial slots)
+//   ctr[3 + per + k]    tiles done of block slot k
+//   ctr[3 + 2 per + j]  moving-side update units done of moving strip j
+// Group g (host-made, int4): tiles {2p, update units of slot k needed, moving
+// strip j, moving-side units of j needed}; updates {2p + 1, tiles of slot k
+// needed, j, 0}. Same tile and update functions, same sums in the same order
+// as the per-sweep launches: the results are equal bit for bit.
+template <bool Y16, int EPI>
+__global__ void __launch_bounds__(NTH, Y16 ? 2 : 1)
+    sweep_tc_flow(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int w0,
+                  const int4* __restrict__ gent, const int* __restrict__ gstart, int ngroups, unsigned* ctr,
+                  uint32_t tmem_cols) {
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    __shared__ TileSync ts;
+    __shared__ int s_cnt[UTC_SR];
+    __shared__ FlowQueue fq;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    constexpr int nsl = TT / UTC_SR;
+    if (warp == 0) tmem_alloc(&ts.tmem_base, tmem_cols);
+    if (tid == 3) {
+        fq.ctr = ctr;
+        fq.gstart = gstart;
+        fq.gent = gent;
+        fq.total = gstart[ngroups];
+        fq.g = 0;
+        fq.next = (int)atomicAdd(ctr, 1u);
+        flow_take(fq, 0);
+    }
+    __syncthreads();
+    uint32_t par = 0;
+    bool init = true;
+    for (int buf = 0;; buf ^= 1) {
+        const int4 it = fq.item[buf];
+        if (it.x >= fq.total) break;
+        const int4 e = fq.ent[buf];
+        const int pi = e.x >> 1, idx = it.y;
+        const int wr = pi / a.per, k = pi - wr * a.per, w = w0 + wr;
+        if ((e.x & 1) == 0) {  // tile idx of block (w, k)
+            if (tc_tile<Y16, false, EPI, true>(a, Lo, &ymap, w, k, idx / a.TJ, idx % a.TJ, smraw, ts, par, init, true,
+                                               &fq, buf)) {
+                par ^= 1u;
+                init = false;
+            }
+            __syncthreads();
+            if (tid == 32) {
+                // the tile's partial (and moment) sums, before its count: a release by a thread that the
+                // CTA barrier ordered after every other thread's stores
+                red_release_add_u32(ctr + 3 + a.per + k, 1u);
+                if (a.family == GMF_NEGBIN && a.alpha_mode == 1) {
+                    __threadfence();
+                    if (atomicAdd(ctr + 2, 1u) + 1u == (unsigned)((wr + 1) * a.per * a.TI * a.TJ)) {
+                        __threadfence();
+                        nb_shape_update(a, w);
+                        red_release_add_u32(ctr + 1, 1u);
+                    }
+                }
+            }
+        } else {  // update unit idx of block (w, k)
+            flow_wait(fq, a, buf, false);
+            // the widest side's column groups take warps 0 .. G-1; the last warp decodes and looks at the
+            // next item meanwhile (it only waits at the update's barriers)
+            if (warp == NTH / 32 - 1) {
+                if ((tid & 31) == 0) flow_take(fq, buf ^ 1);
+                flow_look(fq, a, buf ^ 1);
+            }
+            update_unit_tc(a, w, TT, k * (a.TI + a.TJ) * nsl + idx, s_cnt, e.z);
+            __syncthreads();
+            if (tid == 32) {  // the slice's parameters and smoothed derivatives, before its counts
+                red_release_add_u32(ctr + 3 + k, 1u);
+                const bool rowside = idx < a.TI * nsl;
+                if (rowside != (a.swap != 0)) red_release_add_u32(ctr + 3 + 2 * a.per + e.z, 1u);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(ts.tmem_base, tmem_cols);
+}
+
+template <int EPI>
+const void* tc_flow_fn_epi(int y16) {
+    return y16 ? (const void*)sweep_tc_flow<true, EPI> : (const void*)sweep_tc_flow<false, EPI>;
+}
+const void* tc_flow_fn(int y16, int epi) {
+    return epi == EPI_NB ? tc_flow_fn_epi<EPI_NB>(y16) : epi == EPI_PO ? tc_flow_fn_epi<EPI_PO>(y16)
+                                                                       : tc_flow_fn_epi<EPI_ANY>(y16);
+}
+
 template <int EPI>
 const void* tc_persist_fn_epi(int y16) {
     return y16 ? (const void*)sweep_tc_multi_persist<true, EPI> : (const void*)sweep_tc_multi_persist<false, EPI>;
@@ -997,6 +1209,8 @@ const void* tc_multi_fn(int y16, int epi) {
 
 int tc_cluster_layout(gmf_model* h, TcState* tc);
 int tc_persist_check(gmf_model* h, TcState* tc);
+int tc_flow_setup(gmf_model* h, TcState* tc);
+void gmf_tc_release(TcState* tc);
 
 int fail_str(std::string* err, const char* msg) {
     if (err) *err = msg;
@@ -1050,9 +1264,15 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
     L.JB = 128 / es;
     L.y_bytes = (uint32_t)(TT / L.JB) * ATOM;
     L.off_u = L.y_bytes;
-    // Ddot in place over 16-bit counts; not in the persistent epoch, which loads
-    // the next block's counts while the contractions still read Ddot
-    L.dd_in_y = (h->y16 && !(h->cfg.flags & GMF_FLAG_PERSIST)) ? 1 : 0;
+    // Ddot in place over 16-bit counts; not where the persistent cluster epoch
+    // may run, which loads the next block's counts while the contractions still
+    // read Ddot
+    {
+        const int64_t ti = (std::min<int64_t>(h->cfg.nb_row, h->n) + TT - 1) / TT;
+        const int64_t tj = (std::min<int64_t>(h->cfg.nb_col, h->m) + TT - 1) / TT;
+        const bool cl_epoch = (h->cfg.flags & GMF_FLAG_PERSIST) && !(h->cfg.flags & GMF_FLAG_NO_CLUSTER) && ti * tj <= 16;
+        L.dd_in_y = (h->y16 && !cl_epoch) ? 1 : 0;
+    }
     L.off_dd = L.dd_in_y ? 0u : L.off_u;
     L.off_ddd = L.dd_in_y ? L.off_u : L.off_u + 2u * ATOM;
     const uint32_t size_u = std::max<uint32_t>(2u * L.KA * ATOM, (L.dd_in_y ? 2u : 4u) * ATOM);
@@ -1100,6 +1320,14 @@ int gmf_tc_prepare_checked(gmf_model* h, std::string* err) {
     tc->persist = 0;
     if (!(h->cfg.flags & GMF_FLAG_NO_CLUSTER) && tc->TI * tc->TJ <= 16) tc->cluster = tc_cluster_layout(h, tc);
     if (tc->cluster && (h->cfg.flags & GMF_FLAG_PERSIST)) tc->persist = tc_persist_check(h, tc);
+    if (!tc->cluster && (h->cfg.flags & GMF_FLAG_PERSIST)) {
+        const int rc = tc_flow_setup(h, tc);
+        if (rc != GMF_OK) {
+            gmf_tc_release(tc);
+            if (err) *err = "device allocation for the dataflow epoch failed";
+            return rc;
+        }
+    }
     h->tc = tc;
     return GMF_OK;
 }
@@ -1156,6 +1384,54 @@ int tc_cluster_layout(gmf_model* h, TcState* tc) {
 // The persistent epoch needs every cluster of a sweep resident at once (the
 // same occupancy test) and a fixed NB shape: the per-sweep shape estimate of
 // alpha_mode 1 pools all clusters of a sweep, which this launch never joins.
+// The dataflow epoch's grid: as many CTAs as fit on the device at once by
+// registers, shared memory, threads and TMEM (each CTA holds its tile's TMEM
+// for the whole launch), computed from the kernel's attributes (the launch
+// needs no co-residency, so an estimate that is too high only queues CTAs).
+// Returns GMF_OK with tc->flow = 0 where it cannot run (the per-sweep launches
+// stay), an error only when an allocation fails.
+int tc_flow_setup(gmf_model* h, TcState* tc) {
+    const void* fn = tc_flow_fn(h->y16, tc->epi);
+    int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, resv = 0;
+    cudaFuncAttributes fa;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        gmf_smem_limit(fn, tc->lay.smem) != cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return GMF_OK;
+    }
+    const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * (NTH / 32);  // allocated per warp, 256 at a time
+    const size_t smem_cta = (size_t)tc->lay.smem + fa.sharedSizeBytes + (size_t)resv;
+    int per_sm = std::min({regs_sm / std::max(regs_cta, 1), (int)((size_t)smem_sm / smem_cta), thr_sm / NTH,
+                           (int)(512u / tc->lay.tmem_cols)});
+    if (per_sm < 1) return GMF_OK;
+    const size_t groups = (size_t)2 * h->nsw * h->per;
+    const size_t nctr = 3 + 2 * (size_t)h->per + (size_t)std::max(h->r, h->s);
+    if (cudaMalloc(&tc->fent, sizeof(int4) * groups) != cudaSuccess ||
+        cudaMalloc(&tc->fstart, sizeof(int) * (groups + 1)) != cudaSuccess ||
+        cudaMalloc(&tc->fctr, sizeof(unsigned) * nctr) != cudaSuccess) {
+        cudaGetLastError();
+        return GMF_ERR_OOM;
+    }
+    tc->flow_grid = per_sm * sms;
+    tc->flow = 1;
+    return GMF_OK;
+}
+
+void gmf_tc_release(TcState* tc) {
+    if (tc->fent) cudaFree(tc->fent);
+    if (tc->fstart) cudaFree(tc->fstart);
+    if (tc->fctr) cudaFree(tc->fctr);
+    delete tc;
+}
+
 int tc_persist_check(gmf_model* h, TcState* tc) {
     if (h->cfg.family == GMF_NEGBIN && h->cfg.alpha_mode == 1) return 0;
     if (tc->lay.dd_in_y) return 0;  // the next block's count tile would overwrite Ddot
@@ -1213,8 +1489,11 @@ cudaError_t gmf_tc_launch_update(gmf_model* h, const StepArgs& base, int w, cuda
 
 // The sweeps [w0, w1) as one persistent launch (sweep_tc_epoch): the strip
 // completion counts start from zero.
+static cudaError_t tc_launch_flow(gmf_model* h, int w0, int w1, cudaStream_t st);
+
 cudaError_t gmf_tc_launch_epoch(gmf_model* h, int w0, int w1, cudaStream_t st) {
     TcState* tc = (TcState*)h->tc;
+    if (tc->flow) return tc_launch_flow(h, w0, w1, st);
     cudaError_t e = cudaMemsetAsync(h->strip_done, 0, sizeof(unsigned) * (size_t)std::max(h->r, h->s), st);
     if (e != cudaSuccess) return e;
     StepArgs a = gmf_make_args(h);
@@ -1236,7 +1515,84 @@ cudaError_t gmf_tc_launch_epoch(gmf_model* h, int w0, int w1, cudaStream_t st) {
     return cudaLaunchKernelExC(&cfg, tc_epoch_fn(h->y16, tc->epi), args);
 }
 
-int gmf_tc_persistent(const gmf_model* h) { return h->tc && ((const TcState*)h->tc)->persist; }
+int gmf_tc_persistent(const gmf_model* h) {
+    return h->tc && (((const TcState*)h->tc)->persist || ((const TcState*)h->tc)->flow);
+}
+int gmf_tc_flow(const gmf_model* h) { return h->tc && ((const TcState*)h->tc)->flow; }
+
+// The group order of the dataflow launch over sweeps [w0, w1) (see
+// sweep_tc_flow): T(p) in block order; U(p) once `lag` later tile groups are
+// out, or earlier where a tile group reads what U(p) writes. Each entry holds
+// the counts its items wait for. Staged with the epoch's schedule.
+int gmf_tc_stage_flow(gmf_model* h, const int32_t* sigma, int w0, int w1, cudaStream_t st) {
+    TcState* tc = (TcState*)h->tc;
+    const int per = h->per, swap = h->swap, mod = swap ? h->s : h->r;
+    const int P = (w1 - w0) * per;
+    const int tij = tc->TI * tc->TJ, nsl = TT / UTC_SR, ub = (tc->TI + tc->TJ) * nsl;
+    const int mu = (swap ? tc->TJ : tc->TI) * nsl;  // moving-side units of a block
+    const int lag = std::max(0, h->flow_lag);
+    std::vector<int4> ent;
+    std::vector<int> start;
+    ent.reserve((size_t)2 * P);
+    start.reserve((size_t)2 * P + 1);
+    std::vector<int> last((size_t)mod, -1), visits((size_t)mod, 0);
+    std::deque<int> pending;  // tile groups whose update group is not out yet, in order
+    int ticket = 0;
+    auto strip = [&](int p) { return (sigma[w0 + p / per] + p % per) % mod; };
+    auto updates_through = [&](int q) {
+        while (!pending.empty() && pending.front() <= q) {
+            const int u = pending.front();
+            pending.pop_front();
+            start.push_back(ticket);
+            ent.push_back(make_int4(2 * u + 1, (u / per + 1) * tij, strip(u), 0));
+            ticket += ub;
+        }
+    };
+    for (int p = 0; p < P; p++) {
+        const int wr = p / per;
+        const int j = strip(p);
+        if (wr > 0) updates_through(p - per);
+        if (last[(size_t)j] >= 0) updates_through(last[(size_t)j]);
+        const int nd = visits[(size_t)j] + h->need_extra;  // earlier visits of the moving strip in this launch
+        start.push_back(ticket);
+        ent.push_back(make_int4(2 * p, wr * ub, j, nd * mu));
+        ticket += tij;
+        pending.push_back(p);
+        last[(size_t)j] = p;
+        visits[(size_t)j]++;
+        while ((int)pending.size() > lag) updates_through(pending.front());
+    }
+    updates_through(P);
+    start.push_back(ticket);
+    tc->flow_groups = (int)ent.size();
+    if (ent.empty()) return GMF_OK;
+    if (cudaMemcpyAsync(tc->fent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(tc->fstart, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+        return GMF_ERR_CUDA;
+    return GMF_OK;
+}
+
+static cudaError_t tc_launch_flow(gmf_model* h, int w0, int w1, cudaStream_t st) {
+    TcState* tc = (TcState*)h->tc;
+    const size_t nctr = 3 + 2 * (size_t)h->per + (size_t)std::max(h->r, h->s);
+    cudaError_t e = cudaMemsetAsync(tc->fctr, 0, sizeof(unsigned) * nctr, st);
+    if (e != cudaSuccess) return e;
+    StepArgs a = gmf_make_args(h);
+    a.TI = tc->TI;
+    a.TJ = tc->TJ;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tc->flow_grid);
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = tc->lay.smem;
+    cfg.stream = st;
+    uint32_t cols = tc->lay.tmem_cols;
+    int ng = tc->flow_groups;
+    void* args[] = {&a, (void*)&tc->lay, (void*)&tc->ymap[h->ycur], &w0, (void*)&tc->fent, (void*)&tc->fstart, &ng,
+                    (void*)&tc->fctr, &cols};
+    (void)w1;
+    return cudaLaunchKernelExC(&cfg, tc_flow_fn(h->y16, tc->epi), args);
+}
 
 size_t gmf_tc_layout_size() { return sizeof(TcLayout); }
 const void* gmf_tc_layout(const gmf_model* h) { return &((const TcState*)h->tc)->lay; }
@@ -1316,6 +1672,6 @@ cudaError_t gmf_tc_launch_multi_persist(const gmf_model* h0, const StepArgs* d_a
 int gmf_tc_cluster(const gmf_model* h) { return h->tc && ((const TcState*)h->tc)->cluster; }
 
 void gmf_tc_free(gmf_model* h) {
-    delete (TcState*)h->tc;
+    if (h->tc) gmf_tc_release((TcState*)h->tc);
     h->tc = nullptr;
 }

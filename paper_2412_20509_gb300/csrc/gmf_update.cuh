@@ -45,6 +45,18 @@ __device__ __forceinline__ BlockGeo block_geo(const StepArgs& a, int w, int k) {
     return g;
 }
 
+// The same block from its moving strip j (the row chunk, or the column chunk
+// when the roles swap), which the caller already knows: no load of sigma.
+__device__ __forceinline__ BlockGeo block_geo_strip(const StepArgs& a, int j, int k) {
+    const int rc = a.swap ? k : j, cc = a.swap ? j : k;
+    BlockGeo g;
+    g.r0 = (int64_t)rc * a.nb_row;
+    g.nI = min((int64_t)a.nb_row, a.n - g.r0);
+    g.c0 = (int64_t)cc * a.nb_col;
+    g.mJ = min((int64_t)a.nb_col, a.m - g.c0);
+    return g;
+}
+
 template <int NT>
 __device__ __forceinline__ float block_sum_f(float v, float* red) {
 #pragma unroll
@@ -387,14 +399,16 @@ __device__ __forceinline__ void slice_update_tc(const StepArgs& a, const float* 
     if (wq == 0 && r < nr) cnt[row] = s_cnt[r] + 1;
 }
 
-// One unit of the tensor-core update launch (tile edge T = 128).
-__device__ __forceinline__ void update_unit_tc(const StepArgs& a, int w, int T, int unit, int* s_cnt) {
+// One unit of the tensor-core update launch (tile edge T = 128). strip >= 0:
+// the block's moving strip, known to the caller.
+__device__ __forceinline__ void update_unit_tc(const StepArgs& a, int w, int T, int unit, int* s_cnt,
+                                               int strip = -1) {
     const int nsl = (T + UTC_SR - 1) / UTC_SR;
     const int per_block = (a.TI + a.TJ) * nsl;
     const int kz = unit / per_block;
     const int k = block_of_slot(a, kz);
     const int rem = unit - kz * per_block;
-    const BlockGeo g = block_geo(a, w, k);
+    const BlockGeo g = strip >= 0 ? block_geo_strip(a, strip, k) : block_geo(a, w, k);
     const int nTI = (int)((g.nI + T - 1) / T), nTJ = (int)((g.mJ + T - 1) / T);
     const float rhoc_blk = a.rhoc[w * a.per + k];
     if (rem < a.TI * nsl) {  // row strip ti of block k

@@ -93,6 +93,7 @@ def test_null_handle_calls_fail_cleanly(gmf):
     assert L.gmf_orthogonalize(None, 1, None) == gmf.GMF_ERR_ARG
     assert L.gmf_num_sweeps(None) == -1
     assert L.gmf_set_wait_limit(None, 0, 0) == gmf.GMF_ERR_ARG
+    assert L.gmf_set_flow_lag(None, 2) == gmf.GMF_ERR_ARG
     L.gmf_free(None)
 
 
