@@ -379,6 +379,7 @@ KERNEL_SOURCES = {
     "sweep_tc_kernel": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
     "sweep_tc_cluster": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
     "sweep_tc_epoch": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
+    "sweep_tc_flow": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
     "sweep_kernel": ["gmf_step_simt.cu", "gmf_update.cuh", "gmf_internal.cuh"],
     "update_kernel": ["gmf_update.cu", "gmf_update.cuh", "gmf_internal.cuh"],
     "update_tc_kernel": ["gmf_update.cu", "gmf_update.cuh", "gmf_internal.cuh"],
