@@ -744,7 +744,7 @@ __device__ __forceinline__ bool tc_tile(const StepArgs& a, const TcLayout& Lo, c
         if (fq && warp == 8) flow_look(*fq, a, cur ^ 1);  // beside the partial stores of warps 0-7
         if (ok) store_partials<CL>(a, Lo, sm, tb, k, ti, tj, nr, nc);
         if (!ok && tid == 0) atomicOr(a.err, GMF_DEVERR_TIMEOUT);
-        fence_proxy_async_smem();  // a next tile of this CTA loads its counts over this one's operands
+        if (tmem_held) fence_proxy_async_smem();  // a next tile of this CTA loads its counts over this one's operands
         tc_fence_before();
         __syncthreads();
         if (warp == 0 && !tmem_held) tmem_dealloc(tb, Lo.tmem_cols);
@@ -1076,7 +1076,7 @@ __global__ void __launch_bounds__(NTH, Y16 ? 2 : 1)
         __syncthreads();
         if (threadIdx.x == 0) s_a = av[order[slot]];
         __syncthreads();
-        update_unit_tc(s_a, w, TT, it - slot * units, s_cnt);
+        update_unit_tc<true>(s_a, w, TT, it - slot * units, s_cnt);
     }
     if (threadIdx.x == 0)
         for (int mm = blockIdx.x; mm < nmod; mm += gridDim.x) nb_shape_update(av[mm], w);
@@ -1166,7 +1166,7 @@ __global__ void __launch_bounds__(NTH, Y16 ? 2 : 1)
                 if ((tid & 31) == 0) flow_take(fq, buf ^ 1);
                 flow_look(fq, a, buf ^ 1);
             }
-            update_unit_tc(a, w, TT, k * (a.TI + a.TJ) * nsl + idx, s_cnt, e.z);
+            update_unit_tc<true>(a, w, TT, k * (a.TI + a.TJ) * nsl + idx, s_cnt, e.z);
             __syncthreads();
             if (tid == 32) {  // the slice's parameters and smoothed derivatives, before its counts
                 red_release_add_u32(ctr + 3 + k, 1u);

@@ -31,8 +31,14 @@ __global__ void __launch_bounds__(UPD_NT) update_multi(const StepArgs* __restric
     if (blockIdx.x == 0 && threadIdx.x == 0) nb_shape_update(s_a, w);
 }
 
-// The update launch of the tensor-core path (row-major partial slots).
-__global__ void __launch_bounds__(1024) update_tc_kernel(StepArgs a, int w, int T) {
+// The update launch of the tensor-core path (column-major partial slots). Two
+// instances: blocks of up to 384 threads (q + d and p + d up to 24) capped at
+// 40 registers, so four CTAs share an SM and a sweep's units run as one wave
+// (480 units of 384 threads on 152 SMs for 5 blocks of 2048 x 1024; the
+// register cap costs a few spilled values, measured faster than 2 or 3 CTAs
+// per SM), and any width up to 1024 threads.
+template <int NTMAX, int MINB>
+__global__ void __launch_bounds__(NTMAX, MINB) update_tc_kernel(StepArgs a, int w, int T) {
     __shared__ int s_cnt[UTC_SR];
     grid_launch_dependents();
     update_unit_tc(a, w, T, blockIdx.x, s_cnt);  // waits for the tile launch inside
@@ -40,7 +46,8 @@ __global__ void __launch_bounds__(1024) update_tc_kernel(StepArgs a, int w, int 
 }
 
 // Several models sharing the partitions (rank sweep): blockIdx.y = model.
-__global__ void __launch_bounds__(1024) update_tc_multi(const StepArgs* __restrict__ av, int w, int T) {
+template <int NTMAX, int MINB>
+__global__ void __launch_bounds__(NTMAX, MINB) update_tc_multi(const StepArgs* __restrict__ av, int w, int T) {
     __shared__ StepArgs s_a;
     __shared__ int s_cnt[UTC_SR];
     grid_launch_dependents();
@@ -90,15 +97,22 @@ cudaError_t gmf_launch_chunk_state(float* P, float* Gb, float* Hb, int* cnt, int
     return cudaGetLastError();
 }
 
+constexpr int UTC_NARROW = 384;  // widest block of the four-per-SM instances
+
 cudaError_t gmf_launch_update_tc(const StepArgs& a, int w, int T, cudaStream_t st) {
-    return gmf_launch_pdl(update_tc_kernel, dim3((unsigned)utc_units(a.nk, a.TI, a.TJ, T)),
-                          dim3((unsigned)(UTC_SR * utc_groups(a.fr, a.fc))), 0, st, a, w, T);
+    const int threads = UTC_SR * utc_groups(a.fr, a.fc);
+    const dim3 grid((unsigned)utc_units(a.nk, a.TI, a.TJ, T));
+    if (threads <= UTC_NARROW)
+        return gmf_launch_pdl(update_tc_kernel<UTC_NARROW, 4>, grid, dim3((unsigned)threads), 0, st, a, w, T);
+    return gmf_launch_pdl(update_tc_kernel<1024, 1>, grid, dim3((unsigned)threads), 0, st, a, w, T);
 }
 
 cudaError_t gmf_launch_update_tc_multi(const StepArgs* d_args, int nmodels, int units, int threads, int w, int T,
                                        cudaStream_t st) {
-    return gmf_launch_pdl(update_tc_multi, dim3((unsigned)units, (unsigned)nmodels), dim3((unsigned)threads), 0, st,
-                          d_args, w, T);
+    const dim3 grid((unsigned)units, (unsigned)nmodels);
+    if (threads <= UTC_NARROW)
+        return gmf_launch_pdl(update_tc_multi<UTC_NARROW, 4>, grid, dim3((unsigned)threads), 0, st, d_args, w, T);
+    return gmf_launch_pdl(update_tc_multi<1024, 1>, grid, dim3((unsigned)threads), 0, st, d_args, w, T);
 }
 
 int gmf_update_tc_threads(const StepArgs& a) { return UTC_SR * utc_groups(a.fr, a.fc); }

@@ -327,12 +327,13 @@ __host__ __device__ __forceinline__ int utc_units(int nk, int TI, int TJ, int T)
     return nk * (TI + TJ) * ((T + UTC_SR - 1) / UTC_SR);
 }
 
+template <bool PASSES>
 __device__ __forceinline__ void slice_update_tc(const StepArgs& a, const float* __restrict__ part, size_t slot_stride,
                                                 int nslots, int T, int o_begin, int nr, int nf, int64_t first,
                                                 bool rowside, float scale, float rhoc_blk, int* s_cnt) {
     const int r = threadIdx.x & 31, wq = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int G = (nf + UTC_CG - 1) / UTC_CG;  // column groups of this side
-    const int npass = (G + nw - 1) / nw;       // 1 when the block has a warp per group (the update launch)
+    const int npass = PASSES ? (G + nw - 1) / nw : 1;  // PASSES = false: a warp per group (the update launch)
     float* P = rowside ? a.L : a.R;
     float* Gb = rowside ? a.GbR : a.GbC;
     float* Hb = rowside ? a.HbR : a.HbC;
@@ -400,7 +401,9 @@ __device__ __forceinline__ void slice_update_tc(const StepArgs& a, const float* 
 }
 
 // One unit of the tensor-core update launch (tile edge T = 128). strip >= 0:
-// the block's moving strip, known to the caller.
+// the block's moving strip, known to the caller. PASSES: the CTA may have
+// fewer warps than the widest side has column groups (persistent kernels).
+template <bool PASSES = false>
 __device__ __forceinline__ void update_unit_tc(const StepArgs& a, int w, int T, int unit, int* s_cnt,
                                                int strip = -1) {
     const int nsl = (T + UTC_SR - 1) / UTC_SR;
@@ -419,7 +422,7 @@ __device__ __forceinline__ void update_unit_tc(const StepArgs& a, int w, int T, 
             return;
         }
         const size_t ss = (size_t)T * 2 * a.fr;
-        slice_update_tc(a, a.partR + (size_t)((k * a.TI + ti) * a.TJ) * ss, ss, nTJ, T, o_begin,
+        slice_update_tc<PASSES>(a, a.partR + (size_t)((k * a.TI + ti) * a.TJ) * ss, ss, nTJ, T, o_begin,
                         min(UTC_SR, nstrip - o_begin), a.fr, g.r0 + (int64_t)ti * T + o_begin, true,
                         (float)a.m / (float)g.mJ, rhoc_blk, s_cnt);
     } else {  // column strip tj of block k
@@ -431,7 +434,7 @@ __device__ __forceinline__ void update_unit_tc(const StepArgs& a, int w, int T, 
             return;
         }
         const size_t ss = (size_t)T * 2 * a.fc;
-        slice_update_tc(a, a.partC + (size_t)((k * a.TJ + tj) * a.TI) * ss, ss, nTI, T, o_begin,
+        slice_update_tc<PASSES>(a, a.partC + (size_t)((k * a.TJ + tj) * a.TI) * ss, ss, nTI, T, o_begin,
                         min(UTC_SR, nstrip - o_begin), a.fc, g.c0 + (int64_t)tj * T + o_begin, false,
                         (float)a.n / (float)g.nI, rhoc_blk, s_cnt);
     }
