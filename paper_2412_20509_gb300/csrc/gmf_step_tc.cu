@@ -349,19 +349,25 @@ __device__ __forceinline__ void build_operands(const StepArgs& a, const TcLayout
             const int c = c0 + lane;
             const bool cok = c < nf;
             const int col = cok ? (isL ? (c < a.p ? 1 + c : 1 + a.q + c) : 1 + a.p + c) : 0;
-            for (int rg = wq; rg < TT / 8; rg += 4) {
-                float v[8];
+            // the warp's four 8-row groups rg = wq + 4 it: all 32 loads in flight before the first store
+            float v[4][8];
+#pragma unroll
+            for (int it = 0; it < 4; it++)
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
-                    const int rr = 8 * rg + u;
-                    v[u] = (cok && rr < nvalid) ? ld_state<COH>(base + (int64_t)rr * a.KP + col) : 0.f;
+                    const int rr = 8 * (wq + 4 * it) + u;
+                    v[it][u] = (cok && rr < nvalid) ? ld_state<COH>(base + (int64_t)rr * a.KP + col) : 0.f;
                 }
-                if (c < NF) {
+            if (c < NF) {
+#pragma unroll
+                for (int it = 0; it < 4; it++) {
+                    const int rg = wq + 4 * it;
+                    const float* x = v[it];
                     const uint32_t off = (uint32_t)(rg >> 3) * atom + sw128_off(c, (8 * rg & 63) * 2);
-                    st_shared_v4(o1 + off, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                                 pack_bf16x2(v[6], v[7]));
-                    st_shared_v4(o2 + off, pack_bf16x2(v[0] * v[0], v[1] * v[1]), pack_bf16x2(v[2] * v[2], v[3] * v[3]),
-                                 pack_bf16x2(v[4] * v[4], v[5] * v[5]), pack_bf16x2(v[6] * v[6], v[7] * v[7]));
+                    st_shared_v4(o1 + off, pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]), pack_bf16x2(x[4], x[5]),
+                                 pack_bf16x2(x[6], x[7]));
+                    st_shared_v4(o2 + off, pack_bf16x2(x[0] * x[0], x[1] * x[1]), pack_bf16x2(x[2] * x[2], x[3] * x[3]),
+                                 pack_bf16x2(x[4] * x[4], x[5] * x[5]), pack_bf16x2(x[6] * x[6], x[7] * x[7]));
                 }
             }
         }
