@@ -540,6 +540,30 @@ int gmf_get_gene_shapes(gmf_model* h, double* alpha, void* stream);
 int gmf_gene_shape_moments(gmf_model* h, double eps, double cap, double* alpha_out, void* stream);
 
 /*
+ * gmf_gene_shape_ml -- maximum-likelihood negative binomial shape of every gene
+ * with the fit's means held fixed: for gene j, alpha_j maximises the NB
+ * log-likelihood of App. B (Table S1's NB density, the lgamma terms included)
+ * over the gene's observed entries, weights applied. Newton's method in
+ * log alpha, all genes at once: each iteration is one pass over the counts
+ * forming l'_j and l''_j (digamma and trigamma differences: exact sums of
+ * 1/(alpha + k) for counts below 16, shifted asymptotic series above; FP32 terms
+ * with compensated sums, FP64 across threads), then per gene a Newton step
+ * where l is concave in log alpha, else a unit step uphill; steps are capped at
+ * 1 in log alpha and alpha is kept in [lo, hi] (a gene without overdispersion
+ * goes to hi). A gene stops when its step is at most tol. start (m values,
+ * caller's gene order) is the first iterate, or NULL for the fit's current
+ * shapes (per gene with alpha_mode 2, else the one shape). alpha_out (host, m
+ * values, caller's order) receives the estimates and iters_done (may be NULL)
+ * the passes made (1 <= iters <= 200). The shapes of the fit are not changed
+ * (gmf_set_gene_shapes sets them). Synchronous.
+ * Errors: GMF_ERR_ARG (NULL pointers, values out of range), GMF_ERR_STATE (not
+ * a negative binomial fit), GMF_ERR_OOM, GMF_ERR_CUDA, and the handle's status
+ * word (GMF_ERR_TIMEOUT, GMF_ERR_NONFINITE).
+ */
+int gmf_gene_shape_ml(gmf_model* h, const double* start, int32_t iters, double tol, double lo, double hi,
+                      double* alpha_out, int32_t* iters_done, void* stream);
+
+/*
  * gmf_initialize -- the starting values of Sec. 4.1 in the least-squares form
  * the paper gives for high-dimensional data, written over the handle's B,
  * Gamma, U and V (X, Z, the offset, the counts and the NB shape are kept):

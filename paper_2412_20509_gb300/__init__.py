@@ -38,6 +38,7 @@ EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
            "gmf_set_wait_limit", "gmf_set_flow_lag", "gmf_sgd_sweep_blocks", "gmf_chunk_bytes", "gmf_chunk_state", "gmf_holdout",
            "gmf_loglik", "gmf_initialize", "gmf_set_gene_shapes", "gmf_get_gene_shapes", "gmf_gene_shape_moments",
+           "gmf_gene_shape_ml",
            "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_set_group", "gmf_sweep_group", "gmf_sweep_autotune",
            "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
            "gmf_mlp_set_params", "gmf_mlp_get_params", "gmf_mlp_get_grads", "gmf_mlp_forward", "gmf_mlp_loss_grad",
@@ -94,6 +95,8 @@ def lib():
         "gmf_set_gene_shapes": (C.c_int, [VP, VP, VP]),
         "gmf_get_gene_shapes": (C.c_int, [VP, VP, VP]),
         "gmf_gene_shape_moments": (C.c_int, [VP, C.c_double, C.c_double, VP, VP]),
+        "gmf_gene_shape_ml": (C.c_int, [VP, VP, C.c_int32, C.c_double, C.c_double, C.c_double, VP,
+                                        C.POINTER(C.c_int32), VP]),
         "gmf_get_params": (C.c_int, [VP, VP, VP, VP, VP, VP, VP]),
         "gmf_set_params": (C.c_int, [VP, VP, VP, VP, VP, VP, VP]),
         "gmf_get_ema": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
@@ -331,6 +334,16 @@ class Model:
         out = np.empty(self.dims[1])
         check(lib().gmf_gene_shape_moments(self._h, float(eps), float(cap), out.ctypes.data, _stream(stream)))
         return out
+
+    def gene_shape_ml(self, start=None, iters=30, tol=1e-6, lo=1e-3, hi=1e4, stream=None):
+        """Maximum-likelihood NB shape per gene at the current means (gmf_gene_shape_ml); returns
+        (shapes in the caller's gene order, Newton passes made)."""
+        out = np.empty(self.dims[1])
+        st = None if start is None else np.ascontiguousarray(start, dtype=np.float64)
+        done = C.c_int32(0)
+        check(lib().gmf_gene_shape_ml(self._h, None if st is None else st.ctypes.data, int(iters), float(tol),
+                                      float(lo), float(hi), out.ctypes.data, C.byref(done), _stream(stream)))
+        return out, int(done.value)
 
     def initialize(self, power_iters=2, seed=0, stream=None):
         """The least-squares start of Sec. 4.1 (gmf_initialize); returns the residual's d leading singular values."""

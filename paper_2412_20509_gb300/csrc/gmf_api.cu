@@ -770,6 +770,41 @@ extern "C" int gmf_gene_shape_moments(gmf_model* h, double eps, double cap, doub
     return check_err_word(h, st);
 }
 
+int gmf_gene_ml_run(gmf_model* h, double* alpha, int iters, double tol, double lo, double hi, int* iters_done,
+                    cudaStream_t st, const char** why);
+
+extern "C" int gmf_gene_shape_ml(gmf_model* h, const double* start, int32_t iters, double tol, double lo, double hi,
+                                 double* alpha_out, int32_t* iters_done, void* stream) {
+    if (!h || !alpha_out) return fail(GMF_ERR_ARG, "gmf_gene_shape_ml: NULL argument");
+    if (h->cfg.family != GMF_NEGBIN) return fail(GMF_ERR_STATE, "gmf_gene_shape_ml: the fit is not negative binomial");
+    if (iters < 1 || iters > 200) return fail(GMF_ERR_ARG, "gmf_gene_shape_ml: iters %d outside [1, 200]", iters);
+    if (!(lo > 0) || !(hi >= lo) || !std::isfinite(hi) || !(tol >= 0))
+        return fail(GMF_ERR_ARG, "gmf_gene_shape_ml: need 0 < lo <= hi < inf and tol >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> al((size_t)h->m);
+    if (start) {
+        for (int64_t jp = 0; jp < h->m; jp++) {
+            const double v = start[h->h_cperm[jp]];
+            if (!(v > 0) || !std::isfinite(v)) return fail(GMF_ERR_ARG, "gmf_gene_shape_ml: start shapes must be positive");
+            al[jp] = std::min(std::max(v, lo), hi);
+        }
+    } else {
+        std::vector<float> cur((size_t)(h->cfg.alpha_mode == 2 ? h->m : 1));
+        CUDA_TRY(cudaMemcpyAsync(cur.data(), h->cfg.alpha_mode == 2 ? h->alpha_col : h->alpha,
+                                 sizeof(float) * cur.size(), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t jp = 0; jp < h->m; jp++)
+            al[jp] = std::min(std::max((double)cur[h->cfg.alpha_mode == 2 ? jp : 0], lo), hi);
+    }
+    const char* why = "";
+    int done = 0;
+    const int rc = gmf_gene_ml_run(h, al.data(), iters, tol, lo, hi, &done, st, &why);
+    if (rc) return fail(rc, "gmf_gene_shape_ml: %s", why);
+    for (int64_t jp = 0; jp < h->m; jp++) alpha_out[h->h_cperm[jp]] = al[jp];
+    if (iters_done) *iters_done = done;
+    return check_err_word(h, st);
+}
+
 int gmf_init_run(gmf_model* h, int power_iters, uint64_t seed, double* sv_out, cudaStream_t st, std::string* err);
 
 extern "C" int gmf_initialize(gmf_model* h, int32_t power_iters, uint64_t seed, double* sv_out, void* stream) {

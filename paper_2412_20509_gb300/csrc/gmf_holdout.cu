@@ -217,6 +217,104 @@ __global__ void __launch_bounds__(NT) gene_moments_kernel(StepArgs a, double* pa
     }
 }
 
+// ---- maximum-likelihood NB shape per gene (App. B's likelihood, one gene's
+// shape alpha with the fit's means held fixed). With l(alpha) the NB
+// log-likelihood of the gene's observed entries, Newton's method in
+// theta = log alpha needs per gene
+//   l'  = sum_i w [psi(y + a) - psi(a) - log1p(mu / a) + (mu - y) / (a + mu)]
+//   l'' = sum_i w [psi'(y + a) - psi'(a) + mu / (a (a + mu)) + (y - mu) / (a + mu)^2].
+// The digamma and trigamma differences are sums of 1 / (a + k) and -1 / (a + k)^2
+// over k < y (psi(x + 1) = psi(x) + 1 / x); from k = 16 on, for y > 16, the
+// shifted differences psi(y + a) - psi(a + 16) come from the asymptotic series
+// of psi and psi' (Abramowitz and Stegun 6.3.18 and 6.4.12), whose arguments
+// are then at least 16. Terms in FP32, compensated (Kahan) FP32 sums per thread.
+constexpr int ML_DIRECT = 16;
+
+__device__ __forceinline__ float psi_asym(float x) {  // x >= 16: ln x - 1/(2x) - 1/(12x^2) + 1/(120x^4) - 1/(252x^6)
+    const float r = 1.f / x, r2 = r * r;
+    return logf(x) - 0.5f * r - r2 * (1.f / 12.f - r2 * (1.f / 120.f - r2 * (1.f / 252.f)));
+}
+__device__ __forceinline__ float psi1_asym(float x) {  // x >= 16: 1/x + 1/(2x^2) + 1/(6x^3) - 1/(30x^5) + 1/(42x^7)
+    const float r = 1.f / x, r2 = r * r;
+    return r + 0.5f * r2 + r * r2 * (1.f / 6.f - r2 * (1.f / 30.f - r2 * (1.f / 42.f)));
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float yv = v - c;
+    const float t = s + yv;
+    c = (t - s) - yv;
+    s = t;
+}
+
+// part[ry][j] = {l'_j, l''_j} over the observed entries of row tiles ry, ry + gridDim.y, ... of column tile
+// blockIdx.x; alpha: the current shape of each (permuted) gene.
+__global__ void __launch_bounds__(NT) gene_ml_kernel(StepArgs a, const float* __restrict__ alpha, double* part) {
+    __shared__ __align__(16) float Ls[GMF_KMAX * LDT];
+    __shared__ __align__(16) float Rs[GMF_KMAX * LDT];
+    __shared__ double red[NT][2];
+    const int tid = threadIdx.x;
+    const int64_t col0 = (int64_t)blockIdx.x * T;
+    const int nc = (int)min((int64_t)T, a.m - col0);
+    const int64_t tiles_r = (a.n + T - 1) / T;
+    const int j = tid % T;
+    const float aj = j < nc ? __ldg(alpha + col0 + j) : 1.f;
+    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    for (int e = tid; e < T * a.K; e += NT) {
+        const int i = e / a.K, c = e - i * a.K;
+        Rs[c * LDT + i] = i < nc ? a.R[(col0 + i) * a.KP + c] : 0.f;
+    }
+    for (int64_t rt = blockIdx.y; rt < tiles_r; rt += gridDim.y) {
+        const int64_t row0 = rt * T;
+        const int nr = (int)min((int64_t)T, a.n - row0);
+        __syncthreads();
+        for (int e = tid; e < T * a.K; e += NT) {
+            const int i = e / a.K, c = e - i * a.K;
+            Ls[c * LDT + i] = i < nr ? a.L[(row0 + i) * a.KP + c] : 0.f;
+        }
+        __syncthreads();
+        if (j < nc) {
+            for (int i = tid / T; i < nr; i += NT / T) {
+                const int64_t idx = (row0 + i) * a.m + col0 + j;
+                const float y = yval(a.Y, a.y16, idx);
+                if (a.missing && y == a.ymiss) continue;
+                const float w = a.W ? __ldg(a.W + idx) : 1.f;
+                float eta = 0.f;
+                for (int c = 0; c < a.K; c++) eta = fmaf(Ls[c * LDT + i], Rs[c * LDT + j], eta);
+                const float mu = expf(fminf(fmaxf(eta, -a.clamp), a.clamp));
+                const int yi = (int)y;
+                const int kd = min(yi, ML_DIRECT);
+                float d1 = 0.f, d2 = 0.f;
+                for (int k = 0; k < kd; k++) {
+                    const float r = 1.f / (aj + (float)k);
+                    d1 += r;
+                    d2 -= r * r;
+                }
+                if (yi > ML_DIRECT) {
+                    d1 += psi_asym(y + aj) - psi_asym(aj + (float)ML_DIRECT);
+                    d2 += psi1_asym(y + aj) - psi1_asym(aj + (float)ML_DIRECT);
+                }
+                const float am = aj + mu;
+                const float g = d1 - log1pf(mu / aj) + (mu - y) / am;
+                const float hh = d2 + mu / (aj * am) + (y - mu) / (am * am);
+                kahan_add(s1, c1, w * g);
+                kahan_add(s2, c2, w * hh);
+            }
+        }
+    }
+    red[tid][0] = (double)s1;
+    red[tid][1] = (double)s2;
+    __syncthreads();
+    if (tid < T && tid < nc) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int u = tid; u < NT; u += T) {
+            t1 += red[u][0];
+            t2 += red[u][1];
+        }
+        part[((int64_t)blockIdx.y * a.m + col0 + tid) * 2] = t1;
+        part[((int64_t)blockIdx.y * a.m + col0 + tid) * 2 + 1] = t2;
+    }
+}
+
 }  // namespace
 
 int gmf_gene_moments_run(gmf_model* h, double* sums, cudaStream_t st, const char** why) {
@@ -313,5 +411,71 @@ int gmf_holdout_run(gmf_model* h, const void* Ytrue, double* out, cudaStream_t s
     out[1] = tot[0][3] / tot[1][1];
     out[2] = tot[0][0] / tot[0][1];
     out[3] = tot[0][4];
+    return GMF_OK;
+}
+
+// Newton's method in theta = log alpha for every gene at once: per iteration
+// one pass of gene_ml_kernel (FP64 sums over the row-tile partials in order),
+// then per gene dtheta = -g / h with g = a l', h = a l' + a^2 l'' where h < 0,
+// else a step of +-1 in the direction of g; steps capped at 1 in theta, theta
+// kept in [log lo, log hi]. alpha (permuted order, FP64) holds the start and
+// receives the estimate; iters_done the passes made.
+int gmf_gene_ml_run(gmf_model* h, double* alpha, int iters, double tol, double lo, double hi, int* iters_done,
+                    cudaStream_t st, const char** why) {
+    StepArgs a = gmf_make_args(h);
+    const int RY = 16;
+    const size_t m = (size_t)h->m;
+    double* part = nullptr;
+    float* ad = nullptr;
+    if (cudaMallocAsync((void**)&part, sizeof(double) * 2 * RY * m, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&ad, sizeof(float) * m, st) != cudaSuccess) {
+        if (part) cudaFreeAsync(part, st);
+        *why = "device allocation of the per-gene sums failed";
+        return GMF_ERR_OOM;
+    }
+    std::vector<double> hp(2 * RY * m);
+    std::vector<float> af(m);
+    std::vector<char> done(m, 0);
+    const double tlo = log(lo), thi = log(hi);
+    cudaError_t e = cudaSuccess;
+    int it = 0;
+    for (; it < iters; it++) {
+        for (size_t jp = 0; jp < m; jp++) af[jp] = (float)alpha[jp];
+        e = cudaMemcpyAsync(ad, af.data(), sizeof(float) * m, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) break;
+        gene_ml_kernel<<<dim3((unsigned)((h->m + T - 1) / T), RY), NT, 0, st>>>(a, ad, part);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        bool all = true;
+        for (size_t jp = 0; jp < m; jp++) {
+            if (done[jp]) continue;
+            double g1 = 0.0, g2 = 0.0;
+            for (int r = 0; r < RY; r++) {
+                g1 += hp[((size_t)r * m + jp) * 2];
+                g2 += hp[((size_t)r * m + jp) * 2 + 1];
+            }
+            const double al = alpha[jp], th = log(al);
+            const double g = al * g1, hs = al * g1 + al * al * g2;
+            double step = hs < 0.0 ? -g / hs : (g > 0.0 ? 1.0 : g < 0.0 ? -1.0 : 0.0);
+            step = std::min(1.0, std::max(-1.0, step));
+            const double tn = std::min(thi, std::max(tlo, th + step));
+            alpha[jp] = exp(tn);
+            if (fabs(tn - th) <= tol) done[jp] = 1;
+            else all = false;
+        }
+        if (all) {
+            it++;
+            break;
+        }
+    }
+    cudaFreeAsync(part, st);
+    cudaFreeAsync(ad, st);
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return GMF_ERR_CUDA;
+    }
+    *iters_done = it;
     return GMF_OK;
 }

@@ -104,3 +104,56 @@ def test_estimated_gene_shapes_raise_the_likelihood(gmf):
     # the estimates follow the drawn sizes (rank correlation)
     r = np.corrcoef(np.argsort(np.argsort(shapes)), np.argsort(np.argsort(prob.nb_size)))[0, 1]
     assert r > 0.5
+
+
+@pytest.mark.parametrize("y_dtype,missing", [("int32", False), ("uint16", True)])
+def test_gene_shape_ml_matches_oracle(gmf, oracle_mod, y_dtype, missing):
+    """Per-gene maximum-likelihood NB shapes (gmf_gene_shape_ml) against the FP64
+    oracle's Newton iteration from the same start, at the means of the GPU's
+    own fit: within 2e-3 (FP32 terms with compensated sums; the small-count
+    digamma differences exact, counts above 16 through the asymptotic series,
+    which these data reach), with unobserved entries left out (held-out ones and,
+    with 16-bit counts, counts saturated at the marker 65535). The estimates
+    raise the fit's log-likelihood above the moment estimates' (the ML shapes
+    maximise each gene's likelihood at these means)."""
+    from oracle.shapes import gene_shape_ml, gene_shape_moments
+    n, m, d, nbr, nbc = 1100, 704, 6, 500, 384
+    prob = synth.make_problem(n, m, 3, 1, d, "negbin", seed=23, zero_frac=0.6, offset=True, y_dtype=y_dtype, scale=0.8)
+    Y = prob.Y
+    obs = None
+    if missing:
+        obs = synth.holdout_mask(n, m, 0.2, 23)
+        Y = synth.with_missing(prob.Y, obs)
+        # a count saturated at 65535 is the uint16 missing marker: unobserved for the GPU as well
+        obs = obs & (prob.Y != synth.MISSING_UINT16)
+    assert prob.Y.max() > 16
+    rp, cp = synth.partitions(n, m, 23)
+    Yd = torch.from_numpy(Y.view(np.int16) if Y.dtype == np.uint16 else Y).cuda()
+    model = gmf.Model(Yd, prob.X, prob.Z, prob.offset, synth.crude_start(prob, d, seed=23), family="negbin",
+                      nb_row=nbr, nb_col=nbc, row_perm=rp, col_perm=cp, precision="fp32",
+                      settings=synth.fit_settings(alpha_mode=2, missing=int(missing)))
+    model.set_gene_shapes(np.full(m, 1.0))
+    for s in synth.sweep_orders(n, m, nbr, nbc, 3, 23):
+        model.epoch(s)
+    par = model.get_params()
+    mu = np.exp(np.clip(prob.offset[:, None] + prob.X @ par["B"].T + par["Gamma"] @ prob.Z.T
+                        + par["U"] @ par["V"].T, -30, 30))
+    start = np.full(m, 1.0)
+    got, it = model.gene_shape_ml(start=start, iters=40, tol=1e-7, lo=1e-3, hi=1e4)
+    ref, it_ref = gene_shape_ml(prob.Y, mu, start, iters=40, tol=1e-7, lo=1e-3, hi=1e4, observed=obs)
+    assert it <= 40 and it_ref <= 40
+    inner = ref < 1e3  # genes with a finite maximiser well inside the bounds
+    assert inner.sum() > m // 2
+    np.testing.assert_allclose(got[inner], ref[inner], rtol=2e-3)
+    assert np.all(got[~inner] > 5e2)
+    # NULL start: the fit's current shapes (all 1) give the same estimates
+    got2, _ = model.gene_shape_ml(iters=40, tol=1e-7, lo=1e-3, hi=1e4)
+    np.testing.assert_array_equal(got2, got)
+    # the ML shapes raise the log-likelihood at these means above the moment shapes
+    model.set_gene_shapes(model.gene_shape_moments(eps=1e-3, cap=1e4))
+    ll_mom = model.loglik()["loglik"]
+    model.set_gene_shapes(got)
+    ll_ml = model.loglik()["loglik"]
+    assert ll_ml >= ll_mom
+    with pytest.raises(gmf.GmfError):
+        model.gene_shape_ml(iters=0)
