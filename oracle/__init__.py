@@ -91,7 +91,7 @@ def _p(a):
 
 
 def entry(family, y, eta, w=1.0, alpha=1.0, clamp=30.0):
-    """(mu, Ddot, Dddot) of one entry (Sec. 3, log link)."""
+    """(mu, Ddot, Dddot) of one entry (Sec. 3); alpha is the family's scalar (NB shape or dispersion phi)."""
     mu, dd, ddd = C.c_double(), C.c_double(), C.c_double()
     lib().gmfo_entry(int(family), float(y), float(eta), float(w), float(alpha), float(clamp),
                      C.byref(mu), C.byref(dd), C.byref(ddd))
@@ -102,18 +102,23 @@ def entry_deviance(family, y, mu, w=1.0, alpha=1.0):
     return lib().gmfo_entry_deviance(int(family), float(y), float(mu), float(w), float(alpha))
 
 
-FAMILIES = {"poisson": 0, "negbin": 1}
+# Table S1: log link for the count families, the Gamma and the inverse Gaussian; identity (Gaussian) and
+# logit (Bernoulli, "binomial") as their canonical links
+FAMILIES = {"poisson": 0, "negbin": 1, "gaussian": 2, "binomial": 3, "gamma": 4, "invgauss": 5}
+Y_DTYPES = {np.dtype(np.int32): 0, np.dtype(np.uint16): 1, np.dtype(np.float32): 2}
 
 
 class OracleFit:
     """State of one fit: parameters in the original row/column order, the
-    smoothed derivatives of eq. 12, visit counters, the NB shape and t."""
+    smoothed derivatives of eq. 12, visit counters, the family's scalar (NB
+    shape or dispersion phi, in ``alpha``) and t. Y: int32 / uint16 counts,
+    or float32 responses (NaN = missing)."""
 
     def __init__(self, Y, X, Z, offset, start, *, family, nb_row, nb_col, row_perm, col_perm,
                  settings, W=None, alpha_col=None):
         self.Y = np.ascontiguousarray(Y)
-        if self.Y.dtype not in (np.int32, np.uint16):
-            raise TypeError("Y must be int32 or uint16")
+        if self.Y.dtype not in Y_DTYPES:
+            raise TypeError("Y must be int32, uint16 or float32")
         n, m = self.Y.shape
         self.X = np.ascontiguousarray(X, dtype=np.float64)
         self.Z = np.ascontiguousarray(Z, dtype=np.float64)
@@ -144,7 +149,7 @@ class OracleFit:
                            lambda_=(C.c_double * 4)(*s["lambda_"]),
                            a1=s["a1"], a2=s["a2"], k0=s["k0"], k1=s["k1"], tau=s["tau"],
                            damping=s["damping"], eps=s["eps"], eta_clamp=s["eta_clamp"])
-        self._data = _Data(Y=self.Y.ctypes.data, y_dtype=0 if self.Y.dtype == np.int32 else 1,
+        self._data = _Data(Y=self.Y.ctypes.data, y_dtype=Y_DTYPES[self.Y.dtype],
                            W=_p(self.W), X=_p(self.X), Z=_p(self.Z), offset=_p(self.offset),
                            row_perm=_p(self.row_perm), col_perm=_p(self.col_perm), alpha_col=_p(self.alpha_col))
         self._state = _State(**{k: getattr(self, k).ctypes.data for k, _ in _State._fields_})

@@ -14,6 +14,7 @@
  *   update .......... eq. 11, 12, 14 (EMA, bias correction, local step)
  *   loop ............ Algorithm 1
  *   NB shape ........ App. B, stochastic moment estimator
+ *   dispersion ...... App. B, smoothed stochastic Pearson estimator
  *   deviance ........ Table S1 and App. B (NB)
  *
  * Readings of points the paper leaves open (each is also a config field):
@@ -34,7 +35,21 @@
  *     updated once at the end of the sweep with rho of the sweep's first block;
  *     skipped when the denominator is not positive.
  *   - eta is clamped to [-eta_clamp, eta_clamp] before the inverse link.
- *   - phi = 1 (Poisson and NB have no free dispersion in this model).
+ *   - Families (Table S1): Poisson, NB, Bernoulli with phi = 1; Gaussian,
+ *     Gamma and inverse Gaussian with a dispersion phi.  Links: log for the
+ *     count families (Sec. 2), identity for the Gaussian and logit for the
+ *     Bernoulli (their canonical links), log for the Gamma and the inverse
+ *     Gaussian (their canonical links 1/mu and 1/mu^2 leave mu > 0 to the
+ *     optimiser; the log link keeps it, and Sec. 2 allows any link).  The
+ *     family's scalar parameter is held in one slot: the NB shape, or phi.
+ *   - phi (alpha_mode 1 for the three families with a dispersion): the
+ *     Pearson sum w (y - mu)^2 / nu(mu) pooled over one sweep, scaled by
+ *     nm / (entries of the sweep) and divided by the model's residual degrees
+ *     of freedom N = nm - mp - nq - (n + m) d - 1, then smoothed as the NB
+ *     shape is (rho of the sweep's first block, floored at eps); skipped when
+ *     N <= 0.  Missing entries are left out of the sum and of the count.
+ *   - eta is clamped for every family, the identity link included.
+ *   - Continuous responses are float32 (y_dtype 2); NaN marks a missing one.
  *   - Per-gene NB shapes (alpha_mode 2): gene j has its own fixed shape alpha_j
  *     (the model of App. B with the shape made column-specific, as the data
  *     laws draw it); the derivatives and deviance of entry (i, j) use alpha_j.
@@ -52,10 +67,11 @@
 typedef struct {
     int64_t n, m;
     int32_t p, q, d;
-    int32_t family;     /* 0 Poisson, 1 negative binomial; log link */
+    int32_t family;     /* 0 Poisson, 1 NB, 2 Gaussian, 3 Bernoulli, 4 Gamma, 5 inverse Gaussian */
     int32_t nb_row, nb_col;
     int32_t bias_corr;  /* 0 printed formula, 1 per-visit */
-    int32_t alpha_mode; /* 0 fixed NB shape, 1 stochastic moment estimator, 2 fixed per-gene shapes */
+    int32_t alpha_mode; /* 0 fixed NB shape / phi, 1 stochastic estimator (NB moments, Pearson phi),
+                           2 fixed per-gene NB shapes */
     int32_t missing;    /* 1: the sentinel count marks a missing entry (imputed by mu, Sec. 3.2) */
     double lambda[4];   /* penalties on B, Gamma, U, V */
     double a1, a2;      /* EMA weights of eq. 12 */
@@ -66,8 +82,8 @@ typedef struct {
 } gmfo_config;
 
 typedef struct {
-    const void* Y;         /* n x m counts, row-major, original order */
-    int32_t y_dtype;       /* 0 int32, 1 uint16 */
+    const void* Y;         /* n x m responses, row-major, original order */
+    int32_t y_dtype;       /* 0 int32, 1 uint16, 2 float32 */
     const double* W;       /* n x m weights or NULL (= 1) */
     const double* X;       /* n x p */
     const double* Z;       /* m x q */
@@ -88,12 +104,13 @@ typedef struct {
     double* Hb_col; /* m x (p+d) */
     int64_t* cnt_row; /* n: visits of each row */
     int64_t* cnt_col; /* m */
-    double* alpha;  /* smoothed NB shape */
+    double* alpha;  /* the family's scalar: smoothed NB shape, or dispersion phi */
     int64_t* t;     /* blocks processed so far */
 } gmfo_state;
 
 static double y_at(const gmfo_data* D, int64_t m, int64_t i, int64_t j) {
     if (D->y_dtype == 0) return (double)((const int32_t*)D->Y)[i * m + j];
+    if (D->y_dtype == 2) return (double)((const float*)D->Y)[i * m + j];
     return (double)((const uint16_t*)D->Y)[i * m + j];
 }
 
@@ -101,6 +118,7 @@ static double y_at(const gmfo_data* D, int64_t m, int64_t i, int64_t j) {
 static int missing_at(const gmfo_config* c, const gmfo_data* D, int64_t i, int64_t j) {
     if (!c->missing) return 0;
     if (D->y_dtype == 0) return ((const int32_t*)D->Y)[i * c->m + j] == -1;
+    if (D->y_dtype == 2) return isnan(((const float*)D->Y)[i * c->m + j]);
     return ((const uint16_t*)D->Y)[i * c->m + j] == 65535;
 }
 
@@ -108,34 +126,68 @@ static double w_at(const gmfo_data* D, int64_t m, int64_t i, int64_t j) {
     return D->W ? D->W[i * m + j] : 1.0;
 }
 
-/* Variance function nu(mu) of Table S1 (Poisson, negative binomial). */
+/* Variance function nu(mu) of Table S1 (alpha: the NB shape). */
 static double variance_fn(int family, double mu, double alpha) {
-    return family == 0 ? mu : mu * (1.0 + mu / alpha);
+    switch (family) {
+    case 0: return mu;
+    case 1: return mu * (1.0 + mu / alpha);
+    case 2: return 1.0;
+    case 3: return mu * (1.0 - mu);
+    case 4: return mu * mu;
+    default: return mu * mu * mu;
+    }
+}
+
+/* The families with a free dispersion phi (Gaussian, Gamma, inverse Gaussian). */
+static int has_dispersion(int family) { return family == 2 || family == 4 || family == 5; }
+
+/* Inverse link: identity (Gaussian), logistic (Bernoulli), exp (the others). */
+static double inv_link(int family, double e) {
+    if (family == 2) return e;
+    if (family == 3) return 1.0 / (1.0 + exp(-e));
+    return exp(e);
+}
+
+/* g'(mu) of the same links. */
+static double link_deriv(int family, double mu) {
+    if (family == 2) return 1.0;
+    if (family == 3) return 1.0 / (mu * (1.0 - mu));
+    return 1.0 / mu;
 }
 
 /*
- * Per-entry derivatives of Sec. 3 for the log link (g = log, g'(mu) = 1/mu),
- * phi = 1:  Ddot = w (y - mu) / (nu(mu) g'(mu)),  Dddot = w / (nu(mu) g'(mu)^2),
- * the expected (Fisher) second derivative, alpha(mu) = 1.
+ * Per-entry derivatives of Sec. 3:  Ddot = w (y - mu) / (phi nu(mu) g'(mu)),
+ * Dddot = w / (phi nu(mu) g'(mu)^2), the expected (Fisher) second derivative,
+ * alpha(mu) = 1.  scal is the family's scalar: the NB shape, or phi for the
+ * families with a dispersion (phi = 1 for the others).
  */
-void gmfo_entry(int family, double y, double eta, double w, double alpha, double clamp,
+void gmfo_entry(int family, double y, double eta, double w, double scal, double clamp,
                 double* mu_out, double* ddot, double* dddot) {
     double e = eta;
     if (e > clamp) e = clamp;
     if (e < -clamp) e = -clamp;
-    double mu = exp(e);
-    double nu = variance_fn(family, mu, alpha);
-    double gdot = 1.0 / mu;
+    const double mu = inv_link(family, e);
+    const double nu = variance_fn(family, mu, scal);
+    const double gdot = link_deriv(family, mu);
+    const double phi = has_dispersion(family) ? scal : 1.0;
     if (mu_out) *mu_out = mu;
-    if (ddot) *ddot = w * (y - mu) / (nu * gdot);
-    if (dddot) *dddot = w / (nu * gdot * gdot);
+    if (ddot) *ddot = w * (y - mu) / (phi * nu * gdot);
+    if (dddot) *dddot = w / (phi * nu * gdot * gdot);
 }
 
-/* Unit deviance 2 w [ ... ] of Table S1 (Poisson) and App. B (NB), 0 log 0 = 0. */
+/* x log(x / z) with 0 log 0 = 0. */
+static double xlogxz(double x, double z) { return x > 0 ? x * log(x / z) : 0.0; }
+
+/* Unit deviance D(y, mu) = 2 w [D / 2a(phi) of Table S1] (App. B for NB), not divided by phi. */
 double gmfo_entry_deviance(int family, double y, double mu, double w, double alpha) {
-    double ylog = y > 0 ? y * log(y / mu) : 0.0;
-    if (family == 0) return 2.0 * w * (ylog - (y - mu));
-    return 2.0 * w * (ylog - (y + alpha) * log((y + alpha) / (mu + alpha)));
+    switch (family) {
+    case 0: return 2.0 * w * (xlogxz(y, mu) - (y - mu));
+    case 1: return 2.0 * w * (xlogxz(y, mu) - (y + alpha) * log((y + alpha) / (mu + alpha)));
+    case 2: return w * (y - mu) * (y - mu);
+    case 3: return 2.0 * w * (xlogxz(y, mu) + xlogxz(1.0 - y, 1.0 - mu));
+    case 4: return 2.0 * w * ((y - mu) / mu - log(y / mu));
+    default: return w * (y - mu) * (y - mu) / (y * mu * mu);
+    }
 }
 
 /* eta_ij = o_i + x_i' beta_j + gamma_i' z_j + u_i' v_j   (eq. 3 plus the offset) */
@@ -154,7 +206,9 @@ static double eta_at(const gmfo_config* c, const gmfo_data* D, const gmfo_state*
  *   Grow[i,c] = -(m/|J|) sum_j Ddot_ij [Z, V]_jc     Hrow = (m/|J|) sum_j Dddot_ij [Z*Z, V*V]_jc
  *   Gcol[j,c] = -(n/|I|) sum_i Ddot_ij [X, U]_ic     Hcol = (n/|I|) sum_i Dddot_ij [X*X, U*U]_ic
  * Row outputs are |I| x (q+d), column outputs |J| x (p+d).  nb_sums (may be
- * NULL) accumulates sum w mu^2 and sum w ((y-mu)^2 - mu) over the block.
+ * NULL) accumulates sum w mu^2 and sum w ((y-mu)^2 - mu) over the block (NB),
+ * or the Pearson sum w (y - mu)^2 / nu(mu) and the number of observed entries
+ * (families with a dispersion).
  */
 int gmfo_block_grad(const gmfo_config* c, const gmfo_data* D, const gmfo_state* S, double alpha,
                     const int32_t* I, int64_t nI, const int32_t* J, int64_t mJ,
@@ -178,7 +232,12 @@ int gmfo_block_grad(const gmfo_config* c, const gmfo_data* D, const gmfo_state* 
             double y = y_at(D, m, i, j);
             if (missing_at(c, D, i, j)) gmfo_entry(c->family, 0.0, eta, w, aj, c->eta_clamp, &y, NULL, NULL);
             gmfo_entry(c->family, y, eta, w, aj, c->eta_clamp, &mu, &dd, &ddd);
-            if (nb_sums) {
+            if (nb_sums && has_dispersion(c->family)) {
+                if (!missing_at(c, D, i, j)) {
+                    nb_sums[0] += w * (y - mu) * (y - mu) / variance_fn(c->family, mu, aj);
+                    nb_sums[1] += 1.0;
+                }
+            } else if (nb_sums) {
                 nb_sums[0] += w * mu * mu;
                 nb_sums[1] += w * ((y - mu) * (y - mu) - mu);
             }
@@ -308,6 +367,16 @@ int gmfo_sgd_sweeps(const gmfo_config* c, const gmfo_data* D, gmfo_state* S, con
             const double rho = rho_at(c, t_first);
             *S->alpha = (1.0 - rho) * (*S->alpha) + rho * ahat;
         }
+        if (has_dispersion(c->family) && c->alpha_mode == 1 && sums[1] > 0.0) {
+            const double nm = (double)c->n * (double)c->m;
+            const double dof = nm - (double)c->m * c->p - (double)c->n * c->q - (double)(c->n + c->m) * c->d - 1.0;
+            if (dof > 0.0) {
+                double phat = (nm / sums[1]) * sums[0] / dof;
+                if (phat < c->eps) phat = c->eps;
+                const double rho = rho_at(c, t_first);
+                *S->alpha = (1.0 - rho) * (*S->alpha) + rho * phat;
+            }
+        }
     }
     return 0;
 }
@@ -324,7 +393,7 @@ int gmfo_sgd_sweep_blocks(const gmfo_config* c, const gmfo_data* D, gmfo_state* 
     const int swap = r < s;
     const int64_t per = swap ? r : s;
     if (nblocks == per) return gmfo_sgd_sweeps(c, D, S, sigma, w, w + 1);
-    if (c->family == 1 && c->alpha_mode == 1) return -2;
+    if ((c->family == 1 || has_dispersion(c->family)) && c->alpha_mode == 1) return -2;
     const int64_t t0 = *S->t;
     double sums[2] = {0.0, 0.0};
     for (int64_t b = 0; b < nblocks; b++) {

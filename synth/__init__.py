@@ -32,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "WORKLOADS", "Problem", "make_problem", "partitions", "sweep_orders",
-    "n_sweeps", "crude_start", "fit_settings", "holdout_mask", "with_missing",
+    "n_sweeps", "crude_start", "fit_settings", "holdout_mask", "with_missing", "make_family_problem",
 ]
 
 
@@ -154,6 +154,45 @@ def make_problem(n, m, p, q, d, family="poisson", *, seed=0, y_dtype="int32",
                    U=U, V=V, nb_size=size, family=family, saturated=saturated)
 
 
+def make_family_problem(n, m, p, q, d, family, *, phi=0.5, seed=0, offset=False, scale=0.5, shift=0.0):
+    """Draw float32 responses from one of the other laws of Table S1 under the
+    same linear predictor (eta = o + X B^T + Gamma Z^T + U V^T, gene
+    intercepts shifted by `shift`): "gaussian" N(eta, phi) (identity link),
+    "binomial" Bernoulli(1 / (1 + e^-eta)) (logit link; 0 / 1 values),
+    "gamma" Gamma with mean e^eta and shape 1/phi, "invgauss" inverse Gaussian
+    with mean e^eta and shape 1/phi (log links). Returns a Problem whose
+    nb_size holds the dispersion phi of every gene."""
+    rng = np.random.default_rng([seed, 5])
+    X = np.empty((n, p))
+    X[:, 0] = 1.0
+    if p > 1:
+        X[:, 1:] = rng.standard_normal((n, p - 1))
+    Z = np.ones((m, q)) if q >= 1 else np.zeros((m, 0))
+    if q > 1:
+        Z[:, 1:] = rng.standard_normal((m, q - 1))
+    B = scale * rng.standard_normal((m, p))
+    B[:, 0] += shift
+    Gamma = scale * rng.standard_normal((n, q))
+    U = scale * rng.standard_normal((n, d))
+    V = scale * rng.standard_normal((m, d))
+    off = rng.normal(0.0, 0.5, size=n) if offset else np.zeros(n)
+    eta = _eta(X, B, Gamma, Z, U, V, off, slice(0, n))
+    if family == "gaussian":
+        Y = eta + math.sqrt(phi) * rng.standard_normal((n, m))
+    elif family == "binomial":
+        Y = (rng.random((n, m)) < 1.0 / (1.0 + np.exp(-eta))).astype(np.float64)
+    elif family == "gamma":
+        mu = np.exp(eta)
+        Y = rng.gamma(1.0 / phi, mu * phi)
+    elif family == "invgauss":
+        mu = np.exp(eta)
+        Y = rng.wald(mu, 1.0 / phi)
+    else:
+        raise ValueError(family)
+    return Problem(Y=np.ascontiguousarray(Y, dtype=np.float32), X=X, Z=Z, offset=off, B=B, Gamma=Gamma, U=U, V=V,
+                   nb_size=np.full(m, float(phi)), family=family)
+
+
 def workload_problem(name, seed=0, n=None, m=None):
     """Draw the named workload (optionally at a reduced n x m with the same law)."""
     w = WORKLOADS[name]
@@ -192,6 +231,18 @@ def crude_start(prob: Problem, d, *, seed=0, scale=0.1):
     n, m = prob.Y.shape
     p = prob.X.shape[1]
     q = prob.Z.shape[1]
+    if prob.family in ("gaussian", "binomial"):
+        # identity / logit link: column means (clipped into (0, 1) for 0 / 1 data) and row deviations
+        Yf = np.nan_to_num(prob.Y.astype(np.float64), nan=float(np.nanmean(prob.Y)))
+        link = (lambda v: v) if prob.family == "gaussian" else (lambda v: np.log(v / (1 - v)))
+        clip = (lambda v: v) if prob.family == "gaussian" else (lambda v: np.clip(v, 0.02, 0.98))
+        B0 = np.zeros((m, p))
+        B0[:, 0] = link(clip(Yf.mean(0)))
+        G0 = np.zeros((n, q))
+        if q >= 1:
+            G0[:, 0] = link(clip(Yf.mean(1))) - link(clip(Yf.mean()))
+        return dict(B=B0, Gamma=G0, U=scale * rng.standard_normal((n, d)), V=scale * rng.standard_normal((m, d)),
+                    alpha=1.0)
     colsum = prob.Y.sum(axis=0, dtype=np.float64)
     rowsum = prob.Y.sum(axis=1, dtype=np.float64)
     B0 = np.zeros((m, p))
@@ -283,10 +334,11 @@ def holdout_mask(n, m, frac, seed):
 
 
 def with_missing(Y, observed):
-    """A copy of Y with the held-out entries set to the missing-count marker of
-    its dtype (int32: -1, uint16: 65535)."""
+    """A copy of Y with the held-out entries set to the missing marker of its
+    dtype (int32: -1, uint16: 65535, float32: NaN)."""
     Y = np.array(Y, copy=True)
-    Y[~np.asarray(observed, bool)] = MISSING_INT32 if Y.dtype == np.int32 else MISSING_UINT16
+    marker = {np.dtype(np.int32): MISSING_INT32, np.dtype(np.uint16): MISSING_UINT16}.get(Y.dtype, np.nan)
+    Y[~np.asarray(observed, bool)] = marker
     return Y
 
 

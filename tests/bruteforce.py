@@ -3,7 +3,8 @@
 Used only by the oracle pin tests: it is written separately from the scalar C
 oracle (whole-block matrix products instead of per-entry loops, the NB
 derivatives in their simplified closed form alpha (y - mu)/(alpha + mu) and
-alpha mu/(alpha + mu) instead of the nu / g' form), so that an indexing,
+alpha mu/(alpha + mu) instead of the nu / g' form, and likewise for the other
+families of Table S1), so that an indexing,
 transposition or bookkeeping slip in either one shows up as a mismatch.
 """
 import math
@@ -62,17 +63,34 @@ class BruteFit:
                 Yb, Wb = self.Y[np.ix_(I, J)], self.W[np.ix_(I, J)]
                 eta = (self.off[I, None] + self.X[I] @ self.B[J].T + self.G[I] @ self.Z[J].T
                        + self.U[I] @ self.V[J].T)
-                mu = np.exp(np.clip(eta, -cfg["eta_clamp"], cfg["eta_clamp"]))
-                Yb = np.where(self.obs[np.ix_(I, J)], Yb, mu)
-                if self.family == "poisson":
-                    f = np.ones_like(mu)
+                e = np.clip(eta, -cfg["eta_clamp"], cfg["eta_clamp"])
+                fam = self.family
+                mu = e if fam == "gaussian" else (1 / (1 + np.exp(-e)) if fam == "binomial" else np.exp(e))
+                ob = self.obs[np.ix_(I, J)]
+                Yb = np.where(ob, Yb, mu)
+                phi = self.alpha    # the dispersion of the Gaussian, Gamma and inverse Gaussian families
+                if fam in ("poisson", "negbin"):
+                    if fam == "poisson":
+                        f = np.ones_like(mu)
+                    else:
+                        a = self.alpha if self.alpha_col is None else self.alpha_col[J][None, :]
+                        f = a / (a + mu)
+                    Dd = Wb * (Yb - mu) * f
+                    Ddd = Wb * mu * f
+                    s1 += float((Wb * mu * mu).sum())
+                    s2 += float((Wb * ((Yb - mu) ** 2 - mu)).sum())
+                elif fam == "binomial":           # canonical link: the score is the raw residual
+                    Dd = Wb * (Yb - mu)
+                    Ddd = Wb * mu * (1 - mu)
                 else:
-                    a = self.alpha if self.alpha_col is None else self.alpha_col[J][None, :]
-                    f = a / (a + mu)
-                Dd = Wb * (Yb - mu) * f
-                Ddd = Wb * mu * f
-                s1 += float((Wb * mu * mu).sum())
-                s2 += float((Wb * ((Yb - mu) ** 2 - mu)).sum())
+                    # closed forms of the score and Fisher weight under the identity (Gaussian) and log links
+                    Dd = {"gaussian": Wb * (Yb - mu), "gamma": Wb * (Yb / mu - 1),
+                          "invgauss": Wb * (Yb - mu) / mu ** 2}[fam] / phi
+                    Ddd = {"gaussian": Wb, "gamma": Wb, "invgauss": Wb / mu}[fam] / phi
+                    pearson = {"gaussian": (Yb - mu) ** 2, "gamma": ((Yb - mu) / mu) ** 2,
+                               "invgauss": (Yb - mu) ** 2 / mu ** 3}[fam]
+                    s1 += float((Wb * pearson)[ob].sum())
+                    s2 += float(ob.sum())
                 Rf = np.hstack([self.Z[J], self.V[J]])
                 Lf = np.hstack([self.X[I], self.U[I]])
                 thR = np.hstack([self.G[I], self.U[I]])
@@ -100,3 +118,10 @@ class BruteFit:
                 ahat = max(cfg["eps"], s1 / s2)
                 rho = cfg["k0"] / (1 + cfg["k0"] * cfg["k1"] * t_first) ** cfg["tau"]
                 self.alpha = (1 - rho) * self.alpha + rho * ahat
+            if self.family in ("gaussian", "gamma", "invgauss") and cfg["alpha_mode"] == 1 and s2 > 0:
+                # App. B: the Pearson statistic of the sweep scaled to the whole matrix over the residual dof
+                dof = n * m - m * p - n * q - (n + m) * d - 1
+                if dof > 0:
+                    phat = max(cfg["eps"], (n * m / s2) * s1 / dof)
+                    rho = cfg["k0"] / (1 + cfg["k0"] * cfg["k1"] * t_first) ** cfg["tau"]
+                    self.alpha = (1 - rho) * self.alpha + rho * phat
