@@ -376,10 +376,11 @@ def source_hash(paths):
 
 
 KERNEL_SOURCES = {
-    "sweep_tc_kernel": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
-    "sweep_tc_cluster": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
-    "sweep_tc_epoch": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
-    "sweep_tc_flow": ["gmf_step_tc.cu", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
+    "sweep_tc_kernel": ["gmf_step_tc.cu", "gmf_tc_tile.cuh", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
+    "sweep_tc_cluster": ["gmf_step_tc.cu", "gmf_tc_tile.cuh", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
+    "sweep_tc_epoch": ["gmf_step_tc.cu", "gmf_tc_tile.cuh", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
+    "sweep_tc_flow": ["gmf_step_tc.cu", "gmf_tc_tile.cuh", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
+    "deviance_tc": ["gmf_deviance_tc.cu", "gmf_tc_tile.cuh", "gmf_update.cuh", "gmf_sm100.cuh", "gmf_internal.cuh"],
     "sweep_kernel": ["gmf_step_simt.cu", "gmf_update.cuh", "gmf_internal.cuh"],
     "update_kernel": ["gmf_update.cu", "gmf_update.cuh", "gmf_internal.cuh"],
     "update_tc_kernel": ["gmf_update.cu", "gmf_update.cuh", "gmf_internal.cuh"],
@@ -593,8 +594,9 @@ def run_headline(args, w):
     stream = torch.cuda.current_stream()
     eps = w.epochs                      # epochs per step: one full fit pass
 
-    def make(precision, Y=None):
-        flags = gmf.GMF_FLAG_PERSIST if (precision == "mixed" and args.epoch_launch == "persistent") else 0
+    def make(precision, Y=None, flags=0):
+        if precision == "mixed" and args.epoch_launch == "persistent":
+            flags |= gmf.GMF_FLAG_PERSIST
         mdl = gmf.Model(prob.Y if Y is None else Y, prob.X, prob.Z, prob.offset, start, family=w.family,
                         nb_row=w.nb_row, nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=settings,
                         precision=precision, flags=flags)
@@ -643,6 +645,7 @@ def run_headline(args, w):
     entries_step = n * m * eps
     value = whole_job_rate(entries_step * args.steps, ws, elapsed_ms / 1e3)
     dev1 = model.deviance()
+    devk = deviance_timing(gmf, model, make, stream, n * m, K)
     launches_per_sweep = model.launches_per_sweep
     epoch_mode = model.epoch_mode
     # context only: the tile launches of one step bracketed one by one with events (outside the graph)
@@ -727,7 +730,7 @@ def run_headline(args, w):
                    "api": "per step: gmf_update_y_async of the counts (2 GB, issued one step ahead so the upload "
                           "overlaps the previous step), 10 x gmf_sgd_epoch, gmf_deviance_async + D2H"},
            "gpu_launches": int(launches_per_sweep * nsw * eps * args.steps), "epoch_mode": epoch_mode,
-           "clocks": clk, "deviance": {"after_warmup": dev0, "after_timed_steps": dev1}}
+           "clocks": clk, "deviance": {"after_warmup": dev0, "after_timed_steps": dev1, **devk}}
 
     if extras:
         # ---------------- the FP32 path on the same fit
@@ -789,10 +792,41 @@ def run_headline(args, w):
     return 0
 
 
+def deviance_timing(gmf, model, make, stream, entries, K, reps=5):
+    """The full deviance (gmf_deviance_async) of the fitted model: the tensor-core kernel of mixed handles and
+    the CUDA-core kernel (GMF_FLAG_SIMT_DEVIANCE) on the same parameters, each the mean of `reps` calls timed
+    with events on the stream; bytes = the counts (2 B per entry) + the factor rows read once."""
+    import torch
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    twin = make("mixed", flags=gmf.GMF_FLAG_SIMT_DEVIANCE)
+    twin.set_params(model.get_params())
+    res = {}
+    for name, mdl in (("tensor_core", model), ("cuda_core", twin)):
+        mdl.deviance_async(out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            mdl.deviance_async(out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        res[name] = {"ms": ms, "entries_per_s": entries / (ms / 1e3), "total": float(out.item())}
+    n, m = model.dims[:2]
+    byts = 2 * entries + 4 * (n + m) * K
+    res["tensor_core"]["hbm_gbs"] = byts / (res["tensor_core"]["ms"] / 1e3) / 1e9
+    res["bytes_per_call"] = byts
+    res["rel_gap"] = res["tensor_core"]["total"] / res["cuda_core"]["total"] - 1.0
+    del twin
+    torch.cuda.empty_cache()
+    return {"full_deviance": res}
+
+
 def run_case(args):
     """--case: one-kernel measurement cases of a size an ncu capture handles.
     atlas_sweep: 4 sweeps of the atlas workload's launch shape (5 blocks of 2048 x 1024, d = 20, uint16) on
       50000 x 5000 counts, one tile launch and one update launch each.
+    deviance_50000: one full deviance of a d = 20 NB model on 50000 x 5000 uint16 counts (after one epoch).
     project_20000: a d = 20 NB model (2 fit epochs, mixed precision) on 20000 cells x 3000 genes,
       then the tensor-core projection of 20000 held-out cells with 3 Fisher passes.
     encoder_16384: the forward pass of a 3000-256-256-20 encoder (first layer on the tensor cores) on 16384
@@ -824,6 +858,24 @@ def run_case(args):
         full = [i for i in range(r) if all((int(sg[1][i]) + k) % r != r - 1 for k in range(5))][:4]
         run = lambda: [model.sweeps(sg[1], i, i + 1) for i in full]
         units, unit = sum(sweep_entries(n, w.m, w.nb_row, w.nb_col, int(sg[1][i])) for i in full), "entries/s"
+    elif args.case == "deviance_50000":
+        # the full deviance (tensor-core kernel) of a d = 20 NB model on 50000 x 5000 uint16 counts (500 MB,
+        # larger than L2) after one fit epoch
+        w = synth.WORKLOADS["nb_atlas"]
+        n = 50000
+        prob = synth.make_problem_device(n, w.m, w.p, w.q, w.d, w.family, seed=1, zero_frac=w.zero_frac,
+                                         offset=True)
+        hp = synth.Problem(Y=prob.Y.cpu().numpy().view(np.uint16), X=prob.X, Z=prob.Z, offset=prob.offset,
+                           B=prob.B, Gamma=prob.Gamma, U=prob.U, V=prob.V, nb_size=prob.nb_size, family=w.family)
+        start = synth.crude_start(hp, w.d, seed=1)
+        rp, cp = synth.partitions(n, w.m, 1)
+        model = gmf.Model(prob.Y, prob.X, prob.Z, prob.offset, start, family=w.family, nb_row=w.nb_row,
+                          nb_col=w.nb_col, row_perm=rp, col_perm=cp, settings=synth.fit_settings(),
+                          precision=args.precision)
+        model.epoch(synth.sweep_orders(n, w.m, w.nb_row, w.nb_col, 1, 1)[0])
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        run = lambda: model.deviance_async(out)
+        units, unit = n * w.m, "entries/s"
     elif args.case == "project_20000":
         n_fit = n_new = 20000
         m, d = 3000, 20
@@ -1011,7 +1063,8 @@ def main():
     ap.add_argument("--flow-lag", type=int, default=None, help="item order of the persistent epoch (gmf_set_flow_lag)")
     ap.add_argument("--encoder-precision", default="mixed", choices=["fp32", "mixed"],
                     help="nb_project: the encoder's first layer on the tensor cores (mixed) or FP32")
-    ap.add_argument("--case", default=None, choices=["atlas_sweep", "project_20000", "encoder_16384"],
+    ap.add_argument("--case", default=None, choices=["atlas_sweep", "deviance_50000", "project_20000",
+                                                     "encoder_16384"],
                     help="a one-kernel measurement case (the profiles' captures)")
     args = ap.parse_args()
     if args.case:

@@ -44,9 +44,22 @@ enum {
     GMF_ERR_STATE = -6      /* handle not in a state that allows the call */
 };
 
-enum { GMF_POISSON = 0, GMF_NEGBIN = 1 };          /* log link for both */
-enum { GMF_Y_INT32 = 0, GMF_Y_UINT16 = 1 };        /* count storage type */
-enum { GMF_MISSING_INT32 = -1, GMF_MISSING_UINT16 = 65535 };  /* missing-entry markers (cfg.missing = 1) */
+/* Families of Table S1 and their links: log for the Poisson, the negative
+   binomial, the Gamma and the inverse Gaussian; identity for the Gaussian and
+   logit for the Bernoulli (their canonical links). The Gaussian, Gamma and
+   inverse Gaussian have a dispersion phi (App. B), held where the negative
+   binomial holds its shape (alpha0, gmf_get_params' alpha). */
+enum {
+    GMF_POISSON = 0,
+    GMF_NEGBIN = 1,
+    GMF_GAUSSIAN = 2,   /* float32 responses */
+    GMF_BINOMIAL = 3,   /* Bernoulli: responses in [0, 1] (counts 0 / 1, or float32) */
+    GMF_GAMMA = 4,      /* float32 responses > 0 */
+    GMF_INVGAUSS = 5    /* float32 responses > 0 */
+};
+enum { GMF_Y_INT32 = 0, GMF_Y_UINT16 = 1, GMF_Y_FLOAT32 = 2 };  /* response storage type */
+/* missing-entry markers (cfg.missing = 1); float32 responses mark a missing entry by NaN */
+enum { GMF_MISSING_INT32 = -1, GMF_MISSING_UINT16 = 65535 };
 enum {
     GMF_PREC_FP32 = 0,   /* FP32 on the CUDA cores throughout (reference path) */
     GMF_PREC_MIXED = 1   /* tcgen05 tensor cores: eta as split-BF16 (3 products),
@@ -75,7 +88,11 @@ enum {
        and the updates of the current one finish. Without a device that can
        keep every CTA resident the per-sweep launches stay (gmf_epoch_mode
        tells which mode runs). */
-    GMF_FLAG_PERSIST = 2
+    GMF_FLAG_PERSIST = 2,
+    /* Mixed precision: gmf_deviance computes eta in FP32 on the CUDA cores (the
+       kernel of the FP32 path) instead of from the block step's split-BF16
+       tensor-core products. */
+    GMF_FLAG_SIMT_DEVIANCE = 4
 };
 
 typedef struct gmf_model gmf_model;  /* opaque, library-owned */
@@ -87,13 +104,18 @@ typedef struct gmf_model gmf_model;  /* opaque, library-owned */
 typedef struct {
     int64_t n, m;        /* rows (cells) and columns (genes) of Y */
     int32_t p, q, d;     /* columns of X, columns of Z, latent rank (d >= 0) */
-    int32_t family;      /* GMF_POISSON or GMF_NEGBIN */
+    int32_t family;      /* GMF_POISSON, GMF_NEGBIN, GMF_GAUSSIAN, GMF_BINOMIAL, GMF_GAMMA or GMF_INVGAUSS */
     int32_t nb_row;      /* row minibatch size n* (rows per partition chunk) */
     int32_t nb_col;      /* column minibatch size m* */
     int32_t bias_corr;   /* 0: c_t = (1-a2^t)/(1-a1^t), global block count t (eq. 11);
                             1: c = (1-(1-a2)^k)/(1-(1-a1)^k), k = visits of the row/column */
-    int32_t alpha_mode;  /* NB only. 0: shape fixed; 1: stochastic moment estimator (App. B),
-                            pooled per sweep; 2: one fixed shape per gene (gmf_set_gene_shapes) */
+    int32_t alpha_mode;  /* NB: 0 shape fixed; 1 stochastic moment estimator (App. B), pooled per
+                            sweep; 2 one fixed shape per gene (gmf_set_gene_shapes).
+                            Gaussian, Gamma, inverse Gaussian: 0 phi fixed; 1 the smoothed stochastic
+                            Pearson estimator of App. B, pooled per sweep: the sweep's sum of
+                            w (y - mu)^2 / nu(mu) times nm / (its observed entries), over the residual
+                            degrees of freedom nm - mp - nq - (n+m)d - 1, smoothed with rho of the
+                            sweep's first block (floored at eps). Poisson, Bernoulli: 0. */
     int32_t precision;   /* GMF_PREC_FP32 or GMF_PREC_MIXED */
     int32_t flags;       /* GMF_FLAG_* bits; 0 for the defaults */
     int32_t missing;     /* 1: a count equal to GMF_MISSING_INT32 / GMF_MISSING_UINT16 marks an entry
@@ -104,8 +126,8 @@ typedef struct {
     double a1, a2;       /* EMA weights of eq. 12 [0.1, 0.01] */
     double k0, k1, tau;  /* rho_t = k0 / (1 + k0 k1 t)^tau (Sec. 3.2) [0.01, 1e-3, 0.75] */
     double damping;      /* added to every curvature estimate [1e-3] */
-    double eps;          /* floor of the NB shape update (App. B) [1e-8] */
-    double eta_clamp;    /* eta is clamped to [-eta_clamp, eta_clamp] before exp [30] */
+    double eps;          /* floor of the NB shape and dispersion updates (App. B) [1e-8] */
+    double eta_clamp;    /* eta is clamped to [-eta_clamp, eta_clamp] before the inverse link [30] */
 } gmf_config;
 
 /* Fill *cfg with the defaults above for the given sizes. */
@@ -121,14 +143,22 @@ void gmf_config_default(gmf_config* cfg, int64_t n, int64_t m, int32_t p, int32_
  * col_perm and nb_col (the last chunk may be smaller). The library stores Y
  * (and W) and the parameters permuted so that every block is contiguous.
  *
- *   Y           n x m counts, y_dtype GMF_Y_INT32 or GMF_Y_UINT16; host or
- *               device memory as y_on_device says. Copied; counts must be >= 0.
+ *   Y           n x m responses: counts (y_dtype GMF_Y_INT32 or GMF_Y_UINT16,
+ *               >= 0) for the Poisson, NB and Bernoulli families, float32
+ *               (GMF_Y_FLOAT32) for the Gaussian, Gamma, inverse Gaussian and
+ *               Bernoulli; host or device memory as y_on_device says. Copied.
+ *               Fits of the families beyond Poisson and NB support the block
+ *               step, the deviance, the orthogonalisation and the parameter /
+ *               state calls; the count-model calls (projection, held-out
+ *               metrics, log-likelihood, start, gene shapes, rank sweep)
+ *               return GMF_ERR_STATE for them.
  *   W           NULL (all weights 1) or n x m float32 weights w_ij > 0
  *               (a_ij(phi) = phi/w_ij, Sec. 2), same memory space as Y. Copied.
  *   X, Z        host double, n x p and m x q.  offset: host double n, or NULL.
  *   row_perm    host int32 permutation of 0..n-1; col_perm of 0..m-1.
  *   B0..V0      host double starting values (m x p, n x q, n x d, m x d).
- *   alpha0      starting NB shape (> 0; ignored for Poisson).
+ *   alpha0      starting NB shape, or starting dispersion phi (> 0; ignored for
+ *               the Poisson and Bernoulli families).
  * The smoothed derivatives start at zero and t at 0. Synchronous.
  * Errors: GMF_ERR_ARG for bad sizes/pointers/permutations, GMF_ERR_OOM, GMF_ERR_CUDA.
  */
@@ -268,7 +298,10 @@ int gmf_chunk_state(gmf_model* h, int32_t side, int32_t chunk, void* buf, int32_
 /*
  * gmf_deviance -- total deviance sum_ij D(y_ij, mu_ij) at the current
  * parameters (Table S1; App. B for NB, with the current shape), each entry in
- * FP32, summed per tile with compensation and combined in FP64. Entries marked
+ * FP32, summed per tile with compensation and combined in FP64. eta: FP32 on
+ * the CUDA cores for FP32 handles (and with GMF_FLAG_SIMT_DEVIANCE); on
+ * mixed-precision handles the block step's split-BF16 tensor-core products
+ * (relative error of eta a few 1e-6 of sum_k |L_ik R_jk|). Entries marked
  * missing (cfg.missing = 1) add nothing (D(mu, mu) = 0 after imputation).
  * Synchronous; *out_total is host memory.
  */

@@ -17,16 +17,17 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgmf.so")
 
 GMF_OK, GMF_ERR_ARG, GMF_ERR_CUDA, GMF_ERR_OOM, GMF_ERR_TIMEOUT, GMF_ERR_NONFINITE, GMF_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
-GMF_POISSON, GMF_NEGBIN = 0, 1
-GMF_Y_INT32, GMF_Y_UINT16 = 0, 1
+GMF_POISSON, GMF_NEGBIN, GMF_GAUSSIAN, GMF_BINOMIAL, GMF_GAMMA, GMF_INVGAUSS = 0, 1, 2, 3, 4, 5
+GMF_Y_INT32, GMF_Y_UINT16, GMF_Y_FLOAT32 = 0, 1, 2
 GMF_PREC_FP32, GMF_PREC_MIXED = 0, 1
 GMF_ORTH_B1, GMF_ORTH_B2, GMF_ORTH_B3 = 1, 2, 3
-GMF_FLAG_NO_CLUSTER, GMF_FLAG_PERSIST = 1, 2
+GMF_FLAG_NO_CLUSTER, GMF_FLAG_PERSIST, GMF_FLAG_SIMT_DEVIANCE = 1, 2, 4
 GMF_SWEEP_SEQUENTIAL, GMF_SWEEP_PERSISTENT = -1, -3
 GMF_EPOCH_SEPARATE, GMF_EPOCH_CLUSTER, GMF_EPOCH_PERSISTENT = 0, 1, 2
 EPOCH_MODES = {GMF_EPOCH_SEPARATE: "separate", GMF_EPOCH_CLUSTER: "cluster", GMF_EPOCH_PERSISTENT: "persistent"}
 
-FAMILIES = {"poisson": GMF_POISSON, "negbin": GMF_NEGBIN}
+FAMILIES = {"poisson": GMF_POISSON, "negbin": GMF_NEGBIN, "gaussian": GMF_GAUSSIAN, "binomial": GMF_BINOMIAL,
+            "gamma": GMF_GAMMA, "invgauss": GMF_INVGAUSS}
 PRECISIONS = {"fp32": GMF_PREC_FP32, "mixed": GMF_PREC_MIXED}
 ORTH = {"B1": GMF_ORTH_B1, "B2": GMF_ORTH_B2, "B3": GMF_ORTH_B3}
 
@@ -164,13 +165,15 @@ def _stream(stream):
 
 
 def _torch_ydt(Y):
-    """Count type of a torch tensor: int32, or 16-bit counts (uint16, or their int16 view)."""
+    """Response type of a torch tensor: int32, 16-bit counts (uint16, or their int16 view), or float32."""
     import torch
     if Y.dtype == torch.int32:
         return GMF_Y_INT32
+    if Y.dtype == torch.float32:
+        return GMF_Y_FLOAT32
     if Y.dtype == torch.int16 or (hasattr(torch, "uint16") and Y.dtype == torch.uint16):
         return GMF_Y_UINT16
-    raise TypeError("counts must be int32 or 16-bit (uint16 / int16 view)")
+    raise TypeError("responses must be int32, 16-bit counts (uint16 / int16 view) or float32")
 
 
 def strip_schedule(r, s, sigma, w_begin=0, w_end=None):
@@ -221,9 +224,10 @@ class Model:
         else:
             Y = np.ascontiguousarray(Y)
             n, m = Y.shape
-            ydt = {np.dtype(np.int32): GMF_Y_INT32, np.dtype(np.uint16): GMF_Y_UINT16}.get(Y.dtype)
+            ydt = {np.dtype(np.int32): GMF_Y_INT32, np.dtype(np.uint16): GMF_Y_UINT16,
+                   np.dtype(np.float32): GMF_Y_FLOAT32}.get(Y.dtype)
             if ydt is None:
-                raise TypeError("Y must be int32 or uint16")
+                raise TypeError("Y must be int32, uint16 or float32")
         X = np.ascontiguousarray(X, dtype=np.float64)
         Z = np.ascontiguousarray(Z, dtype=np.float64)
         p, q = X.shape[1], Z.shape[1]

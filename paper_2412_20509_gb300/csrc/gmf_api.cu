@@ -223,7 +223,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
                      const double* U0, const double* V0, double alpha0, void* stream, const gmf_model* share) {
     if (share) {
         Y = share->Yp;
-        y_dtype = share->y16 ? GMF_Y_UINT16 : GMF_Y_INT32;
+        y_dtype = share->yf32 ? GMF_Y_FLOAT32 : share->y16 ? GMF_Y_UINT16 : GMF_Y_INT32;
         y_on_device = 1;
         W = share->Wp;
         row_perm = share->h_rperm;
@@ -243,18 +243,25 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     const int K = 1 + c.p + c.q + c.d;
     if (K > GMF_KMAX || c.q + c.d > GMF_FREE_MAX || c.p + c.d > GMF_FREE_MAX)
         return fail(GMF_ERR_ARG, "gmf_init: 1+p+q+d must be <= %d", GMF_KMAX);
-    if (c.family != GMF_POISSON && c.family != GMF_NEGBIN) return fail(GMF_ERR_ARG, "gmf_init: unknown family");
+    if (c.family < GMF_POISSON || c.family > GMF_INVGAUSS) return fail(GMF_ERR_ARG, "gmf_init: unknown family");
     if (c.nb_row <= 0 || c.nb_col <= 0) return fail(GMF_ERR_ARG, "gmf_init: minibatch sizes must be positive");
     if (c.bias_corr != 0 && c.bias_corr != 1) return fail(GMF_ERR_ARG, "gmf_init: bias_corr must be 0 or 1");
     if (c.alpha_mode < 0 || c.alpha_mode > 2) return fail(GMF_ERR_ARG, "gmf_init: alpha_mode must be 0, 1 or 2");
     if (c.precision != GMF_PREC_FP32 && c.precision != GMF_PREC_MIXED)
         return fail(GMF_ERR_ARG, "gmf_init: unknown precision");
-    if (c.flags & ~(GMF_FLAG_NO_CLUSTER | GMF_FLAG_PERSIST)) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
+    if (c.flags & ~(GMF_FLAG_NO_CLUSTER | GMF_FLAG_PERSIST | GMF_FLAG_SIMT_DEVIANCE)) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
     if (c.missing != 0 && c.missing != 1) return fail(GMF_ERR_ARG, "gmf_init: missing must be 0 or 1");
     if (!(c.a1 > 0 && c.a1 <= 1 && c.a2 > 0 && c.a2 <= 1)) return fail(GMF_ERR_ARG, "gmf_init: a1, a2 in (0, 1]");
     if (!(c.k0 > 0) || c.k1 < 0 || !(c.tau > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad learning-rate schedule");
     if (c.damping < 0 || !(c.eta_clamp > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad damping or eta_clamp");
-    if (y_dtype != GMF_Y_INT32 && y_dtype != GMF_Y_UINT16) return fail(GMF_ERR_ARG, "gmf_init: bad y_dtype");
+    if (y_dtype != GMF_Y_INT32 && y_dtype != GMF_Y_UINT16 && y_dtype != GMF_Y_FLOAT32)
+        return fail(GMF_ERR_ARG, "gmf_init: bad y_dtype");
+    if (c.family <= GMF_NEGBIN && y_dtype == GMF_Y_FLOAT32)
+        return fail(GMF_ERR_ARG, "gmf_init: the Poisson and NB families take int32 or uint16 counts");
+    if ((c.family == GMF_GAUSSIAN || c.family == GMF_GAMMA || c.family == GMF_INVGAUSS) && y_dtype != GMF_Y_FLOAT32)
+        return fail(GMF_ERR_ARG, "gmf_init: the Gaussian, Gamma and inverse Gaussian families take float32 responses");
+    if (c.alpha_mode == 2 && c.family != GMF_NEGBIN)
+        return fail(GMF_ERR_ARG, "gmf_init: alpha_mode 2 (per-gene shapes) is for the negative binomial");
     if (!Y || !X || !Z || !row_perm || !col_perm || !B0 || !G0 || !U0 || !V0)
         return fail(GMF_ERR_ARG, "gmf_init: a required pointer is NULL");
     if ((c.p > 0 && !X) || !(alpha0 > 0) ) return fail(GMF_ERR_ARG, "gmf_init: alpha0 must be > 0");
@@ -283,6 +290,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     h->TI = (int)((std::min<int64_t>(c.nb_row, c.n) + GMF_TILE - 1) / GMF_TILE);
     h->TJ = (int)((std::min<int64_t>(c.nb_col, c.m) + GMF_TILE - 1) / GMF_TILE);
     h->y16 = y_dtype == GMF_Y_UINT16;
+    h->yf32 = y_dtype == GMF_Y_FLOAT32;
     h->h_rperm = new int32_t[c.n];
     h->h_cperm = new int32_t[c.m];
     memcpy(h->h_rperm, row_perm, sizeof(int32_t) * c.n);
@@ -677,7 +685,7 @@ extern "C" int gmf_sgd_sweep_blocks(gmf_model* h, const int32_t* sigma, int32_t 
             return fail(GMF_ERR_ARG, "gmf_sgd_sweep_blocks: blocks must increase within [0, %d)", h->per);
     if (!is_perm(sigma, h->nsw))
         return fail(GMF_ERR_ARG, "gmf_sgd_sweep_blocks: sigma is not a permutation of 0..%d", h->nsw - 1);
-    if (h->cfg.family == GMF_NEGBIN && h->cfg.alpha_mode == 1 && nblocks < h->per)
+    if (h->cfg.alpha_mode == 1 && h->cfg.family != GMF_POISSON && h->cfg.family != GMF_BINOMIAL && nblocks < h->per)
         return fail(GMF_ERR_STATE, "gmf_sgd_sweep_blocks: the pooled NB shape update needs every block of the sweep");
     cudaStream_t st = (cudaStream_t)stream;
     {
@@ -731,6 +739,7 @@ static int check_err_word(gmf_model* h, cudaStream_t st);
 
 extern "C" int gmf_set_gene_shapes(gmf_model* h, const double* alpha, void* stream) {
     if (!h || !alpha) return fail(GMF_ERR_ARG, "gmf_set_gene_shapes: NULL argument");
+    if (h->cfg.family > GMF_NEGBIN) return fail(GMF_ERR_STATE, "gmf_set_gene_shapes: Poisson and negative binomial fits only");
     if (h->cfg.alpha_mode != 2) return fail(GMF_ERR_STATE, "gmf_set_gene_shapes: the fit has one shape (alpha_mode != 2)");
     std::vector<float> ac((size_t)h->m);
     for (int64_t jp = 0; jp < h->m; jp++) {
@@ -757,6 +766,7 @@ extern "C" int gmf_get_gene_shapes(gmf_model* h, double* alpha, void* stream) {
 
 extern "C" int gmf_gene_shape_moments(gmf_model* h, double eps, double cap, double* alpha_out, void* stream) {
     if (!h || !alpha_out) return fail(GMF_ERR_ARG, "gmf_gene_shape_moments: NULL argument");
+    if (h->cfg.family > GMF_NEGBIN) return fail(GMF_ERR_STATE, "gmf_gene_shape_moments: Poisson and negative binomial fits only");
     if (!(eps > 0) || !(cap >= eps)) return fail(GMF_ERR_ARG, "gmf_gene_shape_moments: need 0 < eps <= cap");
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<double> sums((size_t)2 * h->m);
@@ -809,6 +819,7 @@ int gmf_init_run(gmf_model* h, int power_iters, uint64_t seed, double* sv_out, c
 
 extern "C" int gmf_initialize(gmf_model* h, int32_t power_iters, uint64_t seed, double* sv_out, void* stream) {
     if (!h) return fail(GMF_ERR_ARG, "gmf_initialize: NULL handle");
+    if (h->cfg.family > GMF_NEGBIN) return fail(GMF_ERR_STATE, "gmf_initialize: Poisson and negative binomial fits only");
     if (power_iters < 0 || power_iters > 20)
         return fail(GMF_ERR_ARG, "gmf_initialize: power_iters %d outside [0, 20]", power_iters);
     if (h->cfg.missing) return fail(GMF_ERR_STATE, "gmf_initialize: the least-squares start needs every count observed");
@@ -870,6 +881,7 @@ int gmf_loglik_run(gmf_model* h, double* out, cudaStream_t st, const char** why)
 
 extern "C" int gmf_loglik(gmf_model* h, double* out, void* stream) {
     if (!h || !out) return fail(GMF_ERR_ARG, "gmf_loglik: NULL argument");
+    if (h->cfg.family > GMF_NEGBIN) return fail(GMF_ERR_STATE, "gmf_loglik: Poisson and negative binomial fits only");
     cudaStream_t st = (cudaStream_t)stream;
     const char* why = "";
     const int rc = gmf_loglik_run(h, out, st, &why);
@@ -879,6 +891,7 @@ extern "C" int gmf_loglik(gmf_model* h, double* out, void* stream) {
 
 extern "C" int gmf_holdout(gmf_model* h, const void* Ytrue, double* out, void* stream) {
     if (!h || !Ytrue || !out) return fail(GMF_ERR_ARG, "gmf_holdout: NULL argument");
+    if (h->cfg.family > GMF_NEGBIN) return fail(GMF_ERR_STATE, "gmf_holdout: Poisson and negative binomial fits only");
     if (!h->cfg.missing) return fail(GMF_ERR_STATE, "gmf_holdout: the fit has no missing entries (cfg.missing = 0)");
     cudaStream_t st = (cudaStream_t)stream;
     const char* why = "";
@@ -1053,6 +1066,7 @@ extern "C" int gmf_project_cells(gmf_model* h, const void* Ynew, int32_t y_dtype
                                  const float* offset_new, const float* U_start, int32_t n_steps, float* U_out,
                                  float* G_out, float* dev_out, void* stream) {
     if (!h) return fail(GMF_ERR_ARG, "gmf_project_cells: NULL handle");
+    if (h->cfg.family > GMF_NEGBIN) return fail(GMF_ERR_STATE, "gmf_project_cells: Poisson and negative binomial fits only");
     if (n_new < 0 || n_new > (int64_t)INT32_MAX) return fail(GMF_ERR_ARG, "gmf_project_cells: bad n_new");
     if (y_dtype != GMF_Y_INT32 && y_dtype != GMF_Y_UINT16) return fail(GMF_ERR_ARG, "gmf_project_cells: bad y_dtype");
     if (n_steps < 0 || n_steps > 1000) return fail(GMF_ERR_ARG, "gmf_project_cells: n_steps in [0, 1000]");

@@ -43,6 +43,7 @@ struct StepArgs {
     float a1, a2, damping, eps, clamp;
     const void* Y;              // Yp (permuted)
     int y16;                    // 1 if uint16 counts
+    int yf32;                   // 1 if float32 responses (NaN marks a missing one)
     const float* W;             // permuted weights or nullptr
     float* L;
     float* R;
@@ -81,6 +82,7 @@ struct gmf_model {
     int r, s, nsw, per, swap;
     int TI, TJ;
     int y16;
+    int yf32;                   // float32 responses (GMF_Y_FLOAT32)
     // device storage
     void* Yp;
     float* Wp;
@@ -211,6 +213,10 @@ StepArgs gmf_make_args(gmf_model* h);
 cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaStream_t st);
 cudaError_t gmf_sweep_simt_attr(gmf_model* h);
 cudaError_t gmf_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st);
+cudaError_t gmf_launch_sum_parts(const double* part, int count, double* out, cudaStream_t st);
+// gmf_step_tc.cu: the full deviance on the tensor cores (mixed-precision handles)
+int gmf_tc_deviance_ok(const gmf_model* h);
+cudaError_t gmf_tc_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st);
 cudaError_t gmf_launch_permute_y(const void* src, void* dst, int y16, int64_t n, int64_t m,
                                  const int* rperm, const int* cperm, cudaStream_t st);
 // Yp[i][j] = Y[rperm[i]][cperm[j]] with Y in mapped host memory (16-byte

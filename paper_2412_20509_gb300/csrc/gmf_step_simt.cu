@@ -37,14 +37,19 @@ constexpr int LDD = T + 4;  // Ddot / Dddot tiles (row-major)
 constexpr int NW = GMF_THREADS / 32;
 constexpr int CHP = 2;      // 4-column chunks per contraction pass
 
-__device__ __forceinline__ float load_y(const void* Y, int y16, int64_t idx) {
+__device__ __forceinline__ float load_y(const void* Y, int y16, int64_t idx, int yf32 = 0) {
+    if (yf32) return __ldg((const float*)Y + idx);
     return y16 ? (float)__ldg((const unsigned short*)Y + idx) : (float)__ldg((const int*)Y + idx);
 }
 
 // Four consecutive counts of one row (vector load when aligned).
-__device__ __forceinline__ void load_y4(const void* Y, int y16, int64_t idx, bool vec, int valid, float y[4]) {
+__device__ __forceinline__ void load_y4(const void* Y, int y16, int64_t idx, bool vec, int valid, float y[4],
+                                        int yf32 = 0) {
     if (vec && valid == 4) {
-        if (y16) {
+        if (yf32) {
+            const float4 v = __ldg((const float4*)((const float*)Y + idx));
+            y[0] = v.x; y[1] = v.y; y[2] = v.z; y[3] = v.w;
+        } else if (y16) {
             const ushort4 v = __ldg((const ushort4*)((const unsigned short*)Y + idx));
             y[0] = v.x; y[1] = v.y; y[2] = v.z; y[3] = v.w;
         } else {
@@ -54,7 +59,7 @@ __device__ __forceinline__ void load_y4(const void* Y, int y16, int64_t idx, boo
         return;
     }
 #pragma unroll
-    for (int b = 0; b < 4; b++) y[b] = b < valid ? load_y(Y, y16, idx + b) : 0.f;
+    for (int b = 0; b < 4; b++) y[b] = b < valid ? load_y(Y, y16, idx + b, yf32) : 0.f;
 }
 
 // Rows [row0, row0+nr) of F (row stride KP, a multiple of 4) -> St[c*LD + i]
@@ -194,7 +199,8 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
     const int nTI = (int)((g.nI + T - 1) / T), nTJ = (int)((g.mJ + T - 1) / T);
     const bool active = ti < nTI && tj < nTJ;
     const bool nb = a.family == GMF_NEGBIN;
-    const bool moments = nb && a.alpha_mode == 1;
+    const bool glm = a.family >= GMF_GAUSSIAN;  // the other families of Table S1
+    const bool moments = scalar_estimated(a.family, a.alpha_mode);
     grid_dependency_wait();  // the previous sweep's update launch writes the model state
     grid_launch_dependents();  // this sweep's update may start: the previous one has completed
     const float alpha = *a.alpha;
@@ -216,7 +222,7 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
             const int il = 4 * ty + u, jl0 = 4 * tx;
             const int valid = il < nr ? max(0, min(4, nc - jl0)) : 0;
             const int64_t idx = (row0 + il) * a.m + col0 + jl0;
-            if (valid > 0) load_y4(a.Y, a.y16, idx, vec, valid, yv[u]);
+            if (valid > 0) load_y4(a.Y, a.y16, idx, vec, valid, yv[u], a.yf32);
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 if (valid == 0) yv[u][v] = 0.f;
@@ -251,7 +257,21 @@ __device__ __forceinline__ void simt_tile(const StepArgs& a, int w, int k, float
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 dd[v] = ddd[v] = 0.f;
-                if (v < valid) {
+                if (v < valid && glm) {
+                    const float w8 = wv[u][v];
+                    const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
+                    const float mu = glm_mean(a.family, e);
+                    const bool miss = y_missing(a, yv[u][v]);
+                    const float y = miss ? mu : yv[u][v];
+                    float d1, d2;
+                    glm_derivs(a.family, y, mu, alpha, d1, d2);
+                    dd[v] = w8 * d1;
+                    ddd[v] = w8 * d2;
+                    if (moments && !miss) {
+                        s1 += w8 * (y - mu) * (y - mu) / glm_variance(a.family, mu);
+                        s2 += 1.f;
+                    }
+                } else if (v < valid) {
                     const float w8 = wv[u][v];
                     const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
                     const float mu = expf(e);
@@ -295,35 +315,6 @@ __global__ void __launch_bounds__(GMF_THREADS, 3) sweep_multi(const StepArgs* __
     if (threadIdx.x == 0) s_a = av[order[blockIdx.z / per]];
     __syncthreads();
     simt_tile(s_a, w, blockIdx.z % per, smem);
-}
-
-// Unit deviance / 2 without branches on y (every lane of a warp takes the same path):
-//   Poisson  y (log y - eta) - (y - mu)
-//   NB       y (log y - eta) - (y + a)(log(y + a) - log a - log1p(mu / a)),
-// the y log y term zero at y = 0, so a zero count (most entries) is exactly a log1p(mu / a). log y and
-// log(y + a) come from per-CTA tables for y < 256. Near mu = y the logarithms cancel: the rounding is
-// ~6e-8 (y + a) log(y + a) per entry, ~1e-7 of a whole matrix's deviance. The form takes log mu = eta
-// but mu itself from exp(eta), so an error in mu enters at first order (as mu times its relative error):
-// mu comes from the accurate expf, whose error is a fraction of an ulp without a common sign. (The fast
-// exponential scales eta by a rounded log2(e) and carries a relative bias of ~1e-8 |eta|, which at
-// counts of a few hundred moved whole-matrix deviances by 4e-5.) Counts of 32 and more take the ratio
-// form instead (half_dev_ratio: log1p of the relative residual), which keeps y log(y/mu) - (y - mu)
-// accurate when y and mu are large and close; they are rare in count data, so the branch seldom
-// splits a warp.
-__device__ __forceinline__ float half_dev_tab(bool nb, float y, float e, float mu, float alpha, float la,
-                                              const float* tlog, const float* tloga) {
-    if (y >= 32.f) return half_dev_ratio(nb, y, e, mu, alpha);
-    const int yi = (int)y;
-    float ly, lya;
-    if (yi < 256) {
-        ly = tlog[yi];
-        lya = tloga[yi];
-    } else {
-        ly = logf(y);
-        lya = logf(y + alpha);
-    }
-    const float t1 = yi > 0 ? y * (ly - e) : 0.f;
-    return nb ? t1 - (y + alpha) * ((lya - la) - log1pf(__fdividef(mu, alpha))) : t1 - (y - mu);
 }
 
 // Deviance of one 64 x 64 tile of the whole (permuted) matrix.
@@ -371,14 +362,16 @@ __global__ void __launch_bounds__(GMF_THREADS) deviance_kernel(StepArgs a, doubl
         if (valid == 0) continue;
         const int64_t idx = (row0 + il) * a.m + col0 + jl0;
         float y[4];
-        load_y4(a.Y, a.y16, idx, vec, valid, y);
+        load_y4(a.Y, a.y16, idx, vec, valid, y, a.yf32);
 #pragma unroll
         for (int v = 0; v < 4; v++) {
-            if (v < valid && !(a.missing && y[v] == a.ymiss)) {   // y <- mu: D(mu, mu) = 0
+            if (v < valid && !y_missing(a, y[v])) {   // y <- mu: D(mu, mu) = 0
                 const float wv = a.W ? __ldg(a.W + idx + v) : 1.f;
                 const float e = fminf(fmaxf(acc[u][v], -a.clamp), a.clamp);
                 float hd;
-                if (a.alpha_col) {   // per-gene shapes: no tables of log(y + alpha)
+                if (a.family >= GMF_GAUSSIAN) {
+                    hd = 0.5f * glm_unit_dev(a.family, y[v], e, glm_mean(a.family, e));
+                } else if (a.alpha_col) {   // per-gene shapes: no tables of log(y + alpha)
                     const float aj = __ldg(a.alpha_col + col0 + jl0 + v), mu = expf(e);
                     hd = y[v] > 0.f ? half_dev_ratio(nb, y[v], e, mu, aj) : (nb ? aj * log1pf(mu / aj) : mu);
                 } else {
@@ -491,6 +484,7 @@ StepArgs gmf_make_args(gmf_model* h) {
     a.clamp = (float)c.eta_clamp;
     a.Y = h->Yp;
     a.y16 = h->y16;
+    a.yf32 = h->yf32;
     a.W = h->Wp;
     a.L = h->L;
     a.R = h->R;
@@ -538,7 +532,15 @@ cudaError_t gmf_launch_sweep_simt(gmf_model* h, const StepArgs& a, int w, cudaSt
     return e;
 }
 
+cudaError_t gmf_launch_sum_parts(const double* part, int count, double* out, cudaStream_t st) {
+    sum_parts_kernel<<<1, GMF_THREADS, 0, st>>>(part, count, out);
+    return cudaGetLastError();
+}
+
+// Mixed-precision handles take eta from the tensor cores (deviance_tc) unless
+// GMF_FLAG_SIMT_DEVIANCE asks for this kernel (FP32 eta on the CUDA cores).
 cudaError_t gmf_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st) {
+    if (gmf_tc_deviance_ok(h)) return gmf_tc_launch_deviance(h, d_out, st);
     StepArgs a = gmf_make_args(h);
     dim3 grid((unsigned)((h->m + T - 1) / T), (unsigned)((h->n + T - 1) / T));
     const size_t smem = sizeof(float) * 2 * (size_t)h->KP * LD;

@@ -79,6 +79,7 @@ extern "C" int gmf_sweep_init(gmf_sweep** out, const gmf_config* cfg, const int3
     if (!out || !cfg || !d_list || !B0 || !G0 || !U0 || !V0 || !alpha0)
         return gmf_fail(GMF_ERR_ARG, "gmf_sweep_init: NULL argument");
     *out = nullptr;
+    if (cfg->family > GMF_NEGBIN) return gmf_fail(GMF_ERR_STATE, "gmf_sweep_init: Poisson and negative binomial fits only");
     if (n_models < 1 || n_models > 64) return gmf_fail(GMF_ERR_ARG, "gmf_sweep_init: 1 <= n_models <= 64");
     gmf_sweep* s = new gmf_sweep();
     s->mixed = cfg->precision == GMF_PREC_MIXED;

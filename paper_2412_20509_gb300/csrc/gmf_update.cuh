@@ -93,6 +93,107 @@ __device__ __forceinline__ float half_dev_ratio(bool nb, float y, float e, float
     return y * l1 - (y + alpha) * l2;
 }
 
+// Unit deviance / 2 without branches on y (every lane of a warp takes the same path):
+//   Poisson  y (log y - eta) - (y - mu)
+//   NB       y (log y - eta) - (y + a)(log(y + a) - log a - log1p(mu / a)),
+// the y log y term zero at y = 0, so a zero count (most entries) is exactly a log1p(mu / a). log y and
+// log(y + a) come from per-CTA tables for y < 256. Near mu = y the logarithms cancel: the rounding is
+// ~6e-8 (y + a) log(y + a) per entry, ~1e-7 of a whole matrix's deviance. The form takes log mu = eta
+// but mu itself from exp(eta), so an error in mu enters at first order (as mu times its relative error):
+// mu comes from the accurate expf, whose error is a fraction of an ulp without a common sign. (The fast
+// exponential scales eta by a rounded log2(e) and carries a relative bias of ~1e-8 |eta|, which at
+// counts of a few hundred moved whole-matrix deviances by 4e-5.) Counts of 32 and more take the ratio
+// form instead (half_dev_ratio: log1p of the relative residual), which keeps y log(y/mu) - (y - mu)
+// accurate when y and mu are large and close; they are rare in count data, so the branch seldom
+// splits a warp.
+__device__ __forceinline__ float half_dev_tab(bool nb, float y, float e, float mu, float alpha, float la,
+                                              const float* tlog, const float* tloga) {
+    if (y >= 32.f) return half_dev_ratio(nb, y, e, mu, alpha);
+    const int yi = (int)y;
+    float ly, lya;
+    if (yi < 256) {
+        ly = tlog[yi];
+        lya = tloga[yi];
+    } else {
+        ly = logf(y);
+        lya = logf(y + alpha);
+    }
+    const float t1 = yi > 0 ? y * (ly - e) : 0.f;
+    return nb ? t1 - (y + alpha) * ((lya - la) - log1pf(__fdividef(mu, alpha))) : t1 - (y - mu);
+}
+
+// ---- the other families of Table S1 (GMF_GAUSSIAN .. GMF_INVGAUSS): identity
+// link (Gaussian), logit (Bernoulli), log (Gamma, inverse Gaussian); phi is
+// the dispersion (1 for the Bernoulli).
+
+// The family's scalar is estimated once per sweep: the NB shape by moments,
+// the dispersion of the Gaussian, Gamma and inverse Gaussian by Pearson (App. B).
+__host__ __device__ __forceinline__ bool scalar_estimated(int family, int alpha_mode) {
+    return alpha_mode == 1 && (family == GMF_NEGBIN || family == GMF_GAUSSIAN || family == GMF_GAMMA ||
+                               family == GMF_INVGAUSS);
+}
+
+// An unobserved entry (cfg.missing): the dtype's marker count, or NaN in float32 responses.
+__device__ __forceinline__ bool y_missing(const StepArgs& a, float y) {
+    return a.missing && (a.yf32 ? y != y : y == a.ymiss);
+}
+
+// Inverse link at the clamped linear predictor e.
+__device__ __forceinline__ float glm_mean(int fam, float e) {
+    if (fam == GMF_GAUSSIAN) return e;
+    if (fam == GMF_BINOMIAL) return 1.f / (1.f + expf(-e));
+    return expf(e);
+}
+
+// Variance function nu(mu).
+__device__ __forceinline__ float glm_variance(int fam, float mu) {
+    if (fam == GMF_GAUSSIAN) return 1.f;
+    if (fam == GMF_BINOMIAL) return mu * (1.f - mu);
+    return fam == GMF_GAMMA ? mu * mu : mu * mu * mu;
+}
+
+// Ddot / w = (y - mu) / (phi nu g') and Dddot / w = 1 / (phi nu g'^2) of Sec. 3 in closed form.
+__device__ __forceinline__ void glm_derivs(int fam, float y, float mu, float phi, float& d1, float& d2) {
+    if (fam == GMF_GAUSSIAN) {
+        d1 = (y - mu) / phi;
+        d2 = 1.f / phi;
+    } else if (fam == GMF_BINOMIAL) {
+        d1 = y - mu;
+        d2 = mu * (1.f - mu);
+    } else if (fam == GMF_GAMMA) {
+        d1 = (y - mu) / (phi * mu);
+        d2 = 1.f / phi;
+    } else {
+        d1 = (y - mu) / (phi * mu * mu);
+        d2 = 1.f / (phi * mu);
+    }
+}
+
+// r - log1p(r) without cancellation: its Taylor series for |r| < 1/4 (14 terms,
+// truncation below 1e-8 relative), else the difference.
+__device__ __forceinline__ float r_minus_log1p(float r) {
+    if (fabsf(r) >= 0.25f) return r - log1pf(r);
+    float s = 1.f / 14.f;
+#pragma unroll
+    for (int k = 13; k >= 2; k--) s = 1.f / (float)k - r * s;
+    return r * r * s;
+}
+
+// log(1 + e^x) for any x.
+__device__ __forceinline__ float softplus_f(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
+
+// x log x, 0 at x = 0.
+__device__ __forceinline__ float xlogx_f(float x) { return x > 0.f ? x * logf(x) : 0.f; }
+
+// Unit deviance D(y, mu) / w of Table S1 (not divided by phi); e = the clamped eta.
+__device__ __forceinline__ float glm_unit_dev(int fam, float y, float e, float mu) {
+    if (fam == GMF_GAUSSIAN) return (y - mu) * (y - mu);
+    if (fam == GMF_BINOMIAL)  // log mu = -softplus(-e), log(1 - mu) = -softplus(e)
+        return 2.f * (xlogx_f(y) + xlogx_f(1.f - y) + y * softplus_f(-e) + (1.f - y) * softplus_f(e));
+    if (fam == GMF_GAMMA) return 2.f * r_minus_log1p((y - mu) / mu);
+    return (y - mu) * (y - mu) / (y * mu * mu);
+}
+
 // Smoothed local step of eq. 12 / eq. 14 for one free parameter.
 __device__ __forceinline__ void smoothed_step(float& theta, float& gbar, float& hbar, float gsum, float hsum,
                                               float scale, float lam, const StepArgs& a, float rho_c) {
@@ -123,7 +224,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int NT>
 __device__ __forceinline__ void tile_moments(const StepArgs& a, int k, int ti, int tj, float s1, float s2) {
     __shared__ float red[NT / 32];
-    if (a.family == GMF_NEGBIN && a.alpha_mode == 1) {
+    if (scalar_estimated(a.family, a.alpha_mode)) {
         const float S1 = block_sum_f<NT>(s1, red);
         const float S2 = block_sum_f<NT>(s2, red);
         if (threadIdx.x == 0) {
@@ -440,15 +541,28 @@ __device__ __forceinline__ void update_unit_tc(const StepArgs& a, int w, int T, 
     }
 }
 
-// NB shape: moment sums of all tiles of the sweep, in tile order, then one
-// smoothed update per sweep (App. B). One thread.
+// NB shape or dispersion: moment (Pearson) sums of all tiles of the sweep, in
+// tile order, then one smoothed update per sweep (App. B). One thread.
 __device__ __forceinline__ void nb_shape_update(const StepArgs& a, int w) {
-    if (a.family != GMF_NEGBIN || a.alpha_mode != 1) return;
+    if (!scalar_estimated(a.family, a.alpha_mode)) return;
     const int total = a.TJ * a.TI * a.per;
     double T1 = 0.0, T2 = 0.0;
     for (int c = 0; c < total; c++) {
         T1 += __ldcg(a.nbpart + 2 * c);
         T2 += __ldcg(a.nbpart + 2 * c + 1);
+    }
+    if (a.family != GMF_NEGBIN) {
+        // Pearson sum and observed entries of the sweep, scaled to the whole
+        // matrix over the residual degrees of freedom
+        const double nm = (double)a.n * (double)a.m;
+        const double dof = nm - (double)a.m * a.p - (double)a.n * a.q - (double)(a.n + a.m) * a.d - 1.0;
+        if (T2 > 0.0 && dof > 0.0) {
+            float phat = (float)((nm / T2) * T1 / dof);
+            if (phat < a.eps) phat = a.eps;
+            const float rf = a.rho1[w];
+            *a.alpha = (1.f - rf) * (*a.alpha) + rf * phat;
+        }
+        return;
     }
     if (T2 > 0.0) {
         float ahat = (float)(T1 / T2);

@@ -64,7 +64,7 @@ def _init(gmf, cfg, **over):
 @pytest.mark.parametrize("field,value,msg", [
     ("n", 0, "positive"), ("d", 70, "1+p+q+d"), ("family", 7, "family"), ("nb_row", 0, "minibatch"),
     ("bias_corr", 2, "bias_corr"), ("alpha_mode", 3, "alpha_mode"), ("precision", 9, "precision"),
-    ("a1", 0.0, "a1"), ("k0", -1.0, "learning-rate"), ("flags", 4, "flags"),
+    ("a1", 0.0, "a1"), ("k0", -1.0, "learning-rate"), ("flags", 8, "flags"),
 ])
 def test_init_rejects_bad_config(gmf, field, value, msg):
     cfg = gmf.gmf_config()
@@ -73,6 +73,29 @@ def test_init_rejects_bad_config(gmf, field, value, msg):
     rc, err = _init(gmf, cfg)
     assert rc == gmf.GMF_ERR_ARG
     assert msg in err
+
+
+@pytest.mark.parametrize("family,y_dtype,alpha_mode,msg", [
+    (0, 2, 0, "int32 or uint16 counts"), (1, 2, 0, "int32 or uint16 counts"),
+    (2, 0, 0, "float32 responses"), (4, 1, 0, "float32 responses"), (5, 0, 1, "float32 responses"),
+    (2, 2, 2, "alpha_mode 2"), (3, 0, 2, "alpha_mode 2"), (6, 2, 0, "unknown family"),
+])
+def test_init_matches_families_and_response_types(gmf, family, y_dtype, alpha_mode, msg):
+    """Counts for the Poisson and NB families, float32 for the Gaussian, Gamma and
+    inverse Gaussian (Table S1's supports); per-gene shapes only for the NB."""
+    cfg = gmf.gmf_config()
+    gmf.lib().gmf_config_default(C.byref(cfg), 8, 6, 2, 1, 2, family, 4, 3)
+    cfg.alpha_mode = alpha_mode
+    h = C.c_void_p()
+    n, m = 8, 6
+    Y = np.ones((n, m), np.float32 if y_dtype == 2 else (np.uint16 if y_dtype == 1 else np.int32))
+    z = lambda *s: np.zeros(s)
+    rc = gmf.lib().gmf_init(C.byref(h), C.byref(cfg), Y.ctypes.data, y_dtype, 0, None, np.ones((n, 2)).ctypes.data,
+                            np.ones((m, 1)).ctypes.data, None, np.arange(n, dtype=np.int32).ctypes.data,
+                            np.arange(m, dtype=np.int32).ctypes.data, z(m, 2).ctypes.data, z(n, 1).ctypes.data,
+                            z(n, 2).ctypes.data, z(m, 2).ctypes.data, 1.0, None)
+    assert rc == gmf.GMF_ERR_ARG
+    assert msg in gmf.lib().gmf_last_error().decode()
 
 
 def test_init_rejects_bad_permutation(gmf):
