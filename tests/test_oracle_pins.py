@@ -701,6 +701,53 @@ def test_init_ols_starts_closer_than_the_crude_start(oracle_lib):
     assert fi.deviance() < fc.deviance()
 
 
+@pytest.mark.parametrize("family,lam", [("negbin", 0.0), ("negbin", 0.7), ("poisson", 0.3)])
+def test_fit_loadings_reaches_each_columns_glm_optimum(family, lam):
+    """Sec. 4.1's column GLMs for V given U: every gene's loadings equal an
+    independent minimisation (BFGS) of -sum_i w_ij log f(y_ij; mu_ij) +
+    lam/2 |v_j|^2 with scipy's log-pmf, and its score U'Ddot_.j - lam v_j is 0."""
+    from scipy import optimize
+    from oracle.init import fit_loadings
+    rng = np.random.default_rng(3)
+    n, m, d, alpha = 80, 6, 3, 1.3
+    prob = synth.make_problem(n, m, 2, 1, d, family, seed=5, zero_frac=0.5, offset=True)
+    W = rng.uniform(0.5, 1.5, (n, m))
+    U = prob.U + 0.2 * rng.standard_normal(prob.U.shape)
+    V0 = np.zeros((m, d))
+    V, f = fit_loadings(prob.Y, prob.X, prob.Z, prob.offset, prob.B, prob.Gamma, U, V0, family=family, alpha=alpha,
+                        lam_v=lam, n_steps=40, W=W)
+    base = prob.X @ prob.B.T + prob.Gamma @ prob.Z.T + prob.offset[:, None]
+    for j in range(m):
+        obj = lambda v: -(W[:, j] * loglik(family, prob.Y[:, j], np.exp(base[:, j] + U @ v), alpha)).sum() \
+            + 0.5 * lam * v @ v
+        ref = optimize.minimize(obj, np.zeros(d), method="BFGS", options=dict(gtol=1e-10)).x
+        np.testing.assert_allclose(V[j], ref, rtol=1e-5, atol=1e-6)
+        h = 1e-6
+        grad = [(obj(V[j] + h * e) - obj(V[j] - h * e)) / (2 * h) for e in np.eye(d)]
+        np.testing.assert_allclose(grad, 0.0, atol=1e-5)
+
+
+def test_fit_loadings_poisson_intercept_closed_form_and_monotone_objective():
+    """With the design a column of ones (d = 1, lam = 0) a Poisson gene's
+    loading is log(sum_i y_ij / sum_i exp(offset_ij)); from a far start the
+    step control never lets a gene's objective rise with more passes."""
+    from oracle.init import fit_loadings
+    n, m = 50, 7
+    prob = synth.make_problem(n, m, 2, 1, 1, "poisson", seed=9, offset=True)
+    U = np.ones((n, 1))
+    V, _ = fit_loadings(prob.Y, prob.X, prob.Z, prob.offset, prob.B, prob.Gamma, U, np.zeros((m, 1)),
+                        family="poisson", alpha=1.0, n_steps=30)
+    base = prob.X @ prob.B.T + prob.Gamma @ prob.Z.T + prob.offset[:, None]
+    np.testing.assert_allclose(V[:, 0], np.log(prob.Y.sum(0) / np.exp(base).sum(0)), rtol=1e-10)
+    prob = synth.make_problem(60, 5, 2, 1, 2, "negbin", seed=4, zero_frac=0.4, offset=True)
+    far = np.full((5, 2), 4.0)
+    fs = [fit_loadings(prob.Y, prob.X, prob.Z, prob.offset, prob.B, prob.Gamma, prob.U, far, family="negbin",
+                       alpha=1.0, n_steps=k)[1] for k in range(8)]
+    for a, b in zip(fs, fs[1:]):
+        assert (b <= a + 1e-12 * np.abs(a)).all()
+    assert (fs[-1] < 0.5 * fs[0]).all()
+
+
 # ---------------------------------------------------------------- per-gene NB shapes (App. B per column)
 
 @pytest.mark.parametrize("shape,blocks", [((12, 7), (5, 3)), ((7, 12), (3, 5))])
