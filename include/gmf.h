@@ -617,6 +617,28 @@ int gmf_gene_shape_ml(gmf_model* h, const double* start, int32_t iters, double t
 int gmf_initialize(gmf_model* h, int32_t power_iters, uint64_t seed, double* sv_out, void* stream);
 
 /*
+ * gmf_fit_loadings -- the last step of the start of Sec. 4.1: with the scores
+ * U and the regression effects B, Gamma held fixed, one GLM per gene for its
+ * loadings v_j, the scores as the design and o_i + x_i'beta_j + gamma_i'z_j as
+ * the offset. Each gene minimises f_j(v) = 0.5 sum_i w_ij D(y_ij, mu_ij) +
+ * 0.5 lambda_V |v|^2 (eq. 6 restricted to v_j; the current NB shape) by
+ * Fisher scoring from the handle's V, v <- v + (U' diag(w Dddot) U +
+ * lambda_V I)^-1 (U' w Ddot - lambda_V v), for n_steps passes with step
+ * control: a pass whose f_j exceeds the best by more than 1e-5 (1 + |f_best|)
+ * halves that gene's last step from its best point (the reading used for the
+ * per-cell projection). Usually called after gmf_initialize, whose V it
+ * replaces. Per pass, in chunks of rows: eta, the derivatives and the
+ * deviances on the device, U' (w Ddot) and the packed Fisher matrices as FP32
+ * cuBLAS GEMMs (plain library GEMMs); the d x d solves in FP64 on the host.
+ * obj_out (host, may be NULL): sum_j f_j at the result. The smoothed
+ * derivatives, visit counts and t restart from zero. Synchronous; allocates
+ * its chunk buffers on the stream (about 2 x 16 MB). Errors: GMF_ERR_ARG
+ * (n_steps outside [0, 100]), GMF_ERR_STATE (families beyond Poisson and NB,
+ * missing entries), GMF_ERR_OOM, GMF_ERR_CUDA.
+ */
+int gmf_fit_loadings(gmf_model* h, int32_t n_steps, double* obj_out, void* stream);
+
+/*
  * gmf_set_wait_limit -- testing hook for the failure detection of the
  * persistent epoch (GMF_FLAG_PERSIST), whose blocks wait on the global timer
  * for the earlier visits of their moving strip (gmf_strip_schedule).

@@ -58,7 +58,8 @@ def _count_deviance(family, y, mu, alpha):
 LOADINGS_SLACK = 1e-5
 
 
-def fit_loadings(Y, X, Z, offset, B, Gamma, U, V0, *, family, alpha, lam_v=0.0, n_steps=8, W=None):
+def fit_loadings(Y, X, Z, offset, B, Gamma, U, V0, *, family, alpha, lam_v=0.0, n_steps=8, W=None,
+                 margins=False):
     """The last step of Sec. 4.1: with the scores U and the regression effects
     B, Gamma fixed, one GLM per gene j for its loadings v_j, the scores as the
     design and o_i + x_i'beta_j + gamma_i'z_j as the offset. Each gene
@@ -68,7 +69,10 @@ def fit_loadings(Y, X, Z, offset, B, Gamma, U, V0, *, family, alpha, lam_v=0.0, 
     from V0, with the step control of the per-cell projection (the same
     reading: accept a point whose f is within 1e-5 (1 + |f_best|) of the best,
     else halve the last step from the best point). n_steps passes take at most
-    n_steps steps. Returns (V, f) with f the genes' objectives at V."""
+    n_steps steps. Returns (V, f) with f the genes' objectives at V; with
+    margins=True also, per gene, the smallest |(f - f_best)/(1 + |f_best|) -
+    1e-5| over its accept / halve tests (how far each decision was from going
+    the other way)."""
     Y = np.asarray(Y, float)
     n, m = Y.shape
     d = U.shape[1]
@@ -78,11 +82,14 @@ def fit_loadings(Y, X, Z, offset, B, Gamma, U, V0, *, family, alpha, lam_v=0.0, 
     best = V.copy()
     f_best = np.full(m, np.inf)
     step = np.zeros_like(V)
+    margin = np.full(m, np.inf)
     for k in range(n_steps + 1):          # pass k evaluates V; passes 0 .. n_steps-1 also step
         eta = base + U @ V.T
         mu, dd, ddd = _count_derivs(family, Y, eta, alpha)
         f = 0.5 * (Wt * _count_deviance(family, Y, mu, alpha)).sum(axis=0) + 0.5 * lam_v * (V ** 2).sum(axis=1)
         for j in range(m):
+            if k > 0:
+                margin[j] = min(margin[j], abs((f[j] - f_best[j]) / (1.0 + abs(f_best[j])) - LOADINGS_SLACK))
             if k == 0 or f[j] <= f_best[j] + LOADINGS_SLACK * (1.0 + abs(f_best[j])):
                 best[j], f_best[j] = V[j], f[j]
                 if k < n_steps:
@@ -94,4 +101,6 @@ def fit_loadings(Y, X, Z, offset, B, Gamma, U, V0, *, family, alpha, lam_v=0.0, 
             else:
                 step[j] *= 0.5
                 V[j] = best[j] + step[j]
+    if margins:
+        return best, f_best, margin
     return best, f_best

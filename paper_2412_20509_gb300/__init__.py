@@ -38,7 +38,7 @@ EXPORTS = ("gmf_config_default", "gmf_init", "gmf_update_y", "gmf_update_y_async
            "gmf_deviance", "gmf_deviance_async", "gmf_get_params", "gmf_set_params", "gmf_get_ema", "gmf_set_ema",
            "gmf_orthogonalize", "gmf_project_cells", "gmf_trace", "gmf_trace_read", "gmf_deviance_noalloc",
            "gmf_set_wait_limit", "gmf_set_flow_lag", "gmf_sgd_sweep_blocks", "gmf_chunk_bytes", "gmf_chunk_state", "gmf_holdout",
-           "gmf_loglik", "gmf_initialize", "gmf_set_gene_shapes", "gmf_get_gene_shapes", "gmf_gene_shape_moments",
+           "gmf_loglik", "gmf_initialize", "gmf_fit_loadings", "gmf_set_gene_shapes", "gmf_get_gene_shapes", "gmf_gene_shape_moments",
            "gmf_gene_shape_ml",
            "gmf_sweep_init", "gmf_sweep_epoch", "gmf_sweep_set_group", "gmf_sweep_group", "gmf_sweep_autotune",
            "gmf_sweep_model", "gmf_sweep_free", "gmf_mlp_create",
@@ -93,6 +93,7 @@ def lib():
         "gmf_holdout": (C.c_int, [VP, VP, VP, VP]),
         "gmf_loglik": (C.c_int, [VP, VP, VP]),
         "gmf_initialize": (C.c_int, [VP, C.c_int32, C.c_uint64, VP, VP]),
+        "gmf_fit_loadings": (C.c_int, [VP, C.c_int32, VP, VP]),
         "gmf_set_gene_shapes": (C.c_int, [VP, VP, VP]),
         "gmf_get_gene_shapes": (C.c_int, [VP, VP, VP]),
         "gmf_gene_shape_moments": (C.c_int, [VP, C.c_double, C.c_double, VP, VP]),
@@ -355,6 +356,13 @@ class Model:
         sv = np.zeros(max(d, 1))
         check(lib().gmf_initialize(self._h, int(power_iters), int(seed), sv.ctypes.data, _stream(stream)))
         return sv[:d]
+
+    def fit_loadings(self, n_steps=8, stream=None):
+        """Column GLMs for V given U, B and Gamma, the last step of Sec. 4.1 (gmf_fit_loadings); returns the summed
+        objective 0.5 deviance + 0.5 lambda_V |V|^2 at the result."""
+        out = C.c_double()
+        check(lib().gmf_fit_loadings(self._h, int(n_steps), C.addressof(out), _stream(stream)))
+        return out.value
 
     def loglik(self, stream=None):
         """Log-likelihood, Pearson statistic and observed-entry count at the current parameters (gmf_loglik)."""

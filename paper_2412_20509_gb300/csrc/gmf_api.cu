@@ -816,6 +816,33 @@ extern "C" int gmf_gene_shape_ml(gmf_model* h, const double* start, int32_t iter
 }
 
 int gmf_init_run(gmf_model* h, int power_iters, uint64_t seed, double* sv_out, cudaStream_t st, std::string* err);
+int gmf_loadings_run(gmf_model* h, int n_steps, double* obj_out, cudaStream_t st, std::string* err);
+
+// A new start: the smoothed derivatives, visit counts and t begin again.
+static int restart_optimiser(gmf_model* h, cudaStream_t st) {
+    CUDA_TRY(cudaMemsetAsync(h->GbR, 0, sizeof(float) * h->n * h->fr, st));
+    CUDA_TRY(cudaMemsetAsync(h->HbR, 0, sizeof(float) * h->n * h->fr, st));
+    CUDA_TRY(cudaMemsetAsync(h->GbC, 0, sizeof(float) * h->m * h->fc, st));
+    CUDA_TRY(cudaMemsetAsync(h->HbC, 0, sizeof(float) * h->m * h->fc, st));
+    CUDA_TRY(cudaMemsetAsync(h->cntR, 0, sizeof(int) * h->n, st));
+    CUDA_TRY(cudaMemsetAsync(h->cntC, 0, sizeof(int) * h->m, st));
+    h->t = 0;
+    return GMF_OK;
+}
+
+extern "C" int gmf_fit_loadings(gmf_model* h, int32_t n_steps, double* obj_out, void* stream) {
+    if (!h) return fail(GMF_ERR_ARG, "gmf_fit_loadings: NULL handle");
+    if (h->cfg.family > GMF_NEGBIN) return fail(GMF_ERR_STATE, "gmf_fit_loadings: Poisson and negative binomial fits only");
+    if (n_steps < 0 || n_steps > 100) return fail(GMF_ERR_ARG, "gmf_fit_loadings: n_steps %d outside [0, 100]", n_steps);
+    if (h->cfg.missing) return fail(GMF_ERR_STATE, "gmf_fit_loadings: the column GLMs need every count observed");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::string err;
+    const int rc = gmf_loadings_run(h, n_steps, obj_out, st, &err);
+    if (rc) return fail(rc, "gmf_fit_loadings: %s", err.c_str());
+    const int rr = restart_optimiser(h, st);
+    if (rr) return rr;
+    return check_err_word(h, st);
+}
 
 extern "C" int gmf_initialize(gmf_model* h, int32_t power_iters, uint64_t seed, double* sv_out, void* stream) {
     if (!h) return fail(GMF_ERR_ARG, "gmf_initialize: NULL handle");

@@ -24,6 +24,7 @@
 
 #include "gmf_internal.cuh"
 #include "gmf_linalg.h"
+#include "gmf_update.cuh"
 
 namespace {
 
@@ -137,6 +138,55 @@ int cholqr2(cublasHandle_t bl, double* A, int64_t rows, int k, double* G, double
                           &one, Ri, k, A, (int)rows, A, (int)rows));
     }
     return GMF_OK;
+}
+
+// ---- column GLMs for the loadings (the last step of Sec. 4.1). One launch per
+// chunk of rows: thread = gene j of a segment of the chunk's rows; eta (from the
+// chunk's SGEMM, in E) becomes w Ddot in place and w Dddot in DD (Sec. 3, log
+// link); the segment's weighted unit deviances (Table S1, App. B) are summed
+// with compensation and added to devpart[seg][j] (the same thread across the
+// chunks, so the sums are deterministic).
+__global__ void glm_col_kernel(const void* Y, int y16, const float* W, float* E, float* DD, double* devpart,
+                               int64_t r0, int rows, int64_t m, int seg_rows, const float* alpha_p,
+                               const float* alpha_col, int nb, float clamp) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int s = blockIdx.y;
+    const int i0 = s * seg_rows, i1 = min(rows, i0 + seg_rows);
+    const float a = alpha_col ? alpha_col[j] : *alpha_p;
+    float sum = 0.f, comp = 0.f;
+    for (int i = i0; i < i1; i++) {
+        const int64_t g = (r0 + i) * m + j, c = (int64_t)i * m + j;
+        const float y = y16 ? (float)((const unsigned short*)Y)[g] : (float)((const int*)Y)[g];
+        const float w = W ? W[g] : 1.f;
+        const float e = fminf(fmaxf(E[c], -clamp), clamp);
+        const float mu = expf(e);
+        const float f = nb ? a / (a + mu) : 1.f;
+        E[c] = w * f * (y - mu);
+        DD[c] = w * f * mu;
+        const float hd = y > 0.f ? gmfdev::half_dev_ratio(nb, y, e, mu, a) : (nb ? a * log1pf(mu / a) : mu);
+        const float t = 2.f * w * hd - comp;
+        const float u = sum + t;
+        comp = (u - sum) - t;
+        sum = u;
+    }
+    devpart[(int64_t)s * m + j] += (double)sum;
+}
+
+// KR[i][pair(a, b)] = u_ia u_ib, a <= b (pairs in row order of the upper triangle), for the chunk's rows.
+__global__ void kr_kernel(const float* L, int KP, int c0, int64_t r0, int rows, int d, int P, float* KR) {
+    const int64_t total = (int64_t)rows * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / P;
+        int pr = (int)(e - i * P), a = 0;
+        while (pr >= d - a) {
+            pr -= d - a;
+            a++;
+        }
+        const int b = a + pr;
+        const float* u = L + (r0 + i) * KP + c0;
+        KR[e] = u[a] * u[b];
+    }
 }
 
 }  // namespace
@@ -342,6 +392,129 @@ int gmf_init_run(gmf_model* h, int power_iters, uint64_t seed, double* sv_out, c
         IN_CU(cudaStreamSynchronize(st));   // Wu, Rh leave scope after the copies
     } else {
         IN_CU(cudaStreamSynchronize(st));
+    }
+    return GMF_OK;
+}
+
+// Column GLMs for V given U, B and Gamma (the last step of Sec. 4.1): for each
+// gene, Fisher scoring of f_j(v) = 0.5 sum_i w_ij D(y_ij, mu_ij) + 0.5 lam_V |v|^2
+// with the step control of the per-cell projection. Per pass, over chunks of
+// rows: eta = L R' (SGEMM), the derivatives and deviances (glm_col_kernel),
+// G += U' (w Ddot) and H += KR(U)' (w Dddot) (SGEMMs; H packed by pairs); then
+// on the host, per gene in FP64: accept or halve, and the Fisher step
+// (H_j + lam I)^-1 (G_j - lam v_j) by Cholesky. obj_out: sum_j f_j at the result.
+int gmf_loadings_run(gmf_model* h, int n_steps, double* obj_out, cudaStream_t st, std::string* err) {
+    const int64_t n = h->n, m = h->m;
+    const int p = h->p, q = h->q, d = h->d, KP = h->KP, K = h->K;
+    const int c0 = 1 + p + q, P = d * (d + 1) / 2;
+    const double lam = h->cfg.lambda[3];
+    const int64_t rows = std::min<int64_t>(n, std::max<int64_t>(256, (int64_t)(1 << 22) / m));
+    const int SEG = 32, seg_rows = (int)((rows + SEG - 1) / SEG);
+    Work w{{}, st};
+    float* E = w.alloc<float>((size_t)rows * m);
+    float* DD = w.alloc<float>((size_t)rows * m);
+    float* KR = w.alloc<float>((size_t)rows * std::max(P, 1));
+    float* G = w.alloc<float>((size_t)std::max(d, 1) * m);
+    float* H = w.alloc<float>((size_t)std::max(P, 1) * m);
+    double* devpart = w.alloc<double>((size_t)SEG * m);
+    if (!E || !DD || !KR || !G || !H || !devpart) {
+        *err = "no device memory for the chunk buffers";
+        return GMF_ERR_OOM;
+    }
+    cublasHandle_t bl = nullptr;
+    if (cublasCreate(&bl) != CUBLAS_STATUS_SUCCESS) {
+        *err = "cublasCreate failed";
+        return GMF_ERR_CUDA;
+    }
+    struct BlGuard {
+        cublasHandle_t b;
+        ~BlGuard() { cublasDestroy(b); }
+    } guard{bl};
+    IN_BL(cublasSetStream(bl, st));
+    IN_BL(cublasSetMathMode(bl, CUBLAS_PEDANTIC_MATH));   // FP32 products, no TF32
+    const float onef = 1.f, zerof = 0.f;
+
+    std::vector<float> Rh((size_t)m * KP);
+    IN_CU(cudaMemcpyAsync(Rh.data(), h->R, sizeof(float) * Rh.size(), cudaMemcpyDeviceToHost, st));
+    IN_CU(cudaStreamSynchronize(st));
+    Mat V((size_t)m * d), best((size_t)m * d), step((size_t)m * d, 0.0);
+    for (int64_t j = 0; j < m; j++)
+        for (int c = 0; c < d; c++) V[j * d + c] = Rh[j * KP + c0 + c];
+    best = V;
+    std::vector<double> f_best(m, INFINITY);
+    std::vector<float> Gh((size_t)d * m), Hh((size_t)P * m);
+    std::vector<double> devh((size_t)SEG * m);
+    const int nb = h->cfg.family == GMF_NEGBIN;
+    for (int k = 0; k <= n_steps; k++) {   // pass k evaluates V; passes 0 .. n_steps-1 also step
+        IN_CU(cudaMemsetAsync(devpart, 0, sizeof(double) * SEG * m, st));
+        for (int64_t r0 = 0; r0 < n; r0 += rows) {
+            const int nr = (int)std::min<int64_t>(rows, n - r0);
+            const float beta = r0 == 0 ? 0.f : 1.f;
+            // eta (row-major nr x m) = L_chunk R'
+            IN_BL(cublasSgemm(bl, CUBLAS_OP_T, CUBLAS_OP_N, (int)m, nr, K, &onef, h->R, KP, h->L + r0 * KP, KP, &zerof,
+                              E, (int)m));
+            glm_col_kernel<<<dim3((unsigned)((m + 255) / 256), (unsigned)((nr + seg_rows - 1) / seg_rows)), 256, 0,
+                             st>>>(h->Yp, h->y16, h->Wp, E, DD, devpart, r0, nr, m, seg_rows, h->alpha,
+                                   h->cfg.alpha_mode == 2 ? h->alpha_col : nullptr, nb, (float)h->cfg.eta_clamp);
+            IN_CU(cudaGetLastError());
+            if (d > 0) {
+                // G (d x m, column-major) += U_chunk' (w Ddot)
+                IN_BL(cublasSgemm(bl, CUBLAS_OP_N, CUBLAS_OP_T, d, (int)m, nr, &onef, h->L + r0 * KP + c0, KP, E,
+                                  (int)m, &beta, G, d));
+                kr_kernel<<<grid_of((int64_t)nr * P), 256, 0, st>>>(h->L, KP, c0, r0, nr, d, P, KR);
+                IN_CU(cudaGetLastError());
+                // H (P x m, column-major) += KR(U_chunk)' (w Dddot)
+                IN_BL(cublasSgemm(bl, CUBLAS_OP_N, CUBLAS_OP_T, P, (int)m, nr, &onef, KR, P, DD, (int)m, &beta, H, P));
+            }
+        }
+        IN_CU(cudaMemcpyAsync(devh.data(), devpart, sizeof(double) * devh.size(), cudaMemcpyDeviceToHost, st));
+        if (d > 0) {
+            IN_CU(cudaMemcpyAsync(Gh.data(), G, sizeof(float) * Gh.size(), cudaMemcpyDeviceToHost, st));
+            IN_CU(cudaMemcpyAsync(Hh.data(), H, sizeof(float) * Hh.size(), cudaMemcpyDeviceToHost, st));
+        }
+        IN_CU(cudaStreamSynchronize(st));
+        for (int64_t j = 0; j < m; j++) {
+            double dev = 0.0, vv = 0.0;
+            for (int s = 0; s < SEG; s++) dev += devh[(size_t)s * m + j];
+            for (int c = 0; c < d; c++) vv += V[j * d + c] * V[j * d + c];
+            const double f = 0.5 * dev + 0.5 * lam * vv;
+            double* vj = &V[j * d];
+            if (k == 0 || f <= f_best[j] + 1e-5 * (1.0 + fabs(f_best[j]))) {
+                f_best[j] = f;
+                for (int c = 0; c < d; c++) best[j * d + c] = vj[c];
+                if (k < n_steps && d > 0) {
+                    Mat F((size_t)d * d), g((size_t)d);
+                    const float* Hj = &Hh[(size_t)j * P];
+                    int pr = 0;
+                    for (int a = 0; a < d; a++)
+                        for (int b = a; b < d; b++, pr++) F[a * d + b] = F[b * d + a] = (double)Hj[pr];
+                    for (int a = 0; a < d; a++) {
+                        F[a * d + a] += lam;
+                        g[a] = (double)Gh[(size_t)j * d + a] - lam * best[j * d + a];
+                    }
+                    if (spd_solve(F, d, g, 1))
+                        for (int c = 0; c < d; c++) step[j * d + c] = g[c];
+                    else
+                        for (int c = 0; c < d; c++) step[j * d + c] = 0.0;
+                    for (int c = 0; c < d; c++) vj[c] = best[j * d + c] + step[j * d + c];
+                }
+            } else {
+                for (int c = 0; c < d; c++) {
+                    step[j * d + c] *= 0.5;
+                    vj[c] = best[j * d + c] + step[j * d + c];
+                }
+            }
+        }
+        const Mat& up = k == n_steps ? best : V;
+        for (int64_t j = 0; j < m; j++)
+            for (int c = 0; c < d; c++) Rh[j * KP + c0 + c] = (float)up[j * d + c];
+        IN_CU(cudaMemcpyAsync(h->R, Rh.data(), sizeof(float) * Rh.size(), cudaMemcpyHostToDevice, st));
+    }
+    IN_CU(cudaStreamSynchronize(st));
+    if (obj_out) {
+        double t = 0.0;
+        for (int64_t j = 0; j < m; j++) t += f_best[j];
+        *obj_out = t;
     }
     return GMF_OK;
 }
