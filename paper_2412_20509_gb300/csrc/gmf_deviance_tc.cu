@@ -64,8 +64,94 @@ __device__ __forceinline__ float half_dev_tc(bool nb, float y, float e, float al
 
 constexpr int DTH = 256;
 
+// Epilogue of one tile: the sum of 2 w D/2w over this thread's row i and its
+// 64 columns (64 ch ..), from eta in TMEM at tacc and the counts at Ys; eight
+// columns per step, summed in FP32, the 8-column sums with compensation.
 template <bool Y16, bool GEN>
-__global__ void __launch_bounds__(DTH, 2)
+__device__ __forceinline__ float tile_deviance(const StepArgs& a, const uint8_t* Ys, uint32_t tacc, int q, int ch,
+                                               int64_t row0, int64_t col0, int nr, int nc, bool nb, float alpha,
+                                               float la, const float2* tab) {
+    const int i = 32 * q + (threadIdx.x & 31);
+    const bool row_ok = i < nr;
+    const float* Wrow = (GEN && a.W) ? a.W + (row0 + i) * a.m + col0 : nullptr;
+    float s = 0.f, comp = 0.f;
+#pragma unroll 1
+    for (int gq = 0; gq < 8; gq++) {
+        const int j0 = 64 * ch + 8 * gq;
+        uint32_t ev[8];
+        tmem_ld8(tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)j0, ev);
+        float y[8];
+        int yi[8];
+        uint32_t big;  // nonzero when a count of the 8 is 32 or more
+        if (Y16) {
+            const uint4 u = *(const uint4*)(Ys + (j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2));
+            const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                yi[2 * v] = (int)(uu[v] & 0xFFFFu);
+                yi[2 * v + 1] = (int)(uu[v] >> 16);
+            }
+            big = (u.x | u.y | u.z | u.w) & 0xFFE0FFE0u;
+        } else {
+            const uint32_t byte = (uint32_t)(j0 & 31) * 4u;
+            const int4 u0 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte));
+            const int4 u1 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte + 16));
+            yi[0] = u0.x; yi[1] = u0.y; yi[2] = u0.z; yi[3] = u0.w;
+            yi[4] = u1.x; yi[5] = u1.y; yi[6] = u1.z; yi[7] = u1.w;
+            big = (uint32_t)(u0.x | u0.y | u0.z | u0.w | u1.x | u1.y | u1.z | u1.w) & ~31u;
+        }
+#pragma unroll
+        for (int v = 0; v < 8; v++) y[v] = (GEN && a.yf32) ? __int_as_float(yi[v]) : (float)yi[v];
+        tmem_wait_ld();
+        float g8 = 0.f;
+        if (!GEN && big == 0u && row_ok && j0 + 8 <= nc) {
+            // counts below 32 and every entry inside the tile (nearly all groups): no per-entry tests
+#pragma unroll
+            for (int v = 0; v < 8; v++) {
+                const float e = fminf(fmaxf(__uint_as_float(ev[v]), -a.clamp), a.clamp);
+                const float2 t = tab[yi[v]];
+                const float t1 = y[v] * (t.x - e);
+                if (nb) {
+                    const float ya = y[v] + alpha;
+                    g8 += fmaf(ya, softplus_01(e - la), fmaf(-ya, t.y, t1));
+                } else {
+                    g8 += t1 - y[v] + expf(e);
+                }
+            }
+            g8 *= 2.f;
+        } else {
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+            const int j = j0 + v;
+            const bool valid = row_ok && j < nc && !(GEN && y_missing(a, y[v]));
+            const float e = fminf(fmaxf(__uint_as_float(ev[v]), -a.clamp), a.clamp);
+            float hd;
+            if (GEN && a.family >= GMF_GAUSSIAN) {
+                hd = valid ? 0.5f * glm_unit_dev(a.family, y[v], e, glm_mean(a.family, e)) : 0.f;
+            } else if (GEN && a.alpha_col) {
+                const float aj = valid ? __ldg(a.alpha_col + col0 + j) : 1.f, mu = expf(e);
+                hd = y[v] > 0.f ? half_dev_ratio_ool(nb, y[v], e, aj) : (nb ? aj * softplus_01(e - logf(aj)) : mu);
+            } else {
+                hd = half_dev_tc(nb, y[v], e, alpha, la, tab);
+            }
+            const float wv = (Wrow && valid) ? __ldg(Wrow + j) : 1.f;
+            g8 += valid ? 2.f * wv * hd : 0.f;
+        }
+        }
+        const float yk = g8 - comp;
+        const float tk = s + yk;
+        comp = (tk - s) - yk;
+        s = tk;
+    }
+    return s;
+}
+
+// ST = 2: two count buffers and two TMEM accumulators (the next tile's counts
+// and eta MMAs in flight during this tile's epilogue), two CTAs per SM. ST = 1:
+// one of each and a serial tile loop, three CTAs per SM (16-bit counts and
+// K <= 32), whose warps hide one another's waits.
+template <bool Y16, bool GEN, int ST>
+__global__ void __launch_bounds__(DTH, ST == 1 ? 3 : 2)
     deviance_tc(StepArgs a, TcLayout Lo, const __grid_constant__ CUtensorMap ymap, int ntj, int ntiles,
                 double* part) {
     extern __shared__ __align__(1024) uint8_t smraw[];
@@ -73,6 +159,7 @@ __global__ void __launch_bounds__(DTH, 2)
     __shared__ uint32_t tmem_base;
     __shared__ float2 tab[256];  // (log v, log(v + alpha) - log alpha), v < 256
     __shared__ double red[DTH / 32];
+    constexpr uint32_t TCOLS = ST == 1 ? 128u : 256u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
     const float alpha = *a.alpha;
@@ -84,14 +171,13 @@ __global__ void __launch_bounds__(DTH, 2)
         mbar_init(&bars[2], 1);
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(&tmem_base, 256);
+    if (warp == 0) tmem_alloc(&tmem_base, TCOLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tb = tmem_base;
     const bool nb = a.family == GMF_NEGBIN;
     const int q = warp & 3, ch = warp >> 2;  // TMEM lanes 32q.., columns 64ch..64ch+63
-    const int i = 32 * q + lane;
     double total = 0.0;
     bool ok = true;
     // phases issued on / waited for at each mbarrier (at most one outstanding per
@@ -106,110 +192,87 @@ __global__ void __launch_bounds__(DTH, 2)
         nr = (int)min((int64_t)TT, a.n - row0);
         nc = (int)min((int64_t)TT, a.m - col0);
     };
-    if (t < ntiles) {
-        int64_t row0, col0;
-        int nr, nc;
-        tile_origin(t, row0, col0, nr, nc);
-        if (tid == 0) issue_counts(Lo, &ymap, sm, row0, col0, &bars[0]);
-        is0++;
-        build_operands<false>(a, Lo, sm, row0, col0, nr, nc);
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) issue_eta(Lo, sm, tb, &bars[2]);
-        is2++;
-    }
-    for (int it = 0; t < ntiles; it++, t += G) {
-        const int b = it & 1;
-        const int tn = t + G;
-        int64_t row0, col0, rown = 0, coln = 0;
-        int nr, nc, nrn = 0, ncn = 0;
-        tile_origin(t, row0, col0, nr, nc);
-        if (tn < ntiles) tile_origin(tn, rown, coln, nrn, ncn);
-        if (tn < ntiles) {
-            if (tid == 0) issue_counts(Lo, &ymap, sm + (b ^ 1) * Lo.y_bytes, rown, coln, &bars[b ^ 1]);
-            if (b) is0++; else is1++;
-        }
-        // eta of tile t is complete: its operands may be overwritten
-        ok = cta_wait(&bars[2], (uint32_t)(wt2 & 1), a.err);
-        wt2++;
-        if (!ok) break;
-        tc_fence_after();
-        if (tn < ntiles) {
-            build_operands<false>(a, Lo, sm, rown, coln, nrn, ncn);
+    if (ST == 1) {
+        for (; t < ntiles; t += G) {
+            int64_t row0, col0;
+            int nr, nc;
+            tile_origin(t, row0, col0, nr, nc);
+            if (tid == 0) issue_counts(Lo, &ymap, sm, row0, col0, &bars[0]);
+            is0++;
+            build_operands<false>(a, Lo, sm, row0, col0, nr, nc);
             fence_proxy_async_smem();
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
-            if (tid == 0) issue_eta(Lo, sm, tb + (uint32_t)(TT * (b ^ 1)), &bars[2]);
+            if (tid == 0) issue_eta(Lo, sm, tb, &bars[2]);
+            is2++;
+            ok = cta_wait(&bars[2], (uint32_t)(wt2 & 1), a.err);
+            wt2++;
+            if (ok) {
+                ok = cta_wait(&bars[0], (uint32_t)(wt0 & 1), a.err);
+                wt0++;
+            }
+            if (!ok) break;
+            tc_fence_after();
+            total += (double)tile_deviance<Y16, GEN>(a, sm, tb, q, ch, row0, col0, nr, nc, nb, alpha, la, tab);
+            // the counts, the operands and the accumulator are dead: the next tile may reuse them
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        }
+    } else {
+        if (t < ntiles) {
+            int64_t row0, col0;
+            int nr, nc;
+            tile_origin(t, row0, col0, nr, nc);
+            if (tid == 0) issue_counts(Lo, &ymap, sm, row0, col0, &bars[0]);
+            is0++;
+            build_operands<false>(a, Lo, sm, row0, col0, nr, nc);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) issue_eta(Lo, sm, tb, &bars[2]);
             is2++;
         }
-        ok = cta_wait(&bars[b], (uint32_t)((b ? wt1 : wt0) & 1), a.err);
-        if (b) wt1++; else wt0++;
-        if (!ok) break;
-        tc_fence_after();
-        const uint8_t* Ys = sm + b * Lo.y_bytes;
-        const bool row_ok = i < nr;
-        const float* Wrow = (GEN && a.W) ? a.W + (row0 + i) * a.m + col0 : nullptr;
-        float s = 0.f, comp = 0.f;
-#pragma unroll 1
-        for (int gq = 0; gq < 8; gq++) {
-            const int j0 = 64 * ch + 8 * gq;
-            uint32_t ev[8];
-            tmem_ld8(tb + (uint32_t)(TT * b) + ((uint32_t)(32 * q) << 16) + (uint32_t)j0, ev);
-            float y[8];
-            if (Y16) {
-                const uint4 u = *(const uint4*)(Ys + (j0 >> 6) * ATOM + sw128_off(i, (j0 & 63) * 2));
-                const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                for (int v = 0; v < 4; v++) {
-                    y[2 * v] = (float)(uu[v] & 0xFFFFu);
-                    y[2 * v + 1] = (float)(uu[v] >> 16);
-                }
-            } else {
-                const uint32_t byte = (uint32_t)(j0 & 31) * 4u;
-                const int4 u0 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte));
-                const int4 u1 = *(const int4*)(Ys + (j0 >> 5) * ATOM + sw128_off(i, byte + 16));
-                if (GEN && a.yf32) {
-                    y[0] = __int_as_float(u0.x); y[1] = __int_as_float(u0.y); y[2] = __int_as_float(u0.z);
-                    y[3] = __int_as_float(u0.w); y[4] = __int_as_float(u1.x); y[5] = __int_as_float(u1.y);
-                    y[6] = __int_as_float(u1.z); y[7] = __int_as_float(u1.w);
-                } else {
-                    y[0] = (float)u0.x; y[1] = (float)u0.y; y[2] = (float)u0.z; y[3] = (float)u0.w;
-                    y[4] = (float)u1.x; y[5] = (float)u1.y; y[6] = (float)u1.z; y[7] = (float)u1.w;
-                }
+        for (int it = 0; t < ntiles; it++, t += G) {
+            const int b = it & 1;
+            const int tn = t + G;
+            int64_t row0, col0, rown = 0, coln = 0;
+            int nr, nc, nrn = 0, ncn = 0;
+            tile_origin(t, row0, col0, nr, nc);
+            if (tn < ntiles) tile_origin(tn, rown, coln, nrn, ncn);
+            if (tn < ntiles) {
+                if (tid == 0) issue_counts(Lo, &ymap, sm + (b ^ 1) * Lo.y_bytes, rown, coln, &bars[b ^ 1]);
+                if (b) is0++; else is1++;
             }
-            tmem_wait_ld();
-            float g8 = 0.f;
-#pragma unroll
-            for (int v = 0; v < 8; v++) {
-                const int j = j0 + v;
-                const bool valid = row_ok && j < nc && !(GEN && y_missing(a, y[v]));
-                const float e = fminf(fmaxf(__uint_as_float(ev[v]), -a.clamp), a.clamp);
-                float hd;
-                if (GEN && a.family >= GMF_GAUSSIAN) {
-                    hd = valid ? 0.5f * glm_unit_dev(a.family, y[v], e, glm_mean(a.family, e)) : 0.f;
-                } else if (GEN && a.alpha_col) {
-                    const float aj = valid ? __ldg(a.alpha_col + col0 + j) : 1.f, mu = expf(e);
-                    hd = y[v] > 0.f ? half_dev_ratio_ool(nb, y[v], e, aj) : (nb ? aj * softplus_01(e - logf(aj)) : mu);
-                } else {
-                    hd = half_dev_tc(nb, y[v], e, alpha, la, tab);
-                }
-                const float wv = (Wrow && valid) ? __ldg(Wrow + j) : 1.f;
-                g8 += valid ? 2.f * wv * hd : 0.f;
+            // eta of tile t is complete: its operands may be overwritten
+            ok = cta_wait(&bars[2], (uint32_t)(wt2 & 1), a.err);
+            wt2++;
+            if (!ok) break;
+            tc_fence_after();
+            if (tn < ntiles) {
+                build_operands<false>(a, Lo, sm, rown, coln, nrn, ncn);
+                fence_proxy_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                tc_fence_after();
+                if (tid == 0) issue_eta(Lo, sm, tb + (uint32_t)(TT * (b ^ 1)), &bars[2]);
+                is2++;
             }
-            const float yk = g8 - comp;
-            const float tk = s + yk;
-            comp = (tk - s) - yk;
-            s = tk;
+            ok = cta_wait(&bars[b], (uint32_t)((b ? wt1 : wt0) & 1), a.err);
+            if (b) wt1++; else wt0++;
+            if (!ok) break;
+            tc_fence_after();
+            total += (double)tile_deviance<Y16, GEN>(a, sm + b * Lo.y_bytes, tb + (uint32_t)(TT * b), q, ch, row0,
+                                                     col0, nr, nc, nb, alpha, la, tab);
+            // tile t's counts and accumulator are dead: the loads and MMAs of tile t + 2 may reuse them
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
         }
-        total += (double)s;
-        // tile t's counts and accumulator are dead: the loads and MMAs of tile t + 2 may reuse them
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
     }
     if (!ok) {
         // a wait gave up: let this CTA's own copies and MMAs still in flight finish (bounded) before TMEM goes
@@ -222,7 +285,7 @@ __global__ void __launch_bounds__(DTH, 2)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tb, 256);
+    if (warp == 0) tmem_dealloc(tb, TCOLS);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
     if (lane == 0) red[warp] = total;
@@ -234,44 +297,73 @@ __global__ void __launch_bounds__(DTH, 2)
     }
 }
 
-template <bool GEN>
+template <bool GEN, int ST>
 const void* dev_tc_fn_gen(int y16) {
-    return y16 ? (const void*)deviance_tc<true, GEN> : (const void*)deviance_tc<false, GEN>;
+    return y16 ? (const void*)deviance_tc<true, GEN, ST> : (const void*)deviance_tc<false, GEN, ST>;
 }
-const void* dev_tc_fn(int y16, int gen) { return gen ? dev_tc_fn_gen<true>(y16) : dev_tc_fn_gen<false>(y16); }
+const void* dev_tc_fn(int y16, int gen, int st) {
+    if (st == 1) return gen ? dev_tc_fn_gen<true, 1>(y16) : dev_tc_fn_gen<false, 1>(y16);
+    return gen ? dev_tc_fn_gen<true, 2>(y16) : dev_tc_fn_gen<false, 2>(y16);
+}
 
 }  // namespace
 
-// The tensor-core deviance: two count buffers and one set of eta operands per
-// CTA, 256 TMEM columns (two accumulators), so at most two CTAs per SM; the
-// grid is what the device holds at once. With flags asking for the CUDA-core
-// kernel, or where the launch does not fit, dev_grid stays 0.
-void gmf_tc_deviance_setup(gmf_model* h, TcState* tc) {
-    tc->dev_grid = 0;
-    if (h->cfg.flags & GMF_FLAG_SIMT_DEVIANCE) return;
-    tc->dev_gen = (h->Wp || h->cfg.missing || h->cfg.alpha_mode == 2 || h->cfg.family > GMF_NEGBIN) ? 1 : 0;
-    tc->dev_smem = 2u * tc->lay.y_bytes + 2u * (uint32_t)tc->lay.KA * ATOM + 1024u;
-    const void* fn = dev_tc_fn(h->y16, tc->dev_gen);
-    int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0, resv = 0;
+namespace {
+
+// Dynamic shared memory of the ST-stage variant: ST count buffers, one set of
+// eta operands, alignment slack.
+uint32_t dev_smem_of(const TcState* tc, int st) {
+    return (uint32_t)st * tc->lay.y_bytes + 2u * (uint32_t)tc->lay.KA * ATOM + 1024u;
+}
+int dev_stages(const TcState* tc) { return tc->dev_smem == dev_smem_of(tc, 1) ? 1 : 2; }
+
+// CTAs per SM of the ST-stage variant from registers, shared memory and TMEM
+// (ST x 128 columns each; the occupancy query reports one CTA per SM for these
+// kernels where the SM holds more); 0 where it cannot run.
+int dev_ctas_per_sm(const gmf_model* h, const TcState* tc, int st, int gen) {
+    const void* fn = dev_tc_fn(h->y16, gen, st);
+    const uint32_t smem = dev_smem_of(tc, st);
+    int dev = 0, smem_sm = 0, regs_sm = 0, resv = 0;
     cudaFuncAttributes fa;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-        gmf_smem_limit(fn, tc->dev_smem) != cudaSuccess ||
+        gmf_smem_limit(fn, smem) != cudaSuccess ||
         cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared) !=
             cudaSuccess ||
         cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
         cudaGetLastError();
+        return 0;
+    }
+    const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * (DTH / 32);
+    const size_t smem_cta = (size_t)smem + fa.sharedSizeBytes + (size_t)resv;
+    return std::min({regs_sm / std::max(regs_cta, 1), (int)((size_t)smem_sm / smem_cta), 4 / st});
+}
+
+}  // namespace
+
+// The tensor-core deviance of a handle: the single-stage variant where three
+// of its CTAs fit an SM (16-bit counts, K <= 32), else the double-buffered one
+// at two per SM; the grid is what the device holds at once. With flags asking
+// for the CUDA-core kernel, or where neither fits, dev_grid stays 0.
+void gmf_tc_deviance_setup(gmf_model* h, TcState* tc) {
+    tc->dev_grid = 0;
+    if (h->cfg.flags & GMF_FLAG_SIMT_DEVIANCE) return;
+    tc->dev_gen = (h->Wp || h->cfg.missing || h->cfg.alpha_mode == 2 || h->cfg.family > GMF_NEGBIN) ? 1 : 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
         return;
     }
-    // CTAs per SM from registers, shared memory and TMEM (256 columns each); the
-    // occupancy query reports one for these kernels where the SM holds two
-    const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * (DTH / 32);
-    const size_t smem_cta = (size_t)tc->dev_smem + fa.sharedSizeBytes + (size_t)resv;
-    const int per_sm = std::min({regs_sm / std::max(regs_cta, 1), (int)((size_t)smem_sm / smem_cta), 2});
+    int st = 1, per_sm = dev_ctas_per_sm(h, tc, 1, tc->dev_gen);
+    if (per_sm < 3) {
+        st = 2;
+        per_sm = std::min(dev_ctas_per_sm(h, tc, 2, tc->dev_gen), 2);
+    }
     if (per_sm < 1) return;
+    tc->dev_smem = dev_smem_of(tc, st);
     const int64_t ntiles = ((h->n + TT - 1) / TT) * ((h->m + TT - 1) / TT);
     tc->dev_grid = (int)std::min<int64_t>((int64_t)per_sm * sms, std::max<int64_t>(ntiles, 1));
 }
@@ -283,11 +375,12 @@ int gmf_tc_deviance_ok(const gmf_model* h) { return h->tc && ((const TcState*)h-
 cudaError_t gmf_tc_launch_deviance(gmf_model* h, double* d_out, cudaStream_t st) {
     const TcState* tc = (const TcState*)h->tc;
     const StepArgs a = gmf_make_args(h);
+    const int stages = dev_stages(tc);
     TcLayout L = tc->lay;
-    L.off_u = 2u * L.y_bytes;  // two count buffers, then the eta operands
+    L.off_u = (uint32_t)stages * L.y_bytes;  // the count buffers, then the eta operands
     const int ntj = (int)((h->m + TT - 1) / TT);
     const int ntiles = (int)(((h->n + TT - 1) / TT) * ntj);
-    const void* fn = dev_tc_fn(h->y16, tc->dev_gen);
+    const void* fn = dev_tc_fn(h->y16, tc->dev_gen, stages);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)tc->dev_grid);
     cfg.blockDim = dim3(DTH);
