@@ -132,3 +132,26 @@ def test_atlas_full_size_first_sweep(gmf, oracle_mod):
         np.testing.assert_array_equal(got[k][~touched], before[k][~touched])
     for k, refv in (("V", ref.V), ("B", ref.B)):
         check_per_entry(k, got[k], refv, before[k], rtol, atol)
+
+
+def test_atlas_full_size_deviance_both_kernels(gmf):
+    """At the benchmark's full size (10^9 entries, 61035 tiles over the
+    persistent CTAs) the tensor-core deviance equals the CUDA-core kernel's on
+    the same parameters within 2e-6 (its parity bar against the oracle on
+    smaller cases), after one epoch so that the residuals have both signs."""
+    w = synth.WORKLOADS["nb_atlas"]
+    prob = synth.make_problem_device(w.n, w.m, w.p, w.q, w.d, w.family, seed=0, zero_frac=w.zero_frac,
+                                     offset=w.offset)
+    hp = synth.Problem(Y=prob.Y.cpu().numpy().view(np.uint16), X=prob.X, Z=prob.Z, offset=prob.offset, B=prob.B,
+                       Gamma=prob.Gamma, U=prob.U, V=prob.V, nb_size=prob.nb_size, family=w.family)
+    start = synth.crude_start(hp, w.d, seed=0)
+    rp, cp = synth.partitions(w.n, w.m, 0)
+    kw = dict(family=w.family, nb_row=w.nb_row, nb_col=w.nb_col, row_perm=rp, col_perm=cp,
+              settings=synth.fit_settings(), precision="mixed")
+    model = gmf.Model(prob.Y, prob.X, prob.Z, prob.offset, start, **kw)
+    model.epoch(synth.sweep_orders(w.n, w.m, w.nb_row, w.nb_col, 1, 0)[0])
+    twin = gmf.Model(prob.Y, prob.X, prob.Z, prob.offset, start, flags=gmf.GMF_FLAG_SIMT_DEVIANCE, **kw)
+    twin.set_params(model.get_params())
+    got, ref = model.deviance(), twin.deviance()
+    assert got == pytest.approx(ref, rel=2e-6), (got, ref, got / ref - 1)
+    assert model.deviance() == got
