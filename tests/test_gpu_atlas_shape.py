@@ -25,7 +25,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.test_gpu_parity import Pair
+from tests.test_gpu_parity import Pair, check_per_entry
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -49,15 +49,6 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
-
-
-def check_per_entry(name, got, ref, before, rtol, atol):
-    step = ref - before
-    err = np.abs(got - ref)
-    colmax = np.abs(step).max(axis=0, keepdims=True)
-    bound = rtol * np.abs(step) + atol * colmax + 1e-7 * np.abs(ref)
-    bad = err > bound
-    assert not bad.any(), (name, int(bad.sum()), float((err - bound).max()), float(colmax.max()))
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])

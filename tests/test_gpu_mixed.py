@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.test_gpu_parity import Pair, rel
+from tests.test_gpu_parity import Pair, check_per_entry, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -68,6 +68,7 @@ def test_mixed_one_sweep_teacher_forced(gmf, oracle_mod, case):
         if ref[k].size == 0:
             continue
         assert rel(got[k], ref[k]) <= 5e-4, (k, rel(got[k], ref[k]))
+        check_per_entry(k, got[k], ref[k], before[k], 3e-2, 5e-3)   # and per entry (the atlas shape's bar)
         step_ref = ref[k] - before[k]
         if np.abs(step_ref).max() > 0:
             step_gpu = got[k] - before[k].astype(np.float32).astype(np.float64)

@@ -39,6 +39,18 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-30))
 
 
+def check_per_entry(name, got, ref, before, rtol, atol):
+    """Each parameter against its own oracle value after a step from `before`:
+    |got - ref| <= rtol |step| + atol max|step of its column| + 1e-7 |ref| (the
+    last term is the FP32 storage of the parameter)."""
+    step = ref - before
+    err = np.abs(got - ref)
+    colmax = np.abs(step).max(axis=0, keepdims=True)
+    bound = rtol * np.abs(step) + atol * colmax + 1e-7 * np.abs(ref)
+    bad = err > bound
+    assert not bad.any(), (name, int(bad.sum()), float((err - bound).max()), float(colmax.max()))
+
+
 class Pair:
     """The same fit in the oracle and on the GPU."""
 
@@ -108,6 +120,7 @@ def test_one_sweep_teacher_forced(gmf, oracle_mod, case):
         if ref[k].size == 0:
             continue
         assert rel(got[k], ref[k]) <= 1e-5, (k, rel(got[k], ref[k]))
+        check_per_entry(k, got[k], ref[k], before[k], 1e-3, 1e-5)   # and per entry, as at the atlas shape
         step_ref = ref[k] - before[k]
         if np.abs(step_ref).max() > 0:
             step_gpu = got[k] - before[k].astype(np.float32).astype(np.float64)
