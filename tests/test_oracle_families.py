@@ -95,8 +95,8 @@ def test_family_fisher_weight_is_expected_information(oracle_lib, family):
 
 @pytest.mark.parametrize("family", list(FAM))
 def test_family_deviance_is_the_scaled_likelihood_ratio(oracle_lib, family):
-    """D(y, mu) = -2 phi w [log f(y; mu) - log f(y; y)] (Table S1's D / 2a(phi)
-    times 2 phi / w... with a(phi) = phi / w): zero at mu = y, positive
+    """D(y, mu) = -2 phi w [log f(y; mu) - log f(y; y)], i.e. 2 w times Table
+    S1's D / 2a(phi) column with a(phi) = phi / w: zero at mu = y, positive
     elsewhere, linear in w, free of phi."""
     for y in YS[family]:
         for eta in ETAS[family]:
@@ -207,3 +207,67 @@ def test_gaussian_d0_full_batch_reaches_least_squares(oracle_lib):
     A = np.array(rows)
     fit = A @ np.linalg.lstsq(A, Y.reshape(-1).astype(np.float64), rcond=None)[0]
     np.testing.assert_allclose(f.eta().reshape(-1), fit, rtol=1e-8, atol=1e-8)
+
+
+@pytest.mark.parametrize("family", list(FAM))
+def test_family_block_gradient_matches_finite_differences(oracle_lib, family):
+    """Matrix level (App. B): the full-batch estimators of every free block
+    [Gamma, U] and [B, V] equal the derivatives of the weighted negative
+    log-likelihood from scipy's densities (phi = 0.7 where the family has one);
+    for the canonical links (Gaussian, Bernoulli) the curvature estimates equal
+    the exact second derivatives too."""
+    n, m, p, q, d, phi = 6, 5, 2, 1, 2, 0.7
+    f, _, P = family_fit(oracle_lib, family, n, m, n, m, seed=2, d=d)
+    f.alpha[0] = 1.0 if family == "binomial" else phi
+    rng = np.random.default_rng(4)
+    W = rng.uniform(0.5, 1.5, size=(n, m))
+    f.W = np.ascontiguousarray(W)
+    f._data.W = f.W.ctypes.data
+    Grow, Hrow, Gcol, Hcol, _ = f.block_grad(np.arange(n), np.arange(m))
+    Y = P.Y.astype(np.float64)
+    th = dict(B=f.B.copy(), Gamma=f.G.copy(), U=f.U.copy(), V=f.V.copy())
+
+    def nll(T):
+        eta = P.X @ T["B"].T + T["Gamma"] @ P.Z.T + T["U"] @ T["V"].T + P.offset[:, None]
+        mu = np.vectorize(lambda e: mean_of(family, e))(eta)
+        return -sum(W[i, j] * logpdf(family, Y[i, j], mu[i, j], f.alpha[0]) for i in range(n) for j in range(m))
+
+    h, hh = 1e-5, 1e-3
+
+    def fd(name, i, c):
+        Tp = {k: v.copy() for k, v in th.items()}; Tm = {k: v.copy() for k, v in th.items()}
+        Tp[name][i, c] += h; Tm[name][i, c] -= h
+        g = (nll(Tp) - nll(Tm)) / (2 * h)
+        Tp[name][i, c] += hh - h; Tm[name][i, c] -= hh - h
+        return g, (nll(Tp) - 2 * nll(th) + nll(Tm)) / hh ** 2
+
+    canonical = family in ("gaussian", "binomial")
+    for i in range(n):
+        for c in range(q + d):
+            g, h2 = fd(*(("Gamma", i, c) if c < q else ("U", i, c - q)))
+            assert Grow[i, c] == pytest.approx(g, rel=1e-6, abs=1e-6)
+            if canonical:
+                assert Hrow[i, c] == pytest.approx(h2, rel=1e-4, abs=1e-5)
+    for j in range(m):
+        for c in range(p + d):
+            g, h2 = fd(*(("B", j, c) if c < p else ("V", j, c - p)))
+            assert Gcol[j, c] == pytest.approx(g, rel=1e-6, abs=1e-6)
+            if canonical:
+                assert Hcol[j, c] == pytest.approx(h2, rel=1e-4, abs=1e-5)
+
+
+@pytest.mark.parametrize("family", list(FAM))
+def test_family_block_estimators_are_unbiased_over_a_partition(oracle_lib, family):
+    """sum_J (|J|/m) G_row(I, J) = G_row(I, all) (eq. 15's unbiasedness) for
+    every family, with a ragged last chunk."""
+    n, m = 9, 7
+    f, _, _ = family_fit(oracle_lib, family, n, m, n, m, seed=6)
+    I = np.arange(n)
+    full = f.block_grad(I, np.arange(m))
+    acc = [np.zeros_like(full[0]), np.zeros_like(full[1])]
+    for J in (np.array([0, 4, 6]), np.array([1, 2, 3]), np.array([5])):
+        g = f.block_grad(I, J)
+        acc[0] += len(J) / m * g[0]
+        acc[1] += len(J) / m * g[1]
+    np.testing.assert_allclose(acc[0], full[0], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(acc[1], full[1], rtol=1e-12, atol=1e-12)
