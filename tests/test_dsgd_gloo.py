@@ -22,6 +22,7 @@ CASES = {
     # name: (n, m, d, family, nb_row, nb_col) -- r >= s (rows move) and r < s (columns move), ragged chunks
     "rows_move": (300, 200, 3, "negbin", 64, 50),
     "cols_move": (150, 410, 2, "poisson", 64, 50),
+    "gamma_rows_move": (300, 200, 3, "gamma", 64, 50),   # a family of Table S1 with float32 responses
 }
 
 
@@ -68,7 +69,11 @@ class OracleEngine:
 def _setup(case, seed=4):
     import oracle
     n, m, d, fam, nbr, nbc = CASES[case]
-    prob = synth.make_problem(n, m, 2, 1, d, fam, seed=seed, zero_frac=0.7 if fam == "negbin" else None, offset=True)
+    if fam in ("poisson", "negbin"):
+        prob = synth.make_problem(n, m, 2, 1, d, fam, seed=seed, zero_frac=0.7 if fam == "negbin" else None,
+                                  offset=True)
+    else:
+        prob = synth.make_family_problem(n, m, 2, 1, d, fam, phi=0.3, seed=seed, offset=True, shift=0.5)
     start = synth.crude_start(prob, d, seed=seed)
     rp, cp = synth.partitions(n, m, seed)
     sig = synth.sweep_orders(n, m, nbr, nbc, 2, seed)
