@@ -118,6 +118,7 @@ def test_null_handle_calls_fail_cleanly(gmf):
     assert L.gmf_set_wait_limit(None, 0, 0) == gmf.GMF_ERR_ARG
     assert L.gmf_set_flow_lag(None, 2) == gmf.GMF_ERR_ARG
     assert L.gmf_gene_shape_ml(None, None, 10, 1e-6, 1e-3, 1e4, None, None, None) == gmf.GMF_ERR_ARG
+    assert L.gmf_fit_loadings(None, 4, None, None) == gmf.GMF_ERR_ARG
     L.gmf_free(None)
 
 
