@@ -627,7 +627,9 @@ def run_headline(args, w):
             clk.mark(False)
         return e0.elapsed_time(e1)
 
-    model = make("mixed")
+    # uploads by the copy engines into a staging buffer: the gather kernel's CTAs would take SM room from the
+    # epochs running beside it (the end-to-end leg below measures both routes)
+    model = make("mixed", flags=gmf.GMF_FLAG_STAGED_UPLOAD)
     nsw = model.num_sweeps
     n, m, p, q, d = model.dims
     K, fr, fc = 1 + p + q + d, q + d, p + d
@@ -660,28 +662,36 @@ def run_headline(args, w):
     res = torch.zeros(1, dtype=torch.float64, device="cuda")
     res_h = torch.zeros(1, dtype=torch.float64).pin_memory()
 
-    def e2e_run(count):
+    def e2e_run(mdl, count):
         # every step: the upload of its counts (issued during the previous step, so it overlaps that
         # step's epochs; the first one here), the fit pass, and the D2H read of its FP64 deviance
-        model.update_y_async(Yh)
+        mdl.update_y_async(Yh)
         for s in range(count):
-            step(model)
-            model.deviance_async(res)
+            step(mdl)
+            mdl.deviance_async(res)
             res_h.copy_(res, non_blocking=True)
             if s + 1 < count:
-                model.update_y_async(Yh)
+                mdl.update_y_async(Yh)
             stream.synchronize()
             float(res_h.item())
 
-    e2e_run(2)
+    def e2e_timed(mdl):
+        e2e_run(mdl, 2)
+        barrier()
+        t0 = time.perf_counter()
+        e2e_run(mdl, e2e_steps)
+        barrier()
+        return max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+
     e2e_steps = max(3, min(args.steps, 8))
-    barrier()
-    t0 = time.perf_counter()
-    e2e_run(e2e_steps)
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_s = e2e_timed(model)
     e2e_value = whole_job_rate(entries_step * e2e_steps, ws, e2e_s)
-    del model, Yh
+    del model
+    torch.cuda.empty_cache()
+    # context: the same leg with the direct gather from host memory into a second count buffer
+    mg = make("mixed")
+    e2e_gather = whole_job_rate(entries_step * e2e_steps, ws, e2e_timed(mg)) if extras else None
+    del mg, Yh
     torch.cuda.empty_cache()
 
     # ---------------- roofline: one sweep (tile launch + update launch) is the unit
@@ -727,8 +737,11 @@ def run_headline(args, w):
            "roofline": roof,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * m * 2 + 4 * nsw * eps),
                    "d2h_bytes_per_step": 8,
-                   "api": "per step: gmf_update_y_async of the counts (2 GB, issued one step ahead so the upload "
-                          "overlaps the previous step), 10 x gmf_sgd_epoch, gmf_deviance_async + D2H"},
+                   "api": "per step: gmf_update_y_async of the counts (2 GB by the copy engines into a staging "
+                          "buffer, GMF_FLAG_STAGED_UPLOAD, issued one step ahead so the copy overlaps the previous "
+                          "step; the permutation into the count matrix runs on the stream), 10 x gmf_sgd_epoch, "
+                          "gmf_deviance_async + D2H",
+                   "value_with_direct_gather": e2e_gather},
            "gpu_launches": int(launches_per_sweep * nsw * eps * args.steps), "epoch_mode": epoch_mode,
            "clocks": clk, "deviance": {"after_warmup": dev0, "after_timed_steps": dev1, **devk}}
 

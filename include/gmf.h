@@ -92,7 +92,16 @@ enum {
     /* Mixed precision: gmf_deviance computes eta in FP32 on the CUDA cores (the
        kernel of the FP32 path) instead of from the block step's split-BF16
        tensor-core products. */
-    GMF_FLAG_SIMT_DEVIANCE = 4
+    GMF_FLAG_SIMT_DEVIANCE = 4,
+    /* gmf_update_y_async: copy the counts by the copy engines into a device
+       staging buffer and permute them on the stream, even where the device
+       could gather them straight from host memory. The gather's CTAs take SM
+       room from kernels running beside it (an SM that holds one has registers
+       for one block-step tile instead of two), while the copy engines are
+       otherwise idle; the permutation then runs on the stream (a read and a
+       write of n x m counts in HBM). Costs two staging buffers of n x m
+       counts. */
+    GMF_FLAG_STAGED_UPLOAD = 8
 };
 
 typedef struct gmf_model gmf_model;  /* opaque, library-owned */

@@ -21,7 +21,7 @@ GMF_POISSON, GMF_NEGBIN, GMF_GAUSSIAN, GMF_BINOMIAL, GMF_GAMMA, GMF_INVGAUSS = 0
 GMF_Y_INT32, GMF_Y_UINT16, GMF_Y_FLOAT32 = 0, 1, 2
 GMF_PREC_FP32, GMF_PREC_MIXED = 0, 1
 GMF_ORTH_B1, GMF_ORTH_B2, GMF_ORTH_B3 = 1, 2, 3
-GMF_FLAG_NO_CLUSTER, GMF_FLAG_PERSIST, GMF_FLAG_SIMT_DEVIANCE = 1, 2, 4
+GMF_FLAG_NO_CLUSTER, GMF_FLAG_PERSIST, GMF_FLAG_SIMT_DEVIANCE, GMF_FLAG_STAGED_UPLOAD = 1, 2, 4, 8
 GMF_SWEEP_SEQUENTIAL, GMF_SWEEP_PERSISTENT = -1, -3
 GMF_EPOCH_SEPARATE, GMF_EPOCH_CLUSTER, GMF_EPOCH_PERSISTENT = 0, 1, 2
 EPOCH_MODES = {GMF_EPOCH_SEPARATE: "separate", GMF_EPOCH_CLUSTER: "cluster", GMF_EPOCH_PERSISTENT: "persistent"}

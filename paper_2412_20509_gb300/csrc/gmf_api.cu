@@ -249,7 +249,7 @@ static int init_impl(gmf_model** out, const gmf_config* cfg, const void* Y, int3
     if (c.alpha_mode < 0 || c.alpha_mode > 2) return fail(GMF_ERR_ARG, "gmf_init: alpha_mode must be 0, 1 or 2");
     if (c.precision != GMF_PREC_FP32 && c.precision != GMF_PREC_MIXED)
         return fail(GMF_ERR_ARG, "gmf_init: unknown precision");
-    if (c.flags & ~(GMF_FLAG_NO_CLUSTER | GMF_FLAG_PERSIST | GMF_FLAG_SIMT_DEVIANCE)) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
+    if (c.flags & ~(GMF_FLAG_NO_CLUSTER | GMF_FLAG_PERSIST | GMF_FLAG_SIMT_DEVIANCE | GMF_FLAG_STAGED_UPLOAD)) return fail(GMF_ERR_ARG, "gmf_init: unknown bits in flags");
     if (c.missing != 0 && c.missing != 1) return fail(GMF_ERR_ARG, "gmf_init: missing must be 0 or 1");
     if (!(c.a1 > 0 && c.a1 <= 1 && c.a2 > 0 && c.a2 <= 1)) return fail(GMF_ERR_ARG, "gmf_init: a1, a2 in (0, 1]");
     if (!(c.k0 > 0) || c.k1 < 0 || !(c.tau > 0)) return fail(GMF_ERR_ARG, "gmf_init: bad learning-rate schedule");
@@ -438,7 +438,7 @@ extern "C" int gmf_update_y_async(gmf_model* h, const void* Y, void* stream) {
     // Direct path: page-locked, mapped host memory is read by one gather kernel on
     // the copy stream into the count buffer that is not current; the handle then
     // switches buffers, so work already enqueued on `st` keeps its counts.
-    const void* dsrc = h->y_fixed ? nullptr : host_gather_src(h, Y);
+    const void* dsrc = (h->y_fixed || (h->cfg.flags & GMF_FLAG_STAGED_UPLOAD)) ? nullptr : host_gather_src(h, Y);
     if (dsrc) {
         if (!h->ybuf[1]) {  // the second buffer, its events and its TMA descriptor, all or nothing
             void* buf = nullptr;

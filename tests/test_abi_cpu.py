@@ -64,7 +64,7 @@ def _init(gmf, cfg, **over):
 @pytest.mark.parametrize("field,value,msg", [
     ("n", 0, "positive"), ("d", 70, "1+p+q+d"), ("family", 7, "family"), ("nb_row", 0, "minibatch"),
     ("bias_corr", 2, "bias_corr"), ("alpha_mode", 3, "alpha_mode"), ("precision", 9, "precision"),
-    ("a1", 0.0, "a1"), ("k0", -1.0, "learning-rate"), ("flags", 8, "flags"),
+    ("a1", 0.0, "a1"), ("k0", -1.0, "learning-rate"), ("flags", 16, "flags"),
 ])
 def test_init_rejects_bad_config(gmf, field, value, msg):
     cfg = gmf.gmf_config()

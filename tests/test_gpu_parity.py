@@ -55,7 +55,7 @@ class Pair:
     """The same fit in the oracle and on the GPU."""
 
     def __init__(self, gmf, oracle_mod, n, m, p, q, d, family, nb_row, nb_col, *, seed=0, y_dtype="int32",
-                 zero_frac=None, offset=True, weights=False, precision="fp32", **settings):
+                 zero_frac=None, offset=True, weights=False, precision="fp32", flags=0, **settings):
         self.prob = synth.make_problem(n, m, p, q, d, family, seed=seed, y_dtype=y_dtype, zero_frac=zero_frac,
                                        offset=offset)
         self.start = synth.crude_start(self.prob, d, seed=seed)
@@ -71,7 +71,7 @@ class Pair:
         self.gpu = gmf.Model(torch.from_numpy(P.Y).cuda(), P.X, P.Z, P.offset, self.start, family=family,
                              nb_row=nb_row, nb_col=nb_col, row_perm=self.rp, col_perm=self.cp,
                              settings=self.settings, W=None if self.W is None else torch.from_numpy(self.W).cuda(),
-                             precision=precision)
+                             precision=precision, flags=flags)
 
     def ref_params(self):
         r = self.ref
@@ -217,7 +217,7 @@ def test_update_y_from_host_and_device(gmf, oracle_mod):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
-@pytest.mark.parametrize("source", ["pinned", "pageable", "unaligned_rows", "pinned_int32"])
+@pytest.mark.parametrize("source", ["pinned", "pageable", "unaligned_rows", "pinned_int32", "pinned_staged"])
 def test_streamed_counts_equal_synchronous_updates(gmf, oracle_mod, precision, source):
     """gmf_update_y_async with the next matrix's upload issued before the current
     epoch has run gives the same fit, bit for bit, as gmf_update_y between
@@ -225,7 +225,8 @@ def test_streamed_counts_equal_synchronous_updates(gmf, oracle_mod, precision, s
     buffer (the handle switches buffers each call); from pageable memory the
     same where the device reads pageable host memory, else through the staging
     copies; rows of 1300 bytes (not a multiple of 16) always through the
-    double-buffered staging copies."""
+    double-buffered staging copies; with GMF_FLAG_STAGED_UPLOAD pinned memory
+    through the staging copies as well."""
     # uint16 counts; 656 genes keep the tensor-core layout's 16-byte rows
     n, m, p, q, d, fam, nbr, nbc = 900, 656, 3, 1, 10, "negbin", 256, 128
     if source == "unaligned_rows":
@@ -235,7 +236,8 @@ def test_streamed_counts_equal_synchronous_updates(gmf, oracle_mod, precision, s
     i32 = source == "pinned_int32"
     extra = dict(y_dtype="int32" if i32 else "uint16", zero_frac=0.85)
     P = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision=precision, **extra)
-    Q = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision=precision, **extra)
+    Q = Pair(gmf, oracle_mod, n, m, p, q, d, fam, nbr, nbc, precision=precision,
+             flags=gmf.GMF_FLAG_STAGED_UPLOAD if source == "pinned_staged" else 0, **extra)
     rng = np.random.default_rng(44)
     mats = [np.ascontiguousarray(np.minimum(P.prob.Y.astype(np.int64) + rng.poisson(0.3, P.prob.Y.shape), 65535)
                                  .astype(np.int32 if i32 else np.uint16)) for _ in range(4)]
@@ -251,7 +253,8 @@ def test_streamed_counts_equal_synchronous_updates(gmf, oracle_mod, precision, s
             Q.gpu.update_y_async(srcs[e + 1])   # its upload overlaps this epoch
     torch.cuda.synchronize()
     assert P.gpu.count_buffers == 1
-    assert Q.gpu.count_buffers == {"pinned": 2, "pinned_int32": 2, "unaligned_rows": 1}.get(source, Q.gpu.count_buffers)
+    assert Q.gpu.count_buffers == {"pinned": 2, "pinned_int32": 2, "unaligned_rows": 1,
+                                   "pinned_staged": 1}.get(source, Q.gpu.count_buffers)
     a, b = P.gpu.get_params(), Q.gpu.get_params()
     for k in ("B", "Gamma", "U", "V"):
         np.testing.assert_array_equal(a[k], b[k])
