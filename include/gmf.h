@@ -198,9 +198,10 @@ int gmf_update_y(gmf_model* h, const void* Y, int32_t y_on_device, void* stream)
  * copy stream reads Y over the host link and writes the permuted counts into
  * the handle's second count buffer (allocated on first use, n x m counts), and
  * the handle switches buffers: the upload overlaps work already enqueued on
- * `stream`, which keeps reading the previous buffer. Otherwise the counts are
- * copied on the copy stream into one of two device staging buffers and
- * permuted in place on `stream` after the copy. Y: host, n x m counts of the
+ * `stream`, which keeps reading the previous buffer. Otherwise (and always
+ * with GMF_FLAG_STAGED_UPLOAD) the counts are copied on the copy stream into
+ * one of two device staging buffers and permuted in place on `stream` after
+ * the copy. Y: host, n x m counts of the
  * init dtype; it must stay unchanged until `stream` has passed the work
  * enqueued by this call (e.g. after a later synchronous call on it). At most
  * two calls may be in flight on one handle. The paper has no counterpart (a
